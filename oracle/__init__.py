@@ -1,0 +1,260 @@
+"""FP64 CPU oracle of the EOS-based multiphase LBM step (arXiv 2103.08301).
+
+TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference leg of ``bench.py`` may import this package. The CUDA
+product path (``paper_2103_08301_gb300``) does not import it, shares no code
+with it, and must keep working when this directory is absent.
+
+The arithmetic lives in ``lbm_oracle.c`` (plain C, double precision, one pass
+per algorithmic step). This module compiles it with gcc and exposes it to
+numpy through ctypes. Every function cites the part of the paper it follows
+in the C source.
+
+Parity status: every function here is pinned by the ``-m "not gpu"`` tests
+(closed forms, library routines, physics laws); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbm_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+Q = 9
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` next to the source (portable flags, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("walls", C.c_int32), ("bc_x", C.c_int32),
+                ("a", C.c_double), ("b", C.c_double), ("R", C.c_double), ("T", C.c_double),
+                ("k", C.c_double), ("kappa", C.c_double), ("tau", C.c_double), ("wet", C.c_double),
+                ("rho_in", C.c_double), ("rho_out", C.c_double), ("gx", C.c_double),
+                ("gy", C.c_double)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("mass", C.c_double), ("J", C.c_double), ("tw_min", C.c_double),
+                ("tw_max", C.c_double), ("pw_min", C.c_double), ("pw_max", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_D = C.c_double
+_PD = C.POINTER(C.c_double)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        for name in ("orc_cs_p0", "orc_cs_dp0", "orc_cs_mu"):
+            getattr(L, name).restype = _D
+            getattr(L, name).argtypes = [_D] * 5
+        L.orc_cs_critical.argtypes = [_D, _D, _D, _PD, _PD]
+        L.orc_maxwell.argtypes = [_D, _D, _D, _D, _PD, _PD, _PD]
+        L.orc_gas_root.argtypes = [_D, _D, _D, _D, _D, _PD]
+        L.orc_feq.argtypes = [_D, _D, _D, _PD]
+        L.orc_feq.restype = None
+        L.orc_grad_periodic.argtypes = [C.c_int, C.c_int, _PD, _PD, _PD]
+        L.orc_grad_periodic.restype = None
+        L.orc_lap_periodic.argtypes = [C.c_int, C.c_int, _PD, _PD]
+        L.orc_lap_periodic.restype = None
+        L.orc_init.argtypes = [C.POINTER(Params), _PD, _PD]
+        L.orc_init.restype = None
+        L.orc_step.argtypes = [C.POINTER(Params), _PD, _PD, C.POINTER(Diag)]
+        L.orc_run.argtypes = [C.POINTER(Params), _PD, C.c_long, C.POINTER(Diag)]
+        L.orc_fields.argtypes = [C.POINTER(Params), _PD, _PD, _PD, _PD, _PD, _PD]
+        L.orc_force.argtypes = [C.POINTER(Params), _PD, _PD, _PD]
+        L.orc_num_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_PD)
+
+
+# --------------------------------------------------------------------------
+# Equation of state (Carnahan-Starling)
+# --------------------------------------------------------------------------
+
+def cs_p0(a, b, R, T, rho):
+    return lib().orc_cs_p0(a, b, R, T, rho)
+
+
+def cs_dp0(a, b, R, T, rho):
+    return lib().orc_cs_dp0(a, b, R, T, rho)
+
+
+def cs_mu(a, b, R, T, rho):
+    return lib().orc_cs_mu(a, b, R, T, rho)
+
+
+def cs_critical(a=1.0, b=4.0, R=1.0):
+    Tc, rc = _D(), _D()
+    if lib().orc_cs_critical(a, b, R, C.byref(Tc), C.byref(rc)):
+        raise ValueError("bad EOS parameters")
+    return Tc.value, rc.value
+
+
+def maxwell(a, b, R, T):
+    """(rho_g, rho_l, p_sat) of the Maxwell construction at absolute T."""
+    g, l, p = _D(), _D(), _D()
+    if lib().orc_maxwell(a, b, R, T, C.byref(g), C.byref(l), C.byref(p)):
+        raise ValueError("no coexistence (T >= Tc)")
+    return g.value, l.value, p.value
+
+
+def gas_root(a, b, R, T, p0_target):
+    r = _D()
+    if lib().orc_gas_root(a, b, R, T, p0_target, C.byref(r)):
+        raise ValueError("pressure outside the gas branch")
+    return r.value
+
+
+def feq(rho, ux, uy):
+    out = np.zeros(Q)
+    lib().orc_feq(rho, ux, uy, _ptr(out))
+    return out
+
+
+def grad_periodic(psi: np.ndarray):
+    psi = np.ascontiguousarray(psi, dtype=np.float64)
+    ny, nx = psi.shape
+    gx, gy = np.zeros_like(psi), np.zeros_like(psi)
+    lib().orc_grad_periodic(nx, ny, _ptr(psi), _ptr(gx), _ptr(gy))
+    return gx, gy
+
+
+def lap_periodic(psi: np.ndarray):
+    psi = np.ascontiguousarray(psi, dtype=np.float64)
+    ny, nx = psi.shape
+    out = np.zeros_like(psi)
+    lib().orc_lap_periodic(nx, ny, _ptr(psi), _ptr(out))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Simulation
+# --------------------------------------------------------------------------
+
+@dataclass
+class Setup:
+    """Physical set-up of one channel or periodic box (mesh units)."""
+    nx: int
+    ny: int
+    walls: bool = False
+    bc_x: bool = False          # pressure inlet / outlet columns
+    a: float = 1.0
+    b: float = 4.0
+    R: float = 1.0
+    T_over_Tc: float = 0.8
+    k: float = 1.0
+    kappa: float = 1.0
+    tau: float = 1.0
+    wet: float = 0.0
+    dp: float = 0.0             # pressure drop between inlet and outlet (mesh units)
+    p_ref: float | None = None  # None: k^2 p_sat(T)
+    gx: float = 0.0
+    gy: float = 0.0
+    T: float = field(init=False)
+    rho_in: float = field(init=False, default=0.0)
+    rho_out: float = field(init=False, default=0.0)
+
+    def __post_init__(self):
+        Tc, _ = cs_critical(self.a, self.b, self.R)
+        self.T = self.T_over_Tc * Tc
+        if self.bc_x:
+            k2 = self.k * self.k
+            if self.p_ref is None:
+                _, _, psat = maxwell(self.a, self.b, self.R, self.T)
+                pref = k2 * psat
+            else:
+                pref = self.p_ref
+            self.rho_in = gas_root(self.a, self.b, self.R, self.T, (pref + 0.5 * self.dp) / k2)
+            self.rho_out = gas_root(self.a, self.b, self.R, self.T, (pref - 0.5 * self.dp) / k2)
+
+    def coexistence(self):
+        return maxwell(self.a, self.b, self.R, self.T)
+
+    def params(self) -> Params:
+        return Params(self.nx, self.ny, int(self.walls), int(self.bc_x), self.a, self.b, self.R,
+                      self.T, self.k, self.kappa, self.tau, self.wet, self.rho_in, self.rho_out,
+                      self.gx, self.gy)
+
+
+def init(setup: Setup, rho0: np.ndarray) -> np.ndarray:
+    rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+    assert rho0.shape == (setup.ny, setup.nx)
+    f = np.zeros((Q, setup.ny, setup.nx))
+    p = setup.params()
+    lib().orc_init(C.byref(p), _ptr(rho0), _ptr(f))
+    return f
+
+
+def step(setup: Setup, f: np.ndarray):
+    """One step; returns (f_next, diagnostics of the state read)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.empty_like(f)
+    d = Diag()
+    p = setup.params()
+    if lib().orc_step(C.byref(p), _ptr(f), _ptr(out), C.byref(d)):
+        raise MemoryError("oracle step")
+    return out, d.as_dict()
+
+
+def run(setup: Setup, f: np.ndarray, nsteps: int):
+    """nsteps steps; returns (f_final, accumulated diagnostics)."""
+    f = np.array(f, dtype=np.float64, order="C", copy=True)
+    d = Diag()
+    p = setup.params()
+    if lib().orc_run(C.byref(p), _ptr(f), int(nsteps), C.byref(d)):
+        raise MemoryError("oracle run")
+    return f, d.as_dict()
+
+
+def fields(setup: Setup, f: np.ndarray):
+    """dict(rho, vx, vy, tau_wall[2, nx], p_wall[2, nx]) of state f."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    ny, nx = setup.ny, setup.nx
+    rho, vx, vy = (np.zeros((ny, nx)) for _ in range(3))
+    tw, pw = np.zeros((2, nx)), np.zeros((2, nx))
+    p = setup.params()
+    if lib().orc_fields(C.byref(p), _ptr(f), _ptr(rho), _ptr(vx), _ptr(vy), _ptr(tw), _ptr(pw)):
+        raise MemoryError("oracle fields")
+    return {"rho": rho, "vx": vx, "vy": vy, "tau_wall": tw, "p_wall": pw}
+
+
+def force(setup: Setup, f: np.ndarray):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    Fx = np.zeros((setup.ny, setup.nx))
+    Fy = np.zeros_like(Fx)
+    p = setup.params()
+    if lib().orc_force(C.byref(p), _ptr(f), _ptr(Fx), _ptr(Fy)):
+        raise MemoryError("oracle force")
+    return Fx, Fy
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
