@@ -1,0 +1,342 @@
+"""Benchmark of the fused EOS-multiphase LBM step on GB300.
+
+Workload (one "step" = one lattice time step, i.e. one pass of the whole hot
+path over the lattice): the airway channel scaled to 16384 x 2048 nodes
+(walls top and bottom, wall films 64 nodes thick, a liquid plug over
+x in [4096, 5120), pressure inlet/outlet with a drop of 1e-3, Carnahan-Starling
+EOS at T = 0.85 Tc, tau = 1, k = 1, kappa = 0.5), FP32 populations, synthetic
+seeded initial density. The 2.4 GB state (two population arrays) is far
+larger than L2, so no flush is needed between steps.
+
+Metric: MLUPS (million lattice-node updates per second, nx*ny*steps/t/1e6),
+whole job over N GPUs, each GPU stepping its own replica of the channel (the
+path shards by independent channels: weak scaling, no collective).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NX, NY = 16384, 2048
+FILM, PLUG_X, PLUG_LEN = 64.0, 4096.0, 1024.0
+PHYS = dict(T_over_Tc=0.85, k=1.0, kappa=0.5, tau=1.0, dp=1e-3)
+BYTES_PER_NODE = {32: 72, 64: 144}  # 9 populations read + 9 written
+METRIC = "MLUPS and % of HBM roofline (FP32 D2Q9 EOS step, 1xGB300) vs FP64 CPU oracle"
+WORKLOAD = "airway channel 16384x2048, FP32, CS EOS T=0.85Tc, dp=1e-3 (roofline stress)"
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SRC = os.path.join(ROOT, "paper_2103_08301_gb300", "csrc", "lbm_kernels.cuh")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_fp32_16384x2048.md")
+
+
+def _dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm_gb_s"):
+                if k in d and d[k]:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def _kernel_hash():
+    import hashlib
+    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+
+
+def _profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    vals = {}
+    for line in open(PROFILE_SUMMARY):
+        if ":" in line and line.strip().startswith("-"):
+            k, v = line.strip("- \n").split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != _kernel_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _rho0(nx=NX, ny=NY, plug_x=PLUG_X, plug_len=PLUG_LEN, film=FILM):
+    import paper_2103_08301_gb300 as lbm
+    eos = lbm.lbm_eos(1.0, 4.0, 1.0, PHYS["T_over_Tc"], PHYS["k"], PHYS["kappa"])
+    _, g, l, _ = lbm.lbm_coexistence(eos)
+    return lbm.lbm_airway_rho0(nx, ny, film, plug_x, plug_len, l, g)
+
+
+def _lattice_kw(precision):
+    return dict(walls=True, bc_x=True, precision=precision, T_over_Tc=PHYS["T_over_Tc"], k=PHYS["k"],
+                kappa=PHYS["kappa"], tau=PHYS["tau"], dp=PHYS["dp"])
+
+
+def _cpu_baseline(budget_s=15.0):
+    """The oracle, as it stands, on a bounded sample of the workload: a window of
+    the same channel (full 2048-row height, 1024 columns with the plug inside),
+    timed for as many steps as fit in about budget_s seconds."""
+    import oracle
+    nx, ny = 1024, NY
+    s = oracle.Setup(nx=nx, ny=ny, walls=True, bc_x=True, T_over_Tc=PHYS["T_over_Tc"], k=PHYS["k"],
+                     kappa=PHYS["kappa"], tau=PHYS["tau"], dp=PHYS["dp"])
+    g, l, _ = s.coexistence()
+    import synth
+    f = oracle.init(s, synth.airway_rho0(nx, ny, FILM, 256.0, 256.0, l, g))
+    t0 = time.perf_counter()
+    f, _ = oracle.run(s, f, 1)
+    one = time.perf_counter() - t0
+    steps = max(1, min(200, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    f, _ = oracle.run(s, f, steps)
+    dt = time.perf_counter() - t0
+    return {"value": nx * ny * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{steps} FP64 oracle steps of a 1024x2048 window of the same channel "
+                      f"(walls, pressure columns, film 64, plug 256 long), {dt:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 CPU oracle timed on the host cores, each step a
+    bounded sample of the workload (a window of the channel) so the whole run
+    finishes within a few minutes."""
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    oracle.build()
+    budget = 150.0
+    ny = 256
+    s_probe = oracle.Setup(nx=512, ny=ny, walls=True, bc_x=True, T_over_Tc=PHYS["T_over_Tc"], k=PHYS["k"],
+                           kappa=PHYS["kappa"], tau=PHYS["tau"], dp=PHYS["dp"])
+    g, l, _ = s_probe.coexistence()
+    f = oracle.init(s_probe, synth.airway_rho0(512, ny, 8.0, 128.0, 128.0, l, g))
+    t0 = time.perf_counter()
+    oracle.run(s_probe, f, 3)
+    rate = 512 * ny * 3 / (time.perf_counter() - t0)  # node updates / s
+    per_step = budget / max(1, args.steps + args.warmup)
+    nx = int(max(64, min(NX, rate * per_step / ny)))
+    s = oracle.Setup(nx=nx, ny=ny, walls=True, bc_x=True, T_over_Tc=PHYS["T_over_Tc"], k=PHYS["k"],
+                     kappa=PHYS["kappa"], tau=PHYS["tau"], dp=PHYS["dp"])
+    f = oracle.init(s, synth.airway_rho0(nx, ny, 8.0, nx / 4, nx / 8, l, g))
+    f, _ = oracle.run(s, f, args.warmup)
+    t0 = time.perf_counter()
+    f, _ = oracle.run(s, f, args.steps)
+    dt = time.perf_counter() - t0
+    val = nx * ny * args.steps / dt / 1e6
+    sample = f"{args.steps} FP64 oracle steps of a {nx}x{ny} airway window (walls, pressure columns, film, plug)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample_nx": nx, "sample_ny": ny},
+        "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2103_08301_gb300 as lbm
+    from paper_2103_08301_gb300 import build as lbm_build
+
+    torch.cuda.set_device(local)
+    if rank == 0 or not os.path.exists(lbm.LIB_PATH):
+        lbm_build.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+
+    precision = 32
+    rho0 = _rho0()
+    stream = torch.cuda.Stream()
+    lat = lbm.Lattice(NX, NY, rho0, stream=stream, **_lattice_kw(precision))
+    info = lat.launch_info()
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # timed region: K steps, one CUDA-event pair per kernel on the solver's stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_start.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            lat.step(1)
+            ev[i][1].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    kern = [a.elapsed_time(b) / 1e3 for a, b in ev]
+    t = torch.tensor([elapsed], device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    d = lat.diag()
+    lat.close()
+    clocks = clk.summary()
+
+    nodes = NX * NY
+    value = world * nodes * args.steps / t_max / 1e6
+    kmean = sum(kern) / len(kern)
+    bytes_per_launch = BYTES_PER_NODE[precision] * nodes
+    achieved = bytes_per_launch / kmean / 1e9
+    peak, peak_src = _hbm_peak()
+
+    # end to end through the public API: host (pinned) rho0 -> lbm_init (H2D),
+    # per step lbm_step + lbm_diag (D2H of the step's diagnostics), final fields to host
+    rho_pinned = torch.empty((NY, NX), dtype=torch.float64, pin_memory=True)
+    rho_pinned.numpy()[:] = rho0
+    out_rho = torch.empty((NY, NX), dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    lat2 = lbm.Lattice(NX, NY, rho_pinned.numpy(), stream=stream, **_lattice_kw(precision))
+    for _ in range(args.steps):
+        lat2.step(1)
+        lat2.diag()
+    lat2.fields_into(rho=out_rho.numpy())
+    lat2.close()
+    e2e_t = time.perf_counter() - t0
+    et = torch.tensor([e2e_t], device="cuda")
+    if dist:
+        dist.all_reduce(et, op=dist.ReduceOp.MAX)
+    e2e_val = world * nodes * args.steps / float(et.item()) / 1e6
+
+    if rank == 0:
+        cpu = _cpu_baseline() if world == 1 else None
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "precision": precision,
+                       "l2": "state 2.4 GB > 129 MB L2 (no flush needed)",
+                       "launch": info, "parallelism": f"{world} independent channel replicas"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_src,
+                         "traffic": _profiled_traffic(),
+                         "algorithmic_bytes_per_launch": bytes_per_launch,
+                         "kernel_ms_mean": kmean * 1e3,
+                         "kernel_ms_min": min(kern) * 1e3},
+            "clocks": clocks,
+            "e2e": {"value": e2e_val, "unit": "MLUPS",
+                    "h2d_bytes_per_step": NX * NY * 8 / args.steps,
+                    "d2h_bytes_per_step": 7 * 8 + NX * NY * 4 / args.steps},
+            "gpu_launches": args.steps,
+            "cpu_baseline": cpu,
+            "diag": {"mass": d["mass"], "wall_shear_sum": d["wall_shear_sum"], "nan": d["nan_detected"]},
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = _dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * lbm.h — C ABI of the GB300 (sm_103a) EOS-based multiphase lattice Boltzmann
+ * solver: the time-step hot path of He, Qin, Chen & Wen, "Numerical
+ * simulation of pulmonary airway reopening by the EOS-based multiphase lattice
+ * Boltzmann method" (arXiv 2103.08301).
+ *
+ * One time step (lbm_step) is, at every fluid node of a D2Q9 lattice:
+ *   moments        rho = sum f_i, u = sum f_i e_i / rho                 (Sec. 2.1)
+ *   nonideal force F = -grad(k^2 p0(rho) - rho/3) + kappa rho grad(lap rho) + G
+ *                  with the EOS p0 evaluated directly                    (Eqs. 2.12-2.17)
+ *   collision      BGK towards f_eq(rho, u + tau F / rho)               (Eq. 2.2, Sec. 2.1)
+ *   boundaries     half-way bounce-back walls, mirror ghost density for
+ *                  wetting, pressure inlet/outlet columns                (Sec. 2.2)
+ *   streaming      f_i(x + e_i, t + 1) = f*_i(x, t)                     (Eq. 2.1)
+ * The paper names the Peng-Robinson EOS (Eq. 2.18) and an MRT operator; this
+ * ABI computes the Carnahan-Starling EOS, p0 = rho R T (1 + eta + eta^2 -
+ * eta^3)/(1 - eta)^3 - a rho^2 with eta = b rho / 4, and the single-relaxation
+ * (BGK) operator that the paper lists among its LBE variants (Sec. 2.1).
+ *
+ * Conventions
+ *   - Lattice nodes are (x, y), 0 <= x < nx, 0 <= y < ny, node index y*nx + x.
+ *   - Populations are stored as nine planes f[i][y][x] (structure of arrays),
+ *     i = 0..8 with e = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1).
+ *   - Real-valued buffers use the context precision: float for precision 32,
+ *     double for precision 64. Host inputs are always double.
+ *   - All functions return an lbm_status; none aborts or traps. After
+ *     LBM_ERR_NAN the context keeps running but its fields are meaningless
+ *     until lbm_restore or lbm_load_populations.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ *   - Work is issued on the context's CUDA stream. lbm_step is asynchronous;
+ *     lbm_fields, lbm_diag, lbm_populations and lbm_checkpoint synchronise
+ *     that stream before returning.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,   /* NULL pointer, bad size or flag, buffer too small */
+    LBM_ERR_PARAM = 2, /* tau <= 1/2; T >= Tc without explicit p_ref; boundary
+                          pressure off the gas branch; kappa < 0; k <= 0 */
+    LBM_ERR_CUDA = 3,  /* a CUDA runtime call failed (lbm_last_error has the text) */
+    LBM_ERR_OOM = 4,   /* device or host allocation failed */
+    LBM_ERR_NAN = 5,   /* a step met a non-finite or non-positive density */
+    LBM_ERR_STATE = 6  /* checkpoint of another geometry or precision */
+} lbm_status;
+
+/* Lattice and geometry (Sec. 2.2: straight rigid channel of the airway model).
+ * walls: 0 = periodic in y; 1 = rows 0 and ny-1 are solid no-slip walls (the
+ *        channel walls; this is the ABI's wall mask, which the paper's
+ *        geometry reduces to).
+ * bc_x:  0 = periodic in x; 1 = column 0 is the pressure inlet and column
+ *        nx-1 the pressure outlet.
+ * Limits: nx, ny >= 4 (>= 1 for a periodic axis), nx*ny < 2^31 per plane. */
+typedef struct {
+    int32_t nx, ny;
+    int32_t walls;
+    int32_t bc_x;
+    int32_t precision; /* 32 (float state) or 64 (double state) */
+} lbm_grid;
+
+/* Carnahan-Starling EOS and the model coefficients of Eq. 2.17.
+ * T = T_over_Tc * Tc with Tc the EOS critical temperature.
+ * k: proportional coefficient (Eq. 2.13); the mesh-space EOS is k^2 p0 (Eq. 2.14).
+ * kappa: gradient coefficient of Eq. 2.17, taken in mesh units. */
+typedef struct {
+    double a, b, R;
+    double T_over_Tc;
+    double k;
+    double kappa;
+} lbm_eos;
+
+/* Driving. With bc_x = 1 the inlet and outlet columns carry the gas-branch
+ * densities whose mesh pressures k^2 p0 are p_ref + dp/2 and p_ref - dp/2
+ * (pressure drop dp, Sec. 2.2 / Sec. 3.3). p_ref = NaN selects k^2 p_sat(T).
+ * (gx, gy) is a uniform body-force density added to F. */
+typedef struct {
+    double dp;
+    double p_ref;
+    double gx, gy;
+} lbm_drive;
+
+/* Diagnostics (Sec. 3: wall pressure and wall shear; Fig. 3). Per-step
+ * quantities refer to the state each step reads, so after n steps they cover
+ * states 0..n-1. */
+typedef struct {
+    int64_t step;          /* steps taken since lbm_init / last restore */
+    double mass;           /* sum of rho over non-solid nodes of state step-1
+                              (pressure columns count rho_b); 0 before any step */
+    double wall_shear_sum; /* sum over states and columns of tau_w(bottom) + tau_w(top) */
+    double tau_wall_min, tau_wall_max; /* extrema of tau_w over walls and states */
+    double p_wall_min, p_wall_max;     /* extrema of the wall pressure (Eq. 2.4) */
+    int32_t nan_detected;  /* nonzero once any step met a bad density */
+    int32_t pad_;
+    /* thermodynamic set-up derived by lbm_init (host FP64) */
+    double T, Tc, rho_g, rho_l, p_sat, rho_in, rho_out;
+} lbm_diag_t;
+
+/* Bytes of device memory a context of this grid needs (two population
+ * arrays plus diagnostics). 0 on invalid grid. */
+size_t lbm_workspace_bytes(const lbm_grid *grid);
+
+/* Create a context.
+ *   grid, eos, drive: copied. drive may be NULL (no drive).
+ *   tau:      BGK relaxation time, > 1/2.
+ *   wetting:  ghost-density offset added to mirrored wall densities
+ *             (0 = neutral wetting, 90-degree contact angle).
+ *   rho0:     host array of nx*ny doubles, the initial density; the
+ *             populations start at f_eq(rho0, 0). Copied. Required.
+ *   workspace, ws_bytes: device buffer of at least lbm_workspace_bytes(grid)
+ *             bytes, 256-byte aligned, owned by the caller and kept alive
+ *             until lbm_free; NULL lets the library allocate (cudaMalloc) and
+ *             free it.
+ *   stream:   cudaStream_t to issue all work on; NULL = legacy default stream.
+ *   out:      receives the context; *out is NULL on failure.
+ * Errors: LBM_ERR_ARG, LBM_ERR_PARAM, LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, double wetting,
+                    const lbm_drive *drive, const double *rho0, void *workspace,
+                    size_t ws_bytes, void *stream, lbm_ctx **out);
+
+/* Advance n >= 0 time steps (one fused kernel launch each), asynchronously.
+ * Returns LBM_ERR_NAN if a completed earlier step met a bad density (checked
+ * without blocking), LBM_ERR_CUDA on launch failure. */
+lbm_status lbm_step(lbm_ctx *ctx, int64_t n);
+
+/* Macroscopic fields of the current state, computed on the GPU:
+ *   rho, ux, uy: nx*ny values each (v = u + F/(2 rho), Sec. 2.1); solid
+ *                nodes read 0; pressure columns read rho_b and v of their
+ *                interior neighbour.
+ *   tau_wall, p_wall: 2*nx values (bottom wall row then top wall row); zero
+ *                for pressure columns and channels without walls.
+ * Each pointer may be NULL (skipped), a device pointer or a host pointer, of
+ * the context precision. Synchronises the stream. */
+lbm_status lbm_fields(lbm_ctx *ctx, void *rho, void *ux, void *uy, void *tau_wall,
+                      void *p_wall);
+
+/* Reduce the diagnostics on the GPU (fixed order, deterministic) and return
+ * them in *out (host). Synchronises the stream. */
+lbm_status lbm_diag(lbm_ctx *ctx, lbm_diag_t *out);
+
+/* Raw population state: 9*nx*ny values of the context precision, layout
+ * f[i][y][x]. dst / src may be host or device pointers. */
+lbm_status lbm_populations(lbm_ctx *ctx, void *dst);
+lbm_status lbm_load_populations(lbm_ctx *ctx, const void *src);
+
+/* Checkpoint / restore: populations, step counter and diagnostic
+ * accumulators in a host buffer of lbm_checkpoint_bytes(ctx) bytes.
+ * A restored run continues bit-identically. LBM_ERR_STATE if the buffer was
+ * written by a context of another grid or precision. */
+size_t lbm_checkpoint_bytes(const lbm_ctx *ctx);
+lbm_status lbm_checkpoint(lbm_ctx *ctx, void *host_buf, size_t bytes);
+lbm_status lbm_restore(lbm_ctx *ctx, const void *host_buf, size_t bytes);
+
+/* Launch tuning and test hooks:
+ *   LBM_OPT_CTAS_PER_SM  resident CTAs per SM for the step grid (0 = from
+ *                        the occupancy calculator); takes effect at the next step
+ *   LBM_OPT_REVERSE      nonzero: launch the step's work units in reverse CTA
+ *                        order (results must be bit-identical)
+ *   LBM_OPT_STRIP        strip width in nodes (32..128, multiple of 32) */
+typedef enum { LBM_OPT_CTAS_PER_SM = 1, LBM_OPT_REVERSE = 2, LBM_OPT_STRIP = 3 } lbm_option;
+lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value);
+/* Launch geometry of the step kernel: CTAs, threads per CTA, work units. */
+lbm_status lbm_launch_info(const lbm_ctx *ctx, int64_t *ctas, int64_t *threads, int64_t *units);
+
+/* Release everything the library allocated. NULL-safe. */
+void lbm_free(lbm_ctx *ctx);
+
+const char *lbm_status_string(lbm_status s);
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Host helpers (FP64, no GPU needed) ---------------------------------------*/
+
+/* Critical point, Maxwell coexistence (equal pressure and chemical
+ * potential, Sec. 2.1 "Verification") and saturation pressure at
+ * T = T_over_Tc * Tc. LBM_ERR_PARAM above Tc. Any output may be NULL. */
+lbm_status lbm_coexistence(const lbm_eos *eos, double *Tc, double *rho_g, double *rho_l,
+                           double *p_sat);
+
+/* Initial density of the airway channel (Sec. 2.2, Fig. 2): wall films of
+ * thickness `film` measured from the half-way wall planes and a plug
+ * covering x in [plug_x, plug_x + plug_len), smooth tanh profiles of width
+ * `width`; plus uniform noise amp*(2u - 1), u from SplitMix64(seed ^ node).
+ * out: host array of nx*ny doubles. */
+lbm_status lbm_airway_rho0(int32_t nx, int32_t ny, double film, double plug_x, double plug_len,
+                           double rho_l, double rho_g, double width, double noise_amp,
+                           uint64_t seed, double *out);
+
+/* Initial density of a liquid disk of radius r0 centred at (cx, cy). */
+lbm_status lbm_disk_rho0(int32_t nx, int32_t ny, double cx, double cy, double r0, double rho_l,
+                         double rho_g, double width, double noise_amp, uint64_t seed, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

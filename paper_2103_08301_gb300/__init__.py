@@ -1,0 +1,266 @@
+"""GB300-native EOS-based multiphase lattice Boltzmann solver (arXiv 2103.08301).
+
+A thin ctypes binding of the C ABI declared in ``include/lbm.h``: the same entry
+points under the same names, plus a small ``Lattice`` convenience class. The
+binding only marshals arguments; every step of the method runs in the CUDA
+kernels of ``liblbm.so``. PyTorch is used for device buffers and streams.
+
+The library is built in-tree by ``paper_2103_08301_gb300.build.build()``. If
+it is missing this package raises on use: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+LBM_OK, LBM_ERR_ARG, LBM_ERR_PARAM, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_NAN, LBM_ERR_STATE = range(7)
+LBM_OPT_CTAS_PER_SM, LBM_OPT_REVERSE, LBM_OPT_STRIP = 1, 2, 3
+
+
+class lbm_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("walls", C.c_int32), ("bc_x", C.c_int32),
+                ("precision", C.c_int32)]
+
+
+class lbm_eos(C.Structure):
+    _fields_ = [("a", C.c_double), ("b", C.c_double), ("R", C.c_double), ("T_over_Tc", C.c_double),
+                ("k", C.c_double), ("kappa", C.c_double)]
+
+
+class lbm_drive(C.Structure):
+    _fields_ = [("dp", C.c_double), ("p_ref", C.c_double), ("gx", C.c_double), ("gy", C.c_double)]
+
+
+class lbm_diag_t(C.Structure):
+    _fields_ = [("step", C.c_int64), ("mass", C.c_double), ("wall_shear_sum", C.c_double),
+                ("tau_wall_min", C.c_double), ("tau_wall_max", C.c_double),
+                ("p_wall_min", C.c_double), ("p_wall_max", C.c_double),
+                ("nan_detected", C.c_int32), ("pad_", C.c_int32),
+                ("T", C.c_double), ("Tc", C.c_double), ("rho_g", C.c_double), ("rho_l", C.c_double),
+                ("p_sat", C.c_double), ("rho_in", C.c_double), ("rho_out", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+# Every symbol declared in include/lbm.h, with (restype, argtypes).
+_P = C.c_void_p
+_SIGS = {
+    "lbm_workspace_bytes": (C.c_size_t, [C.POINTER(lbm_grid)]),
+    "lbm_init": (C.c_int, [C.POINTER(lbm_grid), C.POINTER(lbm_eos), C.c_double, C.c_double,
+                           C.POINTER(lbm_drive), C.POINTER(C.c_double), _P, C.c_size_t, _P,
+                           C.POINTER(_P)]),
+    "lbm_step": (C.c_int, [_P, C.c_int64]),
+    "lbm_fields": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+    "lbm_diag": (C.c_int, [_P, C.POINTER(lbm_diag_t)]),
+    "lbm_populations": (C.c_int, [_P, _P]),
+    "lbm_load_populations": (C.c_int, [_P, _P]),
+    "lbm_checkpoint_bytes": (C.c_size_t, [_P]),
+    "lbm_checkpoint": (C.c_int, [_P, _P, C.c_size_t]),
+    "lbm_restore": (C.c_int, [_P, _P, C.c_size_t]),
+    "lbm_set_option": (C.c_int, [_P, C.c_int, C.c_int64]),
+    "lbm_launch_info": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "lbm_free": (None, [_P]),
+    "lbm_status_string": (C.c_char_p, [C.c_int]),
+    "lbm_last_error": (C.c_char_p, [_P]),
+    "lbm_coexistence": (C.c_int, [C.POINTER(lbm_eos)] + [C.POINTER(C.c_double)] * 4),
+    "lbm_airway_rho0": (C.c_int, [C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
+                                  C.c_double, C.c_double, C.c_double, C.c_double, C.c_uint64,
+                                  C.POINTER(C.c_double)]),
+    "lbm_disk_rho0": (C.c_int, [C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
+                                C.c_double, C.c_double, C.c_double, C.c_double, C.c_uint64,
+                                C.POINTER(C.c_double)]),
+}
+
+_lib = None
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{status_string(status)} ({status}){': ' + msg if msg else ''}")
+
+
+def lib():
+    """The loaded liblbm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"{LIB_PATH} is missing: build it with paper_2103_08301_gb300.build.build() "
+                "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_string(s: int) -> str:
+    try:
+        return lib().lbm_status_string(int(s)).decode()
+    except ImportError:
+        return f"status {s}"
+
+
+def _check(st, ctx=None):
+    if st != LBM_OK:
+        msg = lib().lbm_last_error(ctx).decode() if ctx else ""
+        raise LBMError(st, msg)
+
+
+# ---------------------------------------------------------------------------
+# Functions with the C names (thin wrappers)
+# ---------------------------------------------------------------------------
+
+def lbm_workspace_bytes(grid: lbm_grid) -> int:
+    return int(lib().lbm_workspace_bytes(C.byref(grid)))
+
+
+def lbm_init(grid, eos, tau, wetting, drive, rho0, workspace=None, ws_bytes=0, stream=None):
+    rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+    ctx = _P()
+    st = lib().lbm_init(C.byref(grid), C.byref(eos), float(tau), float(wetting),
+                        C.byref(drive) if drive is not None else None,
+                        rho0.ctypes.data_as(C.POINTER(C.c_double)),
+                        _P(workspace) if workspace else None, int(ws_bytes),
+                        _P(stream) if stream else None, C.byref(ctx))
+    _check(st)
+    return ctx
+
+
+def lbm_step(ctx, n: int) -> int:
+    return int(lib().lbm_step(ctx, int(n)))
+
+
+def lbm_coexistence(eos: lbm_eos):
+    Tc, g, l, p = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+    _check(lib().lbm_coexistence(C.byref(eos), C.byref(Tc), C.byref(g), C.byref(l), C.byref(p)))
+    return Tc.value, g.value, l.value, p.value
+
+
+def lbm_airway_rho0(nx, ny, film, plug_x, plug_len, rho_l, rho_g, width=4.0, noise=0.0, seed=1):
+    out = np.empty((ny, nx), dtype=np.float64)
+    _check(lib().lbm_airway_rho0(nx, ny, film, plug_x, plug_len, rho_l, rho_g, width, noise, seed,
+                                 out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
+def lbm_disk_rho0(nx, ny, cx, cy, r0, rho_l, rho_g, width=4.0, noise=0.0, seed=1):
+    out = np.empty((ny, nx), dtype=np.float64)
+    _check(lib().lbm_disk_rho0(nx, ny, cx, cy, r0, rho_l, rho_g, width, noise, seed,
+                               out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Convenience class
+# ---------------------------------------------------------------------------
+
+class Lattice:
+    """One channel (or periodic box) resident on the current CUDA device.
+
+    Parameters mirror lbm_init. ``workspace`` may be a CUDA torch tensor of at
+    least ``lbm_workspace_bytes`` bytes (kept alive by this object); by default
+    the library allocates. ``stream`` is a torch.cuda.Stream or None.
+    """
+
+    def __init__(self, nx, ny, rho0, *, walls=False, bc_x=False, precision=32, a=1.0, b=4.0,
+                 R=1.0, T_over_Tc=0.8, k=1.0, kappa=0.5, tau=1.0, wetting=0.0, dp=0.0,
+                 p_ref=None, gx=0.0, gy=0.0, workspace=None, stream=None):
+        self.grid = lbm_grid(nx, ny, int(walls), int(bc_x), int(precision))
+        self.eos = lbm_eos(a, b, R, T_over_Tc, k, kappa)
+        self.drive = lbm_drive(dp, math.nan if p_ref is None else p_ref, gx, gy)
+        self.nx, self.ny, self.precision = nx, ny, precision
+        self.dtype = np.float32 if precision == 32 else np.float64
+        self._ws = workspace
+        self._stream = stream
+        ws_ptr, ws_bytes = None, 0
+        if workspace is not None:
+            ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+        sptr = stream.cuda_stream if stream is not None else None
+        self.ctx = lbm_init(self.grid, self.eos, tau, wetting, self.drive, rho0, ws_ptr, ws_bytes, sptr)
+
+    # -- stepping -----------------------------------------------------------
+    def step(self, n=1):
+        st = lbm_step(self.ctx, n)
+        if st == LBM_ERR_NAN:
+            raise LBMError(st, "a step met a non-finite or non-positive density")
+        _check(st, self.ctx)
+
+    # -- outputs ------------------------------------------------------------
+    def fields(self):
+        """dict(rho, vx, vy, tau_wall[2, nx], p_wall[2, nx]) as numpy arrays."""
+        ny, nx, dt = self.ny, self.nx, self.dtype
+        out = {k: np.zeros((ny, nx), dt) for k in ("rho", "vx", "vy")}
+        out["tau_wall"] = np.zeros((2, nx), dt)
+        out["p_wall"] = np.zeros((2, nx), dt)
+        p = [_P(out[k].ctypes.data) for k in ("rho", "vx", "vy", "tau_wall", "p_wall")]
+        _check(lib().lbm_fields(self.ctx, *p), self.ctx)
+        return out
+
+    def fields_into(self, rho=None, vx=None, vy=None, tau_wall=None, p_wall=None):
+        """Write fields into caller buffers (CUDA torch tensors or numpy arrays)."""
+        def ptr(t):
+            if t is None:
+                return None
+            return _P(t.data_ptr()) if hasattr(t, "data_ptr") else _P(t.ctypes.data)
+        _check(lib().lbm_fields(self.ctx, ptr(rho), ptr(vx), ptr(vy), ptr(tau_wall), ptr(p_wall)), self.ctx)
+
+    def diag(self):
+        d = lbm_diag_t()
+        _check(lib().lbm_diag(self.ctx, C.byref(d)), self.ctx)
+        return d.as_dict()
+
+    def populations(self):
+        f = np.empty((9, self.ny, self.nx), self.dtype)
+        _check(lib().lbm_populations(self.ctx, _P(f.ctypes.data)), self.ctx)
+        return f
+
+    def load_populations(self, f):
+        f = np.ascontiguousarray(f, dtype=self.dtype)
+        assert f.shape == (9, self.ny, self.nx)
+        _check(lib().lbm_load_populations(self.ctx, _P(f.ctypes.data)), self.ctx)
+
+    def checkpoint(self):
+        n = int(lib().lbm_checkpoint_bytes(self.ctx))
+        buf = np.empty(n, np.uint8)
+        _check(lib().lbm_checkpoint(self.ctx, _P(buf.ctypes.data), n), self.ctx)
+        return buf
+
+    def restore(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(lib().lbm_restore(self.ctx, _P(buf.ctypes.data), buf.size), self.ctx)
+
+    def set_option(self, opt, value):
+        _check(lib().lbm_set_option(self.ctx, int(opt), int(value)), self.ctx)
+
+    def launch_info(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib().lbm_launch_info(self.ctx, C.byref(a), C.byref(b), C.byref(c)), self.ctx)
+        return {"ctas": a.value, "threads": b.value, "units": c.value}
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().lbm_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,67 @@
+"""Build the solver's shared library (liblbm.so) in-tree for sm_103a.
+
+Two translation units, compiled in parallel and linked with nvcc:
+  csrc/lbm_api.cu   - C ABI and the CUDA kernels (nvcc, -gencode sm_103a)
+  csrc/lbm_host.cpp - host FP64 thermodynamics and initial profiles (g++)
+Run as ``python -m paper_2103_08301_gb300.build`` or call ``build()``.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "liblbm.so")
+NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+SOURCES = ["lbm_api.cu", "lbm_host.cpp", "lbm_kernels.cuh", "lbm_internal.h"]
+
+
+def _stale() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    deps = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(INCLUDE, "lbm.h"), __file__]
+    return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
+
+
+def _run(cmd):
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"build failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+    return r.stdout + r.stderr
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile liblbm.so if missing or out of date; return its path."""
+    if not force and not _stale():
+        return LIB
+    os.makedirs(BUILD, exist_ok=True)
+    api_o = os.path.join(BUILD, "lbm_api.o")
+    host_o = os.path.join(BUILD, "lbm_host.o")
+    nv = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
+          "-I", CSRC, "-c", os.path.join(CSRC, "lbm_api.cu"), "-o", api_o]
+    if verbose:
+        nv.insert(1, "-Xptxas=-v")
+    gxx = ["g++", "-O2", "-std=c++17", "-fPIC", "-I", INCLUDE, "-I", CSRC, "-c",
+           os.path.join(CSRC, "lbm_host.cpp"), "-o", host_o]
+    with ThreadPoolExecutor(2) as ex:
+        outs = list(ex.map(_run, [nv, gxx]))
+    if verbose:
+        print(outs[0])
+    tmp = LIB + f".tmp{os.getpid()}"
+    _run([NVCC, *ARCH, "-shared", "-o", tmp, api_o, host_o, "-lcudart"])
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
+    print(LIB)

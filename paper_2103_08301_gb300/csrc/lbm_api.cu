@@ -1,0 +1,579 @@
+// C ABI of the GB300 EOS-multiphase lattice Boltzmann solver (see include/lbm.h).
+// Host orchestration only: argument checks, thermodynamic set-up in FP64,
+// device workspace, kernel launches on the context stream, diagnostics and
+// checkpoints. Every step of the method runs in the kernels of lbm_kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+#include "lbm_kernels.cuh"
+
+namespace {
+
+constexpr int BLOCK = 128;
+constexpr size_t ALIGN = 256;
+constexpr uint64_t CKPT_MAGIC = 0x4C424D434B505431ull;  // "LBMCKPT1"
+
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Layout {
+    size_t pops;      // one population array
+    size_t f0, f1, mass, J, ext, err, dout, total;
+};
+
+Layout layout_of(int nx, int ny, int precision)
+{
+    Layout L{};
+    const size_t sz = precision == 64 ? 8 : 4;
+    L.pops = align_up((size_t)9 * nx * ny * sz);
+    size_t o = 0;
+    L.f0 = o; o += L.pops;
+    L.f1 = o; o += L.pops;
+    L.mass = o; o += align_up(lbm::MAX_CTAS * sizeof(double));
+    L.J = o; o += align_up(lbm::MAX_CTAS * sizeof(double));
+    L.ext = o; o += align_up((size_t)lbm::MAX_CTAS * 4 * sz);
+    L.err = o; o += align_up(sizeof(int));
+    L.dout = o; o += align_up(8 * sizeof(double));
+    L.total = o;
+    return L;
+}
+
+bool grid_ok(const lbm_grid *g)
+{
+    if (!g) return false;
+    if (g->precision != 32 && g->precision != 64) return false;
+    if (g->walls != 0 && g->walls != 1) return false;
+    if (g->bc_x != 0 && g->bc_x != 1) return false;
+    if (g->nx < (g->bc_x ? 4 : 1) || g->ny < (g->walls ? 4 : 1)) return false;
+    if ((long long)g->nx * g->ny >= (1ll << 31)) return false;
+    return true;
+}
+
+} // namespace
+
+struct lbm_ctx {
+    lbm_grid grid{};
+    lbm_eos eos{};
+    lbm_drive drive{};
+    double tau = 1.0, wet = 0.0;
+    double T = 0, Tc = 0, rho_g = 0, rho_l = 0, p_sat = 0, rho_in = 0, rho_out = 0;
+    cudaStream_t stream = nullptr;
+    unsigned char *ws = nullptr;
+    bool own_ws = false;
+    Layout L{};
+    int cur = 0;          // which population array holds the current state
+    int64_t step = 0;
+    int W = BLOCK, nstrips = 0, yf0 = 0, nyf = 0;
+    long long units = 0;
+    int nctas = 0;
+    int ctas_per_sm_opt = 0;
+    int reverse = 0;
+    int sms = 0;
+    // fields scratch (allocated on first host-pointer lbm_fields)
+    unsigned char *fscratch = nullptr;
+    // non-blocking NaN check
+    int *h_err = nullptr;
+    cudaEvent_t err_ev = nullptr;
+    bool err_pending = false;
+    char last_error[512] = {0};
+};
+
+namespace {
+
+lbm_status cuda_fail(lbm_ctx *c, cudaError_t e, const char *where)
+{
+    if (c) std::snprintf(c->last_error, sizeof c->last_error, "%s: %s", where, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+}
+
+#define CK(call, where)                                            \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where);   \
+    } while (0)
+
+template <typename real>
+lbm::KArgs<real> make_args(const lbm_ctx *ctx)
+{
+    lbm::KArgs<real> A{};
+    const int src = ctx->cur, dst = 1 - ctx->cur;
+    A.fin = (const real *)(ctx->ws + (src ? ctx->L.f1 : ctx->L.f0));
+    A.fout = (real *)(ctx->ws + (dst ? ctx->L.f1 : ctx->L.f0));
+    A.plane = (long long)ctx->grid.nx * ctx->grid.ny;
+    A.nx = ctx->grid.nx;
+    A.ny = ctx->grid.ny;
+    A.W = ctx->W;
+    A.nstrips = ctx->nstrips;
+    A.yf0 = ctx->yf0;
+    A.nyf = ctx->nyf;
+    A.units = ctx->units;
+    A.nctas = ctx->nctas;
+    A.reverse = ctx->reverse;
+    const double k = ctx->eos.k;
+    A.RT = (real)(ctx->eos.R * ctx->T);
+    A.a = (real)ctx->eos.a;
+    A.b4 = (real)(0.25 * ctx->eos.b);
+    A.k2 = (real)(k * k);
+    A.kappa = (real)ctx->eos.kappa;
+    A.tau = (real)ctx->tau;
+    A.inv_tau = (real)(1.0 / ctx->tau);
+    A.omb = (real)(1.0 - 1.0 / ctx->tau);
+    A.gx = (real)ctx->drive.gx;
+    A.gy = (real)ctx->drive.gy;
+    A.wet = (real)ctx->wet;
+    A.rho_in = (real)ctx->rho_in;
+    A.rho_out = (real)ctx->rho_out;
+    A.nu = (real)((ctx->tau - 0.5) / 3.0);
+    A.mass_part = (double *)(ctx->ws + ctx->L.mass);
+    A.J_acc = (double *)(ctx->ws + ctx->L.J);
+    A.ext = (real *)(ctx->ws + ctx->L.ext);
+    A.err = (int *)(ctx->ws + ctx->L.err);
+    return A;
+}
+
+template <typename real, int MODE>
+void *kernel_ptr(bool walls, bool pres)
+{
+    using namespace lbm;
+    if (walls && pres) return (void *)step_kernel<real, true, true, MODE, BLOCK>;
+    if (walls) return (void *)step_kernel<real, true, false, MODE, BLOCK>;
+    if (pres) return (void *)step_kernel<real, false, true, MODE, BLOCK>;
+    return (void *)step_kernel<real, false, false, MODE, BLOCK>;
+}
+
+void *step_kernel_ptr(const lbm_ctx *ctx, int mode)
+{
+    const bool w = ctx->grid.walls, p = ctx->grid.bc_x;
+    if (ctx->grid.precision == 64)
+        return mode == lbm::MODE_STEP ? kernel_ptr<double, lbm::MODE_STEP>(w, p)
+                                      : kernel_ptr<double, lbm::MODE_FIELDS>(w, p);
+    return mode == lbm::MODE_STEP ? kernel_ptr<float, lbm::MODE_STEP>(w, p)
+                                  : kernel_ptr<float, lbm::MODE_FIELDS>(w, p);
+}
+
+// Strip partition and the CTA count of the step grid.
+lbm_status plan_launch(lbm_ctx *ctx)
+{
+    const int nx = ctx->grid.nx;
+    int W = std::min(ctx->W > 0 ? ctx->W : BLOCK, BLOCK);
+    // the outlet column must not open a strip (its stencil reaches two columns back)
+    if (ctx->grid.bc_x && nx > W && nx % W == 1) {
+        for (int w = W - 1; w >= 2; --w)
+            if (nx % w != 1) { W = w; break; }
+    }
+    ctx->W = W;
+    ctx->nstrips = (nx + W - 1) / W;
+    ctx->yf0 = ctx->grid.walls ? 1 : 0;
+    ctx->nyf = ctx->grid.walls ? ctx->grid.ny - 2 : ctx->grid.ny;
+    ctx->units = (long long)ctx->nstrips * ctx->nyf;
+
+    int per_sm = ctx->ctas_per_sm_opt;
+    if (per_sm <= 0) {
+        int occ = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, step_kernel_ptr(ctx, lbm::MODE_STEP), BLOCK, 0);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy");
+        per_sm = std::max(1, occ);
+    }
+    long long n = (long long)ctx->sms * per_sm;
+    n = std::min<long long>(n, std::max<long long>(1, ctx->units / 2));
+    n = std::min<long long>(n, lbm::MAX_CTAS);
+    ctx->nctas = (int)std::max<long long>(1, n);
+    return LBM_OK;
+}
+
+template <typename real, int MODE>
+cudaError_t launch(lbm_ctx *ctx, const lbm::KArgs<real> &A)
+{
+    void *fn = step_kernel_ptr(ctx, MODE);
+    void *args[] = {(void *)&A};
+    return cudaLaunchKernel(fn, dim3(ctx->nctas), dim3(BLOCK), args, 0, ctx->stream);
+}
+
+template <typename real>
+lbm_status do_steps(lbm_ctx *ctx, int64_t n)
+{
+    for (int64_t s = 0; s < n; ++s) {
+        lbm::KArgs<real> A = make_args<real>(ctx);
+        cudaError_t e = launch<real, lbm::MODE_STEP>(ctx, A);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
+        ctx->cur = 1 - ctx->cur;
+        ctx->step += 1;
+    }
+    return LBM_OK;
+}
+
+template <typename real>
+lbm_status do_fields(lbm_ctx *ctx, void *rho, void *ux, void *uy, void *tw, void *pw)
+{
+    const size_t N = (size_t)ctx->grid.nx * ctx->grid.ny, nx = ctx->grid.nx;
+    const size_t sz = sizeof(real);
+    if (!ctx->fscratch) {
+        CK(cudaMalloc((void **)&ctx->fscratch, align_up(3 * N * sz) + align_up(4 * nx * sz)),
+           "fields scratch");
+    }
+    real *d_rho = (real *)ctx->fscratch, *d_vx = d_rho + N, *d_vy = d_vx + N;
+    real *d_tw = (real *)(ctx->fscratch + align_up(3 * N * sz)), *d_pw = d_tw + 2 * nx;
+    CK(cudaMemsetAsync(ctx->fscratch, 0, align_up(3 * N * sz) + align_up(4 * nx * sz), ctx->stream),
+       "fields memset");
+    lbm::KArgs<real> A = make_args<real>(ctx);
+    A.fout = nullptr;
+    A.o_rho = d_rho; A.o_vx = d_vx; A.o_vy = d_vy; A.o_tw = d_tw; A.o_pw = d_pw;
+    cudaError_t le = launch<real, lbm::MODE_FIELDS>(ctx, A);
+    if (le != cudaSuccess) return cuda_fail(ctx, le, "fields launch");
+    struct { void *dst; real *src; size_t n; } outs[] = {
+        {rho, d_rho, N}, {ux, d_vx, N}, {uy, d_vy, N}, {tw, d_tw, 2 * nx}, {pw, d_pw, 2 * nx}};
+    for (auto &o : outs) {
+        if (!o.dst) continue;
+        CK(cudaMemcpyAsync(o.dst, o.src, o.n * sz, cudaMemcpyDefault, ctx->stream), "fields copy");
+    }
+    CK(cudaStreamSynchronize(ctx->stream), "fields sync");
+    return LBM_OK;
+}
+
+template <typename real>
+void reset_acc(lbm_ctx *ctx)
+{
+    lbm::reset_acc_kernel<real><<<(lbm::MAX_CTAS + 255) / 256, 256, 0, ctx->stream>>>(
+        (double *)(ctx->ws + ctx->L.mass), (double *)(ctx->ws + ctx->L.J),
+        (real *)(ctx->ws + ctx->L.ext), (int *)(ctx->ws + ctx->L.err), lbm::MAX_CTAS);
+}
+
+struct CkptHeader {
+    uint64_t magic;
+    int32_t nx, ny, walls, bc_x, precision, nctas;
+    int64_t step;
+    int32_t cur, pad;
+};
+
+} // namespace
+
+extern "C" {
+
+const char *lbm_status_string(lbm_status s)
+{
+    switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_ARG: return "invalid argument";
+    case LBM_ERR_PARAM: return "invalid physical parameter";
+    case LBM_ERR_CUDA: return "CUDA error";
+    case LBM_ERR_OOM: return "out of memory";
+    case LBM_ERR_NAN: return "non-finite or non-positive density";
+    case LBM_ERR_STATE: return "incompatible checkpoint";
+    }
+    return "unknown status";
+}
+
+const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->last_error : ""; }
+
+size_t lbm_workspace_bytes(const lbm_grid *grid)
+{
+    if (!grid_ok(grid)) return 0;
+    return layout_of(grid->nx, grid->ny, grid->precision).total;
+}
+
+lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, double wetting,
+                    const lbm_drive *drive, const double *rho0, void *workspace, size_t ws_bytes,
+                    void *stream, lbm_ctx **out)
+{
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (!grid_ok(grid) || !eos || !rho0) return LBM_ERR_ARG;
+    if (!(tau > 0.5) || !(eos->k > 0) || !(eos->kappa >= 0) || !(eos->a > 0) || !(eos->b > 0) ||
+        !(eos->R > 0) || !(eos->T_over_Tc > 0) || !std::isfinite(wetting))
+        return LBM_ERR_PARAM;
+
+    lbm_ctx *ctx = new (std::nothrow) lbm_ctx();
+    if (!ctx) return LBM_ERR_OOM;
+    ctx->grid = *grid;
+    ctx->eos = *eos;
+    if (drive) ctx->drive = *drive;
+    else { ctx->drive.dp = 0; ctx->drive.p_ref = NAN; ctx->drive.gx = ctx->drive.gy = 0; }
+    ctx->tau = tau;
+    ctx->wet = wetting;
+    ctx->stream = (cudaStream_t)stream;
+
+    // Thermodynamics (host FP64).
+    double rhoc;
+    lbm::cs_critical(eos->a, eos->b, eos->R, &ctx->Tc, &rhoc);
+    ctx->T = eos->T_over_Tc * ctx->Tc;
+    lbm::Thermo th{eos->a, eos->b, eos->R, ctx->T};
+    bool coexist = lbm::maxwell(th, &ctx->rho_g, &ctx->rho_l, &ctx->p_sat) == 0;
+    if (grid->bc_x) {
+        const double k2 = eos->k * eos->k;
+        double pref = ctx->drive.p_ref;
+        if (std::isnan(pref)) {
+            if (!coexist) { lbm_free(ctx); return LBM_ERR_PARAM; }
+            pref = k2 * ctx->p_sat;
+        }
+        if (lbm::gas_density(th, (pref + 0.5 * ctx->drive.dp) / k2, &ctx->rho_in) ||
+            lbm::gas_density(th, (pref - 0.5 * ctx->drive.dp) / k2, &ctx->rho_out)) {
+            lbm_free(ctx);
+            return LBM_ERR_PARAM;
+        }
+    }
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        lbm_status s = cuda_fail(ctx, e, "device query");
+        lbm_free(ctx);
+        return s;
+    }
+
+    ctx->L = layout_of(grid->nx, grid->ny, grid->precision);
+    if (workspace) {
+        if (ws_bytes < ctx->L.total || ((uintptr_t)workspace % ALIGN) != 0) {
+            lbm_free(ctx);
+            return LBM_ERR_ARG;
+        }
+        ctx->ws = (unsigned char *)workspace;
+    } else {
+        e = cudaMalloc((void **)&ctx->ws, ctx->L.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            lbm_free(ctx);
+            return LBM_ERR_OOM;
+        }
+        ctx->own_ws = true;
+    }
+    e = cudaMallocHost((void **)&ctx->h_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->err_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        lbm_status s = cuda_fail(ctx, e, "host flag");
+        lbm_free(ctx);
+        return s;
+    }
+    *ctx->h_err = 0;
+
+    lbm_status st = plan_launch(ctx);
+    if (st != LBM_OK) { lbm_free(ctx); return st; }
+
+    // Initial state f = f_eq(rho0, 0) in both arrays.
+    const size_t N = (size_t)grid->nx * grid->ny;
+    double *d_rho0 = nullptr;
+    e = cudaMallocAsync((void **)&d_rho0, N * sizeof(double), ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_rho0, rho0, N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) {
+        const int blocks = (int)std::min<size_t>((N + 255) / 256, (size_t)ctx->sms * 8);
+        if (grid->precision == 64) {
+            lbm::init_kernel<double><<<blocks, 256, 0, ctx->stream>>>(
+                d_rho0, (double *)(ctx->ws + ctx->L.f0), (double *)(ctx->ws + ctx->L.f1), (long long)N);
+            reset_acc<double>(ctx);
+        } else {
+            lbm::init_kernel<float><<<blocks, 256, 0, ctx->stream>>>(
+                d_rho0, (float *)(ctx->ws + ctx->L.f0), (float *)(ctx->ws + ctx->L.f1), (long long)N);
+            reset_acc<float>(ctx);
+        }
+        e = cudaGetLastError();
+        cudaFreeAsync(d_rho0, ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        lbm_status s = cuda_fail(ctx, e, "init");
+        lbm_free(ctx);
+        return s;
+    }
+    *out = ctx;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx *ctx, int64_t n)
+{
+    if (!ctx || n < 0) return LBM_ERR_ARG;
+    lbm_status flag = LBM_OK;
+    if (ctx->err_pending && cudaEventQuery(ctx->err_ev) == cudaSuccess) {
+        ctx->err_pending = false;
+        if (*ctx->h_err) flag = LBM_ERR_NAN;
+    }
+    if (n == 0) return flag;
+    lbm_status s = ctx->grid.precision == 64 ? do_steps<double>(ctx, n) : do_steps<float>(ctx, n);
+    if (s != LBM_OK) return s;
+    if (!ctx->err_pending) {
+        cudaError_t e = cudaMemcpyAsync(ctx->h_err, ctx->ws + ctx->L.err, sizeof(int),
+                                        cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->err_ev, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "error flag");
+        ctx->err_pending = true;
+    }
+    return flag;
+}
+
+lbm_status lbm_fields(lbm_ctx *ctx, void *rho, void *ux, void *uy, void *tau_wall, void *p_wall)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    return ctx->grid.precision == 64 ? do_fields<double>(ctx, rho, ux, uy, tau_wall, p_wall)
+                                     : do_fields<float>(ctx, rho, ux, uy, tau_wall, p_wall);
+}
+
+lbm_status lbm_diag(lbm_ctx *ctx, lbm_diag_t *out)
+{
+    if (!ctx || !out) return LBM_ERR_ARG;
+    double *dout = (double *)(ctx->ws + ctx->L.dout);
+    if (ctx->grid.precision == 64)
+        lbm::diag_kernel<double><<<1, 256, 0, ctx->stream>>>(
+            (double *)(ctx->ws + ctx->L.mass), (double *)(ctx->ws + ctx->L.J),
+            (double *)(ctx->ws + ctx->L.ext), (int *)(ctx->ws + ctx->L.err), ctx->nctas, dout);
+    else
+        lbm::diag_kernel<float><<<1, 256, 0, ctx->stream>>>(
+            (double *)(ctx->ws + ctx->L.mass), (double *)(ctx->ws + ctx->L.J),
+            (float *)(ctx->ws + ctx->L.ext), (int *)(ctx->ws + ctx->L.err), ctx->nctas, dout);
+    CK(cudaGetLastError(), "diag launch");
+    double h[8];
+    CK(cudaMemcpyAsync(h, dout, 7 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "diag copy");
+    CK(cudaStreamSynchronize(ctx->stream), "diag sync");
+    std::memset(out, 0, sizeof *out);
+    out->step = ctx->step;
+    out->mass = ctx->step > 0 ? h[0] : 0.0;
+    out->wall_shear_sum = h[1];
+    const bool any = ctx->step > 0 && ctx->grid.walls;
+    out->tau_wall_min = any ? h[2] : 0.0;
+    out->tau_wall_max = any ? h[3] : 0.0;
+    out->p_wall_min = any ? h[4] : 0.0;
+    out->p_wall_max = any ? h[5] : 0.0;
+    out->nan_detected = h[6] != 0.0;
+    out->T = ctx->T; out->Tc = ctx->Tc;
+    out->rho_g = ctx->rho_g; out->rho_l = ctx->rho_l; out->p_sat = ctx->p_sat;
+    out->rho_in = ctx->rho_in; out->rho_out = ctx->rho_out;
+    return LBM_OK;
+}
+
+lbm_status lbm_populations(lbm_ctx *ctx, void *dst)
+{
+    if (!ctx || !dst) return LBM_ERR_ARG;
+    const size_t bytes = (size_t)9 * ctx->grid.nx * ctx->grid.ny * (ctx->grid.precision == 64 ? 8 : 4);
+    CK(cudaMemcpyAsync(dst, ctx->ws + (ctx->cur ? ctx->L.f1 : ctx->L.f0), bytes, cudaMemcpyDefault,
+                       ctx->stream), "populations copy");
+    CK(cudaStreamSynchronize(ctx->stream), "populations sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_load_populations(lbm_ctx *ctx, const void *src)
+{
+    if (!ctx || !src) return LBM_ERR_ARG;
+    const size_t bytes = (size_t)9 * ctx->grid.nx * ctx->grid.ny * (ctx->grid.precision == 64 ? 8 : 4);
+    // both arrays, so never-written slots (solid rows, unreached boundary
+    // slots) agree with the loaded state
+    CK(cudaMemcpyAsync(ctx->ws + ctx->L.f0, src, bytes, cudaMemcpyDefault, ctx->stream), "load copy");
+    CK(cudaMemcpyAsync(ctx->ws + ctx->L.f1, src, bytes, cudaMemcpyDefault, ctx->stream), "load copy");
+    CK(cudaStreamSynchronize(ctx->stream), "load sync");
+    return LBM_OK;
+}
+
+size_t lbm_checkpoint_bytes(const lbm_ctx *ctx)
+{
+    if (!ctx) return 0;
+    const size_t sz = ctx->grid.precision == 64 ? 8 : 4;
+    return sizeof(CkptHeader) + 2 * ctx->L.pops + (size_t)lbm::MAX_CTAS * (16 + 4 * sz) + sizeof(int);
+}
+
+lbm_status lbm_checkpoint(lbm_ctx *ctx, void *host_buf, size_t bytes)
+{
+    if (!ctx || !host_buf || bytes < lbm_checkpoint_bytes(ctx)) return LBM_ERR_ARG;
+    const size_t sz = ctx->grid.precision == 64 ? 8 : 4;
+    CkptHeader h{CKPT_MAGIC, ctx->grid.nx, ctx->grid.ny, ctx->grid.walls, ctx->grid.bc_x,
+                 ctx->grid.precision, ctx->nctas, ctx->step, ctx->cur, 0};
+    unsigned char *p = (unsigned char *)host_buf;
+    std::memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    // both population arrays: slots no population reaches keep older values
+    CK(cudaMemcpyAsync(p, ctx->ws + ctx->L.f0, 2 * ctx->L.pops, cudaMemcpyDeviceToHost, ctx->stream), "ckpt");
+    p += 2 * ctx->L.pops;
+    CK(cudaMemcpyAsync(p, ctx->ws + ctx->L.mass, lbm::MAX_CTAS * 8, cudaMemcpyDeviceToHost, ctx->stream), "ckpt");
+    p += lbm::MAX_CTAS * 8;
+    CK(cudaMemcpyAsync(p, ctx->ws + ctx->L.J, lbm::MAX_CTAS * 8, cudaMemcpyDeviceToHost, ctx->stream), "ckpt");
+    p += lbm::MAX_CTAS * 8;
+    CK(cudaMemcpyAsync(p, ctx->ws + ctx->L.ext, lbm::MAX_CTAS * 4 * sz, cudaMemcpyDeviceToHost, ctx->stream), "ckpt");
+    p += lbm::MAX_CTAS * 4 * sz;
+    CK(cudaMemcpyAsync(p, ctx->ws + ctx->L.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "ckpt");
+    CK(cudaStreamSynchronize(ctx->stream), "ckpt sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_restore(lbm_ctx *ctx, const void *host_buf, size_t bytes)
+{
+    if (!ctx || !host_buf || bytes < lbm_checkpoint_bytes(ctx)) return LBM_ERR_ARG;
+    CkptHeader h;
+    std::memcpy(&h, host_buf, sizeof h);
+    if (h.magic != CKPT_MAGIC || h.nx != ctx->grid.nx || h.ny != ctx->grid.ny || h.walls != ctx->grid.walls ||
+        h.bc_x != ctx->grid.bc_x || h.precision != ctx->grid.precision)
+        return LBM_ERR_STATE;
+    const size_t sz = ctx->grid.precision == 64 ? 8 : 4;
+    const unsigned char *p = (const unsigned char *)host_buf + sizeof h;
+    CK(cudaMemcpyAsync(ctx->ws + ctx->L.f0, p, 2 * ctx->L.pops, cudaMemcpyHostToDevice, ctx->stream), "restore");
+    p += 2 * ctx->L.pops;
+    CK(cudaMemcpyAsync(ctx->ws + ctx->L.mass, p, lbm::MAX_CTAS * 8, cudaMemcpyHostToDevice, ctx->stream), "restore");
+    p += lbm::MAX_CTAS * 8;
+    CK(cudaMemcpyAsync(ctx->ws + ctx->L.J, p, lbm::MAX_CTAS * 8, cudaMemcpyHostToDevice, ctx->stream), "restore");
+    p += lbm::MAX_CTAS * 8;
+    CK(cudaMemcpyAsync(ctx->ws + ctx->L.ext, p, lbm::MAX_CTAS * 4 * sz, cudaMemcpyHostToDevice, ctx->stream), "restore");
+    p += lbm::MAX_CTAS * 4 * sz;
+    CK(cudaMemcpyAsync(ctx->ws + ctx->L.err, p, sizeof(int), cudaMemcpyHostToDevice, ctx->stream), "restore");
+    CK(cudaStreamSynchronize(ctx->stream), "restore sync");
+    ctx->step = h.step;
+    ctx->cur = h.cur;
+    ctx->err_pending = false;
+    // Per-CTA accumulators only line up with the same launch geometry; with
+    // another CTA count they stay valid as totals but the summation order changes.
+    ctx->nctas = std::max(ctx->nctas, 1);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    switch (opt) {
+    case LBM_OPT_CTAS_PER_SM:
+        if (value < 0 || value > 32) return LBM_ERR_ARG;
+        ctx->ctas_per_sm_opt = (int)value;
+        break;
+    case LBM_OPT_REVERSE:
+        ctx->reverse = value != 0;
+        return LBM_OK;
+    case LBM_OPT_STRIP:
+        if (value < 2 || value > BLOCK) return LBM_ERR_ARG;
+        ctx->W = (int)value;
+        break;
+    default:
+        return LBM_ERR_ARG;
+    }
+    // Re-plan; per-CTA accumulators are folded into the new partition only
+    // through their totals, so reset them to keep the reduction exact.
+    int old = ctx->nctas;
+    lbm_status s = plan_launch(ctx);
+    if (s == LBM_OK && old != ctx->nctas) {
+        if (ctx->grid.precision == 64) reset_acc<double>(ctx); else reset_acc<float>(ctx);
+    }
+    return s;
+}
+
+lbm_status lbm_launch_info(const lbm_ctx *ctx, int64_t *ctas, int64_t *threads, int64_t *units)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (ctas) *ctas = ctx->nctas;
+    if (threads) *threads = BLOCK;
+    if (units) *units = ctx->units;
+    return LBM_OK;
+}
+
+void lbm_free(lbm_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream || ctx->ws) cudaStreamSynchronize(ctx->stream);
+    if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
+    if (ctx->fscratch) cudaFree(ctx->fscratch);
+    if (ctx->h_err) cudaFreeHost(ctx->h_err);
+    if (ctx->err_ev) cudaEventDestroy(ctx->err_ev);
+    delete ctx;
+}
+
+} // extern "C"

@@ -1,0 +1,208 @@
+// Host-side FP64 helpers of the solver: Carnahan-Starling thermodynamics
+// (critical point, Maxwell coexistence, gas-branch density for a given
+// pressure) and the initial density profiles of the airway channel and the
+// static droplet. No GPU is needed for anything in this file.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// Carnahan-Starling pressure p0(rho) = rho R T Z(eta) - a rho^2, eta = b rho/4.
+double cs_pressure(const Thermo &t, double rho)
+{
+    double eta = 0.25 * t.b * rho, om = 1.0 - eta;
+    return rho * t.R * t.T * (1.0 + eta * (1.0 + eta * (1.0 - eta))) / (om * om * om) - t.a * rho * rho;
+}
+
+// (eta Z)' and (eta Z)'' with respect to eta.
+static double g1(double e)
+{
+    double om = 1.0 - e;
+    return (1.0 + e * (4.0 + e * (4.0 + e * (-4.0 + e)))) / (om * om * om * om);
+}
+static double g2(double e)
+{
+    double om = 1.0 - e, om2 = om * om;
+    return (8.0 + e * (20.0 - 4.0 * e)) / (om2 * om2 * om);
+}
+static double g3(double e)
+{
+    double om = 1.0 - e, om3 = om * om * om;
+    return (60.0 + e * (72.0 - 12.0 * e)) / (om3 * om3);
+}
+
+double cs_dpressure(const Thermo &t, double rho)
+{
+    return t.R * t.T * g1(0.25 * t.b * rho) - 2.0 * t.a * rho;
+}
+
+// Chemical potential mu = psi'(rho) (free energy density psi with p0 = rho psi' - psi).
+static double cs_mu(const Thermo &t, double rho)
+{
+    double eta = 0.25 * t.b * rho, om = 1.0 - eta;
+    return t.R * t.T * (std::log(rho) + eta * (8.0 + eta * (-9.0 + 3.0 * eta)) / (om * om * om))
+           - 2.0 * t.a * rho;
+}
+
+// Critical packing fraction: h(eta) = g1 - eta g2 = 0, with h' = -eta g3 (since g1' = g2).
+static double critical_eta()
+{
+    double e = 0.13;
+    for (int it = 0; it < 60; ++it) {
+        double h = g1(e) - e * g2(e);
+        double d = -e * g3(e);
+        double step = h / d;
+        e -= step;
+        if (std::fabs(step) < 1e-17) break;
+    }
+    return e;
+}
+
+void cs_critical(double a, double b, double R, double *Tc, double *rhoc)
+{
+    double e = critical_eta();
+    *rhoc = 4.0 * e / b;
+    *Tc = 8.0 * a / (b * R * g2(e));
+}
+
+// Safeguarded Newton for p0(rho) = p on a bracket [lo, hi] where p0 increases.
+static double solve_branch(const Thermo &t, double p, double lo, double hi)
+{
+    double r = 0.5 * (lo + hi);
+    for (int it = 0; it < 200; ++it) {
+        double f = cs_pressure(t, r) - p;
+        if (f > 0.0) hi = r; else lo = r;
+        double d = cs_dpressure(t, r);
+        double rn = (d > 0.0) ? r - f / d : 0.5 * (lo + hi);
+        if (!(rn > lo && rn < hi)) rn = 0.5 * (lo + hi);
+        if (std::fabs(rn - r) <= 1e-16 * r) { r = rn; break; }
+        r = rn;
+    }
+    return r;
+}
+
+// Root of dp0/drho between lo and hi (sign change), by bisection on the sign.
+static double spinodal(const Thermo &t, double lo, double hi)
+{
+    bool slo = cs_dpressure(t, lo) > 0.0;
+    for (int it = 0; it < 200; ++it) {
+        double m = 0.5 * (lo + hi);
+        if ((cs_dpressure(t, m) > 0.0) == slo) lo = m; else hi = m;
+    }
+    return 0.5 * (lo + hi);
+}
+
+int maxwell(const Thermo &t, double *rho_g, double *rho_l, double *p_sat)
+{
+    double Tc, rhoc;
+    cs_critical(t.a, t.b, t.R, &Tc, &rhoc);
+    if (!(t.T < Tc)) return 1;
+    double rmax = 4.0 / t.b * (1.0 - 1e-12);
+    double s1 = spinodal(t, 1e-12, rhoc), s2 = spinodal(t, rhoc, rmax);
+    double plo = std::fmax(cs_pressure(t, s2), 0.0), phi = cs_pressure(t, s1);
+    // Newton in pressure on dmu(p) = mu(rho_g(p)) - mu(rho_l(p)); by Gibbs-Duhem
+    // d dmu / dp = 1/rho_g - 1/rho_l. Bracket kept to stay on both branches.
+    double lo = plo, hi = phi, p = 0.5 * (plo + phi), rg = 0, rl = 0;
+    for (int it = 0; it < 200; ++it) {
+        rg = solve_branch(t, p, 1e-300, s1);
+        rl = solve_branch(t, p, s2, rmax);
+        double dmu = cs_mu(t, rg) - cs_mu(t, rl);
+        if (dmu > 0.0) hi = p; else lo = p;
+        double pn = p - dmu / (1.0 / rg - 1.0 / rl);
+        if (!(pn > lo && pn < hi)) pn = 0.5 * (lo + hi);
+        if (std::fabs(pn - p) <= 1e-17 * p) { p = pn; break; }
+        p = pn;
+    }
+    *p_sat = p;
+    *rho_g = solve_branch(t, p, 1e-300, s1);
+    *rho_l = solve_branch(t, p, s2, rmax);
+    return 0;
+}
+
+int gas_density(const Thermo &t, double p, double *rho)
+{
+    double Tc, rhoc;
+    cs_critical(t.a, t.b, t.R, &Tc, &rhoc);
+    double hi = (t.T < Tc) ? spinodal(t, 1e-12, rhoc) : 4.0 / t.b * (1.0 - 1e-12);
+    if (!(p > 0.0) || !(p < cs_pressure(t, hi))) return 1;
+    *rho = solve_branch(t, p, 1e-300, hi);
+    return 0;
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014) as a counter-based hash.
+static inline uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+double node_noise(uint64_t seed, uint64_t node, double amp)
+{
+    double u = (double)(splitmix64(seed ^ node) >> 11) * (1.0 / 9007199254740992.0);
+    return amp * (2.0 * u - 1.0);
+}
+
+} // namespace lbm
+
+extern "C" {
+
+lbm_status lbm_coexistence(const lbm_eos *eos, double *Tc, double *rho_g, double *rho_l,
+                           double *p_sat)
+{
+    if (!eos || !(eos->a > 0) || !(eos->b > 0) || !(eos->R > 0) || !(eos->T_over_Tc > 0))
+        return LBM_ERR_ARG;
+    double tc, rc;
+    lbm::cs_critical(eos->a, eos->b, eos->R, &tc, &rc);
+    lbm::Thermo t{eos->a, eos->b, eos->R, eos->T_over_Tc * tc};
+    double g, l, p;
+    if (lbm::maxwell(t, &g, &l, &p)) return LBM_ERR_PARAM;
+    if (Tc) *Tc = tc;
+    if (rho_g) *rho_g = g;
+    if (rho_l) *rho_l = l;
+    if (p_sat) *p_sat = p;
+    return LBM_OK;
+}
+
+lbm_status lbm_airway_rho0(int32_t nx, int32_t ny, double film, double plug_x, double plug_len,
+                           double rho_l, double rho_g, double width, double noise_amp,
+                           uint64_t seed, double *out)
+{
+    if (nx <= 0 || ny <= 0 || !out || !(width > 0)) return LBM_ERR_ARG;
+    for (int32_t y = 0; y < ny; ++y)
+        for (int32_t x = 0; x < nx; ++x) {
+            double d_wall = std::fmin(y - 0.5, (ny - 1.5) - y);
+            double s_film = 0.5 * (1.0 - std::tanh(2.0 * (d_wall - film) / width));
+            double s_plug = 0.5 * (std::tanh(2.0 * (x - plug_x) / width)
+                                   - std::tanh(2.0 * (x - plug_x - plug_len) / width));
+            double s = std::fmax(s_film, s_plug);
+            uint64_t node = (uint64_t)y * (uint64_t)nx + (uint64_t)x;
+            double v = rho_g + (rho_l - rho_g) * s;
+            if (noise_amp != 0.0) v += lbm::node_noise(seed, node, noise_amp);
+            out[node] = v;
+        }
+    return LBM_OK;
+}
+
+lbm_status lbm_disk_rho0(int32_t nx, int32_t ny, double cx, double cy, double r0, double rho_l,
+                         double rho_g, double width, double noise_amp, uint64_t seed, double *out)
+{
+    if (nx <= 0 || ny <= 0 || !out || !(width > 0)) return LBM_ERR_ARG;
+    for (int32_t y = 0; y < ny; ++y)
+        for (int32_t x = 0; x < nx; ++x) {
+            double r = std::sqrt((x - cx) * (x - cx) + (y - cy) * (y - cy));
+            double s = 0.5 * (1.0 - std::tanh(2.0 * (r - r0) / width));
+            uint64_t node = (uint64_t)y * (uint64_t)nx + (uint64_t)x;
+            double v = rho_g + (rho_l - rho_g) * s;
+            if (noise_amp != 0.0) v += lbm::node_noise(seed, node, noise_amp);
+            out[node] = v;
+        }
+    return LBM_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,106 @@
+"""CPU tests of the C ABI: the library builds, exports every symbol that
+include/lbm.h declares, validates its arguments, and its host helpers agree
+with the oracle / the seeded input generators (no GPU calls)."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def lbm():
+    from paper_2103_08301_gb300 import build
+    build.build()
+    import paper_2103_08301_gb300 as m
+    m.lib()
+    return m
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(lbm):
+    names = _declared_symbols()
+    assert len(names) >= 18
+    lib = lbm.lib()
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding covers the same set
+    assert set(names) == set(lbm._SIGS), set(names) ^ set(lbm._SIGS)
+
+
+def test_status_strings(lbm):
+    for s in range(7):
+        assert lbm.status_string(s)
+    assert lbm.status_string(0) == "ok"
+
+
+def test_workspace_bytes(lbm):
+    g = lbm.lbm_grid(256, 64, 1, 1, 32)
+    b32 = lbm.lbm_workspace_bytes(g)
+    assert b32 >= 2 * 9 * 256 * 64 * 4
+    g64 = lbm.lbm_grid(256, 64, 1, 1, 64)
+    assert lbm.lbm_workspace_bytes(g64) >= 2 * 9 * 256 * 64 * 8
+    for bad in [lbm.lbm_grid(0, 64, 0, 0, 32), lbm.lbm_grid(64, 3, 1, 0, 32),
+                lbm.lbm_grid(3, 64, 0, 1, 32), lbm.lbm_grid(64, 64, 0, 0, 16),
+                lbm.lbm_grid(64, 64, 2, 0, 32), lbm.lbm_grid(1 << 16, 1 << 15, 0, 0, 32)]:
+        assert lbm.lbm_workspace_bytes(bad) == 0
+
+
+def test_init_rejects_bad_arguments_before_touching_the_gpu(lbm):
+    g = lbm.lbm_grid(16, 16, 0, 0, 32)
+    e = lbm.lbm_eos(1.0, 4.0, 1.0, 0.8, 1.0, 0.5)
+    rho0 = np.full((16, 16), 0.1)
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_init(g, e, 0.5, 0.0, None, rho0)  # tau must exceed 1/2
+    assert ei.value.status == lbm.LBM_ERR_PARAM
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_init(lbm.lbm_grid(0, 16, 0, 0, 32), e, 1.0, 0.0, None, rho0)
+    assert ei.value.status == lbm.LBM_ERR_ARG
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_init(g, lbm.lbm_eos(1.0, 4.0, 1.0, 0.8, 0.0, 0.5), 1.0, 0.0, None, rho0)
+    assert ei.value.status == lbm.LBM_ERR_PARAM
+    assert lbm.lib().lbm_step(None, 1) == lbm.LBM_ERR_ARG
+    lbm.lib().lbm_free(None)  # NULL-safe
+
+
+@pytest.mark.parametrize("t", [0.72, 0.8, 0.85, 0.95])
+def test_coexistence_helper_matches_oracle(lbm, orc, t):
+    Tc, g, l, p = lbm.lbm_coexistence(lbm.lbm_eos(1.0, 4.0, 1.0, t, 1.0, 0.5))
+    Tc2, _ = orc.cs_critical()
+    g2, l2, p2 = orc.maxwell(1.0, 4.0, 1.0, t * Tc2)
+    assert abs(Tc / Tc2 - 1) < 1e-14
+    assert abs(g / g2 - 1) < 1e-11 and abs(l / l2 - 1) < 1e-12 and abs(p / p2 - 1) < 1e-11
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_coexistence(lbm.lbm_eos(1.0, 4.0, 1.0, 1.05, 1.0, 0.5))
+
+
+def test_initial_profiles_match_seeded_generators(lbm):
+    a = lbm.lbm_airway_rho0(300, 70, 8, 60, 40, 0.28, 0.03, 4.0, 1e-3, 7)
+    b = synth.airway_rho0(300, 70, 8, 60, 40, 0.28, 0.03, width=4.0, noise=1e-3, seed=7)
+    assert np.abs(a - b).max() < 1e-15
+    c = lbm.lbm_disk_rho0(128, 96, 64.0, 48.0, 30.0, 0.3, 0.02, 4.0, 1e-3, 1)
+    d = synth.disk_rho0(128, 96, 30.0, 0.3, 0.02, width=4.0, noise=1e-3, seed=1)
+    assert np.abs(c - d).max() < 1e-15
+    # the noise bits themselves are identical (same published generator)
+    n1 = lbm.lbm_disk_rho0(64, 8, 0.0, 0.0, -10.0, 0.0, 0.0, 4.0, 1.0, 3)
+    n2 = synth.node_noise(64, 8, 1.0, 3)
+    assert np.array_equal(n1, n2)
+
+
+def test_splitmix64_known_values():
+    # Reference outputs of SplitMix64 seeded with 0 (successive states
+    # k * 0x9E3779B97F4A7C15), published with the generator.
+    gamma = 0x9E3779B97F4A7C15
+    states = np.array([(k * gamma) % (1 << 64) for k in range(3)], dtype=np.uint64)
+    out = [int(v) for v in synth.splitmix64(states)]
+    assert out == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]

@@ -1,0 +1,244 @@
+"""GPU parity of the fused CUDA step (through the C ABI) against the FP64 oracle.
+
+Tolerances: FP64 build <= 1e-11 and FP32 build <= 1e-4 relative L-infinity on
+rho after 1000 steps. The per-step rounding of the FP32 path (one FP32
+rounding of each population and of the force sum) is ~1e-7 relative; the
+1e-4 bound leaves room for its growth over 1000 steps. FP64 differences come
+only from reassociation / FMA contraction (~1e-16 per operation).
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_08301_gb300 import build
+    build.build()
+    import paper_2103_08301_gb300 as m
+    return m
+
+
+def _pair(orc, lbm, nx, ny, rho0, precision, **kw):
+    s = orc.Setup(nx=nx, ny=ny, **kw)
+    lat_kw = dict(kw)
+    lat = lbm.Lattice(nx, ny, rho0, precision=precision, **lat_kw)
+    return s, lat
+
+
+def _airway(orc, nx, ny, film, plug_x, plug_len, T=0.85, dp=1e-3, noise=0.0):
+    s = orc.Setup(nx=nx, ny=ny, walls=True, bc_x=True, T_over_Tc=T, kappa=0.5, dp=dp)
+    g, l, _ = s.coexistence()
+    return synth.airway_rho0(nx, ny, film, plug_x, plug_len, l, g, noise=noise)
+
+
+CASES = {
+    # config 1 geometry: 128^2 periodic droplet with seeded noise, T = 0.8 Tc
+    "droplet128": dict(nx=128, ny=128, kw=dict(T_over_Tc=0.8, kappa=0.5)),
+    # airway channel: walls, pressure columns, film and plug (config 5 sizes)
+    "airway512x128": dict(nx=512, ny=128, kw=dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=1e-3)),
+    # ragged: width not a multiple of the strip, odd height, periodic
+    "ragged200x37": dict(nx=200, ny=37, kw=dict(T_over_Tc=0.8, kappa=0.5)),
+    # nx % 128 == 1 with pressure columns (strip re-partition), walls
+    "ragged129x20": dict(nx=129, ny=20, kw=dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=2e-4)),
+    # walls, periodic x, wetting offset
+    "wet96x40": dict(nx=96, ny=40, kw=dict(walls=True, T_over_Tc=0.8, kappa=0.5, wet=0.01)),
+}
+
+
+def _rho0(orc, name, c):
+    nx, ny, kw = c["nx"], c["ny"], c["kw"]
+    s = orc.Setup(nx=nx, ny=ny, **kw)
+    g, l, _ = s.coexistence()
+    if name == "droplet128":
+        return synth.disk_rho0(nx, ny, 30, l, g, noise=1e-3, seed=1)
+    if name.startswith("airway"):
+        return synth.airway_rho0(nx, ny, 6, 128, 48, l, g)
+    if name == "ragged200x37":
+        return synth.disk_rho0(nx, ny, 12, l, g, noise=1e-3, seed=5, centre=(150.3, 20.7))
+    if name == "ragged129x20":
+        return synth.airway_rho0(nx, ny, 3, 40, 20, l, g)
+    if name == "wet96x40":
+        return synth.disk_rho0(nx, ny, 14, l, g, centre=(48.0, 0.5))
+    raise KeyError(name)
+
+
+def _lat_kw(kw):
+    out = dict(kw)
+    if "wet" in out:
+        out["wetting"] = out.pop("wet")
+    return out
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("precision,tol", [(64, 1e-11), (32, 1e-4)])
+def test_rho_parity_after_1000_steps(orc, lbm, name, precision, tol):
+    c = CASES[name]
+    nx, ny, kw = c["nx"], c["ny"], c["kw"]
+    rho0 = _rho0(orc, name, c)
+    s = orc.Setup(nx=nx, ny=ny, **kw)
+    f_ref, d_ref = orc.run(s, orc.init(s, rho0), 1000)
+    ref = orc.fields(s, f_ref)
+    with lbm.Lattice(nx, ny, rho0, precision=precision, **_lat_kw(kw)) as lat:
+        lat.step(1000)
+        got = lat.fields()
+        d = lat.diag()
+    err = np.abs(got["rho"] - ref["rho"]).max() / np.abs(ref["rho"]).max()
+    assert err <= tol, f"{name} fp{precision}: rel Linf(rho) {err:.3e}"
+    vscale = max(np.abs(ref["vx"]).max(), np.abs(ref["vy"]).max(), 1e-12)
+    verr = max(np.abs(got["vx"] - ref["vx"]).max(), np.abs(got["vy"] - ref["vy"]).max()) / vscale
+    assert verr <= (1e-9 if precision == 64 else 3e-2), f"velocity {verr:.3e}"
+    # diagnostics of the 1000 states read
+    assert abs(d["mass"] / d_ref["mass"] - 1) <= (1e-12 if precision == 64 else 1e-5)
+    if s.walls:
+        J = d_ref["J"]
+        assert abs(d["wall_shear_sum"] - J) <= (1e-9 if precision == 64 else 1e-2) * max(abs(J), 1e-8)
+        for k_gpu, k_ref in [("p_wall_min", "pw_min"), ("p_wall_max", "pw_max")]:
+            assert abs(d[k_gpu] - d_ref[k_ref]) <= (1e-12 if precision == 64 else 1e-5)
+        for k_gpu, k_ref in [("tau_wall_min", "tw_min"), ("tau_wall_max", "tw_max")]:
+            assert abs(d[k_gpu] - d_ref[k_ref]) <= (1e-12 if precision == 64 else 1e-5)
+        tw_scale = max(np.abs(ref["tau_wall"]).max(), 1e-12)
+        assert np.abs(got["tau_wall"] - ref["tau_wall"]).max() <= (1e-9 if precision == 64 else 3e-2) * tw_scale
+        assert np.abs(got["p_wall"] - ref["p_wall"]).max() <= (1e-13 if precision == 64 else 1e-6)
+
+
+@pytest.mark.parametrize("nx,ny,walls,bc_x", [(4, 4, True, True), (5, 4, True, False), (1, 9, False, False),
+                                              (7, 3, False, False), (33, 6, True, True), (130, 5, True, True)])
+def test_tiny_and_degenerate_grids_fp64(orc, lbm, nx, ny, walls, bc_x):
+    kw = dict(walls=walls, bc_x=bc_x, T_over_Tc=0.85, kappa=0.5, dp=1e-4 if bc_x else 0.0)
+    s = orc.Setup(nx=nx, ny=ny, **kw)
+    g, l, _ = s.coexistence()
+    rng = np.random.default_rng(nx * 100 + ny)
+    rho0 = g + (l - g) * rng.random((ny, nx)) * 0.3
+    f_ref, d_ref = orc.run(s, orc.init(s, rho0), 200)
+    ref = orc.fields(s, f_ref)
+    with lbm.Lattice(nx, ny, rho0, precision=64, **kw) as lat:
+        lat.step(200)
+        got = lat.fields()
+        pops = lat.populations()
+        d = lat.diag()
+    assert np.abs(got["rho"] - ref["rho"]).max() <= 1e-11 * np.abs(ref["rho"]).max()
+    # populations of fluid nodes agree one by one
+    mask = np.ones((ny, nx), bool)
+    if walls:
+        mask[0, :] = mask[-1, :] = False
+    if bc_x:
+        mask[:, 0] = mask[:, -1] = False
+    assert np.abs(pops[:, mask] - f_ref[:, mask]).max() <= 1e-12
+    assert abs(d["mass"] - d_ref["mass"]) <= 1e-12 * d_ref["mass"]
+
+
+def test_single_step_populations_bitwise_structure(orc, lbm):
+    """One FP64 step from a random state: every population slot the step writes
+    matches the oracle, and slots it never writes keep their value."""
+    nx, ny = 150, 24
+    kw = dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=5e-4)
+    s = orc.Setup(nx=nx, ny=ny, **kw)
+    g, l, _ = s.coexistence()
+    rng = np.random.default_rng(11)
+    rho0 = g + (l - g) * rng.random((ny, nx))
+    f0 = orc.init(s, rho0) * (1 + 0.05 * rng.standard_normal((9, ny, nx)))
+    f1, _ = orc.step(s, f0)
+    with lbm.Lattice(nx, ny, rho0, precision=64, **kw) as lat:
+        lat.load_populations(f0)
+        lat.step(1)
+        got = lat.populations()
+    assert np.abs(got - f1).max() <= 1e-14 * np.abs(f1).max()
+
+
+def test_reverse_cta_order_is_bitwise_identical(orc, lbm):
+    rho0 = _airway(orc, 640, 96, 6, 200, 48)
+    out = []
+    for rev in (0, 1):
+        with lbm.Lattice(640, 96, rho0, walls=True, bc_x=True, precision=32, T_over_Tc=0.85,
+                         kappa=0.5, dp=1e-3) as lat:
+            lat.set_option(lbm.LBM_OPT_REVERSE, rev)
+            lat.step(300)
+            out.append((lat.populations(), lat.diag()))
+    assert np.array_equal(out[0][0].view(np.uint32), out[1][0].view(np.uint32))
+    assert out[0][1]["wall_shear_sum"] == out[1][1]["wall_shear_sum"]
+    assert out[0][1]["mass"] == out[1][1]["mass"]
+
+
+def test_checkpoint_restore_continues_bitwise(orc, lbm):
+    rho0 = _airway(orc, 320, 64, 5, 100, 40)
+    kw = dict(walls=True, bc_x=True, precision=32, T_over_Tc=0.85, kappa=0.5, dp=1e-3)
+    with lbm.Lattice(320, 64, rho0, **kw) as a:
+        a.step(150)
+        ck = a.checkpoint()
+        a.step(150)
+        fa, da = a.populations(), a.diag()
+    with lbm.Lattice(320, 64, np.full((64, 320), 0.05), **kw) as b:
+        b.restore(ck)
+        assert b.diag()["step"] == 150
+        b.step(150)
+        fb, db = b.populations(), b.diag()
+    assert np.array_equal(fa.view(np.uint32), fb.view(np.uint32))
+    assert da["wall_shear_sum"] == db["wall_shear_sum"] and da["step"] == db["step"] == 300
+
+
+def test_nan_in_state_is_reported(orc, lbm):
+    """Host-side fault injection: a NaN written into one population value."""
+    nx, ny = 64, 32
+    rho0 = np.full((ny, nx), 0.1)
+    with lbm.Lattice(nx, ny, rho0, precision=32, T_over_Tc=0.8, kappa=0.5) as lat:
+        f = lat.populations()
+        f[3, 10, 20] = np.nan
+        lat.load_populations(f)
+        lat.step(2)
+        assert lat.diag()["nan_detected"]
+        with pytest.raises(lbm.LBMError) as ei:
+            lat.step(1)  # the flag of the completed steps surfaces here
+        assert ei.value.status == lbm.LBM_ERR_NAN
+
+
+def test_caller_workspace_and_stream(orc, lbm):
+    import torch
+    nx, ny = 256, 64
+    rho0 = _airway(orc, nx, ny, 5, 80, 30)
+    g = lbm.lbm_grid(nx, ny, 1, 1, 32)
+    ws = torch.empty(lbm.lbm_workspace_bytes(g), dtype=torch.uint8, device="cuda")
+    st = torch.cuda.Stream()
+    kw = dict(walls=True, bc_x=True, precision=32, T_over_Tc=0.85, kappa=0.5, dp=1e-3)
+    with lbm.Lattice(nx, ny, rho0, workspace=ws, stream=st, **kw) as a:
+        a.step(100)
+        fa = a.populations()
+        rho_dev = torch.zeros((ny, nx), dtype=torch.float32, device="cuda")
+        a.fields_into(rho=rho_dev)
+        rho_host = a.fields()["rho"]
+    with lbm.Lattice(nx, ny, rho0, **kw) as b:
+        b.step(100)
+        fb = b.populations()
+    assert np.array_equal(fa.view(np.uint32), fb.view(np.uint32))
+    assert np.array_equal(rho_dev.cpu().numpy(), rho_host)
+
+
+def test_full_size_one_step_sampled_against_oracle(orc, lbm):
+    """Bench workload (16384 x 2048, FP32, default launch configuration): after
+    20 steps, one more GPU step is compared with one oracle FP64 step taken from
+    the same (FP32-valued) state, on sampled row bands across the whole width
+    (both walls, both pressure columns, the plug)."""
+    nx, ny = 16384, 2048
+    kw = dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=1e-3)
+    s = orc.Setup(nx=nx, ny=ny, **kw)
+    g, l, _ = s.coexistence()
+    rho0 = synth.airway_rho0(nx, ny, 64, 4096, 1024, l, g)
+    with lbm.Lattice(nx, ny, rho0, precision=32, **kw) as lat:
+        lat.step(20)
+        f0 = lat.populations()
+        lat.step(1)
+        f1 = lat.populations()
+        info = lat.launch_info()
+    assert info["ctas"] >= 152
+    f1_ref, _ = orc.step(s, f0.astype(np.float64))
+    bands = [slice(0, 8), slice(60, 70), slice(1020, 1030), slice(ny - 8, ny)]
+    for b in bands:
+        sub = np.abs(f1[:, b, 1:-1].astype(np.float64) - f1_ref[:, b, 1:-1])
+        assert sub.max() <= 2e-6 * np.abs(f1_ref[:, b, 1:-1]).max(), b
+    del f1_ref
