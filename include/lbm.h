@@ -79,9 +79,14 @@ typedef struct {
     double kappa;
 } lbm_eos;
 
-/* Driving. With bc_x = 1 the inlet and outlet columns carry the gas-branch
- * densities whose mesh pressures k^2 p0 are p_ref + dp/2 and p_ref - dp/2
- * (pressure drop dp, Sec. 2.2 / Sec. 3.3). p_ref = NaN selects k^2 p_sat(T).
+/* Driving. With bc_x = 1 the inlet and outlet columns carry the mesh
+ * pressures k^2 p0 = p_ref + dp/2 and p_ref - dp/2 (pressure drop dp,
+ * Sec. 2.2 / Sec. 3.3); p_ref = NaN selects k^2 p_sat(T). A column node's
+ * density is the EOS root at its pressure on the branch of the phase at its
+ * interior neighbour x_f: rho_b = rho_gas + theta (rho_liq - rho_gas),
+ * theta = clamp((rho(x_f) - rho_g) / (rho_l - rho_g), 0, 1) with the Maxwell
+ * densities rho_g, rho_l (theta = 0 above Tc). Its populations are rebuilt
+ * each step by non-equilibrium extrapolation from x_f.
  * (gx, gy) is a uniform body-force density added to F. */
 typedef struct {
     double dp;
@@ -101,8 +106,10 @@ typedef struct {
     double p_wall_min, p_wall_max;     /* extrema of the wall pressure (Eq. 2.4) */
     int32_t nan_detected;  /* nonzero once any step met a bad density */
     int32_t pad_;
-    /* thermodynamic set-up derived by lbm_init (host FP64) */
-    double T, Tc, rho_g, rho_l, p_sat, rho_in, rho_out;
+    /* thermodynamic set-up derived by lbm_init (host FP64); rho_in / rho_out
+       are the gas-branch and rho_in_l / rho_out_l the liquid-branch densities
+       at the inlet / outlet pressures */
+    double T, Tc, rho_g, rho_l, p_sat, rho_in, rho_out, rho_in_l, rho_out_l;
 } lbm_diag_t;
 
 /* Bytes of device memory a context of this grid needs (two population

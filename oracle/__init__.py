@@ -43,8 +43,9 @@ class Params(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("walls", C.c_int32), ("bc_x", C.c_int32),
                 ("a", C.c_double), ("b", C.c_double), ("R", C.c_double), ("T", C.c_double),
                 ("k", C.c_double), ("kappa", C.c_double), ("tau", C.c_double), ("wet", C.c_double),
-                ("rho_in", C.c_double), ("rho_out", C.c_double), ("gx", C.c_double),
-                ("gy", C.c_double)]
+                ("rho_in_g", C.c_double), ("rho_in_l", C.c_double), ("rho_out_g", C.c_double),
+                ("rho_out_l", C.c_double), ("ph_g", C.c_double), ("ph_l", C.c_double),
+                ("gx", C.c_double), ("gy", C.c_double)]
 
 
 class Diag(C.Structure):
@@ -71,6 +72,7 @@ def lib():
         L.orc_cs_critical.argtypes = [_D, _D, _D, _PD, _PD]
         L.orc_maxwell.argtypes = [_D, _D, _D, _D, _PD, _PD, _PD]
         L.orc_gas_root.argtypes = [_D, _D, _D, _D, _D, _PD]
+        L.orc_liquid_root.argtypes = [_D, _D, _D, _D, _D, _PD]
         L.orc_feq.argtypes = [_D, _D, _D, _PD]
         L.orc_feq.restype = None
         L.orc_grad_periodic.argtypes = [C.c_int, C.c_int, _PD, _PD, _PD]
@@ -133,6 +135,13 @@ def gas_root(a, b, R, T, p0_target):
     return r.value
 
 
+def liquid_root(a, b, R, T, p0_target):
+    r = _D()
+    if lib().orc_liquid_root(a, b, R, T, p0_target, C.byref(r)):
+        raise ValueError("pressure outside the liquid branch")
+    return r.value
+
+
 def feq(rho, ux, uy):
     out = np.zeros(Q)
     lib().orc_feq(rho, ux, uy, _ptr(out))
@@ -179,29 +188,41 @@ class Setup:
     gx: float = 0.0
     gy: float = 0.0
     T: float = field(init=False)
-    rho_in: float = field(init=False, default=0.0)
+    rho_in: float = field(init=False, default=0.0)    # gas-branch column densities
     rho_out: float = field(init=False, default=0.0)
+    rho_in_l: float = field(init=False, default=0.0)  # liquid-branch column densities
+    rho_out_l: float = field(init=False, default=0.0)
+    ph_g: float = field(init=False, default=0.0)      # phase-indicator end points
+    ph_l: float = field(init=False, default=0.0)
 
     def __post_init__(self):
         Tc, _ = cs_critical(self.a, self.b, self.R)
         self.T = self.T_over_Tc * Tc
         if self.bc_x:
             k2 = self.k * self.k
+            below = self.T < Tc
             if self.p_ref is None:
                 _, _, psat = maxwell(self.a, self.b, self.R, self.T)
                 pref = k2 * psat
             else:
                 pref = self.p_ref
-            self.rho_in = gas_root(self.a, self.b, self.R, self.T, (pref + 0.5 * self.dp) / k2)
-            self.rho_out = gas_root(self.a, self.b, self.R, self.T, (pref - 0.5 * self.dp) / k2)
+            pin, pout = (pref + 0.5 * self.dp) / k2, (pref - 0.5 * self.dp) / k2
+            self.rho_in = gas_root(self.a, self.b, self.R, self.T, pin)
+            self.rho_out = gas_root(self.a, self.b, self.R, self.T, pout)
+            if below:
+                self.ph_g, self.ph_l, _ = maxwell(self.a, self.b, self.R, self.T)
+                self.rho_in_l = liquid_root(self.a, self.b, self.R, self.T, pin)
+                self.rho_out_l = liquid_root(self.a, self.b, self.R, self.T, pout)
+            else:
+                self.rho_in_l, self.rho_out_l = self.rho_in, self.rho_out
 
     def coexistence(self):
         return maxwell(self.a, self.b, self.R, self.T)
 
     def params(self) -> Params:
         return Params(self.nx, self.ny, int(self.walls), int(self.bc_x), self.a, self.b, self.R,
-                      self.T, self.k, self.kappa, self.tau, self.wet, self.rho_in, self.rho_out,
-                      self.gx, self.gy)
+                      self.T, self.k, self.kappa, self.tau, self.wet, self.rho_in, self.rho_in_l,
+                      self.rho_out, self.rho_out_l, self.ph_g, self.ph_l, self.gx, self.gy)
 
 
 def init(setup: Setup, rho0: np.ndarray) -> np.ndarray:

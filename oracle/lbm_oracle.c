@@ -52,7 +52,13 @@ typedef struct {
     double k, kappa;        /* proportional coefficient (Eq. 2.13) and kappa of Eq. 2.17 */
     double tau;             /* relaxation time */
     double wet;             /* wall ghost-density offset; 0 = neutral wetting */
-    double rho_in, rho_out; /* densities imposed on the inlet / outlet columns */
+    /* Pressure columns. The inlet (outlet) carries the mesh pressure p_in (p_out);
+     * its density is the EOS root at that pressure on the branch of the phase
+     * found at the interior neighbour x_f: rho_b = rho_b_gas + theta (rho_b_liq -
+     * rho_b_gas), theta = clamp((rho_f - ph_g) / (ph_l - ph_g), 0, 1) with
+     * ph_g, ph_l the coexistence densities (theta = 0 when ph_l <= ph_g). */
+    double rho_in_g, rho_in_l, rho_out_g, rho_out_l;
+    double ph_g, ph_l;
     double gx, gy;          /* uniform body-force density added to F */
 } orc_params;
 
@@ -193,6 +199,17 @@ int orc_maxwell(double a, double b, double R, double T, double *rho_g, double *r
     return 0;
 }
 
+/* Density on the liquid branch whose EOS pressure is p0_target (below Tc). */
+int orc_liquid_root(double a, double b, double R, double T, double p0_target, double *rho)
+{
+    double s1, s2;
+    if (spinodals(a, b, R, T, &s1, &s2)) return 1;
+    double rmax = 4.0 / b * (1.0 - 1e-12);
+    if (!(p0_target > orc_cs_p0(a, b, R, T, s2))) return 1;
+    *rho = p0_root(a, b, R, T, p0_target, s2, rmax);
+    return 0;
+}
+
 /* Density on the gas branch whose EOS pressure is p0_target. Below Tc the gas
  * branch ends at the first spinodal; at or above Tc the EOS is monotone. */
 int orc_gas_root(double a, double b, double R, double T, double p0_target, double *rho)
@@ -287,13 +304,28 @@ static int is_pressure_col(const orc_params *p, int x)
     return p->bc_x && (x == 0 || x == p->nx - 1);
 }
 
+/* Density of a pressure column at a row whose interior neighbour has density
+ * rho_f (see orc_params). */
+static double column_density(const orc_params *p, int outlet, double rho_f)
+{
+    double g = outlet ? p->rho_out_g : p->rho_in_g;
+    double l = outlet ? p->rho_out_l : p->rho_in_l;
+    double th = 0.0;
+    if (p->ph_l > p->ph_g) {
+        th = (rho_f - p->ph_g) / (p->ph_l - p->ph_g);
+        if (th < 0.0) th = 0.0;
+        if (th > 1.0) th = 1.0;
+    }
+    return g + th * (l - g);
+}
+
 /* Density seen by a stencil at lattice point (x, y), which may lie up to two
  * nodes outside the fluid:
  *   - periodic axes wrap;
  *   - walls: a solid row at depth d behind the half-way wall plane takes the
  *     density of the fluid row at depth d in front of it (mirror image), plus
  *     the wetting offset 'wet' (0 gives zero normal gradient: neutral wetting);
- *   - pressure columns carry their imposed density, and points beyond them
+ *   - pressure columns carry their boundary density, and points beyond them
  *     take the column's value (clamp). */
 static double rho_ghost(const orc_params *p, const double *rho, int x, int y)
 {
@@ -306,8 +338,8 @@ static double rho_ghost(const orc_params *p, const double *rho, int x, int y)
         y = (int)pmod(y, ny);
     }
     if (p->bc_x) {
-        if (x <= 0) return p->rho_in + add;
-        if (x >= nx - 1) return p->rho_out + add;
+        if (x < 0) x = 0;           /* the column's own density (set from its */
+        if (x > nx - 1) x = nx - 1; /* neighbour's phase) extends beyond it   */
     } else {
         x = (int)pmod(x, nx);
     }
@@ -369,6 +401,15 @@ static void fields_and_force(const orc_params *p, const double *f, orc_work *w)
             w->uy[c] = jy / r;
         }
 
+    /* Pressure columns: boundary density from the neighbour's phase. */
+    if (p->bc_x) {
+        for (int y = 0; y < ny; ++y) {
+            if (is_solid_row(p, y)) continue;
+            w->rho[(long)y * nx] = column_density(p, 0, w->rho[(long)y * nx + 1]);
+            w->rho[(long)y * nx + nx - 1] = column_density(p, 1, w->rho[(long)y * nx + nx - 2]);
+        }
+    }
+
     /* 2.-3. Ghost-extended density and the EOS potential of Eq. 2.17 read as
      *       F = -grad(k^2 p0 - rho/3) + kappa rho grad(lap rho): k^2 p0 is the
      *       mesh-space EOS of Eq. 2.14 and rho/3 = c_s^2 rho the ideal part P0. */
@@ -413,7 +454,6 @@ static void fields_and_force(const orc_params *p, const double *f, orc_work *w)
                 int xb = side ? nx - 1 : 0, xf = side ? nx - 2 : 1;
                 long cb = (long)y * nx + xb, cf = (long)y * nx + xf;
                 double rf = w->rho[cf];
-                w->rho[cb] = side ? p->rho_out : p->rho_in;
                 w->ux[cb] = w->ux[cf] + w->Fx[cf] / (2.0 * rf);
                 w->uy[cb] = w->uy[cf] + w->Fy[cf] / (2.0 * rf);
             }

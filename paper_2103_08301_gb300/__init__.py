@@ -43,7 +43,8 @@ class lbm_diag_t(C.Structure):
                 ("p_wall_min", C.c_double), ("p_wall_max", C.c_double),
                 ("nan_detected", C.c_int32), ("pad_", C.c_int32),
                 ("T", C.c_double), ("Tc", C.c_double), ("rho_g", C.c_double), ("rho_l", C.c_double),
-                ("p_sat", C.c_double), ("rho_in", C.c_double), ("rho_out", C.c_double)]
+                ("p_sat", C.c_double), ("rho_in", C.c_double), ("rho_out", C.c_double),
+                ("rho_in_l", C.c_double), ("rho_out_l", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}

@@ -64,6 +64,7 @@ struct lbm_ctx {
     lbm_drive drive{};
     double tau = 1.0, wet = 0.0;
     double T = 0, Tc = 0, rho_g = 0, rho_l = 0, p_sat = 0, rho_in = 0, rho_out = 0;
+    double rho_in_l = 0, rho_out_l = 0;
     cudaStream_t stream = nullptr;
     unsigned char *ws = nullptr;
     bool own_ws = false;
@@ -128,8 +129,12 @@ lbm::KArgs<real> make_args(const lbm_ctx *ctx)
     A.gx = (real)ctx->drive.gx;
     A.gy = (real)ctx->drive.gy;
     A.wet = (real)ctx->wet;
-    A.rho_in = (real)ctx->rho_in;
-    A.rho_out = (real)ctx->rho_out;
+    A.rho_in_g = (real)ctx->rho_in;
+    A.rho_in_l = (real)ctx->rho_in_l;
+    A.rho_out_g = (real)ctx->rho_out;
+    A.rho_out_l = (real)ctx->rho_out_l;
+    A.ph_g = (real)ctx->rho_g;
+    A.inv_dph = ctx->rho_l > ctx->rho_g ? (real)(1.0 / (ctx->rho_l - ctx->rho_g)) : real(0);
     A.nu = (real)((ctx->tau - 0.5) / 3.0);
     A.mass_part = (double *)(ctx->ws + ctx->L.mass);
     A.J_acc = (double *)(ctx->ws + ctx->L.J);
@@ -313,10 +318,20 @@ lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, double
             if (!coexist) { lbm_free(ctx); return LBM_ERR_PARAM; }
             pref = k2 * ctx->p_sat;
         }
-        if (lbm::gas_density(th, (pref + 0.5 * ctx->drive.dp) / k2, &ctx->rho_in) ||
-            lbm::gas_density(th, (pref - 0.5 * ctx->drive.dp) / k2, &ctx->rho_out)) {
+        const double pin = (pref + 0.5 * ctx->drive.dp) / k2, pout = (pref - 0.5 * ctx->drive.dp) / k2;
+        if (lbm::gas_density(th, pin, &ctx->rho_in) || lbm::gas_density(th, pout, &ctx->rho_out)) {
             lbm_free(ctx);
             return LBM_ERR_PARAM;
+        }
+        if (coexist) {
+            if (lbm::liquid_density(th, pin, &ctx->rho_in_l) || lbm::liquid_density(th, pout, &ctx->rho_out_l)) {
+                lbm_free(ctx);
+                return LBM_ERR_PARAM;
+            }
+        } else {
+            ctx->rho_in_l = ctx->rho_in;
+            ctx->rho_out_l = ctx->rho_out;
+            ctx->rho_g = ctx->rho_l = 0.0;  // single phase: no phase blending
         }
     }
 
@@ -444,6 +459,7 @@ lbm_status lbm_diag(lbm_ctx *ctx, lbm_diag_t *out)
     out->T = ctx->T; out->Tc = ctx->Tc;
     out->rho_g = ctx->rho_g; out->rho_l = ctx->rho_l; out->p_sat = ctx->p_sat;
     out->rho_in = ctx->rho_in; out->rho_out = ctx->rho_out;
+    out->rho_in_l = ctx->rho_in_l; out->rho_out_l = ctx->rho_out_l;
     return LBM_OK;
 }
 

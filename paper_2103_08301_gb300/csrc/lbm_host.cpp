@@ -133,6 +133,18 @@ int gas_density(const Thermo &t, double p, double *rho)
     return 0;
 }
 
+int liquid_density(const Thermo &t, double p, double *rho)
+{
+    double Tc, rhoc;
+    cs_critical(t.a, t.b, t.R, &Tc, &rhoc);
+    if (!(t.T < Tc)) return 1;
+    double rmax = 4.0 / t.b * (1.0 - 1e-12);
+    double s2 = spinodal(t, rhoc, rmax);
+    if (!(p > cs_pressure(t, s2))) return 1;
+    *rho = solve_branch(t, p, s2, rmax);
+    return 0;
+}
+
 // SplitMix64 (Steele, Lea & Flood 2014) as a counter-based hash.
 static inline uint64_t splitmix64(uint64_t x)
 {

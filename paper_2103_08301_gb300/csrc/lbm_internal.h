@@ -17,6 +17,8 @@ void cs_critical(double a, double b, double R, double *Tc, double *rhoc);
 int maxwell(const Thermo &t, double *rho_g, double *rho_l, double *p_sat);
 // Gas-branch density with p0(rho) = p; nonzero if p is outside the branch.
 int gas_density(const Thermo &t, double p, double *rho);
+// Liquid-branch density with p0(rho) = p below Tc; nonzero otherwise.
+int liquid_density(const Thermo &t, double p, double *rho);
 double node_noise(uint64_t seed, uint64_t node, double amp);
 
 } // namespace lbm

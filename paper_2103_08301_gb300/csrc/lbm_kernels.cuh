@@ -44,7 +44,10 @@ struct KArgs {
     long long units;  // nstrips * nyf
     int nctas;        // logical CTAs of the schedule
     int reverse;      // launch the logical CTAs in reverse order
-    real RT, a, b4, k2, kappa, tau, inv_tau, omb, gx, gy, wet, rho_in, rho_out, nu;
+    real RT, a, b4, k2, kappa, tau, inv_tau, omb, gx, gy, wet, nu;
+    // pressure columns: gas / liquid branch densities at the inlet and outlet
+    // pressures, and the phase indicator theta = clamp((rho_f - ph_g) * inv_dph, 0, 1)
+    real rho_in_g, rho_in_l, rho_out_g, rho_out_l, ph_g, inv_dph;
     double *mass_part;  // [nctas] mass of the state read (overwritten each step)
     double *J_acc;      // [nctas] accumulated wall shear
     real *ext;          // [nctas][4] running tw_min, tw_max, pw_min, pw_max
@@ -82,16 +85,35 @@ __device__ __forceinline__ real eos_phi(const KArgs<real> &A, real rho)
     return A.k2 * p0 - rho * real(1.0 / 3.0);
 }
 
-// f_eq_i(rho, u) of Eq. 2.2.
+// f_eq_i(rho, u) of Eq. 2.2. The rest population is taken as rho minus the
+// eight moving ones: the weights 4/9, 1/9, 1/36 all round up in FP32 (their
+// float sum is 1 + 7.5e-9), which would otherwise add that fraction of the
+// mass at every collision.
 template <typename real>
 __device__ __forceinline__ void feq9(real rho, real ux, real uy, real (&fe)[9])
 {
     const real usq = real(1.5) * (ux * ux + uy * uy);
+    real moving = real(0);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
+    for (int i = 1; i < 9; ++i) {
         const real eu = real(ex_(i)) * ux + real(ey_(i)) * uy;
         fe[i] = rho * w_<real>(i) * (real(1) + real(3) * eu + real(4.5) * eu * eu - usq);
+        moving += fe[i];
     }
+    fe[0] = rho - moving;
+}
+
+// Density of a pressure column whose interior neighbour has density rho_f: the
+// EOS root at the column pressure on the branch of the neighbour's phase,
+// blended continuously across an interface (Sec. 2.2 pressure-driven ends).
+template <typename real>
+__device__ __forceinline__ real column_density(const KArgs<real> &A, bool outlet, real rho_f)
+{
+    real th = (rho_f - A.ph_g) * A.inv_dph;
+    th = fmin(fmax(th, real(0)), real(1));
+    const real g = outlet ? A.rho_out_g : A.rho_in_g;
+    const real l = outlet ? A.rho_out_l : A.rho_in_l;
+    return g + th * (l - g);
 }
 
 // Row of the stored lattice that a stencil row yy reads, and whether it is a
@@ -124,8 +146,13 @@ __device__ __forceinline__ long long cut_units(const KArgs<real> &A, int c)
     return u;
 }
 
+// Resident CTAs per SM the register allocation is held to (FP32: 4 x 128
+// threads -> <= 128 registers; FP64 carries twice the state per thread).
+template <typename real>
+struct MinBlocks { static constexpr int value = sizeof(real) == 4 ? 4 : 2; };
+
 template <typename real, bool WALLS, bool PRES, int MODE, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) step_kernel(const KArgs<real> A)
+__global__ void __launch_bounds__(BLOCK, MinBlocks<real>::value) step_kernel(const KArgs<real> A)
 {
     constexpr int SW = BLOCK + 4;
     __shared__ real s_rho[RING][SW];
@@ -161,19 +188,20 @@ __global__ void __launch_bounds__(BLOCK) step_kernel(const KArgs<real> A)
         const bool pin = PRES && active && x == 0;
         const bool pout = PRES && active && x == A.nx - 1;
         const bool pcol = pin || pout;
-        const int xc = pin ? 1 : (pout ? A.nx - 2 : x);  // column whose populations we collide
-        const real rho_b = pin ? A.rho_in : A.rho_out;
+        const int xc = pin ? 1 : (pout ? A.nx - 2 : x);  // column whose populations we load
         const int ccol = xc - x0 + 2;                     // its shared-memory column
 
         // Halo columns: threads 0,1 -> local -2,-1; threads 2,3 -> local xw, xw+1.
-        int hmode = 0, hx = 0, hcol = 0;  // hmode 1: load column hx, 2: rho_in, 3: rho_out
+        // hmode 1: density of column hx; 2 / 3: inlet / outlet column density
+        // derived from column hx = 1 / nx-2 (clamp beyond the pressure columns).
+        int hmode = 0, hx = 0, hcol = 0;
         if (tid < 4) {
             const int hloc = (tid < 2) ? (tid - 2) : (xw + tid - 2);
             hcol = hloc + 2;
             const int gxh = x0 + hloc;
             if (PRES) {
-                if (gxh <= 0) hmode = 2;
-                else if (gxh >= A.nx - 1) hmode = 3;
+                if (gxh <= 0) { hmode = 2; hx = 1; }
+                else if (gxh >= A.nx - 1) { hmode = 3; hx = A.nx - 2; }
                 else { hmode = 1; hx = gxh; }
             } else {
                 hmode = 1;
@@ -195,14 +223,11 @@ __global__ void __launch_bounds__(BLOCK) step_kernel(const KArgs<real> A)
             bool mir;
             const int ysrc = map_row<WALLS>(yy, A.ny, mir);
             if (active) {
-                const bool want = pcol ? (yy >= ya && yy < yb) : true;
-                if (want) {
-                    const real *src = A.fin + (long long)(pcol ? yy : ysrc) * A.nx + xc;
+                const real *src = A.fin + (long long)ysrc * A.nx + xc;
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) dst[i] = __ldg(src + (long long)i * A.plane);
-                }
+                for (int i = 0; i < 9; ++i) dst[i] = __ldg(src + (long long)i * A.plane);
             }
-            if (hmode == 1) {
+            if (hmode) {
                 const real *src = A.fin + (long long)ysrc * A.nx + hx;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) hp[i] = __ldg(src + (long long)i * A.plane);
@@ -224,22 +249,18 @@ __global__ void __launch_bounds__(BLOCK) step_kernel(const KArgs<real> A)
                     // densities of row yy (own column and halo) before reusing hp
                     real rho_own = real(0);
                     if (active) {
-                        if (pcol) rho_own = rho_b + add;
-                        else {
-                            real sum = real(0);
+                        real sum = real(0);
 #pragma unroll
-                            for (int i = 0; i < 9; ++i) sum += p[J][i];
-                            rho_own = sum + add;
-                        }
+                        for (int i = 0; i < 9; ++i) sum += p[J][i];
+                        rho_own = (pcol ? column_density(A, pout, sum) : sum) + add;
                     }
                     real rho_h = real(0);
-                    if (hmode == 1) {
+                    if (hmode) {
                         real sum = real(0);
 #pragma unroll
                         for (int i = 0; i < 9; ++i) sum += hp[i];
-                        rho_h = sum + add;
-                    } else if (hmode == 2) rho_h = A.rho_in + add;
-                    else if (hmode == 3) rho_h = A.rho_out + add;
+                        rho_h = (hmode == 1 ? sum : column_density(A, hmode == 3, sum)) + add;
+                    }
 
                     // prefetch row yy+1 (slot J+1 held row yy-3, already collided)
                     if (yy + 1 < yb + 2) load_row(yy + 1, p[(J + 1) & 3]);
@@ -286,6 +307,7 @@ __global__ void __launch_bounds__(BLOCK) step_kernel(const KArgs<real> A)
                         grad(s_phi, gpx, gpy);
                         grad(s_lap, glx, gly);
                         const real rho = s_rho[q0][c];
+                        const real rho_b = s_rho[q0][tid + 2];  // pressure column's own density
                         const real Fx = -gpx + A.kappa * rho * glx + A.gx;
                         const real Fy = -gpy + A.kappa * rho * gly + A.gy;
                         const real jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
@@ -428,12 +450,12 @@ __global__ void init_kernel(const double *__restrict__ rho0, real *__restrict__ 
 {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
-        const real r = (real)rho0[k];
+        real fe[9];
+        feq9<real>((real)rho0[k], real(0), real(0), fe);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const real v = r * w_<real>(i);
-            fa[i * n + k] = v;
-            fb[i * n + k] = v;
+            fa[i * n + k] = fe[i];
+            fb[i * n + k] = fe[i];
         }
     }
 }

@@ -95,10 +95,14 @@ def test_rho_parity_after_1000_steps(orc, lbm, name, precision, tol):
     verr = max(np.abs(got["vx"] - ref["vx"]).max(), np.abs(got["vy"] - ref["vy"]).max()) / vscale
     assert verr <= (1e-9 if precision == 64 else 3e-2), f"velocity {verr:.3e}"
     # diagnostics of the 1000 states read
+    # FP32: open channels exchange mass through the pressure columns, so the
+    # mass follows the (slightly different) FP32 trajectory
     assert abs(d["mass"] / d_ref["mass"] - 1) <= (1e-12 if precision == 64 else 1e-5)
     if s.walls:
         J = d_ref["J"]
-        assert abs(d["wall_shear_sum"] - J) <= (1e-9 if precision == 64 else 1e-2) * max(abs(J), 1e-8)
+        # scale: the sum of |tau_w| bounds, so a J that cancels to ~0 is not over-weighted
+        Jscale = max(abs(J), 1000 * 2 * nx * max(abs(d_ref["tw_min"]), abs(d_ref["tw_max"])) * 1e-3)
+        assert abs(d["wall_shear_sum"] - J) <= (1e-9 if precision == 64 else 1e-2) * Jscale
         for k_gpu, k_ref in [("p_wall_min", "pw_min"), ("p_wall_max", "pw_max")]:
             assert abs(d[k_gpu] - d_ref[k_ref]) <= (1e-12 if precision == 64 else 1e-5)
         for k_gpu, k_ref in [("tau_wall_min", "tw_min"), ("tau_wall_max", "tw_max")]:
