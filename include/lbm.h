@@ -167,16 +167,28 @@ size_t lbm_checkpoint_bytes(const lbm_ctx *ctx);
 lbm_status lbm_checkpoint(lbm_ctx *ctx, void *host_buf, size_t bytes);
 lbm_status lbm_restore(lbm_ctx *ctx, const void *host_buf, size_t bytes);
 
-/* Launch tuning and test hooks:
+/* Launch tuning and test hooks (set before stepping; changing the CTA count
+ * resets the diagnostic accumulators):
  *   LBM_OPT_CTAS_PER_SM  resident CTAs per SM for the step grid (0 = from
- *                        the occupancy calculator); takes effect at the next step
+ *                        the occupancy calculator)
  *   LBM_OPT_REVERSE      nonzero: launch the step's work units in reverse CTA
  *                        order (results must be bit-identical)
- *   LBM_OPT_STRIP        strip width in nodes (32..128, multiple of 32) */
-typedef enum { LBM_OPT_CTAS_PER_SM = 1, LBM_OPT_REVERSE = 2, LBM_OPT_STRIP = 3 } lbm_option;
+ *   LBM_OPT_STRIP        strip width in nodes (2..128)
+ *   LBM_OPT_STAGED       nonzero (default): stream population rows through
+ *                        shared memory with bulk asynchronous copies when nx
+ *                        and the strip width are multiples of 4; zero: per-
+ *                        thread register prefetch. Both give identical results. */
+typedef enum {
+    LBM_OPT_CTAS_PER_SM = 1,
+    LBM_OPT_REVERSE = 2,
+    LBM_OPT_STRIP = 3,
+    LBM_OPT_STAGED = 4
+} lbm_option;
 lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value);
-/* Launch geometry of the step kernel: CTAs, threads per CTA, work units. */
-lbm_status lbm_launch_info(const lbm_ctx *ctx, int64_t *ctas, int64_t *threads, int64_t *units);
+/* Launch geometry of the step kernel: CTAs, threads per CTA, work units and
+ * whether the staged variant runs. Any output may be NULL. */
+lbm_status lbm_launch_info(const lbm_ctx *ctx, int64_t *ctas, int64_t *threads, int64_t *units,
+                           int64_t *staged);
 
 /* Release everything the library allocated. NULL-safe. */
 void lbm_free(lbm_ctx *ctx);

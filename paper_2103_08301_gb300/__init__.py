@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbm.so")
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_PARAM, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_NAN, LBM_ERR_STATE = range(7)
-LBM_OPT_CTAS_PER_SM, LBM_OPT_REVERSE, LBM_OPT_STRIP = 1, 2, 3
+LBM_OPT_CTAS_PER_SM, LBM_OPT_REVERSE, LBM_OPT_STRIP, LBM_OPT_STAGED = 1, 2, 3, 4
 
 
 class lbm_grid(C.Structure):
@@ -66,7 +66,7 @@ _SIGS = {
     "lbm_checkpoint": (C.c_int, [_P, _P, C.c_size_t]),
     "lbm_restore": (C.c_int, [_P, _P, C.c_size_t]),
     "lbm_set_option": (C.c_int, [_P, C.c_int, C.c_int64]),
-    "lbm_launch_info": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "lbm_launch_info": (C.c_int, [_P] + [C.POINTER(C.c_int64)] * 4),
     "lbm_free": (None, [_P]),
     "lbm_status_string": (C.c_char_p, [C.c_int]),
     "lbm_last_error": (C.c_char_p, [_P]),
@@ -245,9 +245,9 @@ class Lattice:
         _check(lib().lbm_set_option(self.ctx, int(opt), int(value)), self.ctx)
 
     def launch_info(self):
-        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
-        _check(lib().lbm_launch_info(self.ctx, C.byref(a), C.byref(b), C.byref(c)), self.ctx)
-        return {"ctas": a.value, "threads": b.value, "units": c.value}
+        a, b, c, d = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib().lbm_launch_info(self.ctx, C.byref(a), C.byref(b), C.byref(c), C.byref(d)), self.ctx)
+        return {"ctas": a.value, "threads": b.value, "units": c.value, "staged": bool(d.value)}
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -77,6 +77,8 @@ struct lbm_ctx {
     int ctas_per_sm_opt = 0;
     int reverse = 0;
     int sms = 0;
+    bool allow_staged = true;  // LBM_OPT_STAGED
+    bool staged = false;       // bulk-copy staged kernel selected for this grid
     // fields scratch (allocated on first host-pointer lbm_fields)
     unsigned char *fscratch = nullptr;
     // non-blocking NaN check
@@ -143,24 +145,37 @@ lbm::KArgs<real> make_args(const lbm_ctx *ctx)
     return A;
 }
 
-template <typename real, int MODE>
+template <typename real, int MODE, bool STAGED>
 void *kernel_ptr(bool walls, bool pres)
 {
     using namespace lbm;
-    if (walls && pres) return (void *)step_kernel<real, true, true, MODE, BLOCK>;
-    if (walls) return (void *)step_kernel<real, true, false, MODE, BLOCK>;
-    if (pres) return (void *)step_kernel<real, false, true, MODE, BLOCK>;
-    return (void *)step_kernel<real, false, false, MODE, BLOCK>;
+    if (walls && pres) return (void *)step_kernel<real, true, true, MODE, BLOCK, STAGED>;
+    if (walls) return (void *)step_kernel<real, true, false, MODE, BLOCK, STAGED>;
+    if (pres) return (void *)step_kernel<real, false, true, MODE, BLOCK, STAGED>;
+    return (void *)step_kernel<real, false, false, MODE, BLOCK, STAGED>;
+}
+
+template <typename real, int MODE>
+void *kernel_ptr(bool walls, bool pres, bool staged)
+{
+    return staged ? kernel_ptr<real, MODE, true>(walls, pres) : kernel_ptr<real, MODE, false>(walls, pres);
 }
 
 void *step_kernel_ptr(const lbm_ctx *ctx, int mode)
 {
-    const bool w = ctx->grid.walls, p = ctx->grid.bc_x;
+    const bool w = ctx->grid.walls, p = ctx->grid.bc_x, st = ctx->staged;
     if (ctx->grid.precision == 64)
-        return mode == lbm::MODE_STEP ? kernel_ptr<double, lbm::MODE_STEP>(w, p)
-                                      : kernel_ptr<double, lbm::MODE_FIELDS>(w, p);
-    return mode == lbm::MODE_STEP ? kernel_ptr<float, lbm::MODE_STEP>(w, p)
-                                  : kernel_ptr<float, lbm::MODE_FIELDS>(w, p);
+        return mode == lbm::MODE_STEP ? kernel_ptr<double, lbm::MODE_STEP>(w, p, st)
+                                      : kernel_ptr<double, lbm::MODE_FIELDS>(w, p, st);
+    return mode == lbm::MODE_STEP ? kernel_ptr<float, lbm::MODE_STEP>(w, p, st)
+                                  : kernel_ptr<float, lbm::MODE_FIELDS>(w, p, st);
+}
+
+size_t dyn_smem(const lbm_ctx *ctx)
+{
+    if (!ctx->staged) return 0;
+    return ctx->grid.precision == 64 ? lbm::staged_smem_bytes<double, BLOCK>()
+                                     : lbm::staged_smem_bytes<float, BLOCK>();
 }
 
 // Strip partition and the CTA count of the step grid.
@@ -174,16 +189,24 @@ lbm_status plan_launch(lbm_ctx *ctx)
             if (nx % w != 1) { W = w; break; }
     }
     ctx->W = W;
+    // bulk-copy staging needs 16-byte aligned row segments
+    ctx->staged = ctx->allow_staged && (nx % 4 == 0) && (W % 4 == 0);
     ctx->nstrips = (nx + W - 1) / W;
     ctx->yf0 = ctx->grid.walls ? 1 : 0;
     ctx->nyf = ctx->grid.walls ? ctx->grid.ny - 2 : ctx->grid.ny;
     ctx->units = (long long)ctx->nstrips * ctx->nyf;
 
+    const size_t smem = dyn_smem(ctx);
+    for (int mode : {lbm::MODE_STEP, lbm::MODE_FIELDS}) {
+        cudaError_t e = cudaFuncSetAttribute(step_kernel_ptr(ctx, mode),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "smem attribute");
+    }
     int per_sm = ctx->ctas_per_sm_opt;
     if (per_sm <= 0) {
         int occ = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ, step_kernel_ptr(ctx, lbm::MODE_STEP), BLOCK, 0);
+            &occ, step_kernel_ptr(ctx, lbm::MODE_STEP), BLOCK, smem);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy");
         per_sm = std::max(1, occ);
     }
@@ -199,7 +222,7 @@ cudaError_t launch(lbm_ctx *ctx, const lbm::KArgs<real> &A)
 {
     void *fn = step_kernel_ptr(ctx, MODE);
     void *args[] = {(void *)&A};
-    return cudaLaunchKernel(fn, dim3(ctx->nctas), dim3(BLOCK), args, 0, ctx->stream);
+    return cudaLaunchKernel(fn, dim3(ctx->nctas), dim3(BLOCK), args, dyn_smem(ctx), ctx->stream);
 }
 
 template <typename real>
@@ -559,6 +582,9 @@ lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
         if (value < 2 || value > BLOCK) return LBM_ERR_ARG;
         ctx->W = (int)value;
         break;
+    case LBM_OPT_STAGED:
+        ctx->allow_staged = value != 0;
+        break;
     default:
         return LBM_ERR_ARG;
     }
@@ -572,12 +598,14 @@ lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
     return s;
 }
 
-lbm_status lbm_launch_info(const lbm_ctx *ctx, int64_t *ctas, int64_t *threads, int64_t *units)
+lbm_status lbm_launch_info(const lbm_ctx *ctx, int64_t *ctas, int64_t *threads, int64_t *units,
+                           int64_t *staged)
 {
     if (!ctx) return LBM_ERR_ARG;
     if (ctas) *ctas = ctx->nctas;
     if (threads) *threads = BLOCK;
     if (units) *units = ctx->units;
+    if (staged) *staged = ctx->staged ? 1 : 0;
     return LBM_OK;
 }
 

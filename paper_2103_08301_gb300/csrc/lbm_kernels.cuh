@@ -74,33 +74,71 @@ __device__ __forceinline__ constexpr real w_(int i)
     return i == 0 ? real(4.0 / 9.0) : (i <= 4 ? real(1.0 / 9.0) : real(1.0 / 36.0));
 }
 
+// Reciprocal: the FP32 path uses the hardware approximation (a few ulp), the
+// FP64 path the IEEE division.
+__device__ __forceinline__ float rcp_(float v) { return __fdividef(1.0f, v); }
+__device__ __forceinline__ double rcp_(double v) { return 1.0 / v; }
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies global -> shared (cp.async.bulk, completion counted
+// on an mbarrier in bytes), used to stream population rows into a stage ring.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Waits for the phase with the given parity; gives up after a bounded number
+// of polls (each poll itself suspends for a hardware-defined interval) and
+// returns false, so a lost transfer can never hang the GPU.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// Orders this thread's earlier generic-proxy accesses to shared memory before
+// later async-proxy (bulk copy) writes.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // Mesh-space EOS potential phi = k^2 p0(rho) - rho/3 (Eqs. 2.14, 2.17), CS p0.
 template <typename real>
 __device__ __forceinline__ real eos_phi(const KArgs<real> &A, real rho)
 {
-    real eta = A.b4 * rho;
-    real om = real(1) - eta;
-    real num = real(1) + eta * (real(1) + eta * (real(1) - eta));
-    real p0 = rho * A.RT * num / (om * om * om) - A.a * rho * rho;
+    const real eta = A.b4 * rho;
+    const real om = real(1) - eta;
+    const real num = real(1) + eta * (real(1) + eta * (real(1) - eta));
+    const real p0 = rho * A.RT * num * rcp_(om * om * om) - A.a * rho * rho;
     return A.k2 * p0 - rho * real(1.0 / 3.0);
-}
-
-// f_eq_i(rho, u) of Eq. 2.2. The rest population is taken as rho minus the
-// eight moving ones: the weights 4/9, 1/9, 1/36 all round up in FP32 (their
-// float sum is 1 + 7.5e-9), which would otherwise add that fraction of the
-// mass at every collision.
-template <typename real>
-__device__ __forceinline__ void feq9(real rho, real ux, real uy, real (&fe)[9])
-{
-    const real usq = real(1.5) * (ux * ux + uy * uy);
-    real moving = real(0);
-#pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        const real eu = real(ex_(i)) * ux + real(ey_(i)) * uy;
-        fe[i] = rho * w_<real>(i) * (real(1) + real(3) * eu + real(4.5) * eu * eu - usq);
-        moving += fe[i];
-    }
-    fe[0] = rho - moving;
 }
 
 // Density of a pressure column whose interior neighbour has density rho_f: the
@@ -151,10 +189,83 @@ __device__ __forceinline__ long long cut_units(const KArgs<real> &A, int c)
 template <typename real>
 struct MinBlocks { static constexpr int value = sizeof(real) == 4 ? 4 : 2; };
 
-template <typename real, bool WALLS, bool PRES, int MODE, int BLOCK>
+// Stage ring of the staged kernel. At iteration j (after its barrier) the
+// rows j-3 (collision) .. j (newest density row) are in use, rows j+1 ..
+// j+STAGE_AHEAD are in flight, and row j+STAGE_AHEAD+1 is issued into the
+// stage freed by row j-4: STAGE_AHEAD + 5 stages.
+constexpr int STAGE_AHEAD = 1;
+constexpr int NSTAGE = 5 + STAGE_AHEAD;
+
+template <typename real, int BLOCK>
+constexpr size_t staged_smem_bytes()
+{
+    return (size_t)NSTAGE * 9 * BLOCK * sizeof(real) + NSTAGE * sizeof(uint64_t);
+}
+
+// f_eq of Eq. 2.2 built from the (i, opp(i)) pairs, which share their even
+// part c and differ in the sign of their odd part o: f_i = c + o, f_opp = c - o.
+// The rest population is rho minus the eight moving ones (= rho - 2 sum c), so
+// f_eq carries exactly rho up to unbiased rounding.
+template <typename real>
+__device__ __forceinline__ void feq_pairs(real rho, real ux, real uy, real (&fe)[9])
+{
+    const real base = real(1) - real(1.5) * (ux * ux + uy * uy);
+    const real r1 = rho * real(1.0 / 9.0), r2 = rho * real(1.0 / 36.0);
+    const real s = ux + uy, d = uy - ux;  // e.u of directions 5 (1,1) and 6 (-1,1)
+    const real c1 = r1 * (base + real(4.5) * ux * ux), o1 = real(3) * r1 * ux;
+    const real c2 = r1 * (base + real(4.5) * uy * uy), o2 = real(3) * r1 * uy;
+    const real c5 = r2 * (base + real(4.5) * s * s), o5 = real(3) * r2 * s;
+    const real c6 = r2 * (base + real(4.5) * d * d), o6 = real(3) * r2 * d;
+    fe[1] = c1 + o1; fe[3] = c1 - o1;
+    fe[2] = c2 + o2; fe[4] = c2 - o2;
+    fe[5] = c5 + o5; fe[7] = c5 - o5;
+    fe[6] = c6 + o6; fe[8] = c6 - o6;
+    fe[0] = rho - real(2) * ((c1 + c2) + (c5 + c6));
+}
+
+// Unscaled isotropic gradient: 12 * grad psi = (4(E - W) + (NE - NW) + (SE - SW),
+//                                              4(N - S) + (NE - SE) + (NW - SW)).
+template <typename real, int SW>
+__device__ __forceinline__ void grad12(const real (*S)[SW], int qm, int q0, int qp, int c, real &gx,
+                                       real &gy)
+{
+    const real E = S[q0][c + 1], W = S[q0][c - 1], N = S[qp][c], So = S[qm][c];
+    const real NE = S[qp][c + 1], NW = S[qp][c - 1], SE = S[qm][c + 1], SWv = S[qm][c - 1];
+    gx = real(4) * (E - W) + (NE - NW) + (SE - SWv);
+    gy = real(4) * (N - So) + (NE - SE) + (NW - SWv);
+}
+
+// One fused time step (MODE_STEP) or the macroscopic fields (MODE_FIELDS).
+//
+// Per segment (strip of columns x0 .. x0+xw-1, fluid rows ya .. yb-1) the CTA
+// runs iterations yy = ya-2 .. yb+2 with one barrier each:
+//   (1) re-read (L1) the populations of the collision row r = yy-3;
+//   (2) density and phi of stencil row yy from the populations prefetched in
+//       the previous iteration, then prefetch row yy+1;
+//   (3) Laplacian of row yy-2 (its density rows were completed before the
+//       previous barrier);
+//   --- barrier ---
+//   (4) force, collision, boundaries and push-streaming of row r, whose phi
+//       rows r-1..r+1 and Laplacian rows r-1..r+1 are now complete.
+// The ring keeps 8 rows, so the writes of iteration yy+1 never touch the rows
+// iteration yy still reads.
+//
+// STAGED: the strip's populations of each stencil row (9 plane segments of xw
+// values, xw a multiple of 4) are streamed by one producer thread with bulk
+// asynchronous copies into a ring of NSTAGE shared-memory stages, issued
+// STAGE_AHEAD + 1 rows ahead; consumers read densities and collision
+// populations from the stage (needs nx and the strip width to be multiples
+// of 4 for 16-byte aligned copies). Otherwise each thread loads its column
+// with one row of register prefetch and re-reads the collision row from L1.
+template <typename real, bool WALLS, bool PRES, int MODE, int BLOCK, bool STAGED>
 __global__ void __launch_bounds__(BLOCK, MinBlocks<real>::value) step_kernel(const KArgs<real> A)
 {
+    static_assert(BLOCK % 32 == 0 && BLOCK >= 128, "the four halo columns take one warp each");
     constexpr int SW = BLOCK + 4;
+    constexpr int PRODUCER = BLOCK - 1;  // no halo duty
+    extern __shared__ __align__(128) unsigned char dsm[];
+    real *const stages = reinterpret_cast<real *>(dsm);
+    uint64_t *const bars = reinterpret_cast<uint64_t *>(dsm + (size_t)NSTAGE * 9 * BLOCK * sizeof(real));
     __shared__ real s_rho[RING][SW];
     __shared__ real s_phi[RING][SW];
     __shared__ real s_lap[RING][SW];
@@ -162,17 +273,30 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real>::value) step_kernel(con
     __shared__ real s_ext[BLOCK / 32][4];
     __shared__ int s_bad;
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int cta = A.reverse ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
     long long u = cut_units<WALLS>(A, cta);
     const long long u1 = cut_units<WALLS>(A, cta + 1);
 
     const real third = real(1.0 / 3.0), twelfth = real(1.0 / 12.0), sixth = real(1.0 / 6.0);
+    const long long plane = A.plane;
+    const int nx = A.nx, ny = A.ny;
     double mass = 0.0, Jsum = 0.0;
+    real macc = real(0);
+    int mcount = 0;
     real tmin = real(INFINITY), tmax = real(-INFINITY), pmin = real(INFINITY), pmax = real(-INFINITY);
     bool bad = false;
-    // wall-pair carries between rows (bottom: rows 1 -> 2; top: ny-3 -> ny-2)
-    real b_rho1 = 0, b_v1 = 0, t_v2 = 0;
+    real b_rho1 = 0, b_v1 = 0, t_v2 = 0;  // wall-pair carries (rows 1 -> 2, ny-3 -> ny-2)
+    uint32_t kr = 0;                      // stencil rows staged by this CTA so far (uniform)
+    bool lost = false;                    // a bounded wait gave up
+
+    if constexpr (STAGED) {
+        if (tid == 0) {
+            for (int st = 0; st < NSTAGE; ++st) mbar_init(&bars[st], 1);
+            mbar_init_fence();
+        }
+        __syncthreads();
+    }
 
     while (u < u1) {
         const int s = (int)(u / A.nyf);
@@ -182,229 +306,283 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real>::value) step_kernel(con
         u = ue;
 
         const int x0 = s * A.W;
-        const int xw = min(A.W, A.nx - x0);
+        const int xw = min(A.W, nx - x0);
         const bool active = tid < xw;
         const int x = x0 + tid;
         const bool pin = PRES && active && x == 0;
-        const bool pout = PRES && active && x == A.nx - 1;
+        const bool pout = PRES && active && x == nx - 1;
         const bool pcol = pin || pout;
-        const int xc = pin ? 1 : (pout ? A.nx - 2 : x);  // column whose populations we load
-        const int ccol = xc - x0 + 2;                     // its shared-memory column
+        const int xc = pin ? 1 : (pout ? nx - 2 : x);  // column whose populations this thread loads
+        const int ccol = xc - x0 + 2;                  // its shared-memory column
+        // pushes never wrap or leave the lattice in x
+        const bool x_inner = !pcol && (PRES || (x >= 1 && x <= nx - 2));
 
-        // Halo columns: threads 0,1 -> local -2,-1; threads 2,3 -> local xw, xw+1.
+        // Halo columns (lane 0 of warps 0..3): local -2, -1, xw, xw+1.
         // hmode 1: density of column hx; 2 / 3: inlet / outlet column density
         // derived from column hx = 1 / nx-2 (clamp beyond the pressure columns).
         int hmode = 0, hx = 0, hcol = 0;
-        if (tid < 4) {
-            const int hloc = (tid < 2) ? (tid - 2) : (xw + tid - 2);
+        if (lane == 0 && warp < 4) {
+            const int hloc = (warp < 2) ? (warp - 2) : (xw + warp - 2);
             hcol = hloc + 2;
             const int gxh = x0 + hloc;
             if (PRES) {
                 if (gxh <= 0) { hmode = 2; hx = 1; }
-                else if (gxh >= A.nx - 1) { hmode = 3; hx = A.nx - 2; }
+                else if (gxh >= nx - 1) { hmode = 3; hx = nx - 2; }
                 else { hmode = 1; hx = gxh; }
             } else {
                 hmode = 1;
-                hx = ((gxh % A.nx) + A.nx) % A.nx;
+                hx = ((gxh % nx) + nx) % nx;
             }
         }
+        // Laplacian of the two halo columns next to the strip (local -1, xw)
+        const int lhalo = (lane == 1 && warp == 1) ? 1 : ((lane == 1 && warp == 2) ? xw + 2 : -1);
 
-        real p[4][9];
-        real hp[9];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int i = 0; i < 9; ++i) p[j][i] = real(0);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) hp[i] = real(0);
-
-        // Issue the loads of stencil row yy into dst (own column) / hp (halo).
-        auto load_row = [&](int yy, real(&dst)[9]) {
+        const real *__restrict__ col_in = A.fin + xc;
+        const real *__restrict__ hal_in = A.fin + hx;
+        const int scol = xc - x0;            // this thread's column inside a stage
+        const int nrows = yb - ya + 4;       // stencil rows ya-2 .. yb+1
+        real pf[9], hf[9];
+        // halo (and, without staging, own-column) loads of stencil row yy
+        auto prefetch = [&](int yy) {
             bool mir;
-            const int ysrc = map_row<WALLS>(yy, A.ny, mir);
-            if (active) {
-                const real *src = A.fin + (long long)ysrc * A.nx + xc;
+            const long long row = (long long)map_row<WALLS>(yy, ny, mir) * nx;
+            if (!STAGED && active) {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) dst[i] = __ldg(src + (long long)i * A.plane);
+                for (int i = 0; i < 9; ++i) pf[i] = __ldg(col_in + row + i * plane);
             }
             if (hmode) {
-                const real *src = A.fin + (long long)ysrc * A.nx + hx;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) hp[i] = __ldg(src + (long long)i * A.plane);
+                for (int i = 0; i < 9; ++i) hf[i] = __ldg(hal_in + row + i * plane);
             }
         };
-
-        load_row(ya - 2, p[0]);
-
-        for (int y0 = ya - 2; y0 < yb + 2; y0 += 4) {
+        // producer: stream stencil row j of this segment into its stage
+        auto issue = [&](int j) {
+            if (tid == PRODUCER && j < nrows) {
+                bool mir;
+                const long long row = (long long)map_row<WALLS>(ya - 2 + j, ny, mir) * nx;
+                const uint32_t st = (kr + j) % NSTAGE;
+                real *dst = stages + (size_t)st * 9 * BLOCK;
+                const real *src = A.fin + row + x0;
+                const uint32_t bytes = (uint32_t)(xw * sizeof(real));
+                mbar_arrive_expect_tx(&bars[st], 9 * bytes);
 #pragma unroll
-            for (int J = 0; J < 4; ++J) {
-                const int yy = y0 + J;
-                if (yy < yb + 2) {
-                    bool mir;
-                    map_row<WALLS>(yy, A.ny, mir);
-                    const real add = mir ? A.wet : real(0);
-                    const int rs = yy & (RING - 1);
+                for (int i = 0; i < 9; ++i) bulk_copy_g2s(dst + i * BLOCK, src + i * plane, bytes, &bars[st]);
+            }
+        };
+        // stage holding stencil row j of this segment
+        auto stage_of = [&](int j) -> const real * {
+            return stages + (size_t)((kr + j) % NSTAGE) * 9 * BLOCK + scol;
+        };
+#pragma unroll
+        for (int i = 0; i < 9; ++i) { pf[i] = real(0); hf[i] = real(0); }
+        if constexpr (STAGED) {
+            for (int j = 0; j <= STAGE_AHEAD; ++j) issue(j);
+        }
+        prefetch(ya - 2);
 
-                    // densities of row yy (own column and halo) before reusing hp
-                    real rho_own = real(0);
+        for (int yy = ya - 2; yy <= yb + 2; ++yy) {
+            const int r = yy - 3;
+            const int j = yy - (ya - 2);
+            const bool collide = r >= ya && r < yb;  // uniform over the CTA
+
+            // (1) populations of the collision row (read from HBM three iterations ago)
+            real f[9];
+            if (!STAGED && collide && active) {
+                const real *src = col_in + (long long)r * nx;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) f[i] = __ldg(src + i * plane);
+            }
+
+            // (2) density and EOS potential of stencil row yy
+            if (yy <= yb + 1) {
+                bool mir;
+                map_row<WALLS>(yy, ny, mir);
+                const real add = mir ? A.wet : real(0);
+                const int rs = yy & (RING - 1);
+                real rho_own = real(0), rho_h = real(0);
+                if constexpr (STAGED) {
+                    const uint32_t k = kr + j;
+                    if (!mbar_wait_bounded(&bars[k % NSTAGE], (k / NSTAGE) & 1)) lost = true;
                     if (active) {
-                        real sum = real(0);
+                        const real *sp = stage_of(j);
 #pragma unroll
-                        for (int i = 0; i < 9; ++i) sum += p[J][i];
-                        rho_own = (pcol ? column_density(A, pout, sum) : sum) + add;
+                        for (int i = 0; i < 9; ++i) pf[i] = sp[i * BLOCK];
                     }
-                    real rho_h = real(0);
-                    if (hmode) {
-                        real sum = real(0);
+                }
+                if (active) {
+                    real sum = ((pf[0] + pf[1]) + (pf[2] + pf[3])) + ((pf[4] + pf[5]) + (pf[6] + pf[7])) + pf[8];
+                    rho_own = (pcol ? column_density(A, pout, sum) : sum) + add;
+                }
+                if (hmode) {
+                    real sum = ((hf[0] + hf[1]) + (hf[2] + hf[3])) + ((hf[4] + hf[5]) + (hf[6] + hf[7])) + hf[8];
+                    rho_h = (hmode == 1 ? sum : column_density(A, hmode == 3, sum)) + add;
+                }
+                if (yy + 1 <= yb + 1) prefetch(yy + 1);
+                if (active) {
+                    s_rho[rs][tid + 2] = rho_own;
+                    s_phi[rs][tid + 2] = eos_phi(A, rho_own);
+                }
+                if (hmode) {
+                    s_rho[rs][hcol] = rho_h;
+                    s_phi[rs][hcol] = eos_phi(A, rho_h);
+                }
+            }
+
+            // (3) Laplacian of row yy-2 on local columns -1 .. xw
+            if (yy >= ya + 1) {
+                const int lr = (yy - 2) & (RING - 1), lm = (yy - 3) & (RING - 1), lp = (yy - 1) & (RING - 1);
+                auto lap_at = [&](int c) {
+                    const real edges = (s_rho[lr][c - 1] + s_rho[lr][c + 1]) + (s_rho[lm][c] + s_rho[lp][c]);
+                    const real corners = (s_rho[lm][c - 1] + s_rho[lm][c + 1]) + (s_rho[lp][c - 1] + s_rho[lp][c + 1]);
+                    s_lap[lr][c] = (real(4) * edges + corners - real(20) * s_rho[lr][c]) * sixth;
+                };
+                if (active) lap_at(tid + 2);
+                if (lhalo >= 0) lap_at(lhalo);
+            }
+            __syncthreads();
+
+            if constexpr (STAGED) {
+                // the stage of row j-4 was last read by the collision of the
+                // previous iteration, before this barrier: refill it
+                if (tid == PRODUCER) fence_proxy_async_smem();
+                issue(j + STAGE_AHEAD + 1);
+            }
+
+            // (4) collide and stream row r
+            if (collide && active) {
+                if constexpr (STAGED) {
+                    const real *sp = stage_of(j - 3);
 #pragma unroll
-                        for (int i = 0; i < 9; ++i) sum += hp[i];
-                        rho_h = (hmode == 1 ? sum : column_density(A, hmode == 3, sum)) + add;
-                    }
+                    for (int i = 0; i < 9; ++i) f[i] = sp[i * BLOCK];
+                }
+                const int q0 = r & (RING - 1), qm = (r - 1) & (RING - 1), qp = (r + 1) & (RING - 1);
+                const int c = ccol;
+                real gpx, gpy, glx, gly;
+                grad12<real, SW>(s_phi, qm, q0, qp, c, gpx, gpy);
+                grad12<real, SW>(s_lap, qm, q0, qp, c, glx, gly);
+                const real rho = s_rho[q0][c];
+                const real kr = A.kappa * rho;
+                const real Fx = (kr * glx - gpx) * twelfth + A.gx;
+                const real Fy = (kr * gly - gpy) * twelfth + A.gy;
+                const real jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+                const real jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+                const real irho = rcp_(rho);
+                const real ux = jx * irho, uy = jy * irho;
+                const real hFi = real(0.5) * irho;
+                const real vx = ux + hFi * Fx, vy = uy + hFi * Fy;
 
-                    // prefetch row yy+1 (slot J+1 held row yy-3, already collided)
-                    if (yy + 1 < yb + 2) load_row(yy + 1, p[(J + 1) & 3]);
-
-                    if (active) {
-                        s_rho[rs][tid + 2] = rho_own;
-                        s_phi[rs][tid + 2] = eos_phi(A, rho_own);
-                    }
-                    if (hmode) {
-                        s_rho[rs][hcol] = rho_h;
-                        s_phi[rs][hcol] = eos_phi(A, rho_h);
-                    }
-                    __syncthreads();
-
-                    // Laplacian of row yy-1 on local columns -1 .. xw
-                    if (yy >= ya) {
-                        const int lr = (yy - 1) & (RING - 1);
-                        const int lm = (yy - 2) & (RING - 1), lp = yy & (RING - 1);
-                        auto lap_at = [&](int c) {
-                            real edges = s_rho[lr][c - 1] + s_rho[lr][c + 1] + s_rho[lm][c] + s_rho[lp][c];
-                            real corners = s_rho[lm][c - 1] + s_rho[lm][c + 1] + s_rho[lp][c - 1] + s_rho[lp][c + 1];
-                            s_lap[lr][c] = (real(4) * edges + corners - real(20) * s_rho[lr][c]) * sixth;
-                        };
-                        if (active) lap_at(tid + 2);
-                        if (tid == 0) lap_at(1);
-                        if (tid == 1) lap_at(xw + 2);
-                    }
-                    __syncthreads();
-
-                    // collide and stream row r = yy - 2
-                    const int r = yy - 2;
-                    if (r >= ya && active) {
-                        const real(&f)[9] = p[(J + 2) & 3];
-                        const int q0 = r & (RING - 1), qm = (r - 1) & (RING - 1), qp = (r + 1) & (RING - 1);
-                        const int c = ccol;
-                        // isotropic gradients: grad psi = 3 sum_i w_i e_i psi(x + e_i)
-                        auto grad = [&](real (*S)[SW], real &gx_, real &gy_) {
-                            gx_ = (S[q0][c + 1] - S[q0][c - 1]) * third
-                                  + (S[qp][c + 1] - S[qp][c - 1] + S[qm][c + 1] - S[qm][c - 1]) * twelfth;
-                            gy_ = (S[qp][c] - S[qm][c]) * third
-                                  + (S[qp][c + 1] + S[qp][c - 1] - S[qm][c + 1] - S[qm][c - 1]) * twelfth;
-                        };
-                        real gpx, gpy, glx, gly;
-                        grad(s_phi, gpx, gpy);
-                        grad(s_lap, glx, gly);
-                        const real rho = s_rho[q0][c];
-                        const real rho_b = s_rho[q0][tid + 2];  // pressure column's own density
-                        const real Fx = -gpx + A.kappa * rho * glx + A.gx;
-                        const real Fy = -gpy + A.kappa * rho * gly + A.gy;
-                        const real jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
-                        const real jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
-                        const real irho = real(1) / rho;
-                        const real ux = jx * irho, uy = jy * irho;
-                        const real vx = ux + real(0.5) * Fx * irho, vy = uy + real(0.5) * Fy * irho;
-
-                        if (MODE == MODE_STEP) {
-                            real fs[9];
-                            if (!pcol) {
-                                real fe[9];
-                                feq9<real>(rho, ux + A.tau * Fx * irho, uy + A.tau * Fy * irho, fe);
+                if (MODE == MODE_STEP) {
+                    real fs[9];
+                    if (!pcol) {
+                        const real tFi = A.tau * irho;
+                        real fe[9];
+                        feq_pairs<real>(rho, ux + tFi * Fx, uy + tFi * Fy, fe);
 #pragma unroll
-                                for (int i = 0; i < 9; ++i) fs[i] = f[i] + (fe[i] - f[i]) * A.inv_tau;
+                        for (int i = 0; i < 9; ++i) fs[i] = f[i] + (fe[i] - f[i]) * A.inv_tau;
+                    } else {
+                        // non-equilibrium extrapolation from the interior neighbour:
+                        // f_eq(rho_b, v) = (rho_b / rho_f) f_eq(rho_f, v)
+                        const real rho_b = s_rho[q0][tid + 2];
+                        real ff[9];
+                        feq_pairs<real>(rho, vx, vy, ff);
+                        const real sc = rho_b * irho;
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) fs[i] = sc * ff[i] + A.omb * (f[i] - ff[i]);
+                    }
+                    real *o = A.fout + (long long)r * nx + x;
+                    const bool y_inner = WALLS ? (r >= 2 && r <= ny - 3) : (r >= 1 && r <= ny - 2);
+                    if (x_inner && y_inner) {
+                        o[0] = fs[0];
+                        o[plane + 1] = fs[1];
+                        o[2 * plane + nx] = fs[2];
+                        o[3 * plane - 1] = fs[3];
+                        o[4 * plane - nx] = fs[4];
+                        o[5 * plane + nx + 1] = fs[5];
+                        o[6 * plane + nx - 1] = fs[6];
+                        o[7 * plane - nx - 1] = fs[7];
+                        o[8 * plane - nx + 1] = fs[8];
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) {
+                            const int ty = r + ey_(i);
+                            if (WALLS && (ty == 0 || ty == ny - 1)) {
+                                // half-way bounce-back into the opposite slot of this node
+                                o[opp_(i) * plane] = fs[i];
                             } else {
-                                // non-equilibrium extrapolation from the interior neighbour
-                                real fb[9], ff[9];
-                                feq9<real>(rho_b, vx, vy, fb);
-                                feq9<real>(rho, vx, vy, ff);
-#pragma unroll
-                                for (int i = 0; i < 9; ++i) fs[i] = fb[i] + A.omb * (f[i] - ff[i]);
-                            }
-                            // push with half-way bounce-back
-                            real *dst = A.fout;
-#pragma unroll
-                            for (int i = 0; i < 9; ++i) {
-                                const int ty = r + ey_(i);
-                                if (WALLS && (ty == 0 || ty == A.ny - 1)) {
-                                    dst[(long long)opp_(i) * A.plane + (long long)r * A.nx + x] = fs[i];
+                                int tx = x + ex_(i);
+                                if (PRES) {
+                                    if (tx < 0 || tx >= nx) continue;  // leaves through the column
                                 } else {
-                                    int tx = x + ex_(i);
-                                    if (PRES) {
-                                        if (tx < 0 || tx >= A.nx) continue;
-                                    } else {
-                                        tx = tx < 0 ? tx + A.nx : (tx >= A.nx ? tx - A.nx : tx);
-                                    }
-                                    int tyw = ty;
-                                    if (!WALLS) tyw = ty < 0 ? ty + A.ny : (ty >= A.ny ? ty - A.ny : ty);
-                                    dst[(long long)i * A.plane + (long long)tyw * A.nx + tx] = fs[i];
+                                    tx = tx < 0 ? tx + nx : (tx >= nx ? tx - nx : tx);
                                 }
+                                int tyw = ty;
+                                if (!WALLS) tyw = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
+                                A.fout[i * plane + (long long)tyw * nx + tx] = fs[i];
                             }
-                            mass += (double)(pcol ? rho_b : rho);
-                            if (!(rho > real(0)) || !(rho < real(1e30))) bad = true;
-                        } else {
-                            const long long o = (long long)r * A.nx + x;
-                            A.o_rho[o] = pcol ? rho_b : rho;
-                            A.o_vx[o] = vx;
-                            A.o_vy[o] = vy;
                         }
+                    }
+                    const real mrho = pcol ? s_rho[q0][tid + 2] : rho;
+                    if (sizeof(real) == 8) mass += (double)mrho;
+                    else {
+                        macc += mrho;
+                        if (++mcount == 16) { mass += (double)macc; macc = real(0); mcount = 0; }
+                    }
+                    if (!(rho > real(0)) || !(rho < real(1e30))) bad = true;
+                } else {
+                    const long long oi = (long long)r * nx + x;
+                    A.o_rho[oi] = pcol ? s_rho[q0][tid + 2] : rho;
+                    A.o_vx[oi] = vx;
+                    A.o_vy[oi] = vy;
+                }
 
-                        if (WALLS && !pcol) {
-                            // wall shear: quadratic through v = 0 on the half-way plane
-                            // and v at distances 1/2, 3/2 (reading of Fig. 3's tau_w)
-                            auto pwall = [&]() {
-                                real grx, gry;
-                                grad(s_rho, grx, gry);
-                                return s_phi[q0][c] + rho * third - A.kappa * rho * s_lap[q0][c]
-                                       - real(0.5) * A.kappa * (grx * grx + gry * gry);
-                            };
-                            if (r == 1) {
-                                b_rho1 = rho;
-                                b_v1 = vx;
-                                const real pw = pwall();
-                                if (MODE == MODE_STEP) { pmin = fmin(pmin, pw); pmax = fmax(pmax, pw); }
-                                else A.o_pw[x] = pw;
-                            }
-                            if (r == A.ny - 3) t_v2 = vx;
-                            if (r == 2) {
-                                const real tw = b_rho1 * A.nu * (real(9) * b_v1 - vx) * third;
-                                if (MODE == MODE_STEP) { Jsum += (double)tw; tmin = fmin(tmin, tw); tmax = fmax(tmax, tw); }
-                                else A.o_tw[x] = tw;
-                            }
-                            if (r == A.ny - 2) {
-                                const real tw = rho * A.nu * (real(9) * vx - t_v2) * third;
-                                const real pw = pwall();
-                                if (MODE == MODE_STEP) {
-                                    Jsum += (double)tw;
-                                    tmin = fmin(tmin, tw); tmax = fmax(tmax, tw);
-                                    pmin = fmin(pmin, pw); pmax = fmax(pmax, pw);
-                                } else {
-                                    A.o_tw[A.nx + x] = tw;
-                                    A.o_pw[A.nx + x] = pw;
-                                }
-                            }
+                if (WALLS && !pcol && (r <= 2 || r >= ny - 3)) {
+                    // wall shear: quadratic through v = 0 on the half-way plane and
+                    // v at distances 1/2 and 3/2; wall pressure: Eq. 2.4 in mesh units
+                    auto pwall = [&]() {
+                        real grx, gry;
+                        grad12<real, SW>(s_rho, qm, q0, qp, c, grx, gry);
+                        grx *= twelfth;
+                        gry *= twelfth;
+                        return s_phi[q0][c] + rho * third - A.kappa * rho * s_lap[q0][c]
+                               - real(0.5) * A.kappa * (grx * grx + gry * gry);
+                    };
+                    if (r == 1) {
+                        b_rho1 = rho;
+                        b_v1 = vx;
+                        const real pw = pwall();
+                        if (MODE == MODE_STEP) { pmin = fmin(pmin, pw); pmax = fmax(pmax, pw); }
+                        else A.o_pw[x] = pw;
+                    }
+                    if (r == ny - 3) t_v2 = vx;
+                    if (r == 2) {
+                        const real tw = b_rho1 * A.nu * (real(9) * b_v1 - vx) * third;
+                        if (MODE == MODE_STEP) { Jsum += (double)tw; tmin = fmin(tmin, tw); tmax = fmax(tmax, tw); }
+                        else A.o_tw[x] = tw;
+                    }
+                    if (r == ny - 2) {
+                        const real tw = rho * A.nu * (real(9) * vx - t_v2) * third;
+                        const real pw = pwall();
+                        if (MODE == MODE_STEP) {
+                            Jsum += (double)tw;
+                            tmin = fmin(tmin, tw); tmax = fmax(tmax, tw);
+                            pmin = fmin(pmin, pw); pmax = fmax(pmax, pw);
+                        } else {
+                            A.o_tw[nx + x] = tw;
+                            A.o_pw[nx + x] = pw;
                         }
                     }
                 }
             }
         }
-        __syncthreads();  // ring reuse by the next segment
+        __syncthreads();  // ring and stage reuse by the next segment
+        kr += nrows;
     }
 
+    if (STAGED && lost) atomicOr(A.err, 2);
     if (MODE != MODE_STEP) return;
+    mass += (double)macc;
 
     // CTA reduction in a fixed order (deterministic for a fixed schedule)
-    const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         mass += __shfl_xor_sync(0xffffffffu, mass, o);
@@ -451,7 +629,7 @@ __global__ void init_kernel(const double *__restrict__ rho0, real *__restrict__ 
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         real fe[9];
-        feq9<real>((real)rho0[k], real(0), real(0), fe);
+        feq_pairs<real>((real)rho0[k], real(0), real(0), fe);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             fa[i * n + k] = fe[i];

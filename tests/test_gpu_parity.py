@@ -25,13 +25,6 @@ def lbm():
     return m
 
 
-def _pair(orc, lbm, nx, ny, rho0, precision, **kw):
-    s = orc.Setup(nx=nx, ny=ny, **kw)
-    lat_kw = dict(kw)
-    lat = lbm.Lattice(nx, ny, rho0, precision=precision, **lat_kw)
-    return s, lat
-
-
 def _airway(orc, nx, ny, film, plug_x, plug_len, T=0.85, dp=1e-3, noise=0.0):
     s = orc.Setup(nx=nx, ny=ny, walls=True, bc_x=True, T_over_Tc=T, kappa=0.5, dp=dp)
     g, l, _ = s.coexistence()
@@ -109,7 +102,10 @@ def test_rho_parity_after_1000_steps(orc, lbm, name, precision, tol):
             assert abs(d[k_gpu] - d_ref[k_ref]) <= (1e-12 if precision == 64 else 1e-5)
         tw_scale = max(np.abs(ref["tau_wall"]).max(), 1e-12)
         assert np.abs(got["tau_wall"] - ref["tau_wall"]).max() <= (1e-9 if precision == 64 else 3e-2) * tw_scale
-        assert np.abs(got["p_wall"] - ref["p_wall"]).max() <= (1e-13 if precision == 64 else 1e-6)
+        # FP32: the wall pressure inherits the density deviation times the stiff
+        # liquid EOS, so it is bounded relative to its own scale
+        pw_scale = np.abs(ref["p_wall"]).max()
+        assert np.abs(got["p_wall"] - ref["p_wall"]).max() <= (1e-13 if precision == 64 else 1e-3 * pw_scale)
 
 
 @pytest.mark.parametrize("nx,ny,walls,bc_x", [(4, 4, True, True), (5, 4, True, False), (1, 9, False, False),
@@ -168,6 +164,26 @@ def test_reverse_cta_order_is_bitwise_identical(orc, lbm):
     assert np.array_equal(out[0][0].view(np.uint32), out[1][0].view(np.uint32))
     assert out[0][1]["wall_shear_sum"] == out[1][1]["wall_shear_sum"]
     assert out[0][1]["mass"] == out[1][1]["mass"]
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_staged_and_register_paths_agree_bitwise(orc, lbm, precision):
+    """The bulk-copy staged kernel and the register-prefetch kernel do the same
+    arithmetic on the same values."""
+    rho0 = _airway(orc, 512, 96, 6, 200, 48)
+    out = []
+    for staged in (1, 0):
+        with lbm.Lattice(512, 96, rho0, walls=True, bc_x=True, precision=precision, T_over_Tc=0.85,
+                         kappa=0.5, dp=1e-3) as lat:
+            lat.set_option(lbm.LBM_OPT_STAGED, staged)
+            assert lat.launch_info()["staged"] == bool(staged)
+            lat.step(200)
+            out.append((lat.populations(), lat.fields(), lat.diag()))
+    u = np.uint32 if precision == 32 else np.uint64
+    assert np.array_equal(out[0][0].view(u), out[1][0].view(u))
+    for k in ("rho", "vx", "vy", "tau_wall", "p_wall"):
+        assert np.array_equal(out[0][1][k].view(u), out[1][1][k].view(u)), k
+    assert out[0][2]["wall_shear_sum"] == out[1][2]["wall_shear_sum"]
 
 
 def test_checkpoint_restore_continues_bitwise(orc, lbm):
