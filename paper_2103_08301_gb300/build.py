@@ -39,15 +39,18 @@ def _run(cmd):
     return r.stdout + r.stderr
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile liblbm.so if missing or out of date; return its path."""
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, out: str | None = None) -> str:
+    """Compile liblbm.so (or `out`) if missing or out of date; return its path."""
+    lib = out or LIB
+    if not force and out is None and not _stale():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    api_o = os.path.join(BUILD, "lbm_api.o")
-    host_o = os.path.join(BUILD, "lbm_host.o")
+    bdir = BUILD if out is None else out + ".build"
+    os.makedirs(bdir, exist_ok=True)
+    api_o = os.path.join(bdir, "lbm_api.o")
+    host_o = os.path.join(bdir, "lbm_host.o")
+    extra = os.environ.get("LBM_NVCC_FLAGS", "").split()  # tuning experiments, e.g. -DLBM_STAGE_AHEAD=2
     nv = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-          "-I", CSRC, "-c", os.path.join(CSRC, "lbm_api.cu"), "-o", api_o]
+          "-I", CSRC, *extra, "-c", os.path.join(CSRC, "lbm_api.cu"), "-o", api_o]
     if verbose:
         nv.insert(1, "-Xptxas=-v")
     gxx = ["g++", "-O2", "-std=c++17", "-fPIC", "-I", INCLUDE, "-I", CSRC, "-c",
@@ -56,10 +59,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         outs = list(ex.map(_run, [nv, gxx]))
     if verbose:
         print(outs[0])
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     _run([NVCC, *ARCH, "-shared", "-o", tmp, api_o, host_o, "-lcudart"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

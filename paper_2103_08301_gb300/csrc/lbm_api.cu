@@ -17,7 +17,10 @@
 
 namespace {
 
-constexpr int BLOCK = 128;
+#ifndef LBM_BLOCK
+#define LBM_BLOCK 128
+#endif
+constexpr int BLOCK = LBM_BLOCK;  // threads per CTA = strip width
 constexpr size_t ALIGN = 256;
 constexpr uint64_t CKPT_MAGIC = 0x4C424D434B505431ull;  // "LBMCKPT1"
 

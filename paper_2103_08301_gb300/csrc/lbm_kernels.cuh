@@ -184,23 +184,41 @@ __device__ __forceinline__ long long cut_units(const KArgs<real> &A, int c)
     return u;
 }
 
-// Resident CTAs per SM the register allocation is held to (FP32: 4 x 128
-// threads -> <= 128 registers; FP64 carries twice the state per thread).
-template <typename real>
-struct MinBlocks { static constexpr int value = sizeof(real) == 4 ? 4 : 2; };
+// Resident CTAs per SM the register allocation is held to: 512 FP32 threads
+// per SM (<= 128 registers each); FP64 carries twice the state per thread.
+template <typename real, int BLOCK>
+struct MinBlocks { static constexpr int value = (sizeof(real) == 4 ? 512 : 256) / BLOCK; };
 
 // Stage ring of the staged kernel. At iteration j (after its barrier) the
 // rows j-3 (collision) .. j (newest density row) are in use, rows j+1 ..
 // j+STAGE_AHEAD are in flight, and row j+STAGE_AHEAD+1 is issued into the
 // stage freed by row j-4: STAGE_AHEAD + 5 stages.
-constexpr int STAGE_AHEAD = 1;
+#ifndef LBM_STAGE_AHEAD
+#define LBM_STAGE_AHEAD 1
+#endif
+constexpr int STAGE_AHEAD = LBM_STAGE_AHEAD;
 constexpr int NSTAGE = 5 + STAGE_AHEAD;
+
+// A stage holds one stencil row of the strip (local columns 0 .. BLOCK-1) for
+// the nine planes. Each plane segment starts on a 128-byte line when the strip
+// does, so a copy touches no more lines than it needs.
+template <int BLOCK>
+__host__ __device__ constexpr int stage_pitch() { return BLOCK; }
 
 template <typename real, int BLOCK>
 constexpr size_t staged_smem_bytes()
 {
-    return (size_t)NSTAGE * 9 * BLOCK * sizeof(real) + NSTAGE * sizeof(uint64_t);
+    return (size_t)NSTAGE * 9 * stage_pitch<BLOCK>() * sizeof(real) + NSTAGE * sizeof(uint64_t);
 }
+
+// Position in the stage ring (stage index and mbarrier phase parity).
+struct RingPos {
+    uint32_t s = 0, ph = 0;
+    __device__ __forceinline__ void advance()
+    {
+        if (++s == NSTAGE) { s = 0; ph ^= 1u; }
+    }
+};
 
 // f_eq of Eq. 2.2 built from the (i, opp(i)) pairs, which share their even
 // part c and differ in the sign of their odd part o: f_i = c + o, f_opp = c - o.
@@ -251,21 +269,24 @@ __device__ __forceinline__ void grad12(const real (*S)[SW], int qm, int q0, int 
 // iteration yy still reads.
 //
 // STAGED: the strip's populations of each stencil row (9 plane segments of xw
-// values, xw a multiple of 4) are streamed by one producer thread with bulk
-// asynchronous copies into a ring of NSTAGE shared-memory stages, issued
-// STAGE_AHEAD + 1 rows ahead; consumers read densities and collision
-// populations from the stage (needs nx and the strip width to be multiples
-// of 4 for 16-byte aligned copies). Otherwise each thread loads its column
-// with one row of register prefetch and re-reads the collision row from L1.
+// values) are streamed by one producer thread with bulk asynchronous copies
+// into a ring of NSTAGE shared-memory stages, issued STAGE_AHEAD + 1 rows
+// ahead; consumers read densities and collision populations from the stage
+// (needs nx and the strip width to be multiples of 4 for 16-byte aligned
+// copies). Otherwise each thread loads its column with one row of register
+// prefetch and re-reads the collision row from L1. In both variants the four
+// halo lanes load the two columns beyond each strip edge with one row of
+// register prefetch.
 template <typename real, bool WALLS, bool PRES, int MODE, int BLOCK, bool STAGED>
-__global__ void __launch_bounds__(BLOCK, MinBlocks<real>::value) step_kernel(const KArgs<real> A)
+__global__ void __launch_bounds__(BLOCK, MinBlocks<real, BLOCK>::value) step_kernel(const KArgs<real> A)
 {
     static_assert(BLOCK % 32 == 0 && BLOCK >= 128, "the four halo columns take one warp each");
     constexpr int SW = BLOCK + 4;
     constexpr int PRODUCER = BLOCK - 1;  // no halo duty
+    constexpr int SP = stage_pitch<BLOCK>();
     extern __shared__ __align__(128) unsigned char dsm[];
     real *const stages = reinterpret_cast<real *>(dsm);
-    uint64_t *const bars = reinterpret_cast<uint64_t *>(dsm + (size_t)NSTAGE * 9 * BLOCK * sizeof(real));
+    uint64_t *const bars = reinterpret_cast<uint64_t *>(dsm + (size_t)NSTAGE * 9 * SP * sizeof(real));
     __shared__ real s_rho[RING][SW];
     __shared__ real s_phi[RING][SW];
     __shared__ real s_lap[RING][SW];
@@ -287,7 +308,7 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real>::value) step_kernel(con
     real tmin = real(INFINITY), tmax = real(-INFINITY), pmin = real(INFINITY), pmax = real(-INFINITY);
     bool bad = false;
     real b_rho1 = 0, b_v1 = 0, t_v2 = 0;  // wall-pair carries (rows 1 -> 2, ny-3 -> ny-2)
-    uint32_t kr = 0;                      // stencil rows staged by this CTA so far (uniform)
+    RingPos ring_next;                    // stage of the next stencil row to consume (uniform)
     bool lost = false;                    // a bounded wait gave up
 
     if constexpr (STAGED) {
@@ -355,24 +376,27 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real>::value) step_kernel(con
                 for (int i = 0; i < 9; ++i) hf[i] = __ldg(hal_in + row + i * plane);
             }
         };
-        // producer: stream stencil row j of this segment into its stage
+        // producer: stream stencil row j of this segment into stage position ip
+        RingPos ring_issue = ring_next;
         auto issue = [&](int j) {
-            if (tid == PRODUCER && j < nrows) {
-                bool mir;
-                const long long row = (long long)map_row<WALLS>(ya - 2 + j, ny, mir) * nx;
-                const uint32_t st = (kr + j) % NSTAGE;
-                real *dst = stages + (size_t)st * 9 * BLOCK;
-                const real *src = A.fin + row + x0;
-                const uint32_t bytes = (uint32_t)(xw * sizeof(real));
-                mbar_arrive_expect_tx(&bars[st], 9 * bytes);
+            if (j < nrows) {
+                if (tid == PRODUCER) {
+                    bool mir;
+                    const long long row = (long long)map_row<WALLS>(ya - 2 + j, ny, mir) * nx;
+                    const uint32_t st = ring_issue.s;
+                    real *dst = stages + (size_t)st * 9 * SP;
+                    const real *src = A.fin + row + x0;
+                    const uint32_t bytes = (uint32_t)(xw * sizeof(real));
+                    mbar_arrive_expect_tx(&bars[st], 9 * bytes);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) bulk_copy_g2s(dst + i * BLOCK, src + i * plane, bytes, &bars[st]);
+                    for (int i = 0; i < 9; ++i) bulk_copy_g2s(dst + i * SP, src + i * plane, bytes, &bars[st]);
+                }
+                ring_issue.advance();
             }
         };
-        // stage holding stencil row j of this segment
-        auto stage_of = [&](int j) -> const real * {
-            return stages + (size_t)((kr + j) % NSTAGE) * 9 * BLOCK + scol;
-        };
+        // stage of the collision row (three rows behind the consumed row)
+        RingPos ring_coll = ring_next;
+        for (int k = 0; k < NSTAGE - 3; ++k) ring_coll.advance();
 #pragma unroll
         for (int i = 0; i < 9; ++i) { pf[i] = real(0); hf[i] = real(0); }
         if constexpr (STAGED) {
@@ -384,6 +408,7 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real>::value) step_kernel(con
             const int r = yy - 3;
             const int j = yy - (ya - 2);
             const bool collide = r >= ya && r < yb;  // uniform over the CTA
+            const uint32_t st_cons = ring_next.s, ph_cons = ring_next.ph, st_coll = ring_coll.s;
 
             // (1) populations of the collision row (read from HBM three iterations ago)
             real f[9];
@@ -401,12 +426,11 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real>::value) step_kernel(con
                 const int rs = yy & (RING - 1);
                 real rho_own = real(0), rho_h = real(0);
                 if constexpr (STAGED) {
-                    const uint32_t k = kr + j;
-                    if (!mbar_wait_bounded(&bars[k % NSTAGE], (k / NSTAGE) & 1)) lost = true;
+                    if (!mbar_wait_bounded(&bars[st_cons], ph_cons)) lost = true;
+                    const real *stg = stages + (size_t)st_cons * 9 * SP;
                     if (active) {
-                        const real *sp = stage_of(j);
 #pragma unroll
-                        for (int i = 0; i < 9; ++i) pf[i] = sp[i * BLOCK];
+                        for (int i = 0; i < 9; ++i) pf[i] = stg[i * SP + scol];
                     }
                 }
                 if (active) {
@@ -447,13 +471,14 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real>::value) step_kernel(con
                 if (tid == PRODUCER) fence_proxy_async_smem();
                 issue(j + STAGE_AHEAD + 1);
             }
+            if (yy <= yb + 1) ring_next.advance();
 
             // (4) collide and stream row r
             if (collide && active) {
                 if constexpr (STAGED) {
-                    const real *sp = stage_of(j - 3);
+                    const real *sp = stages + (size_t)st_coll * 9 * SP + scol;
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) f[i] = sp[i * BLOCK];
+                    for (int i = 0; i < 9; ++i) f[i] = sp[i * SP];
                 }
                 const int q0 = r & (RING - 1), qm = (r - 1) & (RING - 1), qp = (r + 1) & (RING - 1);
                 const int c = ccol;
@@ -573,9 +598,9 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real>::value) step_kernel(con
                     }
                 }
             }
+            ring_coll.advance();
         }
         __syncthreads();  // ring and stage reuse by the next segment
-        kr += nrows;
     }
 
     if (STAGED && lost) atomicOr(A.err, 2);
