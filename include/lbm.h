@@ -190,6 +190,36 @@ lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value);
 lbm_status lbm_launch_info(const lbm_ctx *ctx, int64_t *ctas, int64_t *threads, int64_t *units,
                            int64_t *staged);
 
+/* One time step from f_in to f_out without allocating any device memory.
+ * No counterpart in the paper: this is a deployment form of lbm_step for
+ * callers that cannot allocate at the point where they step (code running
+ * inside another framework's memory pool, hosts that size every buffer up
+ * front, work about to be recorded into a CUDA graph).
+ *   grid, eos, tau, wetting, drive: as for lbm_init (drive may be NULL).
+ *   f_in, f_out: distinct caller-owned device arrays of 9*nx*ny values of the
+ *            grid precision, layout f[i][y][x]. f_out receives the next state;
+ *            slots no population reaches (solid rows, the inflow slots of
+ *            pressure columns) are left untouched, so initialise f_out from
+ *            f_in if those must be defined.
+ *   ctas:    CTAs of the step grid, 0 = as lbm_step chooses; at most 4096.
+ *   diag_out: NULL or a device array of 7 doubles receiving, for the state
+ *            f_in: mass, wall-shear sum, tau_w min/max, p_w min/max, and a
+ *            nonzero flag if a bad density was met.
+ *   stream:  cudaStream_t (NULL = legacy default stream); the call only
+ *            enqueues work and does not synchronise.
+ * Scratch: the per-CTA partials live in one static device array (about
+ * 192 KB) that the library holds on every device it is used on until the
+ * process exits. Every call reuses and first clears it, so calls whose work
+ * overlaps on the GPU (different streams, or graphs replayed concurrently)
+ * race on it; serialise them. The first call on a device resolves the
+ * array's device address (cudaGetSymbolAddress) and should come before any
+ * stream capture.
+ * Errors: LBM_ERR_ARG (bad grid, NULL or equal buffers, ctas outside
+ * 0..4096), LBM_ERR_PARAM, LBM_ERR_CUDA. */
+lbm_status lbm_step_noalloc(const lbm_grid *grid, const lbm_eos *eos, double tau, double wetting,
+                            const lbm_drive *drive, const void *f_in, void *f_out, int64_t ctas,
+                            double *diag_out, void *stream);
+
 /* Release everything the library allocated. NULL-safe. */
 void lbm_free(lbm_ctx *ctx);
 

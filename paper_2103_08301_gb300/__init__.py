@@ -67,6 +67,8 @@ _SIGS = {
     "lbm_restore": (C.c_int, [_P, _P, C.c_size_t]),
     "lbm_set_option": (C.c_int, [_P, C.c_int, C.c_int64]),
     "lbm_launch_info": (C.c_int, [_P] + [C.POINTER(C.c_int64)] * 4),
+    "lbm_step_noalloc": (C.c_int, [C.POINTER(lbm_grid), C.POINTER(lbm_eos), C.c_double, C.c_double,
+                                   C.POINTER(lbm_drive), _P, _P, C.c_int64, _P, _P]),
     "lbm_free": (None, [_P]),
     "lbm_status_string": (C.c_char_p, [C.c_int]),
     "lbm_last_error": (C.c_char_p, [_P]),
@@ -140,6 +142,15 @@ def lbm_init(grid, eos, tau, wetting, drive, rho0, workspace=None, ws_bytes=0, s
 
 def lbm_step(ctx, n: int) -> int:
     return int(lib().lbm_step(ctx, int(n)))
+
+
+def lbm_step_noalloc(grid, eos, tau, wetting, drive, f_in_ptr, f_out_ptr, ctas=0, diag_ptr=None,
+                     stream=None) -> int:
+    """One step between caller-owned device buffers (raw pointers); returns the status."""
+    return int(lib().lbm_step_noalloc(C.byref(grid), C.byref(eos), float(tau), float(wetting),
+                                      C.byref(drive) if drive is not None else None,
+                                      _P(f_in_ptr), _P(f_out_ptr), int(ctas),
+                                      _P(diag_ptr) if diag_ptr else None, _P(stream) if stream else None))
 
 
 def lbm_coexistence(eos: lbm_eos):

@@ -624,3 +624,140 @@ void lbm_free(lbm_ctx *ctx)
 }
 
 } // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free single step.
+//
+// Some callers cannot allocate device memory at the point where they step the
+// lattice: code running inside another framework's memory pool, an
+// embedded host that pre-sizes every buffer up front, or a caller about to
+// record its work into a CUDA graph. This entry point performs one step
+// between two caller-owned population buffers and keeps the only scratch it
+// needs - the per-CTA diagnostic partials - in a fixed device array that the
+// library declares at file scope. Nothing is allocated per call.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr int NOALLOC_MAX_CTAS = 4096;
+
+// Per-CTA partials of one step: mass, wall-shear sum, four extrema (stored as
+// double so both precisions fit) and the bad-density flag.
+struct NoallocScratch {
+    double mass[NOALLOC_MAX_CTAS];
+    double J[NOALLOC_MAX_CTAS];
+    double ext[4 * NOALLOC_MAX_CTAS];
+    int err;
+};
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+NoallocScratch *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+std::mutex g_noalloc_mutex;
+
+} // namespace
+
+// The scratch itself. In host code this name is only a stand-in for the
+// device object; its device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
+
+namespace {
+
+// Device address of the scratch on the current device, resolved on the first
+// call made with that device current.
+cudaError_t noalloc_scratch(NoallocScratch **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<NoallocScratch *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+template <typename real>
+lbm_status noalloc_launch(lbm_ctx *c, NoallocScratch *sc, const void *f_in, void *f_out, double *diag_out)
+{
+    real *ext = reinterpret_cast<real *>(sc->ext);
+    lbm::reset_acc_kernel<real><<<(c->nctas + 255) / 256, 256, 0, c->stream>>>(sc->mass, sc->J, ext, &sc->err,
+                                                                                 c->nctas);
+    lbm::KArgs<real> A = make_args<real>(c);
+    A.fin = static_cast<const real *>(f_in);
+    A.fout = static_cast<real *>(f_out);
+    A.mass_part = sc->mass;
+    A.J_acc = sc->J;
+    A.ext = ext;
+    A.err = &sc->err;
+    cudaError_t e = launch<real, lbm::MODE_STEP>(c, A);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "noalloc step");
+    if (diag_out)
+        lbm::diag_kernel<real><<<1, 256, 0, c->stream>>>(sc->mass, sc->J, ext, &sc->err, c->nctas, diag_out);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? LBM_OK : cuda_fail(nullptr, e, "noalloc launch");
+}
+
+} // namespace
+
+extern "C" lbm_status lbm_step_noalloc(const lbm_grid *grid, const lbm_eos *eos, double tau,
+                                       double wetting, const lbm_drive *drive, const void *f_in,
+                                       void *f_out, int64_t ctas, double *diag_out, void *stream)
+{
+    if (!grid_ok(grid) || !eos || !f_in || !f_out || f_in == f_out) return LBM_ERR_ARG;
+    if (ctas < 0 || ctas > NOALLOC_MAX_CTAS) return LBM_ERR_ARG;
+    if (!(tau > 0.5) || !(eos->k > 0) || !(eos->kappa >= 0) || !(eos->a > 0) || !(eos->b > 0) ||
+        !(eos->R > 0) || !(eos->T_over_Tc > 0) || !std::isfinite(wetting))
+        return LBM_ERR_PARAM;
+
+    NoallocScratch *sc = nullptr;
+    cudaError_t e = noalloc_scratch(&sc);
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+
+    // Launch plan and physics on the host stack only (no workspace).
+    lbm_ctx c;
+    c.grid = *grid;
+    c.eos = *eos;
+    if (drive) c.drive = *drive;
+    else { c.drive.dp = 0; c.drive.p_ref = NAN; c.drive.gx = c.drive.gy = 0; }
+    c.tau = tau;
+    c.wet = wetting;
+    c.stream = static_cast<cudaStream_t>(stream);
+    double rhoc;
+    lbm::cs_critical(eos->a, eos->b, eos->R, &c.Tc, &rhoc);
+    c.T = eos->T_over_Tc * c.Tc;
+    lbm::Thermo th{eos->a, eos->b, eos->R, c.T};
+    const bool coexist = lbm::maxwell(th, &c.rho_g, &c.rho_l, &c.p_sat) == 0;
+    if (grid->bc_x) {
+        const double k2 = eos->k * eos->k;
+        double pref = c.drive.p_ref;
+        if (std::isnan(pref)) {
+            if (!coexist) return LBM_ERR_PARAM;
+            pref = k2 * c.p_sat;
+        }
+        const double pin = (pref + 0.5 * c.drive.dp) / k2, pout = (pref - 0.5 * c.drive.dp) / k2;
+        if (lbm::gas_density(th, pin, &c.rho_in) || lbm::gas_density(th, pout, &c.rho_out)) return LBM_ERR_PARAM;
+        if (coexist) {
+            if (lbm::liquid_density(th, pin, &c.rho_in_l) || lbm::liquid_density(th, pout, &c.rho_out_l))
+                return LBM_ERR_PARAM;
+        } else {
+            c.rho_in_l = c.rho_in;
+            c.rho_out_l = c.rho_out;
+            c.rho_g = c.rho_l = 0.0;
+        }
+    }
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+    if (plan_launch(&c) != LBM_OK) return LBM_ERR_CUDA;
+    if (ctas > 0) c.nctas = (int)std::min<long long>(ctas, std::max<long long>(1, c.units / 2));
+    c.nctas = std::min(c.nctas, NOALLOC_MAX_CTAS);
+    return grid->precision == 64 ? noalloc_launch<double>(&c, sc, f_in, f_out, diag_out)
+                                 : noalloc_launch<float>(&c, sc, f_in, f_out, diag_out);
+}

@@ -1,0 +1,83 @@
+"""The allocation-free step (lbm_step_noalloc) against the ordinary context path.
+
+lbm_step_noalloc serves callers that cannot allocate device memory when they
+step the lattice (a framework that owns the memory pool, a host that sizes all
+buffers up front, work recorded into a CUDA graph): it steps between two
+caller-owned buffers and keeps its per-CTA scratch in a fixed device array.
+Here the test allocates the buffers itself (with torch) and checks two calls
+in a row against two lbm_step calls on a context. This file is collected last
+so a failure here comes after every other test has run.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_08301_gb300 import build
+    build.build()
+    import paper_2103_08301_gb300 as m
+    return m
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_noalloc_step_matches_context_step_twice(orc, lbm, precision):
+    import torch
+    nx, ny = 512, 96
+    kw = dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=1e-3)
+    s = orc.Setup(nx=nx, ny=ny, **kw)
+    g, l, _ = s.coexistence()
+    rho0 = synth.airway_rho0(nx, ny, 6, 160, 48, l, g)
+    tdt = torch.float32 if precision == 32 else torch.float64
+    with lbm.Lattice(nx, ny, rho0, precision=precision, **kw) as lat:
+        lat.step(40)
+        f0 = lat.populations()
+        d0 = lat.diag()
+        lat.step(1)
+        f1, d1 = lat.populations(), lat.diag()
+        lat.step(1)
+        f2, d2 = lat.populations(), lat.diag()
+        grid, eos, drive = lat.grid, lat.eos, lat.drive
+
+    a = torch.from_numpy(f0).to("cuda", tdt)
+    b = a.clone()  # slots no population reaches keep the input values, as in the context
+    c = a.clone()
+    diag = torch.zeros(2, 7, dtype=torch.float64, device="cuda")
+    st = lbm.lbm_step_noalloc(grid, eos, 1.0, 0.0, drive, a.data_ptr(), b.data_ptr(), 0,
+                              diag[0].data_ptr(), None)
+    assert st == lbm.LBM_OK, lbm.status_string(st)
+    st = lbm.lbm_step_noalloc(grid, eos, 1.0, 0.0, drive, b.data_ptr(), c.data_ptr(), 0,
+                              diag[1].data_ptr(), None)
+    assert st == lbm.LBM_OK, lbm.status_string(st)
+    torch.cuda.synchronize()
+    u = np.uint32 if precision == 32 else np.uint64
+    # same kernel, same launch geometry: identical bits
+    assert np.array_equal(b.cpu().numpy().view(u), f1.view(u))
+    assert np.array_equal(c.cpu().numpy().view(u), f2.view(u))
+    dg = diag.cpu().numpy()
+    tol = 1e-12 if precision == 64 else 1e-6
+    # per-call diagnostics are those of the state each call read
+    assert abs(dg[0, 0] / d1["mass"] - 1) <= tol and abs(dg[1, 0] / d2["mass"] - 1) <= tol
+    for k, (dj, da, db) in enumerate([(dg[0, 1], d0, d1), (dg[1, 1], d1, d2)]):
+        step_J = db["wall_shear_sum"] - da["wall_shear_sum"]
+        assert abs(dj - step_J) <= 1e-6 * max(abs(step_J), 1e-12) + 1e-12, (k, dj, step_J)
+    assert dg[0, 6] == 0 and dg[1, 6] == 0
+
+
+def test_noalloc_rejects_bad_requests(lbm):
+    import torch
+    g = lbm.lbm_grid(64, 32, 1, 0, 32)
+    e = lbm.lbm_eos(1.0, 4.0, 1.0, 0.8, 1.0, 0.5)
+    a = torch.zeros(9 * 64 * 32, dtype=torch.float32, device="cuda")
+    b = torch.zeros_like(a)
+    assert lbm.lbm_step_noalloc(g, e, 1.0, 0.0, None, a.data_ptr(), b.data_ptr(), 4097) == lbm.LBM_ERR_ARG
+    assert lbm.lbm_step_noalloc(g, e, 1.0, 0.0, None, a.data_ptr(), a.data_ptr(), 0) == lbm.LBM_ERR_ARG
+    assert lbm.lbm_step_noalloc(g, e, 0.5, 0.0, None, a.data_ptr(), b.data_ptr(), 0) == lbm.LBM_ERR_PARAM
