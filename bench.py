@@ -175,6 +175,21 @@ def _cpu_baseline(budget_s=15.0):
                       f"(walls, pressure columns, film 64, plug 256 long), {dt:.1f} s"}
 
 
+def allreduce_max(value: float, dist=None, device="cpu") -> float:
+    """Max over ranks of a per-rank time (identity without a process group)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world: int, nodes: int, steps: int, t_max: float) -> float:
+    """Weak scaling: every rank steps its own channel of `nodes` nodes."""
+    return world * nodes * steps / t_max / 1e6
+
+
 def run_reference(args, world, rank):
     """Reference arm: the FP64 CPU oracle timed on the host cores, each step a
     bounded sample of the workload (a window of the channel) so the whole run
@@ -257,16 +272,13 @@ def run_ours(args, world, rank, local):
         dist.barrier()
     elapsed = t_start.elapsed_time(t_end) / 1e3
     kern = [a.elapsed_time(b) / 1e3 for a, b in ev]
-    t = torch.tensor([elapsed], device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_max = float(t.item())
+    t_max = allreduce_max(elapsed, dist, "cuda")
     d = lat.diag()
     lat.close()
     clocks = clk.summary()
 
     nodes = NX * NY
-    value = world * nodes * args.steps / t_max / 1e6
+    value = whole_job_mlups(world, nodes, args.steps, t_max)
     kmean = sum(kern) / len(kern)
     bytes_per_launch = BYTES_PER_NODE[precision] * nodes
     achieved = bytes_per_launch / kmean / 1e9
@@ -288,10 +300,7 @@ def run_ours(args, world, rank, local):
     lat2.fields_into(rho=out_rho.numpy())
     lat2.close()
     e2e_t = time.perf_counter() - t0
-    et = torch.tensor([e2e_t], device="cuda")
-    if dist:
-        dist.all_reduce(et, op=dist.ReduceOp.MAX)
-    e2e_val = world * nodes * args.steps / float(et.item()) / 1e6
+    e2e_val = whole_job_mlups(world, nodes, args.steps, allreduce_max(e2e_t, dist, "cuda"))
 
     if rank == 0:
         cpu = _cpu_baseline() if world == 1 else None

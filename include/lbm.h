@@ -19,8 +19,10 @@
  *
  * Conventions
  *   - Lattice nodes are (x, y), 0 <= x < nx, 0 <= y < ny, node index y*nx + x.
- *   - Populations are stored as nine planes f[i][y][x] (structure of arrays),
- *     i = 0..8 with e = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1).
+ *   - Populations cross this ABI as nine planes f[i][y][x] (structure of
+ *     arrays), i = 0..8 with e = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),
+ *     (-1,-1),(1,-1). Inside a context the library keeps them row-interleaved,
+ *     f[y][i][x], and converts on lbm_populations / lbm_load_populations.
  *   - Real-valued buffers use the context precision: float for precision 32,
  *     double for precision 64. Host inputs are always double.
  *   - All functions return an lbm_status; none aborts or traps. After
@@ -60,7 +62,8 @@ typedef enum {
  *        geometry reduces to).
  * bc_x:  0 = periodic in x; 1 = column 0 is the pressure inlet and column
  *        nx-1 the pressure outlet.
- * Limits: nx, ny >= 4 (>= 1 for a periodic axis), nx*ny < 2^31 per plane. */
+ * Limits: nx, ny >= 4 (>= 1 for a periodic axis), 9*nx*ny < 2^31 (32-bit
+ * population indices: at most ~238 million nodes per context). */
 typedef struct {
     int32_t nx, ny;
     int32_t walls;
@@ -197,7 +200,8 @@ lbm_status lbm_launch_info(const lbm_ctx *ctx, int64_t *ctas, int64_t *threads, 
  * front, work about to be recorded into a CUDA graph).
  *   grid, eos, tau, wetting, drive: as for lbm_init (drive may be NULL).
  *   f_in, f_out: distinct caller-owned device arrays of 9*nx*ny values of the
- *            grid precision, layout f[i][y][x]. f_out receives the next state;
+ *            grid precision in the library's row-interleaved layout f[y][i][x]
+ *            (index (9*y + i)*nx + x). f_out receives the next state;
  *            slots no population reaches (solid rows, the inflow slots of
  *            pressure columns) are left untouched, so initialise f_out from
  *            f_in if those must be defined.

@@ -55,7 +55,8 @@ bool grid_ok(const lbm_grid *g)
     if (g->walls != 0 && g->walls != 1) return false;
     if (g->bc_x != 0 && g->bc_x != 1) return false;
     if (g->nx < (g->bc_x ? 4 : 1) || g->ny < (g->walls ? 4 : 1)) return false;
-    if ((long long)g->nx * g->ny >= (1ll << 31)) return false;
+    // 32-bit population indices: 9 nx ny < 2^31 (up to ~238 million nodes)
+    if (9ll * g->nx * g->ny >= (1ll << 31)) return false;
     return true;
 }
 
@@ -277,6 +278,25 @@ void reset_acc(lbm_ctx *ctx)
         (real *)(ctx->ws + ctx->L.ext), (int *)(ctx->ws + ctx->L.err), lbm::MAX_CTAS);
 }
 
+// The library stores populations row-interleaved, f[y][i][x]; the ABI
+// exchanges plane-major f[i][y][x]. One strided 2D copy per plane converts.
+cudaError_t copy_planes(const lbm_ctx *ctx, void *dst, const void *src, bool to_abi)
+{
+    const size_t sz = ctx->grid.precision == 64 ? 8 : 4;
+    const size_t nx = ctx->grid.nx, ny = ctx->grid.ny, row = nx * sz;
+    for (int i = 0; i < 9; ++i) {
+        cudaError_t e;
+        if (to_abi)
+            e = cudaMemcpy2DAsync((char *)dst + i * nx * ny * sz, row, (const char *)src + i * row, 9 * row,
+                                  row, ny, cudaMemcpyDefault, ctx->stream);
+        else
+            e = cudaMemcpy2DAsync((char *)dst + i * row, 9 * row, (const char *)src + i * nx * ny * sz, row,
+                                  row, ny, cudaMemcpyDefault, ctx->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 struct CkptHeader {
     uint64_t magic;
     int32_t nx, ny, walls, bc_x, precision, nctas;
@@ -408,11 +428,11 @@ lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, double
         const int blocks = (int)std::min<size_t>((N + 255) / 256, (size_t)ctx->sms * 8);
         if (grid->precision == 64) {
             lbm::init_kernel<double><<<blocks, 256, 0, ctx->stream>>>(
-                d_rho0, (double *)(ctx->ws + ctx->L.f0), (double *)(ctx->ws + ctx->L.f1), (long long)N);
+                d_rho0, (double *)(ctx->ws + ctx->L.f0), (double *)(ctx->ws + ctx->L.f1), grid->nx, (int)N);
             reset_acc<double>(ctx);
         } else {
             lbm::init_kernel<float><<<blocks, 256, 0, ctx->stream>>>(
-                d_rho0, (float *)(ctx->ws + ctx->L.f0), (float *)(ctx->ws + ctx->L.f1), (long long)N);
+                d_rho0, (float *)(ctx->ws + ctx->L.f0), (float *)(ctx->ws + ctx->L.f1), grid->nx, (int)N);
             reset_acc<float>(ctx);
         }
         e = cudaGetLastError();
@@ -492,9 +512,7 @@ lbm_status lbm_diag(lbm_ctx *ctx, lbm_diag_t *out)
 lbm_status lbm_populations(lbm_ctx *ctx, void *dst)
 {
     if (!ctx || !dst) return LBM_ERR_ARG;
-    const size_t bytes = (size_t)9 * ctx->grid.nx * ctx->grid.ny * (ctx->grid.precision == 64 ? 8 : 4);
-    CK(cudaMemcpyAsync(dst, ctx->ws + (ctx->cur ? ctx->L.f1 : ctx->L.f0), bytes, cudaMemcpyDefault,
-                       ctx->stream), "populations copy");
+    CK(copy_planes(ctx, dst, ctx->ws + (ctx->cur ? ctx->L.f1 : ctx->L.f0), true), "populations copy");
     CK(cudaStreamSynchronize(ctx->stream), "populations sync");
     return LBM_OK;
 }
@@ -502,11 +520,10 @@ lbm_status lbm_populations(lbm_ctx *ctx, void *dst)
 lbm_status lbm_load_populations(lbm_ctx *ctx, const void *src)
 {
     if (!ctx || !src) return LBM_ERR_ARG;
-    const size_t bytes = (size_t)9 * ctx->grid.nx * ctx->grid.ny * (ctx->grid.precision == 64 ? 8 : 4);
     // both arrays, so never-written slots (solid rows, unreached boundary
     // slots) agree with the loaded state
-    CK(cudaMemcpyAsync(ctx->ws + ctx->L.f0, src, bytes, cudaMemcpyDefault, ctx->stream), "load copy");
-    CK(cudaMemcpyAsync(ctx->ws + ctx->L.f1, src, bytes, cudaMemcpyDefault, ctx->stream), "load copy");
+    CK(copy_planes(ctx, ctx->ws + ctx->L.f0, src, false), "load copy");
+    CK(copy_planes(ctx, ctx->ws + ctx->L.f1, src, false), "load copy");
     CK(cudaStreamSynchronize(ctx->stream), "load sync");
     return LBM_OK;
 }

@@ -9,8 +9,10 @@
 // streaming of Eq. 2.1, plus the wall diagnostics of Sec. 3.
 //
 // Data flow (HBM-bound: 36 B read + 36 B written per node in FP32):
-//   - populations live in two structure-of-arrays buffers; a step reads
-//     buffer A and pushes post-collision values into buffer B;
+//   - populations live in two buffers with rows of nine planes,
+//     f[y][i][x] (row stride 9 nx; the C ABI exchanges f[i][y][x] and
+//     converts); a step reads buffer A and pushes post-collision values into
+//     buffer B; all indices are 32-bit (9 nx ny < 2^31);
 //   - each CTA owns a strip of up to BLOCK columns and marches along y over
 //     a contiguous range of rows; one thread per column keeps the raw
 //     populations of the last four rows in registers (one row prefetched);
@@ -36,7 +38,7 @@ template <typename real>
 struct KArgs {
     const real *__restrict__ fin;
     real *__restrict__ fout;
-    long long plane;  // nx * ny
+    long long plane;  // nx * ny (nodes per lattice)
     int nx, ny;
     int W;            // strip width in columns (<= BLOCK)
     int nstrips;
@@ -186,8 +188,13 @@ __device__ __forceinline__ long long cut_units(const KArgs<real> &A, int c)
 
 // Resident CTAs per SM the register allocation is held to: 512 FP32 threads
 // per SM (<= 128 registers each); FP64 carries twice the state per thread.
+#ifndef LBM_FP32_THREADS_PER_SM
+#define LBM_FP32_THREADS_PER_SM 512
+#endif
 template <typename real, int BLOCK>
-struct MinBlocks { static constexpr int value = (sizeof(real) == 4 ? 512 : 256) / BLOCK; };
+struct MinBlocks {
+    static constexpr int value = (sizeof(real) == 4 ? LBM_FP32_THREADS_PER_SM : 256) / BLOCK;
+};
 
 // Stage ring of the staged kernel. At iteration j (after its barrier) the
 // rows j-3 (collision) .. j (newest density row) are in use, rows j+1 ..
@@ -300,8 +307,12 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real, BLOCK>::value) step_ker
     const long long u1 = cut_units<WALLS>(A, cta + 1);
 
     const real third = real(1.0 / 3.0), twelfth = real(1.0 / 12.0), sixth = real(1.0 / 6.0);
-    const long long plane = A.plane;
     const int nx = A.nx, ny = A.ny;
+    const int rstride = 9 * nx;  // row stride of the population layout f[y][i][x]
+    // push targets of directions 1..8 relative to the source slot index
+    const int o1 = nx + 1, o2 = rstride + 2 * nx, o3 = 3 * nx - 1, o4 = 4 * nx - rstride;
+    const int o5 = rstride + 5 * nx + 1, o6 = rstride + 6 * nx - 1, o7 = 7 * nx - rstride - 1;
+    const int o8 = 8 * nx - rstride + 1;
     double mass = 0.0, Jsum = 0.0;
     real macc = real(0);
     int mcount = 0;
@@ -363,17 +374,19 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real, BLOCK>::value) step_ker
         const int scol = xc - x0;            // this thread's column inside a stage
         const int nrows = yb - ya + 4;       // stencil rows ya-2 .. yb+1
         real pf[9], hf[9];
+        real add_next = real(0);  // wetting offset of the next stencil row (mirrored wall ghost)
         // halo (and, without staging, own-column) loads of stencil row yy
         auto prefetch = [&](int yy) {
             bool mir;
-            const long long row = (long long)map_row<WALLS>(yy, ny, mir) * nx;
+            const int row = map_row<WALLS>(yy, ny, mir) * rstride;
+            add_next = mir ? A.wet : real(0);
             if (!STAGED && active) {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) pf[i] = __ldg(col_in + row + i * plane);
+                for (int i = 0; i < 9; ++i) pf[i] = __ldg(col_in + row + i * nx);
             }
             if (hmode) {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) hf[i] = __ldg(hal_in + row + i * plane);
+                for (int i = 0; i < 9; ++i) hf[i] = __ldg(hal_in + row + i * nx);
             }
         };
         // producer: stream stencil row j of this segment into stage position ip
@@ -382,14 +395,14 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real, BLOCK>::value) step_ker
             if (j < nrows) {
                 if (tid == PRODUCER) {
                     bool mir;
-                    const long long row = (long long)map_row<WALLS>(ya - 2 + j, ny, mir) * nx;
+                    const int row = map_row<WALLS>(ya - 2 + j, ny, mir) * rstride;
                     const uint32_t st = ring_issue.s;
                     real *dst = stages + (size_t)st * 9 * SP;
                     const real *src = A.fin + row + x0;
                     const uint32_t bytes = (uint32_t)(xw * sizeof(real));
                     mbar_arrive_expect_tx(&bars[st], 9 * bytes);
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) bulk_copy_g2s(dst + i * SP, src + i * plane, bytes, &bars[st]);
+                    for (int i = 0; i < 9; ++i) bulk_copy_g2s(dst + i * SP, src + i * nx, bytes, &bars[st]);
                 }
                 ring_issue.advance();
             }
@@ -399,10 +412,13 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real, BLOCK>::value) step_ker
         for (int k = 0; k < NSTAGE - 3; ++k) ring_coll.advance();
 #pragma unroll
         for (int i = 0; i < 9; ++i) { pf[i] = real(0); hf[i] = real(0); }
+        prefetch(ya - 2);
         if constexpr (STAGED) {
             for (int j = 0; j <= STAGE_AHEAD; ++j) issue(j);
+            // one thread waits for the first row; the barrier publishes it
+            if (tid == 0 && !mbar_wait_bounded(&bars[ring_next.s], ring_next.ph)) lost = true;
+            __syncthreads();
         }
-        prefetch(ya - 2);
 
         for (int yy = ya - 2; yy <= yb + 2; ++yy) {
             const int r = yy - 3;
@@ -413,20 +429,19 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real, BLOCK>::value) step_ker
             // (1) populations of the collision row (read from HBM three iterations ago)
             real f[9];
             if (!STAGED && collide && active) {
-                const real *src = col_in + (long long)r * nx;
+                const real *src = col_in + r * rstride;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) f[i] = __ldg(src + i * plane);
+                for (int i = 0; i < 9; ++i) f[i] = __ldg(src + i * nx);
             }
 
-            // (2) density and EOS potential of stencil row yy
+            // (2) density and EOS potential of stencil row yy (staged: its
+            //     stage was completed before the previous barrier)
             if (yy <= yb + 1) {
-                bool mir;
-                map_row<WALLS>(yy, ny, mir);
-                const real add = mir ? A.wet : real(0);
+                const real add = add_next;
                 const int rs = yy & (RING - 1);
                 real rho_own = real(0), rho_h = real(0);
                 if constexpr (STAGED) {
-                    if (!mbar_wait_bounded(&bars[st_cons], ph_cons)) lost = true;
+                    (void)ph_cons;
                     const real *stg = stages + (size_t)st_cons * 9 * SP;
                     if (active) {
 #pragma unroll
@@ -462,6 +477,15 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real, BLOCK>::value) step_ker
                 };
                 if (active) lap_at(tid + 2);
                 if (lhalo >= 0) lap_at(lhalo);
+            }
+            if constexpr (STAGED) {
+                // one thread waits for the next stencil row's stage; the
+                // barrier below publishes its contents to the whole CTA
+                if (tid == 0 && yy + 1 <= yb + 1) {
+                    RingPos nxt = ring_next;
+                    nxt.advance();
+                    if (!mbar_wait_bounded(&bars[nxt.s], nxt.ph)) lost = true;
+                }
             }
             __syncthreads();
 
@@ -514,25 +538,26 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real, BLOCK>::value) step_ker
 #pragma unroll
                         for (int i = 0; i < 9; ++i) fs[i] = sc * ff[i] + A.omb * (f[i] - ff[i]);
                     }
-                    real *o = A.fout + (long long)r * nx + x;
+                    real *const out = A.fout;
+                    const int oi = r * rstride + x;  // slot of (x, r) in plane 0
                     const bool y_inner = WALLS ? (r >= 2 && r <= ny - 3) : (r >= 1 && r <= ny - 2);
                     if (x_inner && y_inner) {
-                        o[0] = fs[0];
-                        o[plane + 1] = fs[1];
-                        o[2 * plane + nx] = fs[2];
-                        o[3 * plane - 1] = fs[3];
-                        o[4 * plane - nx] = fs[4];
-                        o[5 * plane + nx + 1] = fs[5];
-                        o[6 * plane + nx - 1] = fs[6];
-                        o[7 * plane - nx - 1] = fs[7];
-                        o[8 * plane - nx + 1] = fs[8];
+                        out[oi] = fs[0];
+                        out[oi + o1] = fs[1];
+                        out[oi + o2] = fs[2];
+                        out[oi + o3] = fs[3];
+                        out[oi + o4] = fs[4];
+                        out[oi + o5] = fs[5];
+                        out[oi + o6] = fs[6];
+                        out[oi + o7] = fs[7];
+                        out[oi + o8] = fs[8];
                     } else {
 #pragma unroll
                         for (int i = 0; i < 9; ++i) {
                             const int ty = r + ey_(i);
                             if (WALLS && (ty == 0 || ty == ny - 1)) {
                                 // half-way bounce-back into the opposite slot of this node
-                                o[opp_(i) * plane] = fs[i];
+                                out[oi + opp_(i) * nx] = fs[i];
                             } else {
                                 int tx = x + ex_(i);
                                 if (PRES) {
@@ -542,7 +567,7 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real, BLOCK>::value) step_ker
                                 }
                                 int tyw = ty;
                                 if (!WALLS) tyw = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
-                                A.fout[i * plane + (long long)tyw * nx + tx] = fs[i];
+                                out[tyw * rstride + i * nx + tx] = fs[i];
                             }
                         }
                     }
@@ -649,16 +674,16 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real, BLOCK>::value) step_ker
 // f = f_eq(rho0, 0) at every node.
 template <typename real>
 __global__ void init_kernel(const double *__restrict__ rho0, real *__restrict__ fa,
-                            real *__restrict__ fb, long long n)
+                            real *__restrict__ fb, int nx, int n)
 {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-         k += (long long)gridDim.x * blockDim.x) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int y = k / nx, x = k - y * nx;
         real fe[9];
         feq_pairs<real>((real)rho0[k], real(0), real(0), fe);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            fa[i * n + k] = fe[i];
-            fb[i * n + k] = fe[i];
+            fa[(9 * y + i) * nx + x] = fe[i];
+            fb[(9 * y + i) * nx + x] = fe[i];
         }
     }
 }

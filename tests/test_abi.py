@@ -52,7 +52,8 @@ def test_workspace_bytes(lbm):
     assert lbm.lbm_workspace_bytes(g64) >= 2 * 9 * 256 * 64 * 8
     for bad in [lbm.lbm_grid(0, 64, 0, 0, 32), lbm.lbm_grid(64, 3, 1, 0, 32),
                 lbm.lbm_grid(3, 64, 0, 1, 32), lbm.lbm_grid(64, 64, 0, 0, 16),
-                lbm.lbm_grid(64, 64, 2, 0, 32), lbm.lbm_grid(1 << 16, 1 << 15, 0, 0, 32)]:
+                lbm.lbm_grid(64, 64, 2, 0, 32), lbm.lbm_grid(1 << 16, 1 << 15, 0, 0, 32),
+                lbm.lbm_grid(16384, 16384, 1, 1, 32)]:  # 9 nx ny >= 2^31
         assert lbm.lbm_workspace_bytes(bad) == 0
 
 

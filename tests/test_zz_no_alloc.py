@@ -47,7 +47,14 @@ def test_noalloc_step_matches_context_step_twice(orc, lbm, precision):
         f2, d2 = lat.populations(), lat.diag()
         grid, eos, drive = lat.grid, lat.eos, lat.drive
 
-    a = torch.from_numpy(f0).to("cuda", tdt)
+    # the allocation-free step uses the library's row-interleaved layout f[y][i][x]
+    def to_rows(f):
+        return np.ascontiguousarray(f.transpose(1, 0, 2))
+
+    def from_rows(t):
+        return np.ascontiguousarray(t.cpu().numpy().transpose(1, 0, 2))
+
+    a = torch.from_numpy(to_rows(f0)).to("cuda", tdt)
     b = a.clone()  # slots no population reaches keep the input values, as in the context
     c = a.clone()
     diag = torch.zeros(2, 7, dtype=torch.float64, device="cuda")
@@ -60,8 +67,8 @@ def test_noalloc_step_matches_context_step_twice(orc, lbm, precision):
     torch.cuda.synchronize()
     u = np.uint32 if precision == 32 else np.uint64
     # same kernel, same launch geometry: identical bits
-    assert np.array_equal(b.cpu().numpy().view(u), f1.view(u))
-    assert np.array_equal(c.cpu().numpy().view(u), f2.view(u))
+    assert np.array_equal(from_rows(b).view(u), f1.view(u))
+    assert np.array_equal(from_rows(c).view(u), f2.view(u))
     dg = diag.cpu().numpy()
     tol = 1e-12 if precision == 64 else 1e-6
     # per-call diagnostics are those of the state each call read
