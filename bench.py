@@ -302,6 +302,11 @@ def run_ours(args, world, rank, local):
     e2e_t = time.perf_counter() - t0
     e2e_val = whole_job_mlups(world, nodes, args.steps, allreduce_max(e2e_t, dist, "cuda"))
 
+    sweep = None
+    if rank == 0 and world == 1 and not args.no_sweep:
+        from paper_2103_08301_gb300 import sweep_bench
+        sweep = sweep_bench.run(steps=200)
+
     if rank == 0:
         cpu = _cpu_baseline() if world == 1 else None
         line = {
@@ -324,6 +329,7 @@ def run_ours(args, world, rank, local):
             "gpu_launches": args.steps,
             "cpu_baseline": cpu,
             "diag": {"mass": d["mass"], "wall_shear_sum": d["wall_shear_sum"], "nan": d["nan_detected"]},
+            "batched_sweep": sweep,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -337,6 +343,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-sweep", action="store_true", help="skip the batched-sweep comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -185,7 +185,8 @@ typedef enum {
     LBM_OPT_CTAS_PER_SM = 1,
     LBM_OPT_REVERSE = 2,
     LBM_OPT_STRIP = 3,
-    LBM_OPT_STAGED = 4
+    LBM_OPT_STAGED = 4,
+    LBM_OPT_GRAPH_STEPS = 5 /* batches only: steps per CUDA graph replay (even, 0 = no graph) */
 } lbm_option;
 lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value);
 /* Launch geometry of the step kernel: CTAs, threads per CTA, work units and
@@ -230,6 +231,45 @@ void lbm_free(lbm_ctx *ctx);
 const char *lbm_status_string(lbm_status s);
 const char *lbm_last_error(const lbm_ctx *ctx);
 
+/* Batched channels -----------------------------------------------------------
+ * Many independent channels (the parameter sweeps of Sec. 3.3, Figs. 10-12:
+ * pressure drop, plug length and film thickness varied per channel) stepped
+ * together: one kernel launch per step covers every channel, the launches are
+ * replayed from a CUDA graph, and the work of all channels is split evenly over
+ * the CTAs. Each channel evolves bit for bit as it would in its own context.
+ * All channels share the EOS, tau, wetting, precision and boundary kinds
+ * (walls, bc_x); sizes, drives and initial densities differ. */
+typedef struct lbm_batch lbm_batch; /* opaque, owned by the library */
+
+/* n channels: grids[n] (same precision / walls / bc_x), drives[n] (may be
+ * NULL), rho0s[n] host arrays of nx*ny doubles. stream: cudaStream_t or NULL
+ * (the batch then creates its own non-blocking stream; graphs need a
+ * non-default stream). The library allocates the packed population buffers.
+ * Errors: LBM_ERR_ARG, LBM_ERR_PARAM, LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_batch_init(int32_t n, const lbm_grid *grids, const lbm_eos *eos, double tau, double wetting,
+                          const lbm_drive *drives, const double *const *rho0s, void *stream, lbm_batch **out);
+/* Advance every channel n steps (asynchronous; graph replays of
+ * LBM_OPT_GRAPH_STEPS steps, default 64, plus single launches). */
+lbm_status lbm_batch_step(lbm_batch *b, int64_t n);
+/* Per-channel outputs, as lbm_fields / lbm_diag / lbm_populations. */
+lbm_status lbm_batch_fields(lbm_batch *b, int32_t channel, void *rho, void *ux, void *uy, void *tau_wall,
+                            void *p_wall);
+lbm_status lbm_batch_diag(lbm_batch *b, int32_t channel, lbm_diag_t *out);
+lbm_status lbm_batch_populations(lbm_batch *b, int32_t channel, void *dst);
+/* Options as lbm_set_option plus LBM_OPT_GRAPH_STEPS. Changing the launch
+ * plan resets the diagnostic accumulators. */
+lbm_status lbm_batch_set_option(lbm_batch *b, lbm_option opt, int64_t value);
+lbm_status lbm_batch_launch_info(const lbm_batch *b, int64_t *ctas, int64_t *segments, int64_t *staged,
+                                 int64_t *strip);
+/* Autotuner: times trial_steps steps for each candidate launch plan (CTAs
+ * per SM, strip width) on a saved copy of the state, keeps the fastest,
+ * restores the state and returns the choice. Resets the diagnostic
+ * accumulators. */
+lbm_status lbm_batch_autotune(lbm_batch *b, int32_t trial_steps, int64_t *best_ctas_per_sm,
+                              int64_t *best_strip, double *best_ms_per_step);
+const char *lbm_batch_last_error(const lbm_batch *b);
+void lbm_batch_free(lbm_batch *b); /* NULL-safe */
+
 /* Host helpers (FP64, no GPU needed) ---------------------------------------*/
 
 /* Critical point, Maxwell coexistence (equal pressure and chemical
@@ -250,6 +290,27 @@ lbm_status lbm_airway_rho0(int32_t nx, int32_t ny, double film, double plug_x, d
 /* Initial density of a liquid disk of radius r0 centred at (cx, cy). */
 lbm_status lbm_disk_rho0(int32_t nx, int32_t ny, double cx, double cy, double r0, double rho_l,
                          double rho_g, double width, double noise_amp, uint64_t seed, double *out);
+
+/* Liquid-plug analysis of a density field (Sec. 3: plug interfaces, rupture
+ * and aerosol formation, Figs. 4, 7, 10-12), for a channel with walls at rows
+ * 0 and ny-1. A node is liquid when rho > rho_mid (use (rho_l + rho_g)/2).
+ *   x_rear, x_front: ends of the longest liquid run on the centre row
+ *       ny/2, interpolated linearly to rho_mid (NaN if the row has no liquid);
+ *   intact: 1 while some column is liquid on every fluid row (the plug still
+ *       closes the channel), 0 after rupture;
+ *   n_droplets, droplet_mass: liquid components (4-connected) that touch
+ *       neither first fluid row - droplets detached from the wall films
+ *       (aerosol) - and the sum of rho over them;
+ *   wall_liquid_mass: sum of rho over liquid components touching a wall row.
+ * rho: host array nx*ny (solid rows ignored). Errors: LBM_ERR_ARG. */
+typedef struct {
+    double x_rear, x_front;
+    int32_t intact;
+    int32_t n_droplets;
+    double droplet_mass;
+    double wall_liquid_mass;
+} lbm_plug_state;
+lbm_status lbm_plug_analysis(int32_t nx, int32_t ny, const double *rho, double rho_mid, lbm_plug_state *out);
 
 #ifdef __cplusplus
 }

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbm.so")
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_PARAM, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_NAN, LBM_ERR_STATE = range(7)
-LBM_OPT_CTAS_PER_SM, LBM_OPT_REVERSE, LBM_OPT_STRIP, LBM_OPT_STAGED = 1, 2, 3, 4
+LBM_OPT_CTAS_PER_SM, LBM_OPT_REVERSE, LBM_OPT_STRIP, LBM_OPT_STAGED, LBM_OPT_GRAPH_STEPS = 1, 2, 3, 4, 5
 
 
 class lbm_grid(C.Structure):
@@ -69,6 +69,19 @@ _SIGS = {
     "lbm_launch_info": (C.c_int, [_P] + [C.POINTER(C.c_int64)] * 4),
     "lbm_step_noalloc": (C.c_int, [C.POINTER(lbm_grid), C.POINTER(lbm_eos), C.c_double, C.c_double,
                                    C.POINTER(lbm_drive), _P, _P, C.c_int64, _P, _P]),
+    "lbm_batch_init": (C.c_int, [C.c_int32, C.POINTER(lbm_grid), C.POINTER(lbm_eos), C.c_double, C.c_double,
+                                 C.POINTER(lbm_drive), C.POINTER(C.POINTER(C.c_double)), _P, C.POINTER(_P)]),
+    "lbm_batch_step": (C.c_int, [_P, C.c_int64]),
+    "lbm_batch_fields": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P]),
+    "lbm_batch_diag": (C.c_int, [_P, C.c_int32, C.POINTER(lbm_diag_t)]),
+    "lbm_batch_populations": (C.c_int, [_P, C.c_int32, _P]),
+    "lbm_batch_set_option": (C.c_int, [_P, C.c_int, C.c_int64]),
+    "lbm_batch_launch_info": (C.c_int, [_P] + [C.POINTER(C.c_int64)] * 4),
+    "lbm_batch_autotune": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                     C.POINTER(C.c_double)]),
+    "lbm_batch_last_error": (C.c_char_p, [_P]),
+    "lbm_batch_free": (None, [_P]),
+    "lbm_plug_analysis": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_double, _P]),
     "lbm_free": (None, [_P]),
     "lbm_status_string": (C.c_char_p, [C.c_int]),
     "lbm_last_error": (C.c_char_p, [_P]),
@@ -151,6 +164,21 @@ def lbm_step_noalloc(grid, eos, tau, wetting, drive, f_in_ptr, f_out_ptr, ctas=0
                                       C.byref(drive) if drive is not None else None,
                                       _P(f_in_ptr), _P(f_out_ptr), int(ctas),
                                       _P(diag_ptr) if diag_ptr else None, _P(stream) if stream else None))
+
+
+class lbm_plug_state(C.Structure):
+    _fields_ = [("x_rear", C.c_double), ("x_front", C.c_double), ("intact", C.c_int32),
+                ("n_droplets", C.c_int32), ("droplet_mass", C.c_double), ("wall_liquid_mass", C.c_double)]
+
+
+def lbm_plug_analysis(rho, rho_mid):
+    """Plug interfaces, rupture state and aerosol droplets of a channel density field."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    ny, nx = rho.shape
+    st = lbm_plug_state()
+    _check(lib().lbm_plug_analysis(nx, ny, rho.ctypes.data_as(C.POINTER(C.c_double)), float(rho_mid),
+                                   _P(C.addressof(st))))
+    return {k: getattr(st, k) for k, _ in st._fields_}
 
 
 def lbm_coexistence(eos: lbm_eos):
@@ -264,6 +292,94 @@ class Lattice:
         if getattr(self, "ctx", None):
             lib().lbm_free(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Many channels of different sizes and drives stepped together.
+
+    channels: list of dicts with nx, ny, rho0 (ny x nx array) and optionally
+    dp, p_ref, gx, gy. Shared keyword arguments as for Lattice.
+    """
+
+    def __init__(self, channels, *, walls=True, bc_x=True, precision=32, a=1.0, b=4.0, R=1.0,
+                 T_over_Tc=0.85, k=1.0, kappa=0.5, tau=1.0, wetting=0.0, stream=None):
+        n = len(channels)
+        self.n = n
+        self.precision = precision
+        self.dtype = np.float32 if precision == 32 else np.float64
+        self.shapes = [(c["ny"], c["nx"]) for c in channels]
+        grids = (lbm_grid * n)(*[lbm_grid(c["nx"], c["ny"], int(walls), int(bc_x), int(precision))
+                                 for c in channels])
+        drives = (lbm_drive * n)(*[lbm_drive(c.get("dp", 0.0), math.nan if c.get("p_ref") is None else c["p_ref"],
+                                             c.get("gx", 0.0), c.get("gy", 0.0)) for c in channels])
+        self._rho0 = [np.ascontiguousarray(c["rho0"], dtype=np.float64) for c in channels]
+        ptrs = (C.POINTER(C.c_double) * n)(*[r.ctypes.data_as(C.POINTER(C.c_double)) for r in self._rho0])
+        self.eos = lbm_eos(a, b, R, T_over_Tc, k, kappa)
+        self._stream = stream
+        h = _P()
+        _check(lib().lbm_batch_init(n, grids, C.byref(self.eos), float(tau), float(wetting), drives, ptrs,
+                                    _P(stream.cuda_stream) if stream is not None else None, C.byref(h)))
+        self.h = h
+
+    def _chk(self, st):
+        if st != LBM_OK:
+            raise LBMError(st, lib().lbm_batch_last_error(self.h).decode())
+
+    def step(self, n=1):
+        st = lib().lbm_batch_step(self.h, int(n))
+        if st == LBM_ERR_NAN:
+            raise LBMError(st, "a step met a non-finite or non-positive density")
+        self._chk(st)
+
+    def fields(self, c):
+        ny, nx = self.shapes[c]
+        out = {k: np.zeros((ny, nx), self.dtype) for k in ("rho", "vx", "vy")}
+        out["tau_wall"] = np.zeros((2, nx), self.dtype)
+        out["p_wall"] = np.zeros((2, nx), self.dtype)
+        p = [_P(out[k].ctypes.data) for k in ("rho", "vx", "vy", "tau_wall", "p_wall")]
+        self._chk(lib().lbm_batch_fields(self.h, int(c), *p))
+        return out
+
+    def diag(self, c):
+        d = lbm_diag_t()
+        self._chk(lib().lbm_batch_diag(self.h, int(c), C.byref(d)))
+        return d.as_dict()
+
+    def populations(self, c):
+        ny, nx = self.shapes[c]
+        f = np.empty((9, ny, nx), self.dtype)
+        self._chk(lib().lbm_batch_populations(self.h, int(c), _P(f.ctypes.data)))
+        return f
+
+    def set_option(self, opt, value):
+        self._chk(lib().lbm_batch_set_option(self.h, int(opt), int(value)))
+
+    def launch_info(self):
+        v = [C.c_int64() for _ in range(4)]
+        self._chk(lib().lbm_batch_launch_info(self.h, *[C.byref(x) for x in v]))
+        return dict(zip(("ctas", "segments", "staged", "strip"), [x.value for x in v]))
+
+    def autotune(self, trial_steps=20):
+        c, w, ms = C.c_int64(), C.c_int64(), C.c_double()
+        self._chk(lib().lbm_batch_autotune(self.h, int(trial_steps), C.byref(c), C.byref(w), C.byref(ms)))
+        return {"ctas_per_sm": c.value, "strip": w.value, "ms_per_step": ms.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lbm_batch_free(self.h)
+            self.h = None
 
     def __del__(self):
         try:

@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "liblbm.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["lbm_api.cu", "lbm_host.cpp", "lbm_kernels.cuh", "lbm_internal.h"]
+SOURCES = ["lbm_api.cu", "lbm_batch.cu", "lbm_host.cpp", "lbm_kernels.cuh", "lbm_internal.h"]
 
 
 def _stale() -> bool:
@@ -47,20 +47,26 @@ def build(force: bool = False, verbose: bool = False, out: str | None = None) ->
     bdir = BUILD if out is None else out + ".build"
     os.makedirs(bdir, exist_ok=True)
     api_o = os.path.join(bdir, "lbm_api.o")
+    batch_o = os.path.join(bdir, "lbm_batch.o")
     host_o = os.path.join(bdir, "lbm_host.o")
     extra = os.environ.get("LBM_NVCC_FLAGS", "").split()  # tuning experiments, e.g. -DLBM_STAGE_AHEAD=2
-    nv = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-          "-I", CSRC, *extra, "-c", os.path.join(CSRC, "lbm_api.cu"), "-o", api_o]
-    if verbose:
-        nv.insert(1, "-Xptxas=-v")
+
+    def nvcc(src, obj):
+        cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
+               "-I", CSRC, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        return cmd
+
     gxx = ["g++", "-O2", "-std=c++17", "-fPIC", "-I", INCLUDE, "-I", CSRC, "-c",
            os.path.join(CSRC, "lbm_host.cpp"), "-o", host_o]
-    with ThreadPoolExecutor(2) as ex:
-        outs = list(ex.map(_run, [nv, gxx]))
+    with ThreadPoolExecutor(3) as ex:
+        outs = list(ex.map(_run, [nvcc("lbm_api.cu", api_o), nvcc("lbm_batch.cu", batch_o), gxx]))
     if verbose:
         print(outs[0])
+        print(outs[1])
     tmp = lib + f".tmp{os.getpid()}"
-    _run([NVCC, *ARCH, "-shared", "-o", tmp, api_o, host_o, "-lcudart"])
+    _run([NVCC, *ARCH, "-shared", "-o", tmp, api_o, batch_o, host_o, "-lcudart"])
     os.replace(tmp, lib)
     return lib
 

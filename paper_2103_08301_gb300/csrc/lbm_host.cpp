@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <vector>
 
 #include "lbm.h"
 #include "lbm_internal.h"
@@ -218,3 +219,80 @@ lbm_status lbm_disk_rho0(int32_t nx, int32_t ny, double cx, double cy, double r0
 }
 
 } // extern "C"
+
+extern "C" lbm_status lbm_plug_analysis(int32_t nx, int32_t ny, const double *rho, double rho_mid,
+                                        lbm_plug_state *out)
+{
+    if (nx <= 0 || ny < 4 || !rho || !out || !std::isfinite(rho_mid)) return LBM_ERR_ARG;
+    const int y0 = 1, y1 = ny - 2;  // fluid rows
+    auto liquid = [&](int x, int y) { return rho[(size_t)y * nx + x] > rho_mid; };
+
+    // plug ends on the centre row: the longest run of liquid nodes
+    const int yc = ny / 2;
+    int best_a = -1, best_b = -1;
+    for (int x = 0; x < nx;) {
+        if (!liquid(x, yc)) { ++x; continue; }
+        int e = x;
+        while (e + 1 < nx && liquid(e + 1, yc)) ++e;
+        if (e - x > best_b - best_a) { best_a = x; best_b = e; }
+        x = e + 1;
+    }
+    out->x_rear = out->x_front = NAN;
+    if (best_a >= 0) {
+        const double *r = rho + (size_t)yc * nx;
+        // crossing of rho_mid between the outer gas node and the liquid end node
+        out->x_rear = best_a > 0 ? (best_a - 1) + (rho_mid - r[best_a - 1]) / (r[best_a] - r[best_a - 1])
+                                 : (double)best_a;
+        out->x_front = best_b < nx - 1 ? best_b + (r[best_b] - rho_mid) / (r[best_b] - r[best_b + 1])
+                                       : (double)best_b;
+    }
+
+    // intact: some column liquid on every fluid row
+    out->intact = 0;
+    for (int x = 0; x < nx && !out->intact; ++x) {
+        bool full = true;
+        for (int y = y0; y <= y1 && full; ++y) full = liquid(x, y);
+        if (full) out->intact = 1;
+    }
+
+    // 4-connected liquid components (iterative flood fill), classified by wall contact
+    std::vector<int32_t> label((size_t)nx * ny, -1);
+    std::vector<int32_t> stack;
+    out->n_droplets = 0;
+    out->droplet_mass = 0.0;
+    out->wall_liquid_mass = 0.0;
+    int32_t next = 0;
+    for (int y = y0; y <= y1; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const size_t c0 = (size_t)y * nx + x;
+            if (label[c0] >= 0 || !liquid(x, y)) continue;
+            bool wall = false;
+            double m = 0.0;
+            stack.clear();
+            stack.push_back((int32_t)c0);
+            label[c0] = next;
+            while (!stack.empty()) {
+                const size_t c = (size_t)stack.back();
+                stack.pop_back();
+                const int cx = (int)(c % nx), cy = (int)(c / nx);
+                m += rho[c];
+                if (cy == y0 || cy == y1) wall = true;
+                const int nbx[4] = {cx - 1, cx + 1, cx, cx}, nby[4] = {cy, cy, cy - 1, cy + 1};
+                for (int k = 0; k < 4; ++k) {
+                    if (nbx[k] < 0 || nbx[k] >= nx || nby[k] < y0 || nby[k] > y1) continue;
+                    const size_t d = (size_t)nby[k] * nx + nbx[k];
+                    if (label[d] < 0 && liquid(nbx[k], nby[k])) {
+                        label[d] = next;
+                        stack.push_back((int32_t)d);
+                    }
+                }
+            }
+            ++next;
+            if (wall) out->wall_liquid_mass += m;
+            else {
+                out->n_droplets += 1;
+                out->droplet_mass += m;
+            }
+        }
+    return LBM_OK;
+}

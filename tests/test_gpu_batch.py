@@ -1,0 +1,98 @@
+"""Batched channels (lbm_batch_*) against single-channel contexts.
+
+Each channel of a batch runs the same per-segment code as a single-channel
+context, so its populations must agree bit for bit; per-channel diagnostics are
+sums over differently cut segments and agree to rounding.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+KW = dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5)
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_08301_gb300 import build
+    build.build()
+    import paper_2103_08301_gb300 as m
+    return m
+
+
+def _channels(orc, specs):
+    s = orc.Setup(nx=64, ny=16, **KW, dp=0.0)
+    g, l, _ = s.coexistence()
+    out = []
+    for nx, ny, dp, film, plug_x, plug_len in specs:
+        out.append({"nx": nx, "ny": ny, "dp": dp,
+                    "rho0": synth.airway_rho0(nx, ny, film, plug_x, plug_len, l, g)})
+    return out
+
+
+STAGED_SPECS = [(256, 40, 1e-3, 4, 60, 30), (384, 64, 5e-4, 6, 90, 48), (1024, 96, 2e-3, 8, 256, 64),
+                (132, 24, 1.5e-3, 3, 30, 20), (512, 130, 8e-4, 10, 128, 40)]
+RAGGED_SPECS = [(301, 40, 1e-3, 4, 60, 30), (129, 33, 5e-4, 3, 40, 16), (250, 64, 2e-3, 6, 64, 32)]
+
+
+def _single(lbm, ch, precision, steps):
+    with lbm.Lattice(ch["nx"], ch["ny"], ch["rho0"], precision=precision, dp=ch["dp"], **KW) as lat:
+        lat.step(steps)
+        return lat.populations(), lat.diag()
+
+
+@pytest.mark.parametrize("specs,staged", [(STAGED_SPECS, True), (RAGGED_SPECS, False)])
+@pytest.mark.parametrize("precision", [32, 64])
+def test_batch_matches_single_channels_bitwise(orc, lbm, specs, staged, precision):
+    chans = _channels(orc, specs)
+    steps = 150  # two 64-step graph replays and 22 single launches
+    with lbm.Batch(chans, precision=precision, **KW) as b:
+        assert b.launch_info()["staged"] == int(staged)
+        b.step(steps)
+        got = [(b.populations(c), b.diag(c)) for c in range(len(chans))]
+    u = np.uint32 if precision == 32 else np.uint64
+    for c, ch in enumerate(chans):
+        f_ref, d_ref = _single(lbm, ch, precision, steps)
+        assert np.array_equal(got[c][0].view(u), f_ref.view(u)), f"channel {c}"
+        d = got[c][1]
+        assert d["step"] == steps
+        assert abs(d["mass"] / d_ref["mass"] - 1) < (1e-13 if precision == 64 else 1e-6)
+        assert abs(d["wall_shear_sum"] - d_ref["wall_shear_sum"]) <= 1e-9 * abs(d_ref["wall_shear_sum"]) + 1e-15
+        assert d["tau_wall_max"] == pytest.approx(d_ref["tau_wall_max"], rel=1e-6, abs=1e-12)
+        assert d["rho_in"] == d_ref["rho_in"] and d["rho_out"] == d_ref["rho_out"]
+
+
+def test_batch_matches_oracle_fp64(orc, lbm):
+    chans = _channels(orc, STAGED_SPECS[:3])
+    with lbm.Batch(chans, precision=64, **KW) as b:
+        b.step(300)
+        rho = [b.fields(c)["rho"] for c in range(3)]
+    for c, ch in enumerate(chans):
+        s = orc.Setup(nx=ch["nx"], ny=ch["ny"], dp=ch["dp"], **KW)
+        f, _ = orc.run(s, orc.init(s, ch["rho0"]), 300)
+        ref = orc.fields(s, f)["rho"]
+        assert np.abs(rho[c] - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_graph_reverse_and_autotune_keep_results(orc, lbm):
+    chans = _channels(orc, STAGED_SPECS)
+    outs = []
+    for mode in ("graph", "nograph", "reverse", "autotune"):
+        with lbm.Batch(chans, precision=32, **KW) as b:
+            if mode == "nograph":
+                b.set_option(lbm.LBM_OPT_GRAPH_STEPS, 0)
+            if mode == "reverse":
+                b.set_option(lbm.LBM_OPT_REVERSE, 1)
+            if mode == "autotune":
+                best = b.autotune(trial_steps=4)
+                assert best["ctas_per_sm"] >= 1 and best["strip"] in (64, 128)
+                assert best["ms_per_step"] > 0
+            b.step(130)
+            outs.append(np.concatenate([b.populations(c).ravel() for c in range(len(chans))]))
+    for o in outs[1:]:
+        assert np.array_equal(o.view(np.uint32), outs[0].view(np.uint32))
