@@ -287,6 +287,16 @@ lbm_status lbm_airway_rho0(int32_t nx, int32_t ny, double film, double plug_x, d
                            double rho_l, double rho_g, double width, double noise_amp,
                            uint64_t seed, double *out);
 
+/* Partial derivatives of the noise-free airway profile of lbm_airway_rho0
+ * with respect to the film thickness and the plug length:
+ * d_film = (rho_l - rho_g) dS/dfilm, d_plug = (rho_l - rho_g) dS/dplug_len,
+ * with S = max(s_film, s_plug) differentiated along the larger profile (the
+ * film where they tie). Outputs: host arrays of nx*ny doubles (either may be
+ * NULL). Errors: LBM_ERR_ARG. */
+lbm_status lbm_airway_rho0_tangent(int32_t nx, int32_t ny, double film, double plug_x, double plug_len,
+                                   double rho_l, double rho_g, double width, double *d_film,
+                                   double *d_plug);
+
 /* Initial density of a liquid disk of radius r0 centred at (cx, cy). */
 lbm_status lbm_disk_rho0(int32_t nx, int32_t ny, double cx, double cy, double r0, double rho_l,
                          double rho_g, double width, double noise_amp, uint64_t seed, double *out);
@@ -311,6 +321,41 @@ typedef struct {
     double wall_liquid_mass;
 } lbm_plug_state;
 lbm_status lbm_plug_analysis(int32_t nx, int32_t ny, const double *rho, double rho_mid, lbm_plug_state *out);
+
+/* ------------------------------------------------------------------------ */
+/* Discrete adjoint (precision-64 channels)                                  */
+/* ------------------------------------------------------------------------ */
+/* Gradients of the time-integrated wall loads of Sec. 3 (Figs. 10-12),
+ * summed over the states n = 0 .. nsteps-1 that nsteps steps read and over the
+ * interior columns of both walls:
+ *   J[0] = J_tau = sum_n sum_x tau_w,   J[1] = J_p = sum_n sum_x p_w,
+ * tau_w and p_w as lbm_fields reports them (p_w: Eq. 2.4). The adjoint is the
+ * exact transpose of the linearised step of lbm_step (a pressure column's
+ * clamped phase weight contributes no derivative), run backwards over blocks
+ * of block_steps steps recomputed from checkpoints kept in device memory
+ * (9 nx ny doubles per checkpoint: ceil(nsteps/K) checkpoints plus K states
+ * of one block; K = block_steps, or ceil(sqrt(nsteps)) if 0).
+ *
+ * lbm_adjoint_init: grid->precision must be 64 (LBM_ERR_ARG otherwise);
+ *   nsteps >= 1. Allocates on the current device; stream as in lbm_init.
+ * lbm_adjoint_forward: runs nsteps steps from f0 = f_eq(rho0, 0) under
+ *   `drive` (NULL: no drive), keeping checkpoints, and returns J (host,
+ *   2 doubles). rho0: nx*ny doubles, host or device. Synchronises the stream.
+ *   LBM_ERR_NAN if a step met a bad density; LBM_ERR_PARAM as lbm_init.
+ * lbm_adjoint_backward: gradients of w_tau J_tau + w_p J_p for the last
+ *   forward: grad_rho0 (nx*ny doubles, host or device) and grad_drive (host,
+ *   3 doubles: d/d dp, d/d gx, d/d gy; dp enters through the pressure-column
+ *   densities, which are EOS roots at p_ref +- dp/2). May be called several
+ *   times after one forward. LBM_ERR_STATE before any forward.
+ * The handle owns all its memory; lbm_adjoint_free is NULL-safe. */
+typedef struct lbm_adjoint lbm_adjoint;
+lbm_status lbm_adjoint_init(const lbm_grid *grid, const lbm_eos *eos, double tau, double wetting,
+                            int64_t nsteps, int64_t block_steps, void *stream, lbm_adjoint **out);
+lbm_status lbm_adjoint_forward(lbm_adjoint *adj, const lbm_drive *drive, const double *rho0, double *J);
+lbm_status lbm_adjoint_backward(lbm_adjoint *adj, double w_tau, double w_p, double *grad_rho0,
+                                double *grad_drive);
+const char *lbm_adjoint_last_error(const lbm_adjoint *adj);
+void lbm_adjoint_free(lbm_adjoint *adj);
 
 #ifdef __cplusplus
 }

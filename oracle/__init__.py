@@ -50,7 +50,8 @@ class Params(C.Structure):
 
 class Diag(C.Structure):
     _fields_ = [("mass", C.c_double), ("J", C.c_double), ("tw_min", C.c_double),
-                ("tw_max", C.c_double), ("pw_min", C.c_double), ("pw_max", C.c_double)]
+                ("tw_max", C.c_double), ("pw_min", C.c_double), ("pw_max", C.c_double),
+                ("Jp", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -67,6 +67,7 @@ typedef struct {
     double J;      /* sum over columns of bottom + top wall shear stress of that state */
     double tw_min, tw_max; /* extrema of wall shear over both walls */
     double pw_min, pw_max; /* extrema of wall pressure over both walls */
+    double Jp;     /* sum over columns of bottom + top wall pressure of that state */
 } orc_diag;
 
 /* ------------------------------------------------------------------------- */
@@ -508,6 +509,7 @@ static void diag_of(const orc_params *p, const orc_work *w, orc_diag *d)
     }
     d->mass = s + comp;
     d->J = 0.0;
+    d->Jp = 0.0;
     d->tw_min = d->pw_min = INFINITY;
     d->tw_max = d->pw_max = -INFINITY;
     if (!p->walls) { d->tw_min = d->tw_max = d->pw_min = d->pw_max = 0.0; return; }
@@ -519,6 +521,7 @@ static void diag_of(const orc_params *p, const orc_work *w, orc_diag *d)
             if (is_pressure_col(p, x)) continue;
             double t = tw[side * nx + x], q = pw[side * nx + x];
             d->J += t;
+            d->Jp += q;
             if (t < d->tw_min) d->tw_min = t;
             if (t > d->tw_max) d->tw_max = t;
             if (q < d->pw_min) d->pw_min = q;
@@ -633,13 +636,14 @@ int orc_run(const orc_params *p, double *f, long nsteps, orc_diag *acc)
     const long n = (long)p->nx * p->ny;
     double *g = malloc((size_t)Q * n * sizeof(double));
     if (!g) return 1;
-    orc_diag tot = {0.0, 0.0, INFINITY, -INFINITY, INFINITY, -INFINITY};
+    orc_diag tot = {0.0, 0.0, INFINITY, -INFINITY, INFINITY, -INFINITY, 0.0};
     double *a = f, *b = g;
     for (long s = 0; s < nsteps; ++s) {
         orc_diag d;
         if (orc_step(p, a, b, &d)) { free(g); return 1; }
         tot.mass = d.mass;
         tot.J += d.J;
+        tot.Jp += d.Jp;
         if (d.tw_min < tot.tw_min) tot.tw_min = d.tw_min;
         if (d.tw_max > tot.tw_max) tot.tw_max = d.tw_max;
         if (d.pw_min < tot.pw_min) tot.pw_min = d.pw_min;

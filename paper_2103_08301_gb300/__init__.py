@@ -92,6 +92,15 @@ _SIGS = {
     "lbm_disk_rho0": (C.c_int, [C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
                                 C.c_double, C.c_double, C.c_double, C.c_double, C.c_uint64,
                                 C.POINTER(C.c_double)]),
+    "lbm_airway_rho0_tangent": (C.c_int, [C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
+                                          C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double),
+                                          C.POINTER(C.c_double)]),
+    "lbm_adjoint_init": (C.c_int, [C.POINTER(lbm_grid), C.POINTER(lbm_eos), C.c_double, C.c_double,
+                                   C.c_int64, C.c_int64, _P, C.POINTER(_P)]),
+    "lbm_adjoint_forward": (C.c_int, [_P, C.POINTER(lbm_drive), _P, C.POINTER(C.c_double)]),
+    "lbm_adjoint_backward": (C.c_int, [_P, C.c_double, C.c_double, _P, C.POINTER(C.c_double)]),
+    "lbm_adjoint_last_error": (C.c_char_p, [_P]),
+    "lbm_adjoint_free": (None, [_P]),
 }
 
 _lib = None
@@ -192,6 +201,16 @@ def lbm_airway_rho0(nx, ny, film, plug_x, plug_len, rho_l, rho_g, width=4.0, noi
     _check(lib().lbm_airway_rho0(nx, ny, film, plug_x, plug_len, rho_l, rho_g, width, noise, seed,
                                  out.ctypes.data_as(C.POINTER(C.c_double))))
     return out
+
+
+def lbm_airway_rho0_tangent(nx, ny, film, plug_x, plug_len, rho_l, rho_g, width=4.0):
+    """(d rho0 / d film, d rho0 / d plug_len) of the noise-free airway profile."""
+    d_film = np.empty((ny, nx), dtype=np.float64)
+    d_plug = np.empty((ny, nx), dtype=np.float64)
+    _check(lib().lbm_airway_rho0_tangent(nx, ny, film, plug_x, plug_len, rho_l, rho_g, width,
+                                         d_film.ctypes.data_as(C.POINTER(C.c_double)),
+                                         d_plug.ctypes.data_as(C.POINTER(C.c_double))))
+    return d_film, d_plug
 
 
 def lbm_disk_rho0(nx, ny, cx, cy, r0, rho_l, rho_g, width=4.0, noise=0.0, seed=1):

@@ -202,6 +202,29 @@ lbm_status lbm_airway_rho0(int32_t nx, int32_t ny, double film, double plug_x, d
     return LBM_OK;
 }
 
+lbm_status lbm_airway_rho0_tangent(int32_t nx, int32_t ny, double film, double plug_x, double plug_len,
+                                   double rho_l, double rho_g, double width, double *d_film, double *d_plug)
+{
+    if (nx <= 0 || ny <= 0 || !(width > 0)) return LBM_ERR_ARG;
+    for (int32_t y = 0; y < ny; ++y)
+        for (int32_t x = 0; x < nx; ++x) {
+            double d_wall = std::fmin(y - 0.5, (ny - 1.5) - y);
+            double af = 2.0 * (d_wall - film) / width;
+            double a0 = 2.0 * (x - plug_x) / width, a1 = 2.0 * (x - plug_x - plug_len) / width;
+            double s_film = 0.5 * (1.0 - std::tanh(af));
+            double s_plug = 0.5 * (std::tanh(a0) - std::tanh(a1));
+            // d/dh of 0.5 (1 - tanh(2 (d - h) / W)) = sech^2(.) / W; likewise for L
+            double cf = std::cosh(af), cp = std::cosh(a1);
+            double df = 0.0, dl = 0.0;
+            if (s_film >= s_plug) df = 1.0 / (width * cf * cf);
+            else dl = 1.0 / (width * cp * cp);
+            size_t node = (size_t)y * nx + x;
+            if (d_film) d_film[node] = (rho_l - rho_g) * df;
+            if (d_plug) d_plug[node] = (rho_l - rho_g) * dl;
+        }
+    return LBM_OK;
+}
+
 lbm_status lbm_disk_rho0(int32_t nx, int32_t ny, double cx, double cy, double r0, double rho_l,
                          double rho_g, double width, double noise_amp, uint64_t seed, double *out)
 {

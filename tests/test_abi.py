@@ -105,3 +105,35 @@ def test_splitmix64_known_values():
     states = np.array([(k * gamma) % (1 << 64) for k in range(3)], dtype=np.uint64)
     out = [int(v) for v in synth.splitmix64(states)]
     assert out == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_airway_tangent_matches_central_differences(lbm):
+    # d rho0 / d film and d rho0 / d plug_len against central differences of
+    # the seeded generator (the profile is smooth away from the film/plug tie)
+    nx, ny, h, x0, L, rl, rg = 160, 48, 6.3, 40.0, 27.7, 0.28, 0.03
+    d_film, d_plug = lbm.lbm_airway_rho0_tangent(nx, ny, h, x0, L, rl, rg, 4.0)
+    e = 1e-5
+    fd_film = (synth.airway_rho0(nx, ny, h + e, x0, L, rl, rg) - synth.airway_rho0(nx, ny, h - e, x0, L, rl, rg)) / (2 * e)
+    fd_plug = (synth.airway_rho0(nx, ny, h, x0, L + e, rl, rg) - synth.airway_rho0(nx, ny, h, x0, L - e, rl, rg)) / (2 * e)
+    assert np.abs(d_film - fd_film).max() < 1e-8
+    assert np.abs(d_plug - fd_plug).max() < 1e-8
+    assert np.abs(d_film).max() > 0.01 and np.abs(d_plug).max() > 0.01
+
+
+def test_adjoint_rejects_bad_arguments_before_touching_the_gpu(lbm):
+    import ctypes as C
+    e = lbm.lbm_eos(1.0, 4.0, 1.0, 0.85, 1.0, 0.5)
+    h = C.c_void_p()
+    # FP32 channels are not differentiated
+    st = lbm.lib().lbm_adjoint_init(C.byref(lbm.lbm_grid(64, 32, 1, 1, 32)), C.byref(e), 1.0, 0.0, 10, 0, None,
+                                    C.byref(h))
+    assert st == lbm.LBM_ERR_ARG and not h.value
+    st = lbm.lib().lbm_adjoint_init(C.byref(lbm.lbm_grid(64, 32, 1, 1, 64)), C.byref(e), 1.0, 0.0, 0, 0, None,
+                                    C.byref(h))
+    assert st == lbm.LBM_ERR_ARG
+    st = lbm.lib().lbm_adjoint_init(C.byref(lbm.lbm_grid(64, 32, 1, 1, 64)), C.byref(e), 0.5, 0.0, 10, 0, None,
+                                    C.byref(h))
+    assert st == lbm.LBM_ERR_PARAM
+    g = (C.c_double * 3)()
+    assert lbm.lib().lbm_adjoint_backward(None, 1.0, 0.0, None, g) == lbm.LBM_ERR_ARG
+    lbm.lib().lbm_adjoint_free(None)  # NULL-safe

@@ -42,6 +42,9 @@ CASES = {
     "ragged129x20": dict(nx=129, ny=20, kw=dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=2e-4)),
     # walls, periodic x, wetting offset
     "wet96x40": dict(nx=96, ny=40, kw=dict(walls=True, T_over_Tc=0.8, kappa=0.5, wet=0.01)),
+    # the paper's drive: body force along the channel, ends at one pressure
+    "bodyforce256x64": dict(nx=256, ny=64, kw=dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=0.0,
+                                                  gx=1e-6)),
 }
 
 
@@ -59,6 +62,8 @@ def _rho0(orc, name, c):
         return synth.airway_rho0(nx, ny, 3, 40, 20, l, g)
     if name == "wet96x40":
         return synth.disk_rho0(nx, ny, 14, l, g, centre=(48.0, 0.5))
+    if name == "bodyforce256x64":
+        return synth.airway_rho0(nx, ny, 5, 64, 32, l, g, noise=1e-3, seed=2)
     raise KeyError(name)
 
 

@@ -183,3 +183,42 @@ def test_pressure_columns_drive_poiseuille_flow(orc):
     assert np.abs(v - c * shape).max() < 2e-3 * v.max()
     G = dp / (nx - 1)  # pressure gradient between the column centres
     assert abs(c / (G / (2 * fl["rho"][ny // 2, nx // 2] * NU1)) - 1) < 0.01
+
+
+def test_wall_pressure_sum_of_resting_channel(orc):
+    # A uniform channel at rest between walls (periodic in x) is invariant;
+    # with no density gradient Eq. 2.4 leaves p_w = k^2 p0(rho) at every wall
+    # column, so J_p = steps * 2 * nx * k^2 p0(rho) and the wall shear vanishes.
+    for k in (1.0, 0.7):
+        s = orc.Setup(nx=10, ny=9, walls=True, T_over_Tc=0.9, kappa=0.5, k=k)
+        rho = 0.12
+        f = orc.init(s, np.full((9, 10), rho))
+        _, d = orc.run(s, f, 7)
+        p0 = orc.cs_p0(s.a, s.b, s.R, s.T, rho)
+        assert d["Jp"] == pytest.approx(7 * 2 * 10 * k * k * p0, rel=1e-13)
+        assert abs(d["J"]) < 1e-15
+
+
+def test_body_force_drive_with_extrapolated_ends(orc):
+    # The paper's drive (Sec. 2.2): a body force G along the channel, the ends
+    # held at one pressure (dp = 0) by non-equilibrium extrapolation. Single
+    # phase, kappa = 0: the developed flow is Poiseuille on the half-way wall
+    # planes with amplitude (G - dp/dx) / (2 rho nu), dp/dx the small pressure
+    # gradient (p = k^2 p0(rho)) the extrapolated ends leave in the bulk.
+    nx, ny, H, G = 128, 34, 32, 2e-7
+    Tc, _ = orc.cs_critical()
+    pref = orc.cs_p0(1.0, 4.0, 1.0, 1.5 * Tc, 0.2)
+    s = orc.Setup(nx=nx, ny=ny, walls=True, bc_x=True, T_over_Tc=1.5, kappa=0.0, dp=0.0, p_ref=pref, gx=G)
+    assert s.rho_in == s.rho_out
+    f = orc.init(s, np.full((ny, nx), s.rho_in))
+    f, _ = orc.run(s, f, 20000)
+    fl = orc.fields(s, f)
+    y = np.arange(1, ny - 1)
+    shape = (y - 0.5) * (H + 0.5 - y)
+    p1, p3 = (orc.cs_p0(s.a, s.b, s.R, s.T, float(fl["rho"][ny // 2, x])) for x in (nx // 4, 3 * nx // 4))
+    dpdx = (p3 - p1) / (nx // 2)
+    assert 0 < dpdx < 0.02 * G  # a slight adverse gradient
+    for x in (nx // 4, nx // 2, 3 * nx // 4):
+        v = fl["vx"][1:ny - 1, x]
+        exact = (G - dpdx) / (2 * fl["rho"][ny // 2, x] * NU1) * shape
+        assert np.abs(v - exact).max() < 1e-3 * exact.max()
