@@ -71,15 +71,25 @@ typedef struct {
     int32_t precision; /* 32 (float state) or 64 (double state) */
 } lbm_grid;
 
-/* Carnahan-Starling EOS and the model coefficients of Eq. 2.17.
- * T = T_over_Tc * Tc with Tc the EOS critical temperature.
+/* Equation of state and the model coefficients of Eq. 2.17.
+ * kind 0 (LBM_EOS_CS): Carnahan-Starling, p0 = rho R T (1 + e + e^2 - e^3)/(1 - e)^3
+ *   - a rho^2 with e = b rho / 4 (the default of a zero-initialised field).
+ * kind 1 (LBM_EOS_PR): Peng-Robinson (Eq. 2.18), p0 = rho R T / (1 - b rho)
+ *   - a alpha rho^2 / (1 + 2 b rho - b^2 rho^2), alpha = [1 + (0.37464 +
+ *   1.54226 omega - 0.26992 omega^2)(1 - sqrt(T/Tc))]^2 (the standard form of
+ *   the temperature function, which the paper prints garbled).
+ * T = T_over_Tc * Tc with Tc the EOS critical temperature (PR: alpha(Tc) = 1).
  * k: proportional coefficient (Eq. 2.13); the mesh-space EOS is k^2 p0 (Eq. 2.14).
- * kappa: gradient coefficient of Eq. 2.17, taken in mesh units. */
+ * kappa: gradient coefficient of Eq. 2.17, taken in mesh units.
+ * omega: PR acentric factor (0.344 water, 0.011 methane); unused for CS. */
+enum { LBM_EOS_CS = 0, LBM_EOS_PR = 1 };
 typedef struct {
     double a, b, R;
     double T_over_Tc;
     double k;
     double kappa;
+    int32_t kind;
+    double omega;
 } lbm_eos;
 
 /* Driving. With bc_x = 1 the inlet and outlet columns carry the mesh
@@ -169,6 +179,24 @@ lbm_status lbm_load_populations(lbm_ctx *ctx, const void *src);
 size_t lbm_checkpoint_bytes(const lbm_ctx *ctx);
 lbm_status lbm_checkpoint(lbm_ctx *ctx, void *host_buf, size_t bytes);
 lbm_status lbm_restore(lbm_ctx *ctx, const void *host_buf, size_t bytes);
+
+/* Collision operator (Sec. 2.1). kind 0 (LBM_COLL_BGK): single relaxation
+ * time tau, equilibrium velocity u + tau F / rho (the default). kind 1
+ * (LBM_COLL_MRT): multiple relaxation times (Eq. 2.1) in the Lallemand-Luo
+ * moment basis (rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy) with
+ * S = diag(0, s_e, s_eps, s_j, s_q, s_j, s_q, s_nu, s_nu); s_nu <= 0 means
+ * 1/tau. The velocity-shift force enters through the equilibrium velocity
+ * u + F / (s_j rho), so the relaxed momentum gains F per step; s_j = 1/tau
+ * with every rate 1/tau is BGK. The paper's rates are s_e = 1.64,
+ * s_eps = 1.54, s_q = 1.7, s_nu = 1/tau. NULL restores BGK. Applies to
+ * steps issued afterwards. Errors: LBM_ERR_ARG (kind, or a rate outside
+ * (0, 2) other than s_nu <= 0). */
+enum { LBM_COLL_BGK = 0, LBM_COLL_MRT = 1 };
+typedef struct {
+    int32_t kind;
+    double s_e, s_eps, s_j, s_q, s_nu;
+} lbm_collision;
+lbm_status lbm_set_collision(lbm_ctx *ctx, const lbm_collision *c);
 
 /* Launch tuning and test hooks (set before stepping; changing the CTA count
  * resets the diagnostic accumulators):

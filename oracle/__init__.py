@@ -45,7 +45,15 @@ class Params(C.Structure):
                 ("k", C.c_double), ("kappa", C.c_double), ("tau", C.c_double), ("wet", C.c_double),
                 ("rho_in_g", C.c_double), ("rho_in_l", C.c_double), ("rho_out_g", C.c_double),
                 ("rho_out_l", C.c_double), ("ph_g", C.c_double), ("ph_l", C.c_double),
-                ("gx", C.c_double), ("gy", C.c_double)]
+                ("gx", C.c_double), ("gy", C.c_double),
+                ("eos_kind", C.c_int32), ("collision", C.c_int32), ("aalpha", C.c_double),
+                ("s_e", C.c_double), ("s_eps", C.c_double), ("s_j", C.c_double), ("s_q", C.c_double),
+                ("s_nu", C.c_double)]
+
+
+class Eos(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("a", C.c_double), ("b", C.c_double), ("R", C.c_double),
+                ("T", C.c_double), ("aalpha", C.c_double)]
 
 
 class Diag(C.Structure):
@@ -74,6 +82,18 @@ def lib():
         L.orc_maxwell.argtypes = [_D, _D, _D, _D, _PD, _PD, _PD]
         L.orc_gas_root.argtypes = [_D, _D, _D, _D, _D, _PD]
         L.orc_liquid_root.argtypes = [_D, _D, _D, _D, _D, _PD]
+        for name in ("orc_eos_p0", "orc_eos_dp0", "orc_eos_mu"):
+            getattr(L, name).restype = _D
+            getattr(L, name).argtypes = [C.POINTER(Eos), _D]
+        L.orc_pr_alpha.restype = _D
+        L.orc_pr_alpha.argtypes = [_D, _D]
+        L.orc_eos_critical.argtypes = [C.c_int, _D, _D, _D, _PD, _PD]
+        L.orc_eos_maxwell.argtypes = [C.POINTER(Eos), _PD, _PD, _PD]
+        L.orc_eos_gas_root.argtypes = [C.POINTER(Eos), _D, _PD]
+        L.orc_eos_liquid_root.argtypes = [C.POINTER(Eos), _D, _PD]
+        L.orc_eos_column_density.argtypes = [C.POINTER(Eos), C.c_int, _D, _PD, C.POINTER(C.c_int)]
+        L.orc_mrt_moments.argtypes = [_PD, _PD]
+        L.orc_mrt_moments.restype = None
         L.orc_feq.argtypes = [_D, _D, _D, _PD]
         L.orc_feq.restype = None
         L.orc_grad_periodic.argtypes = [C.c_int, C.c_int, _PD, _PD, _PD]
@@ -143,6 +163,73 @@ def liquid_root(a, b, R, T, p0_target):
     return r.value
 
 
+# --------------------------------------------------------------------------
+# Equation of state, either kind (0 Carnahan-Starling, 1 Peng-Robinson)
+# --------------------------------------------------------------------------
+
+EOS_KINDS = {"cs": 0, "pr": 1}
+
+
+def pr_alpha(omega, T_over_Tc):
+    return lib().orc_pr_alpha(omega, T_over_Tc)
+
+
+def eos_critical(kind="cs", a=1.0, b=4.0, R=1.0):
+    Tc, rc = _D(), _D()
+    if lib().orc_eos_critical(EOS_KINDS[kind], a, b, R, C.byref(Tc), C.byref(rc)):
+        raise ValueError("bad EOS parameters")
+    return Tc.value, rc.value
+
+
+def eos_p0(e: Eos, rho):
+    return lib().orc_eos_p0(C.byref(e), rho)
+
+
+def eos_dp0(e: Eos, rho):
+    return lib().orc_eos_dp0(C.byref(e), rho)
+
+
+def eos_mu(e: Eos, rho):
+    return lib().orc_eos_mu(C.byref(e), rho)
+
+
+def eos_maxwell(e: Eos):
+    g, l, p = _D(), _D(), _D()
+    if lib().orc_eos_maxwell(C.byref(e), C.byref(g), C.byref(l), C.byref(p)):
+        raise ValueError("no coexistence (T >= Tc)")
+    return g.value, l.value, p.value
+
+
+def eos_gas_root(e: Eos, p0_target):
+    r = _D()
+    if lib().orc_eos_gas_root(C.byref(e), p0_target, C.byref(r)):
+        raise ValueError("pressure outside the gas branch")
+    return r.value
+
+
+def eos_liquid_root(e: Eos, p0_target):
+    r = _D()
+    if lib().orc_eos_liquid_root(C.byref(e), p0_target, C.byref(r)):
+        raise ValueError("pressure outside the liquid branch")
+    return r.value
+
+
+def eos_column_density(e: Eos, liquid: bool, p0_target):
+    """(density, saturated) of a pressure column on one branch; a pressure beyond
+    the branch's end gives its spinodal density."""
+    r, sat = _D(), C.c_int()
+    if lib().orc_eos_column_density(C.byref(e), int(liquid), p0_target, C.byref(r), C.byref(sat)):
+        raise ValueError("no column density on this branch")
+    return r.value, bool(sat.value)
+
+
+def mrt_moments(f):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    m = np.zeros(Q)
+    lib().orc_mrt_moments(_ptr(f), _ptr(m))
+    return m
+
+
 def feq(rho, ux, uy):
     out = np.zeros(Q)
     lib().orc_feq(rho, ux, uy, _ptr(out))
@@ -188,7 +275,16 @@ class Setup:
     p_ref: float | None = None  # None: k^2 p_sat(T)
     gx: float = 0.0
     gy: float = 0.0
+    eos: str = "cs"             # "cs" Carnahan-Starling, "pr" Peng-Robinson (Eq. 2.18)
+    omega: float = 0.344        # PR acentric factor (water)
+    collision: str = "bgk"      # "bgk" or "mrt" (Eq. 2.1)
+    s_e: float = 1.64           # MRT rates (Sec. 2.1); s_nu None -> 1/tau
+    s_eps: float = 1.54
+    s_q: float = 1.7
+    s_j: float = 1.0
+    s_nu: float | None = None
     T: float = field(init=False)
+    aalpha: float = field(init=False, default=0.0)
     rho_in: float = field(init=False, default=0.0)    # gas-branch column densities
     rho_out: float = field(init=False, default=0.0)
     rho_in_l: float = field(init=False, default=0.0)  # liquid-branch column densities
@@ -196,34 +292,43 @@ class Setup:
     ph_g: float = field(init=False, default=0.0)      # phase-indicator end points
     ph_l: float = field(init=False, default=0.0)
 
+    def eos_spec(self) -> Eos:
+        return Eos(EOS_KINDS[self.eos], self.a, self.b, self.R, self.T, self.aalpha)
+
     def __post_init__(self):
-        Tc, _ = cs_critical(self.a, self.b, self.R)
+        Tc, _ = eos_critical(self.eos, self.a, self.b, self.R)
         self.T = self.T_over_Tc * Tc
+        if self.eos == "pr":
+            self.aalpha = self.a * pr_alpha(self.omega, self.T_over_Tc)
+        e = self.eos_spec()
         if self.bc_x:
             k2 = self.k * self.k
             below = self.T < Tc
             if self.p_ref is None:
-                _, _, psat = maxwell(self.a, self.b, self.R, self.T)
+                _, _, psat = eos_maxwell(e)
                 pref = k2 * psat
             else:
                 pref = self.p_ref
             pin, pout = (pref + 0.5 * self.dp) / k2, (pref - 0.5 * self.dp) / k2
-            self.rho_in = gas_root(self.a, self.b, self.R, self.T, pin)
-            self.rho_out = gas_root(self.a, self.b, self.R, self.T, pout)
+            self.rho_in, _ = eos_column_density(e, False, pin)
+            self.rho_out, _ = eos_column_density(e, False, pout)
             if below:
-                self.ph_g, self.ph_l, _ = maxwell(self.a, self.b, self.R, self.T)
-                self.rho_in_l = liquid_root(self.a, self.b, self.R, self.T, pin)
-                self.rho_out_l = liquid_root(self.a, self.b, self.R, self.T, pout)
+                self.ph_g, self.ph_l, _ = eos_maxwell(e)
+                self.rho_in_l, _ = eos_column_density(e, True, pin)
+                self.rho_out_l, _ = eos_column_density(e, True, pout)
             else:
                 self.rho_in_l, self.rho_out_l = self.rho_in, self.rho_out
 
     def coexistence(self):
-        return maxwell(self.a, self.b, self.R, self.T)
+        return eos_maxwell(self.eos_spec())
 
     def params(self) -> Params:
+        s_nu = 1.0 / self.tau if self.s_nu is None else self.s_nu
         return Params(self.nx, self.ny, int(self.walls), int(self.bc_x), self.a, self.b, self.R,
                       self.T, self.k, self.kappa, self.tau, self.wet, self.rho_in, self.rho_in_l,
-                      self.rho_out, self.rho_out_l, self.ph_g, self.ph_l, self.gx, self.gy)
+                      self.rho_out, self.rho_out_l, self.ph_g, self.ph_l, self.gx, self.gy,
+                      EOS_KINDS[self.eos], int(self.collision == "mrt"), self.aalpha,
+                      self.s_e, self.s_eps, self.s_j, self.s_q, s_nu)
 
 
 def init(setup: Setup, rho0: np.ndarray) -> np.ndarray:

@@ -60,6 +60,16 @@ typedef struct {
     double rho_in_g, rho_in_l, rho_out_g, rho_out_l;
     double ph_g, ph_l;
     double gx, gy;          /* uniform body-force density added to F */
+    /* Equation of state: 0 Carnahan-Starling, 1 Peng-Robinson (Eq. 2.18) with
+     * aalpha = a alpha(T). */
+    int32_t eos_kind;
+    int32_t collision;      /* 0 BGK; 1 MRT (Eq. 2.1) with the rates below */
+    double aalpha;
+    /* MRT relaxation rates of the moments e, epsilon, j, q and the two stress
+     * moments (Lallemand-Luo basis; the density is conserved). The forcing
+     * shifts the equilibrium velocity by F / (s_j rho), so the relaxed
+     * momentum gains F per step; s_j = 1/tau with every rate 1/tau is BGK. */
+    double s_e, s_eps, s_j, s_q, s_nu;
 } orc_params;
 
 typedef struct {
@@ -224,8 +234,239 @@ int orc_gas_root(double a, double b, double R, double T, double p0_target, doubl
 }
 
 /* ------------------------------------------------------------------------- */
+/* Equation of state, either kind.                                            */
+/* Peng-Robinson (Eq. 2.18): p0 = rho R T / (1 - b rho)                       */
+/*     - a alpha rho^2 / (1 + 2 b rho - b^2 rho^2),                          */
+/* alpha(T) = [1 + (0.37464 + 1.54226 w - 0.26992 w^2)(1 - sqrt(T/Tc))]^2,   */
+/* the standard form of the temperature function the paper prints garbled.   */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t kind;           /* 0 Carnahan-Starling, 1 Peng-Robinson */
+    double a, b, R, T;
+    double aalpha;          /* PR: a alpha(T) */
+} orc_eos;
+
+double orc_pr_alpha(double omega, double T_over_Tc)
+{
+    double m = 0.37464 + 1.54226 * omega - 0.26992 * omega * omega;
+    double t = 1.0 + m * (1.0 - sqrt(T_over_Tc));
+    return t * t;
+}
+
+static double pr_den(double b, double rho) { return 1.0 + 2.0 * b * rho - b * b * rho * rho; }
+
+double orc_eos_p0(const orc_eos *e, double rho)
+{
+    if (e->kind == 0) return orc_cs_p0(e->a, e->b, e->R, e->T, rho);
+    return rho * e->R * e->T / (1.0 - e->b * rho) - e->aalpha * rho * rho / pr_den(e->b, rho);
+}
+
+double orc_eos_dp0(const orc_eos *e, double rho)
+{
+    if (e->kind == 0) return orc_cs_dp0(e->a, e->b, e->R, e->T, rho);
+    double om = 1.0 - e->b * rho, D = pr_den(e->b, rho);
+    return e->R * e->T / (om * om) - 2.0 * e->aalpha * rho * (1.0 + e->b * rho) / (D * D);
+}
+
+/* PR chemical potential mu = f + p0/rho with the specific free energy
+ * f = int p0/rho^2 drho = R T ln(rho / (1 - b rho))
+ *     - a alpha / (2 sqrt2 b) ln((sqrt2 - 1 + b rho) / (sqrt2 + 1 - b rho)),
+ * so that d mu / d rho = p0' / rho (Gibbs-Duhem). */
+double orc_eos_mu(const orc_eos *e, double rho)
+{
+    if (e->kind == 0) return orc_cs_mu(e->a, e->b, e->R, e->T, rho);
+    const double r2 = sqrt(2.0), x = e->b * rho;
+    double f = e->R * e->T * log(rho / (1.0 - x))
+               - e->aalpha / (2.0 * r2 * e->b) * log((r2 - 1.0 + x) / (r2 + 1.0 - x));
+    return f + orc_eos_p0(e, rho) / rho;
+}
+
+/* PR critical point (alpha = 1 at Tc). With x = b rho and A = a / (b R T),
+ * p0' = 0 gives A = D^2 / (2 x (1 + x)(1 - x)^2) and p0'' = 0 gives
+ * 2 / (1 - x)^3 = A d/dx[2 x (1 + x) / D^2]; x_c solves both (bisection). */
+static double pr_crit_h(double x)
+{
+    double D = 1.0 + 2.0 * x - x * x, dD = 2.0 - 2.0 * x;
+    double g = 2.0 * x * (1.0 + x), dg = 2.0 + 4.0 * x;
+    double A = D * D / (g * (1.0 - x) * (1.0 - x));
+    double dq = (dg * D - 2.0 * g * dD) / (D * D * D);  /* d/dx (g / D^2) */
+    return 2.0 / ((1.0 - x) * (1.0 - x) * (1.0 - x)) - A * dq;
+}
+
+int orc_eos_critical(int kind, double a, double b, double R, double *Tc, double *rhoc)
+{
+    if (kind == 0) return orc_cs_critical(a, b, R, Tc, rhoc);
+    if (!(a > 0.0 && b > 0.0 && R > 0.0)) return 1;
+    double lo = 0.05, hi = 0.6;
+    double hlo = pr_crit_h(lo);
+    for (int it = 0; it < 400; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double h = pr_crit_h(mid);
+        if ((h > 0.0) == (hlo > 0.0)) { lo = mid; hlo = h; } else hi = mid;
+    }
+    double x = 0.5 * (lo + hi);
+    double D = 1.0 + 2.0 * x - x * x;
+    double A = D * D / (2.0 * x * (1.0 + x) * (1.0 - x) * (1.0 - x));
+    *rhoc = x / b;
+    *Tc = a / (b * R * A);
+    return 0;
+}
+
+static double eos_rmax(const orc_eos *e) { return (e->kind == 0 ? 4.0 : 1.0) / e->b; }
+
+/* Bisection for the root of dp0/drho on [lo, hi] where its sign changes. */
+static double eos_dp0_root(const orc_eos *e, double lo, double hi)
+{
+    double slo = orc_eos_dp0(e, lo);
+    for (int it = 0; it < 400; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double sm = orc_eos_dp0(e, mid);
+        if ((sm > 0.0) == (slo > 0.0)) { lo = mid; slo = sm; } else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* Root of p0(rho) = p on [lo, hi], where p0 is increasing. */
+static double eos_p0_root(const orc_eos *e, double p, double lo, double hi)
+{
+    for (int it = 0; it < 400; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (orc_eos_p0(e, mid) < p) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+static int eos_spinodals(const orc_eos *e, double *s1, double *s2)
+{
+    double Tc, rhoc;
+    if (orc_eos_critical(e->kind, e->a, e->b, e->R, &Tc, &rhoc)) return 1;
+    if (!(e->T < Tc)) return 1;
+    *s1 = eos_dp0_root(e, 1e-14, rhoc);
+    *s2 = eos_dp0_root(e, rhoc, eos_rmax(e) * (1.0 - 1e-9));
+    return 0;
+}
+
+/* Maxwell equal-area construction for either EOS (bisection on p_sat, as for
+ * Carnahan-Starling below). */
+int orc_eos_maxwell(const orc_eos *e, double *rho_g, double *rho_l, double *p_sat)
+{
+    double s1, s2;
+    if (eos_spinodals(e, &s1, &s2)) return 1;
+    double rmax = eos_rmax(e) * (1.0 - 1e-12);
+    double lo = orc_eos_p0(e, s2), hi = orc_eos_p0(e, s1);
+    if (lo < 0.0) lo = 0.0;
+    for (int it = 0; it < 300; ++it) {
+        double p = 0.5 * (lo + hi);
+        if (p <= lo || p >= hi) break;
+        double rg = eos_p0_root(e, p, 1e-300, s1);
+        double rl = eos_p0_root(e, p, s2, rmax);
+        if (orc_eos_mu(e, rg) - orc_eos_mu(e, rl) > 0.0) hi = p; else lo = p;
+    }
+    double p = 0.5 * (lo + hi);
+    *p_sat = p;
+    *rho_g = eos_p0_root(e, p, 1e-300, s1);
+    *rho_l = eos_p0_root(e, p, s2, rmax);
+    return 0;
+}
+
+int orc_eos_liquid_root(const orc_eos *e, double p0_target, double *rho)
+{
+    double s1, s2;
+    if (eos_spinodals(e, &s1, &s2)) return 1;
+    if (!(p0_target > orc_eos_p0(e, s2))) return 1;
+    *rho = eos_p0_root(e, p0_target, s2, eos_rmax(e) * (1.0 - 1e-12));
+    return 0;
+}
+
+int orc_eos_gas_root(const orc_eos *e, double p0_target, double *rho)
+{
+    double s1, s2, hi;
+    if (eos_spinodals(e, &s1, &s2) == 0) hi = s1;
+    else hi = eos_rmax(e) * (1.0 - 1e-12);
+    if (!(p0_target > 0.0) || !(p0_target < orc_eos_p0(e, hi))) return 1;
+    *rho = eos_p0_root(e, p0_target, 1e-300, hi);
+    return 0;
+}
+
+/* Density of a pressure column on one branch (liquid = 0 gas, 1 liquid) at
+ * EOS pressure p0_target. Reading: a pressure beyond the branch's end (above
+ * the gas spinodal pressure, below the liquid one) holds the column at that
+ * branch's spinodal density, *saturated = 1. Above Tc the gas branch is the
+ * whole (monotone) EOS. Returns 1 if p0_target <= 0 on the gas branch or if
+ * there is no liquid branch. */
+int orc_eos_column_density(const orc_eos *e, int liquid, double p0_target, double *rho, int *saturated)
+{
+    double s1, s2;
+    *saturated = 0;
+    if (!liquid) {
+        if (!(p0_target > 0.0)) return 1;
+        if (eos_spinodals(e, &s1, &s2) == 0 && !(p0_target < orc_eos_p0(e, s1))) {
+            *rho = s1;
+            *saturated = 1;
+            return 0;
+        }
+        return orc_eos_gas_root(e, p0_target, rho);
+    }
+    if (eos_spinodals(e, &s1, &s2)) return 1;
+    if (!(p0_target > orc_eos_p0(e, s2))) {
+        *rho = s2;
+        *saturated = 1;
+        return 0;
+    }
+    return orc_eos_liquid_root(e, p0_target, rho);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Lattice operators                                                          */
 /* ------------------------------------------------------------------------- */
+
+/* MRT moments (Lallemand & Luo 2000, the basis the paper cites for Eq. 2.1),
+ * rows in the order (rho, e, epsilon, j_x, q_x, j_y, q_y, p_xx, p_xy) over the
+ * velocities above. The rows are orthogonal, so M^-1 = M^T diag(1/|row|^2). */
+static const double Mrt[Q][Q] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1},
+    {-4, -1, -1, -1, -1, 2, 2, 2, 2},
+    {4, -2, -2, -2, -2, 1, 1, 1, 1},
+    {0, 1, 0, -1, 0, 1, -1, -1, 1},
+    {0, -2, 0, 2, 0, 1, -1, -1, 1},
+    {0, 0, 1, 0, -1, 1, 1, -1, -1},
+    {0, 0, -2, 0, 2, 1, 1, -1, -1},
+    {0, 1, -1, 1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 1, -1, 1, -1}};
+
+/* Moments m = M f of nine populations (for the pins). */
+void orc_mrt_moments(const double *f, double *m)
+{
+    for (int k = 0; k < Q; ++k) {
+        double s = 0.0;
+        for (int i = 0; i < Q; ++i) s += Mrt[k][i] * f[i];
+        m[k] = s;
+    }
+}
+
+/* MRT relaxation of Eq. 2.1: f* = f - M^-1 S M (f - f_eq), with
+ * S = diag(0, s_e, s_eps, s_j, s_q, s_j, s_q, s_nu, s_nu). */
+static void mrt_relax(const orc_params *p, const double *f, const double *feq, double *fs)
+{
+    const double rate[Q] = {0.0, p->s_e, p->s_eps, p->s_j, p->s_q, p->s_j, p->s_q, p->s_nu, p->s_nu};
+    double d[Q], m[Q];
+    for (int i = 0; i < Q; ++i) d[i] = f[i] - feq[i];
+    orc_mrt_moments(d, m);
+    for (int k = 0; k < Q; ++k) {
+        double norm = 0.0;
+        for (int i = 0; i < Q; ++i) norm += Mrt[k][i] * Mrt[k][i];
+        m[k] *= rate[k] / norm;
+    }
+    for (int i = 0; i < Q; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < Q; ++k) s += Mrt[k][i] * m[k];
+        fs[i] = f[i] - s;
+    }
+}
 
 /* Equilibrium, Eq. 2.2: f_i = rho w_i [1 + 3 e.u + 9/2 (e.u)^2 - 3/2 u^2]. */
 void orc_feq(double rho, double ux, double uy, double *feq)
@@ -383,6 +624,7 @@ static void fields_and_force(const orc_params *p, const double *f, orc_work *w)
     const int nx = p->nx, ny = p->ny;
     const long n = (long)nx * ny, sx = nx + 4;
     const double k2 = p->k * p->k;
+    const orc_eos eos = {p->eos_kind, p->a, p->b, p->R, p->T, p->aalpha};
 
     /* 1. Moments at every non-solid node (Sec. 2.1). */
 #pragma omp parallel for schedule(static)
@@ -420,7 +662,7 @@ static void fields_and_force(const orc_params *p, const double *f, orc_work *w)
             long c = (long)ye * sx + xe;
             double r = rho_ghost(p, w->rho, xe - 2, ye - 2);
             w->E[c] = r;
-            w->P[c] = k2 * orc_cs_p0(p->a, p->b, p->R, p->T, r) - r / 3.0;
+            w->P[c] = k2 * orc_eos_p0(&eos, r) - r / 3.0;
         }
 
     /* 4. Laplacian of the density, on the fluid and one node beyond it. */
@@ -473,6 +715,7 @@ static void wall_fields(const orc_params *p, const orc_work *w, double *tw, doub
     const int nx = p->nx, ny = p->ny;
     const long sx = nx + 4;
     const double nu = (p->tau - 0.5) / 3.0, k2 = p->k * p->k;
+    const orc_eos eos = {p->eos_kind, p->a, p->b, p->R, p->T, p->aalpha};
     for (int side = 0; side < 2; ++side)
         for (int x = 0; x < nx; ++x) {
             tw[side * nx + x] = 0.0;
@@ -487,7 +730,7 @@ static void wall_fields(const orc_params *p, const orc_work *w, double *tw, doub
             long ce = (long)(y1 + 2) * sx + (x + 2);
             double grx, gry;
             grad_ext(w->E, sx, ce, &grx, &gry);
-            pw[side * nx + x] = k2 * orc_cs_p0(p->a, p->b, p->R, p->T, r1)
+            pw[side * nx + x] = k2 * orc_eos_p0(&eos, r1)
                                 - p->kappa * r1 * w->L[ce]
                                 - 0.5 * p->kappa * (grx * grx + gry * gry);
         }
@@ -563,21 +806,32 @@ int orc_step(const orc_params *p, const double *fin, double *fout, orc_diag *d)
     fields_and_force(p, fin, &w);
     if (d) diag_of(p, &w, d);
 
-    /* 6. BGK collision with the velocity-shift force (Sec. 2.1):
-     *    u_eq = u + tau F / rho,  f* = f - (f - f_eq(rho, u_eq)) / tau. */
+    /* 6. Collision with the velocity-shift force (Sec. 2.1): BGK,
+     *    u_eq = u + tau F / rho,  f* = f - (f - f_eq(rho, u_eq)) / tau;
+     *    or MRT (Eq. 2.1), u_eq = u + F / (s_j rho),
+     *    f* = f - M^-1 S M (f - f_eq(rho, u_eq)). */
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             long c = (long)y * nx + x;
             if (is_solid_row(p, y) || is_pressure_col(p, x)) continue;
             double r = w.rho[c];
-            double uex = w.ux[c] + p->tau * w.Fx[c] / r;
-            double uey = w.uy[c] + p->tau * w.Fy[c] / r;
+            /* velocity shift: tau F / rho for BGK, F / (s_j rho) for MRT */
+            const double shift = p->collision ? 1.0 / p->s_j : p->tau;
+            double uex = w.ux[c] + shift * w.Fx[c] / r;
+            double uey = w.uy[c] + shift * w.Fy[c] / r;
             double feq[Q];
             orc_feq(r, uex, uey, feq);
-            for (int i = 0; i < Q; ++i) {
-                double fi = fin[i * n + c];
-                fs[i * n + c] = fi - (fi - feq[i]) / p->tau;
+            if (p->collision) {
+                double fl[Q], fo[Q];
+                for (int i = 0; i < Q; ++i) fl[i] = fin[i * n + c];
+                mrt_relax(p, fl, feq, fo);
+                for (int i = 0; i < Q; ++i) fs[i * n + c] = fo[i];
+            } else {
+                for (int i = 0; i < Q; ++i) {
+                    double fi = fin[i * n + c];
+                    fs[i * n + c] = fi - (fi - feq[i]) / p->tau;
+                }
             }
         }
 

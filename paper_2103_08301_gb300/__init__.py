@@ -30,7 +30,16 @@ class lbm_grid(C.Structure):
 
 class lbm_eos(C.Structure):
     _fields_ = [("a", C.c_double), ("b", C.c_double), ("R", C.c_double), ("T_over_Tc", C.c_double),
-                ("k", C.c_double), ("kappa", C.c_double)]
+                ("k", C.c_double), ("kappa", C.c_double), ("kind", C.c_int32), ("omega", C.c_double)]
+
+
+LBM_EOS_CS, LBM_EOS_PR = 0, 1
+LBM_COLL_BGK, LBM_COLL_MRT = 0, 1
+
+
+class lbm_collision(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("s_e", C.c_double), ("s_eps", C.c_double), ("s_j", C.c_double),
+                ("s_q", C.c_double), ("s_nu", C.c_double)]
 
 
 class lbm_drive(C.Structure):
@@ -66,6 +75,7 @@ _SIGS = {
     "lbm_checkpoint": (C.c_int, [_P, _P, C.c_size_t]),
     "lbm_restore": (C.c_int, [_P, _P, C.c_size_t]),
     "lbm_set_option": (C.c_int, [_P, C.c_int, C.c_int64]),
+    "lbm_set_collision": (C.c_int, [_P, C.POINTER(lbm_collision)]),
     "lbm_launch_info": (C.c_int, [_P] + [C.POINTER(C.c_int64)] * 4),
     "lbm_step_noalloc": (C.c_int, [C.POINTER(lbm_grid), C.POINTER(lbm_eos), C.c_double, C.c_double,
                                    C.POINTER(lbm_drive), _P, _P, C.c_int64, _P, _P]),
@@ -234,9 +244,10 @@ class Lattice:
 
     def __init__(self, nx, ny, rho0, *, walls=False, bc_x=False, precision=32, a=1.0, b=4.0,
                  R=1.0, T_over_Tc=0.8, k=1.0, kappa=0.5, tau=1.0, wetting=0.0, dp=0.0,
-                 p_ref=None, gx=0.0, gy=0.0, workspace=None, stream=None):
+                 p_ref=None, gx=0.0, gy=0.0, eos="cs", omega=0.344, collision="bgk", s_e=1.64,
+                 s_eps=1.54, s_j=1.0, s_q=1.7, s_nu=None, workspace=None, stream=None):
         self.grid = lbm_grid(nx, ny, int(walls), int(bc_x), int(precision))
-        self.eos = lbm_eos(a, b, R, T_over_Tc, k, kappa)
+        self.eos = lbm_eos(a, b, R, T_over_Tc, k, kappa, {"cs": LBM_EOS_CS, "pr": LBM_EOS_PR}[eos], omega)
         self.drive = lbm_drive(dp, math.nan if p_ref is None else p_ref, gx, gy)
         self.nx, self.ny, self.precision = nx, ny, precision
         self.dtype = np.float32 if precision == 32 else np.float64
@@ -247,6 +258,14 @@ class Lattice:
             ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
         sptr = stream.cuda_stream if stream is not None else None
         self.ctx = lbm_init(self.grid, self.eos, tau, wetting, self.drive, rho0, ws_ptr, ws_bytes, sptr)
+        if collision != "bgk":
+            if collision != "mrt":
+                raise ValueError(collision)
+            self.set_collision(lbm_collision(LBM_COLL_MRT, s_e, s_eps, s_j, s_q, 0.0 if s_nu is None else s_nu))
+
+    def set_collision(self, coll):
+        """lbm_set_collision with an lbm_collision (None: BGK)."""
+        _check(lib().lbm_set_collision(self.ctx, C.byref(coll) if coll is not None else None), self.ctx)
 
     # -- stepping -----------------------------------------------------------
     def step(self, n=1):

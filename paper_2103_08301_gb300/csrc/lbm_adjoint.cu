@@ -43,7 +43,9 @@ __device__ __forceinline__ double wq(int i) { return lbm::w_<double>(i); }
 
 struct AdjGeo {
     int nx, ny, walls, bc_x;
+    int eos_kind;                 // 0 Carnahan-Starling, 1 Peng-Robinson
     double RT, a, b4, k2, kappa, tau, nu, wet, gx, gy;
+    double bpr, aalpha;           // PR: b and a alpha(T)
     double g_in, l_in, g_out, l_out, ph_g, inv_dph;  // inv_dph = 0: single phase, no blend
     double w_tau, w_p;
 };
@@ -56,14 +58,23 @@ __device__ __forceinline__ int pmod(int a, int n)
     return r < 0 ? r + n : r;
 }
 
-// Carnahan-Starling p0 and dp0/drho, eta = b rho / 4.
+// EOS p0 and dp0/drho: Carnahan-Starling (eta = b rho / 4) or Peng-Robinson
+// (x = b rho, D = 1 + 2x - x^2).
 __device__ __forceinline__ double cs_p0(const AdjGeo &g, double r)
 {
+    if (g.eos_kind == 1) {
+        const double x = g.bpr * r;
+        return r * g.RT / (1.0 - x) - g.aalpha * r * r / (1.0 + x * (2.0 - x));
+    }
     const double eta = g.b4 * r, om = 1.0 - eta;
     return r * g.RT * (1.0 + eta * (1.0 + eta * (1.0 - eta))) / (om * om * om) - g.a * r * r;
 }
 __device__ __forceinline__ double cs_dp0(const AdjGeo &g, double r)
 {
+    if (g.eos_kind == 1) {
+        const double x = g.bpr * r, om = 1.0 - x, D = 1.0 + x * (2.0 - x);
+        return g.RT / (om * om) - 2.0 * g.aalpha * r * (1.0 + x) / (D * D);
+    }
     const double eta = g.b4 * r, om = 1.0 - eta, om2 = om * om;
     return g.RT * (1.0 + eta * (4.0 + eta * (4.0 + eta * (-4.0 + eta)))) / (om2 * om2) - 2.0 * g.a * r;
 }
@@ -636,20 +647,30 @@ lbm_status adj_setup_drive(lbm_adjoint *a, const lbm_drive *drive)
 
     AdjGeo &g = a->geo;
     g.nx = a->grid.nx; g.ny = a->grid.ny; g.walls = a->grid.walls; g.bc_x = a->grid.bc_x;
+    lbm::Thermo th{};
+    double tc;
+    if (lbm::thermo_of(a->eos, &th, &tc)) { a->err = "equation of state"; return LBM_ERR_PARAM; }
+    g.eos_kind = th.kind; g.bpr = th.b; g.aalpha = th.aalpha;
     g.RT = a->eos.R * dg.T; g.a = a->eos.a; g.b4 = 0.25 * a->eos.b; g.k2 = a->eos.k * a->eos.k;
     g.kappa = a->eos.kappa; g.tau = a->tau; g.nu = (a->tau - 0.5) / 3.0; g.wet = a->wet;
     g.gx = d.gx; g.gy = d.gy;
     g.g_in = dg.rho_in; g.l_in = dg.rho_in_l; g.g_out = dg.rho_out; g.l_out = dg.rho_out_l;
     g.ph_g = dg.rho_g;
     g.inv_dph = dg.rho_l > dg.rho_g ? 1.0 / (dg.rho_l - dg.rho_g) : 0.0;
-    // column densities are EOS roots of k^2 p0(rho) = p_ref +- dp/2
+    // column densities are EOS roots of k^2 p0(rho) = p_ref +- dp/2, so
+    // d rho / d dp = +-1 / (2 k^2 p0'(rho)); a density held at a spinodal
+    // does not move with dp
     a->dgin = a->dlin = a->dgout = a->dlout = 0.0;
     if (a->grid.bc_x) {
-        lbm::Thermo th{a->eos.a, a->eos.b, a->eos.R, dg.T};
-        a->dgin = 0.5 / (g.k2 * lbm::cs_dpressure(th, g.g_in));
-        a->dlin = 0.5 / (g.k2 * lbm::cs_dpressure(th, g.l_in));
-        a->dgout = -0.5 / (g.k2 * lbm::cs_dpressure(th, g.g_out));
-        a->dlout = -0.5 / (g.k2 * lbm::cs_dpressure(th, g.l_out));
+        lbm::ChannelThermo ct;
+        if (lbm::channel_thermo(a->eos, d, true, &ct)) { a->err = "column thermodynamics"; return LBM_ERR_PARAM; }
+        auto rate = [&](double rho, bool sat, double sgn) {
+            return sat ? 0.0 : sgn * 0.5 / (g.k2 * lbm::eos_dpressure(ct.th, rho));
+        };
+        a->dgin = rate(g.g_in, ct.sat[0], 1.0);
+        a->dlin = rate(g.l_in, ct.sat[1], 1.0);
+        a->dgout = rate(g.g_out, ct.sat[2], -1.0);
+        a->dlout = rate(g.l_out, ct.sat[3], -1.0);
     }
     return LBM_OK;
 }
@@ -692,8 +713,10 @@ lbm_status lbm_adjoint_init(const lbm_grid *grid, const lbm_eos *eos, double tau
     if (s != LBM_OK) { lbm_adjoint_free(a); return s; }
     a->Ay = a->Ax + n;              // adjacent, summed in one reduction
     a->pw = a->tw + 2 * grid->nx;   // likewise
-    s = adj_setup_drive(a, nullptr);
-    if (s != LBM_OK) { lbm_adjoint_free(a); return s; }
+    // the forward context is built by the first forward, for its drive
+    lbm::Thermo th{};
+    double tc;
+    if (lbm::thermo_of(*eos, &th, &tc)) { lbm_adjoint_free(a); return LBM_ERR_PARAM; }
     *out = a;
     return LBM_OK;
 }

@@ -17,10 +17,13 @@
 
 namespace {
 
-#ifndef LBM_BLOCK
-#define LBM_BLOCK 128
-#endif
-constexpr int BLOCK = LBM_BLOCK;  // threads per CTA = strip width
+constexpr int STRIP = lbm::STRIP;  // widest strip (columns per CTA)
+// threads per CTA of the step kernels of a precision and staging choice
+inline int cta_threads(int precision, bool staged)
+{
+    if (precision == 64) return staged ? lbm::threads_per_cta<double, true>() : lbm::threads_per_cta<double, false>();
+    return staged ? lbm::threads_per_cta<float, true>() : lbm::threads_per_cta<float, false>();
+}
 constexpr size_t ALIGN = 256;
 constexpr uint64_t CKPT_MAGIC = 0x4C424D434B505431ull;  // "LBMCKPT1"
 
@@ -69,13 +72,15 @@ struct lbm_ctx {
     double tau = 1.0, wet = 0.0;
     double T = 0, Tc = 0, rho_g = 0, rho_l = 0, p_sat = 0, rho_in = 0, rho_out = 0;
     double rho_in_l = 0, rho_out_l = 0;
+    lbm::Thermo th{};  // EOS at the working temperature
+    lbm_collision coll{};  // BGK unless lbm_set_collision chose MRT
     cudaStream_t stream = nullptr;
     unsigned char *ws = nullptr;
     bool own_ws = false;
     Layout L{};
     int cur = 0;          // which population array holds the current state
     int64_t step = 0;
-    int W = BLOCK, nstrips = 0, yf0 = 0, nyf = 0;
+    int W = STRIP, nstrips = 0, yf0 = 0, nyf = 0;
     long long units = 0;
     int nctas = 0;
     int ctas_per_sm_opt = 0;
@@ -142,6 +147,17 @@ lbm::KArgs<real> make_args(const lbm_ctx *ctx)
     A.ph_g = (real)ctx->rho_g;
     A.inv_dph = ctx->rho_l > ctx->rho_g ? (real)(1.0 / (ctx->rho_l - ctx->rho_g)) : real(0);
     A.nu = (real)((ctx->tau - 0.5) / 3.0);
+    A.eos_kind = ctx->th.kind;
+    A.bpr = (real)ctx->th.b;
+    A.aalpha = (real)ctx->th.aalpha;
+    const lbm_collision &cl = ctx->coll;
+    A.mrt = cl.kind == LBM_COLL_MRT;
+    A.ushift = A.mrt ? (real)(1.0 / cl.s_j) : (real)ctx->tau;
+    if (A.mrt) {
+        const double s_nu = cl.s_nu > 0 ? cl.s_nu : 1.0 / ctx->tau;
+        A.m_e = (real)(cl.s_e / 36.0); A.m_eps = (real)(cl.s_eps / 36.0);
+        A.m_j = (real)(cl.s_j / 6.0); A.m_q = (real)(cl.s_q / 12.0); A.m_nu = (real)(s_nu / 4.0);
+    }
     A.mass_part = (double *)(ctx->ws + ctx->L.mass);
     A.J_acc = (double *)(ctx->ws + ctx->L.J);
     A.ext = (real *)(ctx->ws + ctx->L.ext);
@@ -153,10 +169,10 @@ template <typename real, int MODE, bool STAGED>
 void *kernel_ptr(bool walls, bool pres)
 {
     using namespace lbm;
-    if (walls && pres) return (void *)step_kernel<real, true, true, MODE, BLOCK, STAGED>;
-    if (walls) return (void *)step_kernel<real, true, false, MODE, BLOCK, STAGED>;
-    if (pres) return (void *)step_kernel<real, false, true, MODE, BLOCK, STAGED>;
-    return (void *)step_kernel<real, false, false, MODE, BLOCK, STAGED>;
+    if (walls && pres) return (void *)step_kernel<real, true, true, MODE, STAGED>;
+    if (walls) return (void *)step_kernel<real, true, false, MODE, STAGED>;
+    if (pres) return (void *)step_kernel<real, false, true, MODE, STAGED>;
+    return (void *)step_kernel<real, false, false, MODE, STAGED>;
 }
 
 template <typename real, int MODE>
@@ -178,15 +194,15 @@ void *step_kernel_ptr(const lbm_ctx *ctx, int mode)
 size_t dyn_smem(const lbm_ctx *ctx)
 {
     if (!ctx->staged) return 0;
-    return ctx->grid.precision == 64 ? lbm::staged_smem_bytes<double, BLOCK>()
-                                     : lbm::staged_smem_bytes<float, BLOCK>();
+    return ctx->grid.precision == 64 ? lbm::staged_smem_bytes<double>()
+                                     : lbm::staged_smem_bytes<float>();
 }
 
 // Strip partition and the CTA count of the step grid.
 lbm_status plan_launch(lbm_ctx *ctx)
 {
     const int nx = ctx->grid.nx;
-    int W = std::min(ctx->W > 0 ? ctx->W : BLOCK, BLOCK);
+    int W = std::min(ctx->W > 0 ? ctx->W : STRIP, STRIP);
     // the outlet column must not open a strip (its stencil reaches two columns back)
     if (ctx->grid.bc_x && nx > W && nx % W == 1) {
         for (int w = W - 1; w >= 2; --w)
@@ -210,7 +226,7 @@ lbm_status plan_launch(lbm_ctx *ctx)
     if (per_sm <= 0) {
         int occ = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ, step_kernel_ptr(ctx, lbm::MODE_STEP), BLOCK, smem);
+            &occ, step_kernel_ptr(ctx, lbm::MODE_STEP), cta_threads(ctx->grid.precision, ctx->staged), smem);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy");
         per_sm = std::max(1, occ);
     }
@@ -226,7 +242,8 @@ cudaError_t launch(lbm_ctx *ctx, const lbm::KArgs<real> &A)
 {
     void *fn = step_kernel_ptr(ctx, MODE);
     void *args[] = {(void *)&A};
-    return cudaLaunchKernel(fn, dim3(ctx->nctas), dim3(BLOCK), args, dyn_smem(ctx), ctx->stream);
+    return cudaLaunchKernel(fn, dim3(ctx->nctas), dim3(cta_threads(ctx->grid.precision, ctx->staged)), args,
+                            dyn_smem(ctx), ctx->stream);
 }
 
 template <typename real>
@@ -352,34 +369,13 @@ lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, double
     ctx->stream = (cudaStream_t)stream;
 
     // Thermodynamics (host FP64).
-    double rhoc;
-    lbm::cs_critical(eos->a, eos->b, eos->R, &ctx->Tc, &rhoc);
-    ctx->T = eos->T_over_Tc * ctx->Tc;
-    lbm::Thermo th{eos->a, eos->b, eos->R, ctx->T};
-    bool coexist = lbm::maxwell(th, &ctx->rho_g, &ctx->rho_l, &ctx->p_sat) == 0;
-    if (grid->bc_x) {
-        const double k2 = eos->k * eos->k;
-        double pref = ctx->drive.p_ref;
-        if (std::isnan(pref)) {
-            if (!coexist) { lbm_free(ctx); return LBM_ERR_PARAM; }
-            pref = k2 * ctx->p_sat;
-        }
-        const double pin = (pref + 0.5 * ctx->drive.dp) / k2, pout = (pref - 0.5 * ctx->drive.dp) / k2;
-        if (lbm::gas_density(th, pin, &ctx->rho_in) || lbm::gas_density(th, pout, &ctx->rho_out)) {
-            lbm_free(ctx);
-            return LBM_ERR_PARAM;
-        }
-        if (coexist) {
-            if (lbm::liquid_density(th, pin, &ctx->rho_in_l) || lbm::liquid_density(th, pout, &ctx->rho_out_l)) {
-                lbm_free(ctx);
-                return LBM_ERR_PARAM;
-            }
-        } else {
-            ctx->rho_in_l = ctx->rho_in;
-            ctx->rho_out_l = ctx->rho_out;
-            ctx->rho_g = ctx->rho_l = 0.0;  // single phase: no phase blending
-        }
-    }
+    lbm::ChannelThermo ct;
+    if (lbm::channel_thermo(*eos, ctx->drive, grid->bc_x, &ct)) { lbm_free(ctx); return LBM_ERR_PARAM; }
+    ctx->th = ct.th;
+    ctx->T = ct.T; ctx->Tc = ct.Tc;
+    ctx->rho_g = ct.rho_g; ctx->rho_l = ct.rho_l; ctx->p_sat = ct.p_sat;
+    ctx->rho_in = ct.rho_in; ctx->rho_out = ct.rho_out;
+    ctx->rho_in_l = ct.rho_in_l; ctx->rho_out_l = ct.rho_out_l;
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -587,6 +583,19 @@ lbm_status lbm_restore(lbm_ctx *ctx, const void *host_buf, size_t bytes)
     return LBM_OK;
 }
 
+lbm_status lbm_set_collision(lbm_ctx *ctx, const lbm_collision *c)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!c) { ctx->coll = lbm_collision{}; return LBM_OK; }
+    if (c->kind == LBM_COLL_BGK) { ctx->coll = *c; return LBM_OK; }
+    if (c->kind != LBM_COLL_MRT) return LBM_ERR_ARG;
+    for (double r : {c->s_e, c->s_eps, c->s_j, c->s_q})
+        if (!(r > 0.0 && r < 2.0)) return LBM_ERR_ARG;
+    if (!(c->s_nu <= 0.0 || c->s_nu < 2.0) || std::isnan(c->s_nu)) return LBM_ERR_ARG;
+    ctx->coll = *c;
+    return LBM_OK;
+}
+
 lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
 {
     if (!ctx) return LBM_ERR_ARG;
@@ -599,7 +608,7 @@ lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
         ctx->reverse = value != 0;
         return LBM_OK;
     case LBM_OPT_STRIP:
-        if (value < 2 || value > BLOCK) return LBM_ERR_ARG;
+        if (value < 2 || value > STRIP) return LBM_ERR_ARG;
         ctx->W = (int)value;
         break;
     case LBM_OPT_STAGED:
@@ -623,7 +632,7 @@ lbm_status lbm_launch_info(const lbm_ctx *ctx, int64_t *ctas, int64_t *threads, 
 {
     if (!ctx) return LBM_ERR_ARG;
     if (ctas) *ctas = ctx->nctas;
-    if (threads) *threads = BLOCK;
+    if (threads) *threads = cta_threads(ctx->grid.precision, ctx->staged);
     if (units) *units = ctx->units;
     if (staged) *staged = ctx->staged ? 1 : 0;
     return LBM_OK;
@@ -745,29 +754,13 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_grid *grid, const lbm_eos *eos,
     c.tau = tau;
     c.wet = wetting;
     c.stream = static_cast<cudaStream_t>(stream);
-    double rhoc;
-    lbm::cs_critical(eos->a, eos->b, eos->R, &c.Tc, &rhoc);
-    c.T = eos->T_over_Tc * c.Tc;
-    lbm::Thermo th{eos->a, eos->b, eos->R, c.T};
-    const bool coexist = lbm::maxwell(th, &c.rho_g, &c.rho_l, &c.p_sat) == 0;
-    if (grid->bc_x) {
-        const double k2 = eos->k * eos->k;
-        double pref = c.drive.p_ref;
-        if (std::isnan(pref)) {
-            if (!coexist) return LBM_ERR_PARAM;
-            pref = k2 * c.p_sat;
-        }
-        const double pin = (pref + 0.5 * c.drive.dp) / k2, pout = (pref - 0.5 * c.drive.dp) / k2;
-        if (lbm::gas_density(th, pin, &c.rho_in) || lbm::gas_density(th, pout, &c.rho_out)) return LBM_ERR_PARAM;
-        if (coexist) {
-            if (lbm::liquid_density(th, pin, &c.rho_in_l) || lbm::liquid_density(th, pout, &c.rho_out_l))
-                return LBM_ERR_PARAM;
-        } else {
-            c.rho_in_l = c.rho_in;
-            c.rho_out_l = c.rho_out;
-            c.rho_g = c.rho_l = 0.0;
-        }
-    }
+    lbm::ChannelThermo ct;
+    if (lbm::channel_thermo(*eos, c.drive, grid->bc_x, &ct)) return LBM_ERR_PARAM;
+    c.th = ct.th;
+    c.T = ct.T; c.Tc = ct.Tc;
+    c.rho_g = ct.rho_g; c.rho_l = ct.rho_l; c.p_sat = ct.p_sat;
+    c.rho_in = ct.rho_in; c.rho_out = ct.rho_out;
+    c.rho_in_l = ct.rho_in_l; c.rho_out_l = ct.rho_out_l;
     int dev = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);

@@ -19,10 +19,13 @@
 
 namespace {
 
-#ifndef LBM_BLOCK
-#define LBM_BLOCK 128
-#endif
-constexpr int BLOCK = LBM_BLOCK;
+constexpr int STRIP = lbm::STRIP;  // widest strip (columns per CTA)
+// threads per CTA of the step kernels of a precision and staging choice
+inline int cta_threads(int precision, bool staged)
+{
+    if (precision == 64) return staged ? lbm::threads_per_cta<double, true>() : lbm::threads_per_cta<double, false>();
+    return staged ? lbm::threads_per_cta<float, true>() : lbm::threads_per_cta<float, false>();
+}
 constexpr int DEFAULT_GRAPH_STEPS = 64;  // even: a replay ends on the buffer it started from
 
 struct ChanHost {
@@ -30,7 +33,7 @@ struct ChanHost {
     lbm_drive drive;
     double rho_in = 0, rho_out = 0, rho_in_l = 0, rho_out_l = 0;
     long long off = 0;  // element offset in the packed buffers
-    int W = BLOCK, nstrips = 0, yf0 = 0, nyf = 0;
+    int W = STRIP, nstrips = 0, yf0 = 0, nyf = 0;
     long long units = 0, unit_base = 0;
 };
 
@@ -42,6 +45,7 @@ struct lbm_batch {
     int n = 0, precision = 32, walls = 0, bc_x = 0;
     lbm_eos eos{};
     double tau = 1.0, wet = 0.0, T = 0, Tc = 0, rho_g = 0, rho_l = 0, p_sat = 0;
+    lbm::Thermo th{};  // EOS at the working temperature
     std::vector<ChanHost> ch;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -92,10 +96,10 @@ template <typename real, bool STAGED>
 void *batch_kernel_ptr(bool walls, bool pres)
 {
     using namespace lbm;
-    if (walls && pres) return (void *)batch_step_kernel<real, true, true, BLOCK, STAGED>;
-    if (walls) return (void *)batch_step_kernel<real, true, false, BLOCK, STAGED>;
-    if (pres) return (void *)batch_step_kernel<real, false, true, BLOCK, STAGED>;
-    return (void *)batch_step_kernel<real, false, false, BLOCK, STAGED>;
+    if (walls && pres) return (void *)batch_step_kernel<real, true, true, STAGED>;
+    if (walls) return (void *)batch_step_kernel<real, true, false, STAGED>;
+    if (pres) return (void *)batch_step_kernel<real, false, true, STAGED>;
+    return (void *)batch_step_kernel<real, false, false, STAGED>;
 }
 
 void *batch_kernel(const lbm_batch *b)
@@ -110,16 +114,16 @@ template <typename real, bool STAGED>
 void *fields_kernel_ptr(bool walls, bool pres)
 {
     using namespace lbm;
-    if (walls && pres) return (void *)step_kernel<real, true, true, MODE_FIELDS, BLOCK, STAGED>;
-    if (walls) return (void *)step_kernel<real, true, false, MODE_FIELDS, BLOCK, STAGED>;
-    if (pres) return (void *)step_kernel<real, false, true, MODE_FIELDS, BLOCK, STAGED>;
-    return (void *)step_kernel<real, false, false, MODE_FIELDS, BLOCK, STAGED>;
+    if (walls && pres) return (void *)step_kernel<real, true, true, MODE_FIELDS, STAGED>;
+    if (walls) return (void *)step_kernel<real, true, false, MODE_FIELDS, STAGED>;
+    if (pres) return (void *)step_kernel<real, false, true, MODE_FIELDS, STAGED>;
+    return (void *)step_kernel<real, false, false, MODE_FIELDS, STAGED>;
 }
 
 size_t staged_bytes(const lbm_batch *b, bool staged)
 {
     if (!staged) return 0;
-    return b->precision == 64 ? lbm::staged_smem_bytes<double, BLOCK>() : lbm::staged_smem_bytes<float, BLOCK>();
+    return b->precision == 64 ? lbm::staged_smem_bytes<double>() : lbm::staged_smem_bytes<float>();
 }
 
 // Shared physics of every channel, in the kernel argument block.
@@ -138,6 +142,11 @@ lbm::KArgs<real> physics_args(const lbm_batch *b)
     A.omb = (real)(1.0 - 1.0 / b->tau);
     A.wet = (real)b->wet;
     A.nu = (real)((b->tau - 0.5) / 3.0);
+    A.eos_kind = b->th.kind;
+    A.bpr = (real)b->th.b;
+    A.aalpha = (real)b->th.aalpha;
+    A.mrt = 0;  // batched channels use BGK
+    A.ushift = (real)b->tau;
     A.ph_g = (real)b->rho_g;
     A.inv_dph = b->rho_l > b->rho_g ? (real)(1.0 / (b->rho_l - b->rho_g)) : real(0);
     A.err = b->d_err;
@@ -154,7 +163,7 @@ lbm_status batch_plan(lbm_batch *b)
     bool all4 = true;
     for (auto &c : b->ch) {
         const int nx = c.grid.nx;
-        int W = std::min(b->W_opt > 0 ? b->W_opt : BLOCK, BLOCK);
+        int W = std::min(b->W_opt > 0 ? b->W_opt : STRIP, STRIP);
         if (b->bc_x && nx > W && nx % W == 1)
             for (int w = W - 1; w >= 2; --w)
                 if (nx % w != 1) { W = w; break; }
@@ -174,7 +183,8 @@ lbm_status batch_plan(lbm_batch *b)
     int per_sm = b->ctas_per_sm_opt;
     if (per_sm <= 0) {
         int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(b), BLOCK, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(b), cta_threads(b->precision, b->staged),
+                                                          smem);
         if (e != cudaSuccess) return bfail(b, e, "occupancy");
         per_sm = std::max(1, occ);
     }
@@ -260,7 +270,8 @@ cudaError_t batch_launch(lbm_batch *b)
     real *ext = static_cast<real *>(b->d_seg_ext);
     void *args[] = {(void *)&A, (void *)&chans, (void *)&b->d_segs, (void *)&b->d_cta_begin,
                     (void *)&b->d_seg_mass, (void *)&b->d_seg_J, (void *)&ext};
-    return cudaLaunchKernel(batch_kernel(b), dim3(b->nctas), dim3(BLOCK), args, staged_bytes(b, b->staged),
+    return cudaLaunchKernel(batch_kernel(b), dim3(b->nctas), dim3(cta_threads(b->precision, b->staged)), args,
+                            staged_bytes(b, b->staged),
                             b->stream);
 }
 
@@ -352,7 +363,8 @@ lbm_status chan_fields(lbm_batch *b, int ci, void *rho, void *ux, void *uy, void
     BCK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attribute");
     A.nctas = (int)std::max<long long>(1, std::min<long long>((long long)b->sms * 4, c.units / 2));
     void *args[] = {(void *)&A};
-    BCK(cudaLaunchKernel(fn, dim3(A.nctas), dim3(BLOCK), args, smem, b->stream), "fields launch");
+    BCK(cudaLaunchKernel(fn, dim3(A.nctas), dim3(cta_threads(b->precision, st)), args, smem, b->stream),
+        "fields launch");
     struct { void *dst; real *src; size_t n; } outs[] = {
         {rho, d_rho, N}, {ux, d_vx, N}, {uy, d_vy, N}, {tw, d_tw, 2 * nx}, {pw, d_pw, 2 * nx}};
     for (auto &o : outs)
@@ -390,40 +402,24 @@ lbm_status lbm_batch_init(int32_t n, const lbm_grid *grids, const lbm_eos *eos, 
     b->eos = *eos;
     b->tau = tau;
     b->wet = wetting;
-    double rhoc;
-    lbm::cs_critical(eos->a, eos->b, eos->R, &b->Tc, &rhoc);
-    b->T = eos->T_over_Tc * b->Tc;
-    lbm::Thermo th{eos->a, eos->b, eos->R, b->T};
-    const bool coexist = lbm::maxwell(th, &b->rho_g, &b->rho_l, &b->p_sat) == 0;
-    if (!coexist) b->rho_g = b->rho_l = 0.0;
+    lbm::ChannelThermo ct0;
+    const lbm_drive none{0.0, NAN, 0.0, 0.0};
+    if (lbm::channel_thermo(*eos, none, false, &ct0)) { lbm_batch_free(b); return LBM_ERR_PARAM; }
+    b->th = ct0.th;
+    b->T = ct0.T; b->Tc = ct0.Tc;
+    b->rho_g = ct0.rho_g; b->rho_l = ct0.rho_l; b->p_sat = ct0.p_sat;
     b->ch.resize(n);
     size_t off = 0;
     for (int i = 0; i < n; ++i) {
         ChanHost &c = b->ch[i];
         c.grid = grids[i];
         if (drives) c.drive = drives[i];
-        else { c.drive.dp = 0; c.drive.p_ref = NAN; c.drive.gx = c.drive.gy = 0; }
+        else c.drive = none;
         if (b->bc_x) {
-            const double k2 = eos->k * eos->k;
-            double pref = c.drive.p_ref;
-            if (std::isnan(pref)) {
-                if (!coexist) { lbm_batch_free(b); return LBM_ERR_PARAM; }
-                pref = k2 * b->p_sat;
-            }
-            const double pin = (pref + 0.5 * c.drive.dp) / k2, pout = (pref - 0.5 * c.drive.dp) / k2;
-            if (lbm::gas_density(th, pin, &c.rho_in) || lbm::gas_density(th, pout, &c.rho_out)) {
-                lbm_batch_free(b);
-                return LBM_ERR_PARAM;
-            }
-            if (coexist) {
-                if (lbm::liquid_density(th, pin, &c.rho_in_l) || lbm::liquid_density(th, pout, &c.rho_out_l)) {
-                    lbm_batch_free(b);
-                    return LBM_ERR_PARAM;
-                }
-            } else {
-                c.rho_in_l = c.rho_in;
-                c.rho_out_l = c.rho_out;
-            }
+            lbm::ChannelThermo ct;
+            if (lbm::channel_thermo(*eos, c.drive, true, &ct)) { lbm_batch_free(b); return LBM_ERR_PARAM; }
+            c.rho_in = ct.rho_in; c.rho_out = ct.rho_out;
+            c.rho_in_l = ct.rho_in_l; c.rho_out_l = ct.rho_out_l;
         }
         c.off = (long long)off;
         off += align_elems((size_t)9 * c.grid.nx * c.grid.ny);
@@ -578,7 +574,7 @@ lbm_status lbm_batch_set_option(lbm_batch *b, lbm_option opt, int64_t value)
         if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
         return LBM_OK;
     case LBM_OPT_STRIP:
-        if (value < 2 || value > BLOCK) return LBM_ERR_ARG;
+        if (value < 2 || value > STRIP) return LBM_ERR_ARG;
         b->W_opt = (int)value;
         break;
     case LBM_OPT_STAGED:
@@ -603,7 +599,7 @@ lbm_status lbm_batch_launch_info(const lbm_batch *b, int64_t *ctas, int64_t *seg
     if (ctas) *ctas = b->nctas;
     if (segments) *segments = b->nseg;
     if (staged) *staged = b->staged ? 1 : 0;
-    if (strip) *strip = b->W_opt > 0 ? b->W_opt : BLOCK;
+    if (strip) *strip = b->W_opt > 0 ? b->W_opt : STRIP;
     return LBM_OK;
 }
 
@@ -636,7 +632,7 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int32_t trial_steps, int64_t *best_c
     int best_c = 0, best_w = 0;
     const int strips[] = {128, 64};
     for (int w : strips) {
-        if (w > BLOCK) continue;
+        if (w > STRIP) continue;
         for (int c = std::max(1, occ_max - 2); c <= occ_max; ++c) {
             b->ctas_per_sm_opt = c;
             b->W_opt = w;

@@ -1,7 +1,8 @@
-// Host-side FP64 helpers of the solver: Carnahan-Starling thermodynamics
-// (critical point, Maxwell coexistence, gas-branch density for a given
-// pressure) and the initial density profiles of the airway channel and the
-// static droplet. No GPU is needed for anything in this file.
+// Host-side FP64 helpers of the solver: thermodynamics of the Carnahan-Starling
+// and Peng-Robinson equations of state (critical point, Maxwell coexistence,
+// branch densities for a given pressure), the initial density profiles of the
+// airway channel and the static droplet, and the liquid-plug analysis. No GPU
+// is needed for anything in this file.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -13,7 +14,7 @@
 namespace lbm {
 
 // Carnahan-Starling pressure p0(rho) = rho R T Z(eta) - a rho^2, eta = b rho/4.
-double cs_pressure(const Thermo &t, double rho)
+static double cs_pressure(const Thermo &t, double rho)
 {
     double eta = 0.25 * t.b * rho, om = 1.0 - eta;
     return rho * t.R * t.T * (1.0 + eta * (1.0 + eta * (1.0 - eta))) / (om * om * om) - t.a * rho * rho;
@@ -36,17 +37,36 @@ static double g3(double e)
     return (60.0 + e * (72.0 - 12.0 * e)) / (om3 * om3);
 }
 
-double cs_dpressure(const Thermo &t, double rho)
+// Peng-Robinson pieces: x = b rho, D = 1 + 2x - x^2.
+static double pr_D(double x) { return 1.0 + x * (2.0 - x); }
+
+double eos_pressure(const Thermo &t, double rho)
 {
-    return t.R * t.T * g1(0.25 * t.b * rho) - 2.0 * t.a * rho;
+    if (t.kind == 0) return cs_pressure(t, rho);
+    const double x = t.b * rho;
+    return rho * t.R * t.T / (1.0 - x) - t.aalpha * rho * rho / pr_D(x);
+}
+
+double eos_dpressure(const Thermo &t, double rho)
+{
+    if (t.kind == 0) return t.R * t.T * g1(0.25 * t.b * rho) - 2.0 * t.a * rho;
+    const double x = t.b * rho, om = 1.0 - x, D = pr_D(x);
+    return t.R * t.T / (om * om) - 2.0 * t.aalpha * rho * (1.0 + x) / (D * D);
 }
 
 // Chemical potential mu = psi'(rho) (free energy density psi with p0 = rho psi' - psi).
-static double cs_mu(const Thermo &t, double rho)
+static double eos_mu(const Thermo &t, double rho)
 {
-    double eta = 0.25 * t.b * rho, om = 1.0 - eta;
-    return t.R * t.T * (std::log(rho) + eta * (8.0 + eta * (-9.0 + 3.0 * eta)) / (om * om * om))
-           - 2.0 * t.a * rho;
+    if (t.kind == 0) {
+        double eta = 0.25 * t.b * rho, om = 1.0 - eta;
+        return t.R * t.T * (std::log(rho) + eta * (8.0 + eta * (-9.0 + 3.0 * eta)) / (om * om * om))
+               - 2.0 * t.a * rho;
+    }
+    // PR: specific free energy int p0/rho^2 drho plus p0/rho
+    const double x = t.b * rho, s2 = std::sqrt(2.0);
+    const double fe = t.R * t.T * std::log(rho / (1.0 - x))
+                      + t.aalpha / (2.0 * s2 * t.b) * std::log((1.0 + s2 - x) / (s2 - 1.0 + x));
+    return fe + eos_pressure(t, rho) / rho;
 }
 
 // Critical packing fraction: h(eta) = g1 - eta g2 = 0, with h' = -eta g3 (since g1' = g2).
@@ -63,21 +83,53 @@ static double critical_eta()
     return e;
 }
 
-void cs_critical(double a, double b, double R, double *Tc, double *rhoc)
+// PR: along dp0/drho = 0 the reduced attraction A = a / (b R T) is
+// D^2 / (2 x (1 + x)(1 - x)^2); the critical point is its minimum over x
+// (below Tc two spinodals share one A). Golden-section search.
+static double pr_A(double x)
 {
-    double e = critical_eta();
-    *rhoc = 4.0 * e / b;
-    *Tc = 8.0 * a / (b * R * g2(e));
+    const double D = pr_D(x), om = 1.0 - x;
+    return D * D / (2.0 * x * (1.0 + x) * om * om);
 }
+
+void eos_critical(int kind, double a, double b, double R, double *Tc, double *rhoc)
+{
+    if (kind == 0) {
+        double e = critical_eta();
+        *rhoc = 4.0 * e / b;
+        *Tc = 8.0 * a / (b * R * g2(e));
+        return;
+    }
+    const double gr = 0.5 * (std::sqrt(5.0) - 1.0);
+    double lo = 0.05, hi = 0.6;
+    double c = hi - gr * (hi - lo), d = lo + gr * (hi - lo);
+    for (int it = 0; it < 200 && hi - lo > 1e-16; ++it) {
+        if (pr_A(c) < pr_A(d)) hi = d; else lo = c;
+        c = hi - gr * (hi - lo);
+        d = lo + gr * (hi - lo);
+    }
+    const double x = 0.5 * (lo + hi);
+    *rhoc = x / b;
+    *Tc = a / (b * R * pr_A(x));
+}
+
+double pr_alpha(double omega, double T_over_Tc)
+{
+    const double m = 0.37464 + omega * (1.54226 - 0.26992 * omega);
+    const double s = 1.0 + m * (1.0 - std::sqrt(T_over_Tc));
+    return s * s;
+}
+
+static double rho_max(const Thermo &t) { return (t.kind == 0 ? 4.0 : 1.0) / t.b * (1.0 - 1e-12); }
 
 // Safeguarded Newton for p0(rho) = p on a bracket [lo, hi] where p0 increases.
 static double solve_branch(const Thermo &t, double p, double lo, double hi)
 {
     double r = 0.5 * (lo + hi);
     for (int it = 0; it < 200; ++it) {
-        double f = cs_pressure(t, r) - p;
+        double f = eos_pressure(t, r) - p;
         if (f > 0.0) hi = r; else lo = r;
-        double d = cs_dpressure(t, r);
+        double d = eos_dpressure(t, r);
         double rn = (d > 0.0) ? r - f / d : 0.5 * (lo + hi);
         if (!(rn > lo && rn < hi)) rn = 0.5 * (lo + hi);
         if (std::fabs(rn - r) <= 1e-16 * r) { r = rn; break; }
@@ -89,29 +141,38 @@ static double solve_branch(const Thermo &t, double p, double lo, double hi)
 // Root of dp0/drho between lo and hi (sign change), by bisection on the sign.
 static double spinodal(const Thermo &t, double lo, double hi)
 {
-    bool slo = cs_dpressure(t, lo) > 0.0;
+    bool slo = eos_dpressure(t, lo) > 0.0;
     for (int it = 0; it < 200; ++it) {
         double m = 0.5 * (lo + hi);
-        if ((cs_dpressure(t, m) > 0.0) == slo) lo = m; else hi = m;
+        if ((eos_dpressure(t, m) > 0.0) == slo) lo = m; else hi = m;
     }
     return 0.5 * (lo + hi);
 }
 
-int maxwell(const Thermo &t, double *rho_g, double *rho_l, double *p_sat)
+// Spinodals s1 < s2 below Tc; nonzero at or above Tc.
+static int spinodals(const Thermo &t, double *s1, double *s2)
 {
     double Tc, rhoc;
-    cs_critical(t.a, t.b, t.R, &Tc, &rhoc);
+    eos_critical(t.kind, t.a, t.b, t.R, &Tc, &rhoc);
     if (!(t.T < Tc)) return 1;
-    double rmax = 4.0 / t.b * (1.0 - 1e-12);
-    double s1 = spinodal(t, 1e-12, rhoc), s2 = spinodal(t, rhoc, rmax);
-    double plo = std::fmax(cs_pressure(t, s2), 0.0), phi = cs_pressure(t, s1);
+    *s1 = spinodal(t, 1e-12, rhoc);
+    *s2 = spinodal(t, rhoc, rho_max(t));
+    return 0;
+}
+
+int maxwell(const Thermo &t, double *rho_g, double *rho_l, double *p_sat)
+{
+    double s1, s2;
+    if (spinodals(t, &s1, &s2)) return 1;
+    const double rmax = rho_max(t);
+    double plo = std::fmax(eos_pressure(t, s2), 0.0), phi = eos_pressure(t, s1);
     // Newton in pressure on dmu(p) = mu(rho_g(p)) - mu(rho_l(p)); by Gibbs-Duhem
     // d dmu / dp = 1/rho_g - 1/rho_l. Bracket kept to stay on both branches.
     double lo = plo, hi = phi, p = 0.5 * (plo + phi), rg = 0, rl = 0;
     for (int it = 0; it < 200; ++it) {
         rg = solve_branch(t, p, 1e-300, s1);
         rl = solve_branch(t, p, s2, rmax);
-        double dmu = cs_mu(t, rg) - cs_mu(t, rl);
+        double dmu = eos_mu(t, rg) - eos_mu(t, rl);
         if (dmu > 0.0) hi = p; else lo = p;
         double pn = p - dmu / (1.0 / rg - 1.0 / rl);
         if (!(pn > lo && pn < hi)) pn = 0.5 * (lo + hi);
@@ -124,25 +185,80 @@ int maxwell(const Thermo &t, double *rho_g, double *rho_l, double *p_sat)
     return 0;
 }
 
-int gas_density(const Thermo &t, double p, double *rho)
+int gas_density(const Thermo &t, double p, double *rho, bool *saturated)
 {
-    double Tc, rhoc;
-    cs_critical(t.a, t.b, t.R, &Tc, &rhoc);
-    double hi = (t.T < Tc) ? spinodal(t, 1e-12, rhoc) : 4.0 / t.b * (1.0 - 1e-12);
-    if (!(p > 0.0) || !(p < cs_pressure(t, hi))) return 1;
-    *rho = solve_branch(t, p, 1e-300, hi);
+    if (saturated) *saturated = false;
+    if (!(p > 0.0)) return 1;
+    double s1, s2;
+    if (spinodals(t, &s1, &s2)) {  // monotone EOS
+        const double hi = rho_max(t);
+        if (!(p < eos_pressure(t, hi))) return 1;
+        *rho = solve_branch(t, p, 1e-300, hi);
+        return 0;
+    }
+    if (!(p < eos_pressure(t, s1))) {  // beyond the gas branch's end
+        *rho = s1;
+        if (saturated) *saturated = true;
+        return 0;
+    }
+    *rho = solve_branch(t, p, 1e-300, s1);
     return 0;
 }
 
-int liquid_density(const Thermo &t, double p, double *rho)
+int liquid_density(const Thermo &t, double p, double *rho, bool *saturated)
 {
-    double Tc, rhoc;
-    cs_critical(t.a, t.b, t.R, &Tc, &rhoc);
-    if (!(t.T < Tc)) return 1;
-    double rmax = 4.0 / t.b * (1.0 - 1e-12);
-    double s2 = spinodal(t, rhoc, rmax);
-    if (!(p > cs_pressure(t, s2))) return 1;
-    *rho = solve_branch(t, p, s2, rmax);
+    if (saturated) *saturated = false;
+    double s1, s2;
+    if (spinodals(t, &s1, &s2)) return 1;
+    if (!(p > eos_pressure(t, s2))) {  // below the liquid branch's end
+        *rho = s2;
+        if (saturated) *saturated = true;
+        return 0;
+    }
+    *rho = solve_branch(t, p, s2, rho_max(t));
+    return 0;
+}
+
+int thermo_of(const lbm_eos &e, Thermo *t, double *Tc)
+{
+    if (!(e.a > 0) || !(e.b > 0) || !(e.R > 0) || !(e.T_over_Tc > 0)) return 1;
+    if (e.kind != 0 && e.kind != 1) return 1;
+    double tc, rc;
+    eos_critical(e.kind, e.a, e.b, e.R, &tc, &rc);
+    *t = Thermo{e.a, e.b, e.R, e.T_over_Tc * tc, e.kind, e.kind == 1 ? e.a * pr_alpha(e.omega, e.T_over_Tc) : 0.0};
+    if (Tc) *Tc = tc;
+    return 0;
+}
+
+int channel_thermo(const lbm_eos &e, const lbm_drive &d, bool bc_x, ChannelThermo *out)
+{
+    ChannelThermo c;
+    if (thermo_of(e, &c.th, &c.Tc)) return 1;
+    c.T = c.th.T;
+    const bool coexist = maxwell(c.th, &c.rho_g, &c.rho_l, &c.p_sat) == 0;
+    if (!coexist) c.rho_g = c.rho_l = c.p_sat = 0.0;
+    if (bc_x) {
+        const double k2 = e.k * e.k;
+        double pref = d.p_ref;
+        if (std::isnan(pref)) {
+            if (!coexist) return 1;
+            pref = k2 * c.p_sat;
+        }
+        const double pin = (pref + 0.5 * d.dp) / k2, pout = (pref - 0.5 * d.dp) / k2;
+        if (gas_density(c.th, pin, &c.rho_in, &c.sat[0]) || gas_density(c.th, pout, &c.rho_out, &c.sat[2]))
+            return 1;
+        if (coexist) {
+            if (liquid_density(c.th, pin, &c.rho_in_l, &c.sat[1]) ||
+                liquid_density(c.th, pout, &c.rho_out_l, &c.sat[3]))
+                return 1;
+        } else {
+            c.rho_in_l = c.rho_in;
+            c.rho_out_l = c.rho_out;
+            c.sat[1] = c.sat[0];
+            c.sat[3] = c.sat[2];
+        }
+    }
+    *out = c;
     return 0;
 }
 
@@ -168,11 +284,9 @@ extern "C" {
 lbm_status lbm_coexistence(const lbm_eos *eos, double *Tc, double *rho_g, double *rho_l,
                            double *p_sat)
 {
-    if (!eos || !(eos->a > 0) || !(eos->b > 0) || !(eos->R > 0) || !(eos->T_over_Tc > 0))
-        return LBM_ERR_ARG;
-    double tc, rc;
-    lbm::cs_critical(eos->a, eos->b, eos->R, &tc, &rc);
-    lbm::Thermo t{eos->a, eos->b, eos->R, eos->T_over_Tc * tc};
+    lbm::Thermo t{};
+    double tc;
+    if (!eos || lbm::thermo_of(*eos, &t, &tc)) return LBM_ERR_ARG;
     double g, l, p;
     if (lbm::maxwell(t, &g, &l, &p)) return LBM_ERR_PARAM;
     if (Tc) *Tc = tc;

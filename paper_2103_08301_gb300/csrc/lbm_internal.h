@@ -3,22 +3,46 @@
 
 #include <cstdint>
 
+#include "lbm.h"
+
 namespace lbm {
 
-// Carnahan-Starling parameters at absolute temperature T.
+// Equation-of-state parameters at absolute temperature T: Carnahan-Starling
+// (kind 0) or Peng-Robinson (kind 1, Eq. 2.18, with aalpha = a alpha(T)).
 struct Thermo {
     double a, b, R, T;
+    int kind = 0;
+    double aalpha = 0.0;
 };
 
-double cs_pressure(const Thermo &t, double rho);
-double cs_dpressure(const Thermo &t, double rho);
-void cs_critical(double a, double b, double R, double *Tc, double *rhoc);
+double eos_pressure(const Thermo &t, double rho);
+double eos_dpressure(const Thermo &t, double rho);
+// Critical point (PR: alpha(Tc) = 1).
+void eos_critical(int kind, double a, double b, double R, double *Tc, double *rhoc);
+// Standard PR temperature function alpha(T) for acentric factor omega.
+double pr_alpha(double omega, double T_over_Tc);
 // Maxwell coexistence below Tc; returns nonzero at or above Tc.
 int maxwell(const Thermo &t, double *rho_g, double *rho_l, double *p_sat);
-// Gas-branch density with p0(rho) = p; nonzero if p is outside the branch.
-int gas_density(const Thermo &t, double p, double *rho);
-// Liquid-branch density with p0(rho) = p below Tc; nonzero otherwise.
-int liquid_density(const Thermo &t, double p, double *rho);
+// Density on the gas (liquid) branch whose EOS pressure is p. A pressure
+// beyond the branch's end gives the spinodal density and sets *saturated.
+// Nonzero if p <= 0 (gas) or if there is no liquid branch (T >= Tc).
+int gas_density(const Thermo &t, double p, double *rho, bool *saturated = nullptr);
+int liquid_density(const Thermo &t, double p, double *rho, bool *saturated = nullptr);
+// Thermodynamic state of an lbm_eos: T, Tc and the Thermo; nonzero on bad parameters.
+int thermo_of(const lbm_eos &e, Thermo *t, double *Tc);
+
+// Thermodynamics of one channel: Maxwell coexistence (rho_g = rho_l = 0 above
+// Tc: no phase blending) and, with pressure columns, the column densities on
+// both branches at the mesh pressures p_ref +- dp/2 (p_ref NaN: k^2 p_sat).
+// sat[0..3] flag a column density held at a spinodal (gas_in, liq_in,
+// gas_out, liq_out). Returns nonzero if the parameters admit no columns.
+struct ChannelThermo {
+    Thermo th{};
+    double T = 0, Tc = 0, rho_g = 0, rho_l = 0, p_sat = 0;
+    double rho_in = 0, rho_out = 0, rho_in_l = 0, rho_out_l = 0;
+    bool sat[4] = {false, false, false, false};
+};
+int channel_thermo(const lbm_eos &e, const lbm_drive &d, bool bc_x, ChannelThermo *out);
 double node_noise(uint64_t seed, uint64_t node, double amp);
 
 } // namespace lbm

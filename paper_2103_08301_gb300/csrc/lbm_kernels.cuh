@@ -13,9 +13,12 @@
 //     f[y][i][x] (row stride 9 nx; the C ABI exchanges f[i][y][x] and
 //     converts); a step reads buffer A and pushes post-collision values into
 //     buffer B; all indices are 32-bit (9 nx ny < 2^31);
-//   - each CTA owns a strip of up to BLOCK columns and marches along y over
-//     a contiguous range of rows; one thread per column keeps the raw
-//     populations of the last four rows in registers (one row prefetched);
+//   - each CTA owns a strip of up to STRIP = 128 columns and marches along y
+//     over a contiguous range of rows; each thread owns one column, or (FP32
+//     staged kernel) a pair of adjacent columns computed with the paired
+//     FP32 instructions; population rows are streamed into a shared-memory
+//     stage ring by bulk asynchronous copies (or, unstaged, prefetched into
+//     registers one row ahead);
 //   - rho, phi = k^2 p0(rho) - rho/3 and lap(rho) of the rows in flight sit
 //     in an 8-row shared-memory ring that covers the strip plus two halo
 //     columns per side; the halo densities are summed from the neighbouring
@@ -40,13 +43,23 @@ struct KArgs {
     real *__restrict__ fout;
     long long plane;  // nx * ny (nodes per lattice)
     int nx, ny;
-    int W;            // strip width in columns (<= BLOCK)
+    int W;            // strip width in columns (<= STRIP)
     int nstrips;
     int yf0, nyf;     // first fluid row and number of fluid rows
     long long units;  // nstrips * nyf
     int nctas;        // logical CTAs of the schedule
     int reverse;      // launch the logical CTAs in reverse order
     real RT, a, b4, k2, kappa, tau, inv_tau, omb, gx, gy, wet, nu;
+    // equation of state: 0 Carnahan-Starling (RT, a, b4), 1 Peng-Robinson
+    // (RT, bpr = b, aalpha = a alpha(T))
+    int eos_kind;
+    real bpr, aalpha;
+    // collision: 0 BGK, 1 MRT with rates over the squared row norms of the
+    // moment basis (m_e = s_e/36, m_eps = s_eps/36, m_j = s_j/6, m_q = s_q/12,
+    // m_nu = s_nu/4); the equilibrium velocity is u + ushift F / rho with
+    // ushift = tau (BGK) or 1/s_j (MRT)
+    int mrt;
+    real ushift, m_e, m_eps, m_j, m_q, m_nu;
     // pressure columns: gas / liquid branch densities at the inlet and outlet
     // pressures, and the phase indicator theta = clamp((rho_f - ph_g) * inv_dph, 0, 1)
     real rho_in_g, rho_in_l, rho_out_g, rho_out_l, ph_g, inv_dph;
@@ -80,6 +93,88 @@ __device__ __forceinline__ constexpr real w_(int i)
 // FP64 path the IEEE division.
 __device__ __forceinline__ float rcp_(float v) { return __fdividef(1.0f, v); }
 __device__ __forceinline__ double rcp_(double v) { return 1.0 / v; }
+__device__ __forceinline__ float2 rcp_(float2 v) { return make_float2(__fdividef(1.0f, v.x), __fdividef(1.0f, v.y)); }
+
+// ---------------------------------------------------------------------------
+// Packs: the values of the CP adjacent columns one thread owns (float2 for a
+// pair of FP32 columns). Every operation is rounded once to nearest and none
+// is contracted, so a pair computed with the paired FP32 instructions and the
+// same columns computed one per thread give identical bits.
+// ---------------------------------------------------------------------------
+template <typename real, int CP>
+struct Pack;
+template <>
+struct Pack<float, 1> { using T = float; };
+template <>
+struct Pack<double, 1> { using T = double; };
+template <>
+struct Pack<float, 2> { using T = float2; };
+
+__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float2 add_(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul_(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma_(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b = (-1) b + a, exact product, one rounding: equal to the scalar subtraction
+__device__ __forceinline__ float2 sub_(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+
+// broadcast a constant into a pack
+template <typename V>
+__device__ __forceinline__ V bc(double v);
+template <>
+__device__ __forceinline__ float bc<float>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ double bc<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float2 bc<float2>(double v) { return make_float2((float)v, (float)v); }
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+template <typename V, typename real>
+__device__ __forceinline__ V bcr(real v);
+template <>
+__device__ __forceinline__ float bcr<float, float>(float v) { return v; }
+template <>
+__device__ __forceinline__ double bcr<double, double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float2 bcr<float2, float>(float v) { return make_float2(v, v); }
+
+// element k of a pack
+__device__ __forceinline__ float el(float v, int) { return v; }
+__device__ __forceinline__ double el(double v, int) { return v; }
+__device__ __forceinline__ float el(float2 v, int k) { return k ? v.y : v.x; }
+__device__ __forceinline__ void set_el(float &v, int, float x) { v = x; }
+__device__ __forceinline__ void set_el(double &v, int, double x) { v = x; }
+__device__ __forceinline__ void set_el(float2 &v, int k, float x)
+{
+    if (k) v.y = x;
+    else v.x = x;
+}
+
+// pack load / store (the address of a pair is 8-byte aligned)
+template <typename V, typename real>
+__device__ __forceinline__ V ldp(const real *p) { return *reinterpret_cast<const V *>(p); }
+template <typename V, typename real>
+__device__ __forceinline__ void stp(real *p, V v) { *reinterpret_cast<V *>(p) = v; }
+
+// x times a constant c that FP32 does not represent (1/3, 1/9, 1/12, 1/36,
+// 1/6): with c = hi + lo, hi = float(c), lo = float(c - hi), fma(x, hi, x lo)
+// is x c under one rounding, free of the constant's own rounding bias (which
+// would otherwise scale every collision's momentum or force the same way).
+template <typename V>
+__device__ __forceinline__ V mulk(V x, double c)
+{
+    if constexpr (sizeof(el(x, 0)) == 8) {
+        return mul_(x, bc<V>(c));
+    } else {
+        const float hi = (float)c, lo = (float)(c - (double)hi);
+        return fma_(x, bc<V>(hi), mul_(x, bc<V>(lo)));
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Bulk asynchronous copies global -> shared (cp.async.bulk, completion counted
@@ -132,20 +227,28 @@ __device__ __forceinline__ void fence_proxy_async_smem()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Mesh-space EOS potential phi = k^2 p0(rho) - rho/3 (Eqs. 2.14, 2.17), CS p0.
-template <typename real>
-__device__ __forceinline__ real eos_phi(const KArgs<real> &A, real rho)
+// Mesh-space EOS potential phi = k^2 p0(rho) - rho/3 (Eqs. 2.14, 2.17), CS p0
+// with eta = b rho / 4: p0 = rho RT (1 + eta + eta^2 - eta^3)/(1 - eta)^3 - a rho^2.
+template <typename V, typename real>
+__device__ __forceinline__ V eos_phi(const KArgs<real> &A, V rho)
 {
-    const real eta = A.b4 * rho;
-    const real om = real(1) - eta;
-    const real num = real(1) + eta * (real(1) + eta * (real(1) - eta));
-    const real p0 = rho * A.RT * num * rcp_(om * om * om) - A.a * rho * rho;
-    return A.k2 * p0 - rho * real(1.0 / 3.0);
+    const V one = bc<V>(1.0);
+    if (A.eos_kind == 1) {
+        // Peng-Robinson (Eq. 2.18): rho RT / (1 - x) - a alpha rho^2 / (1 + x (2 - x)), x = b rho
+        const V x = mul_(bcr<V>(A.bpr), rho);
+        const V i1 = rcp_(fma_(x, bc<V>(-1.0), one));
+        const V iD = rcp_(fma_(x, fma_(x, bc<V>(-1.0), bc<V>(2.0)), one));
+        const V p0 = fma_(mul_(mul_(rho, rho), bcr<V>(-A.aalpha)), iD, mul_(mul_(rho, bcr<V>(A.RT)), i1));
+        return sub_(mul_(bcr<V>(A.k2), p0), mulk(rho, 1.0 / 3.0));
+    }
+    const V eta = mul_(bcr<V>(A.b4), rho);
+    const V om = fma_(eta, bc<V>(-1.0), one);          // 1 - eta
+    const V num = fma_(eta, fma_(eta, om, one), one);  // 1 + eta (1 + eta (1 - eta))
+    const V ir = rcp_(mul_(mul_(om, om), om));
+    const V p0 = fma_(mul_(rho, rho), bcr<V>(-A.a), mul_(mul_(mul_(rho, bcr<V>(A.RT)), num), ir));
+    return sub_(mul_(bcr<V>(A.k2), p0), mulk(rho, 1.0 / 3.0));
 }
 
-// Density of a pressure column whose interior neighbour has density rho_f: the
-// EOS root at the column pressure on the branch of the neighbour's phase,
-// blended continuously across an interface (Sec. 2.2 pressure-driven ends).
 // Per-channel geometry of a segment: population buffers (read / written),
 // lattice size, strip width and the pressure-column branch densities.
 template <typename real>
@@ -156,14 +259,17 @@ struct Geom {
     real rho_in_g, rho_in_l, rho_out_g, rho_out_l;
 };
 
+// Density of a pressure column whose interior neighbour has density rho_f: the
+// EOS root at the column pressure on the branch of the neighbour's phase,
+// blended linearly across an interface (Sec. 2.2 pressure-driven ends).
 template <typename real>
 __device__ __forceinline__ real column_density(const KArgs<real> &A, const Geom<real> &G, bool outlet, real rho_f)
 {
-    real th = (rho_f - A.ph_g) * A.inv_dph;
+    real th = mul_(sub_(rho_f, A.ph_g), A.inv_dph);
     th = fmin(fmax(th, real(0)), real(1));
     const real g = outlet ? G.rho_out_g : G.rho_in_g;
     const real l = outlet ? G.rho_out_l : G.rho_in_l;
-    return g + th * (l - g);
+    return fma_(th, sub_(l, g), g);
 }
 
 // Row of the stored lattice that a stencil row yy reads, and whether it is a
@@ -196,8 +302,33 @@ __device__ __forceinline__ long long cut_units(const KArgs<real> &A, int c)
     return u;
 }
 
-// Resident CTAs per SM the register allocation is held to: 512 FP32 threads
-// per SM (<= 128 registers each); FP64 carries twice the state per thread.
+// Strip width and threads. A CTA owns a strip of up to STRIP columns; each
+// thread owns CP adjacent columns. By default every kernel takes one column
+// per thread (128 threads). LBM_FP32_PAIR=2 builds the FP32 staged kernel
+// with column pairs (float2 arithmetic on the paired FP32 instructions, 64
+// threads, bit-identical results): about a third fewer instructions, but with
+// shared memory holding ~640 columns per SM in flight it runs half the warps,
+// and the paired instructions keep the scalar latency, so it is slower.
+#ifndef LBM_STRIP
+#define LBM_STRIP 128
+#endif
+#ifndef LBM_FP32_PAIR
+#define LBM_FP32_PAIR 1
+#endif
+constexpr int STRIP = LBM_STRIP;
+template <typename real, bool STAGED>
+__host__ __device__ constexpr int cols_per_thread()
+{
+    return (sizeof(real) == 4 && STAGED) ? LBM_FP32_PAIR : 1;
+}
+template <typename real, bool STAGED>
+__host__ __device__ constexpr int threads_per_cta()
+{
+    return STRIP / cols_per_thread<real, STAGED>();
+}
+
+// Register allocation is held to LBM_FP32_THREADS_PER_SM resident FP32
+// threads per SM (256 for FP64, which carries twice the state per thread).
 #ifndef LBM_FP32_THREADS_PER_SM
 #define LBM_FP32_THREADS_PER_SM 512
 #endif
@@ -214,18 +345,20 @@ struct MinBlocks {
 #define LBM_STAGE_AHEAD 1
 #endif
 constexpr int STAGE_AHEAD = LBM_STAGE_AHEAD;
+// the wait for row j+1 comes before the barrier of iteration j, so that row
+// must have been issued in an earlier iteration
+static_assert(STAGE_AHEAD >= 1, "rows are issued at least one iteration before they are awaited");
 constexpr int NSTAGE = 5 + STAGE_AHEAD;
 
-// A stage holds one stencil row of the strip (local columns 0 .. BLOCK-1) for
+// A stage holds one stencil row of the strip (local columns 0 .. STRIP-1) for
 // the nine planes. Each plane segment starts on a 128-byte line when the strip
 // does, so a copy touches no more lines than it needs.
-template <int BLOCK>
-__host__ __device__ constexpr int stage_pitch() { return BLOCK; }
+__host__ __device__ constexpr int stage_pitch() { return STRIP; }
 
-template <typename real, int BLOCK>
+template <typename real>
 constexpr size_t staged_smem_bytes()
 {
-    return (size_t)NSTAGE * 9 * stage_pitch<BLOCK>() * sizeof(real) + NSTAGE * sizeof(uint64_t);
+    return (size_t)NSTAGE * 9 * stage_pitch() * sizeof(real) + NSTAGE * sizeof(uint64_t);
 }
 
 // Position in the stage ring (stage index and mbarrier phase parity).
@@ -239,42 +372,191 @@ struct RingPos {
 
 // f_eq of Eq. 2.2 built from the (i, opp(i)) pairs, which share their even
 // part c and differ in the sign of their odd part o: f_i = c + o, f_opp = c - o.
-// The rest population is rho minus the eight moving ones (= rho - 2 sum c), so
-// f_eq carries exactly rho up to unbiased rounding.
-template <typename real>
-__device__ __forceinline__ void feq_pairs(real rho, real ux, real uy, real (&fe)[9])
+// The odd parts 3 w_i rho (e_i . u) are taken from the momentum m = rho u
+// itself (mx, my; exact sums, no reciprocal), the even parts from u. The rest
+// population is rho minus the eight moving ones (= rho - 2 sum c), so f_eq
+// carries exactly rho and m up to unbiased rounding.
+template <typename V>
+__device__ __forceinline__ void feq_pairs(V rho, V ux, V uy, V mx, V my, V (&fe)[9])
 {
-    const real base = real(1) - real(1.5) * (ux * ux + uy * uy);
-    const real r1 = rho * real(1.0 / 9.0), r2 = rho * real(1.0 / 36.0);
-    const real s = ux + uy, d = uy - ux;  // e.u of directions 5 (1,1) and 6 (-1,1)
-    const real c1 = r1 * (base + real(4.5) * ux * ux), o1 = real(3) * r1 * ux;
-    const real c2 = r1 * (base + real(4.5) * uy * uy), o2 = real(3) * r1 * uy;
-    const real c5 = r2 * (base + real(4.5) * s * s), o5 = real(3) * r2 * s;
-    const real c6 = r2 * (base + real(4.5) * d * d), o6 = real(3) * r2 * d;
-    fe[1] = c1 + o1; fe[3] = c1 - o1;
-    fe[2] = c2 + o2; fe[4] = c2 - o2;
-    fe[5] = c5 + o5; fe[7] = c5 - o5;
-    fe[6] = c6 + o6; fe[8] = c6 - o6;
-    fe[0] = rho - real(2) * ((c1 + c2) + (c5 + c6));
+    const V usq = fma_(ux, ux, mul_(uy, uy));
+    const V base = fma_(usq, bc<V>(-1.5), bc<V>(1.0));
+    const V r1 = mulk(rho, 1.0 / 9.0), r2 = mulk(rho, 1.0 / 36.0);
+    const V s = add_(ux, uy), d = sub_(uy, ux);  // e.u of directions 5 (1,1) and 6 (-1,1)
+    const V h = bc<V>(4.5);
+    const V c1 = mul_(r1, fma_(mul_(ux, h), ux, base)), o1 = mulk(mx, 1.0 / 3.0);
+    const V c2 = mul_(r1, fma_(mul_(uy, h), uy, base)), o2 = mulk(my, 1.0 / 3.0);
+    const V c5 = mul_(r2, fma_(mul_(s, h), s, base)), o5 = mulk(add_(mx, my), 1.0 / 12.0);
+    const V c6 = mul_(r2, fma_(mul_(d, h), d, base)), o6 = mulk(sub_(my, mx), 1.0 / 12.0);
+    fe[1] = add_(c1, o1); fe[3] = sub_(c1, o1);
+    fe[2] = add_(c2, o2); fe[4] = sub_(c2, o2);
+    fe[5] = add_(c5, o5); fe[7] = sub_(c5, o5);
+    fe[6] = add_(c6, o6); fe[8] = sub_(c6, o6);
+    fe[0] = fma_(add_(add_(c1, c2), add_(c5, c6)), bc<V>(-2.0), rho);
 }
 
-// Unscaled isotropic gradient: 12 * grad psi = (4(E - W) + (NE - NW) + (SE - SW),
-//                                              4(N - S) + (NE - SE) + (NW - SW)).
-template <typename real, int SW>
-__device__ __forceinline__ void grad12(const real (*S)[SW], int qm, int q0, int qp, int c, real &gx,
-                                       real &gy)
+// West, centre and east packs of CP adjacent ring columns c .. c+CP-1 on one
+// ring row (c even for pairs: three aligned pair loads).
+template <typename V>
+struct Row3 {
+    V w, c, e;
+};
+template <typename real, int CP, int SW>
+__device__ __forceinline__ Row3<typename Pack<real, CP>::T> row3(const real (*S)[SW], int q, int c)
 {
-    const real E = S[q0][c + 1], W = S[q0][c - 1], N = S[qp][c], So = S[qm][c];
-    const real NE = S[qp][c + 1], NW = S[qp][c - 1], SE = S[qm][c + 1], SWv = S[qm][c - 1];
-    gx = real(4) * (E - W) + (NE - NW) + (SE - SWv);
-    gy = real(4) * (N - So) + (NE - SE) + (NW - SWv);
+    using V = typename Pack<real, CP>::T;
+    Row3<V> r;
+    if constexpr (CP == 1) {
+        r.w = S[q][c - 1];
+        r.c = S[q][c];
+        r.e = S[q][c + 1];
+    } else {
+        const float2 a = ldp<float2>(&S[q][c - 2]), b = ldp<float2>(&S[q][c]), d = ldp<float2>(&S[q][c + 2]);
+        r.w = make_float2(a.y, b.x);
+        r.c = b;
+        r.e = make_float2(b.y, d.x);
+    }
+    return r;
 }
+
+// 12 x isotropic gradient from rows below (m), at (z) and above (p):
+// (4(E - W) + (NE - NW) + (SE - SW), 4(N - S) + (NE - SE) + (NW - SW)).
+template <typename V>
+__device__ __forceinline__ void grad12(const Row3<V> &m, const Row3<V> &z, const Row3<V> &p, V &gx, V &gy)
+{
+    gx = fma_(sub_(z.e, z.w), bc<V>(4.0), add_(sub_(p.e, p.w), sub_(m.e, m.w)));
+    gy = fma_(sub_(p.c, m.c), bc<V>(4.0), add_(sub_(p.e, m.e), sub_(p.w, m.w)));
+}
+// the negated gradient, for the pressure term of the force
+template <typename V>
+__device__ __forceinline__ void ngrad12(const Row3<V> &m, const Row3<V> &z, const Row3<V> &p, V &gx, V &gy)
+{
+    gx = fma_(sub_(z.w, z.e), bc<V>(4.0), add_(sub_(p.w, p.e), sub_(m.w, m.e)));
+    gy = fma_(sub_(m.c, p.c), bc<V>(4.0), add_(sub_(m.e, p.e), sub_(m.w, p.w)));
+}
+// lap psi = 6 sum_i w_i (psi(x + e_i) - psi(x)) = (4 edges + corners - 20 psi) / 6
+template <typename V>
+__device__ __forceinline__ V lap9(const Row3<V> &m, const Row3<V> &z, const Row3<V> &p)
+{
+    const V edges = add_(add_(z.w, z.e), add_(m.c, p.c));
+    const V corners = add_(add_(m.w, m.e), add_(p.w, p.e));
+    return mulk(fma_(z.c, bc<V>(-20.0), fma_(edges, bc<V>(4.0), corners)), 1.0 / 6.0);
+}
+
+// MRT relaxation (Eq. 2.1) f* = f - M^-1 S M (f - f_eq) in the Lallemand-Luo
+// moment basis (rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy): the non-
+// equilibrium moments d = f - f_eq are scaled by s_k / |row_k|^2 and mapped
+// back with M^T (the rows are orthogonal). The density is conserved.
+template <typename V, typename real>
+__device__ __forceinline__ void mrt_relax(const KArgs<real> &A, const V (&f)[9], const V (&fe)[9], V (&fs)[9])
+{
+    V d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = sub_(f[i], fe[i]);
+    const V s14 = add_(add_(d[1], d[2]), add_(d[3], d[4]));
+    const V s58 = add_(add_(d[5], d[6]), add_(d[7], d[8]));
+    const V e = fma_(d[0], bc<V>(-4.0), sub_(mul_(s58, bc<V>(2.0)), s14));    // -4 d0 - s14 + 2 s58
+    const V ep = fma_(d[0], bc<V>(4.0), sub_(s58, mul_(s14, bc<V>(2.0))));    //  4 d0 - 2 s14 + s58
+    const V a13 = sub_(d[1], d[3]), bx = add_(sub_(d[5], d[6]), sub_(d[8], d[7]));
+    const V a24 = sub_(d[2], d[4]), by = sub_(add_(d[5], d[6]), add_(d[7], d[8]));
+    const V jx = add_(a13, bx), qx = fma_(a13, bc<V>(-2.0), bx);
+    const V jy = add_(a24, by), qy = fma_(a24, bc<V>(-2.0), by);
+    const V pxx = sub_(add_(d[1], d[3]), add_(d[2], d[4]));
+    const V pxy = sub_(add_(d[5], d[7]), add_(d[6], d[8]));
+    const V E = mul_(e, bcr<V>(A.m_e)), P = mul_(ep, bcr<V>(A.m_eps));
+    const V JX = mul_(jx, bcr<V>(A.m_j)), JY = mul_(jy, bcr<V>(A.m_j));
+    const V QX = mul_(qx, bcr<V>(A.m_q)), QY = mul_(qy, bcr<V>(A.m_q));
+    const V XX = mul_(pxx, bcr<V>(A.m_nu)), XY = mul_(pxy, bcr<V>(A.m_nu));
+    // M^T applied to the scaled moments
+    const V b14 = sub_(mul_(P, bc<V>(-2.0)), E);  // -E - 2P
+    const V xj = fma_(QX, bc<V>(-2.0), JX), yj = fma_(QY, bc<V>(-2.0), JY);
+    const V b58 = fma_(E, bc<V>(2.0), P);         // 2E + P
+    const V xq = add_(JX, QX), yq = add_(JY, QY);
+    fs[0] = sub_(f[0], mul_(sub_(P, E), bc<V>(4.0)));
+    fs[1] = sub_(f[1], add_(add_(b14, xj), XX));
+    fs[2] = sub_(f[2], sub_(add_(b14, yj), XX));
+    fs[3] = sub_(f[3], add_(sub_(b14, xj), XX));
+    fs[4] = sub_(f[4], sub_(sub_(b14, yj), XX));
+    fs[5] = sub_(f[5], add_(add_(add_(b58, xq), yq), XY));
+    fs[6] = sub_(f[6], sub_(add_(sub_(b58, xq), yq), XY));
+    fs[7] = sub_(f[7], add_(sub_(sub_(b58, xq), yq), XY));
+    fs[8] = sub_(f[8], sub_(sub_(add_(b58, xq), yq), XY));
+}
+
+// Non-equilibrium extrapolation of a pressure column (Sec. 2.2 ends) from its
+// interior neighbour x_f (density rho_f, velocity v, momentum m = rho_f v,
+// populations f):
+// f*_i = f_eq_i(rho_b, v) + (1 - 1/tau)(f_i - f_eq_i(rho_f, v)), with
+// f_eq(rho_b, v) = (rho_b / rho_f) f_eq(rho_f, v).
+template <typename real>
+__device__ __forceinline__ void column_extrapolate(const KArgs<real> &A, real rho_b, real rho_f, real vx, real vy,
+                                                   real mx, real my, const real (&f)[9], real (&fs)[9])
+{
+    real ff[9];
+    feq_pairs<real>(rho_f, vx, vy, mx, my, ff);
+    const real sc = mul_(rho_b, rcp_(rho_f));
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fs[i] = fma_(sc, ff[i], mul_(A.omb, sub_(f[i], ff[i])));
+}
+
+// Wall pressure (Eq. 2.4 in mesh units) at ring column cc of row q0:
+// k^2 p0 - kappa rho lap rho - (kappa/2)|grad rho|^2, with k^2 p0 = phi + rho/3.
+template <typename real, int SW>
+__device__ __forceinline__ real wall_pressure(const KArgs<real> &A, const real (*R)[SW], const real (*P)[SW],
+                                              const real (*L)[SW], int qm, int q0, int qp, int cc, real rho)
+{
+    real grx, gry;
+    grad12<real>(row3<real, 1, SW>(R, qm, cc), row3<real, 1, SW>(R, q0, cc), row3<real, 1, SW>(R, qp, cc), grx,
+                 gry);
+    grx = mulk(grx, 1.0 / 12.0);
+    gry = mulk(gry, 1.0 / 12.0);
+    const real k2p0 = add_(P[q0][cc], mulk(rho, 1.0 / 3.0));
+    const real t = fma_(mul_(A.kappa, rho), -L[q0][cc], k2p0);
+    return fma_(fma_(grx, grx, mul_(gry, gry)), mul_(real(-0.5), A.kappa), t);
+}
+
+// Per-thread diagnostic accumulators of the states read.
+template <typename real, int CP>
+struct Acc {
+    using V = typename Pack<real, CP>::T;
+    double mass, J;
+    V macc;
+    int mcount;
+    real tmin, tmax, pmin, pmax;
+    bool bad;
+    __device__ __forceinline__ void reset()
+    {
+        mass = 0.0; J = 0.0; macc = bc<V>(0.0); mcount = 0;
+        tmin = pmin = real(INFINITY); tmax = pmax = real(-INFINITY);
+        bad = false;
+    }
+    __device__ __forceinline__ void flush()
+    {
+#pragma unroll
+        for (int k = 0; k < CP; ++k) mass += (double)el(macc, k);
+        macc = bc<V>(0.0);
+        mcount = 0;
+    }
+};
+
+// Static shared-memory working set of a CTA: the 8-row stencil ring (density,
+// EOS potential, Laplacian; strip plus two halo columns per side) and the
+// reduction scratch.
+template <typename real, int BLOCK>
+struct Smem {
+    __align__(16) real rho[RING][STRIP + 4];
+    __align__(16) real phi[RING][STRIP + 4];
+    __align__(16) real lap[RING][STRIP + 4];
+    double red[BLOCK / 32][2];
+    real ext[BLOCK / 32][4];
+    int bad;
+};
 
 // One fused time step (MODE_STEP) or the macroscopic fields (MODE_FIELDS).
 //
 // Per segment (strip of columns x0 .. x0+xw-1, fluid rows ya .. yb-1) the CTA
 // runs iterations yy = ya-2 .. yb+2 with one barrier each:
-//   (1) re-read (L1) the populations of the collision row r = yy-3;
+//   (1) (unstaged) re-read (L1) the populations of the collision row r = yy-3;
 //   (2) density and phi of stencil row yy from the populations prefetched in
 //       the previous iteration, then prefetch row yy+1;
 //   (3) Laplacian of row yy-2 (its density rows were completed before the
@@ -285,82 +567,67 @@ __device__ __forceinline__ void grad12(const real (*S)[SW], int qm, int q0, int 
 // The ring keeps 8 rows, so the writes of iteration yy+1 never touch the rows
 // iteration yy still reads.
 //
-// STAGED: the strip's populations of each stencil row (9 plane segments of xw
-// values) are streamed by one producer thread with bulk asynchronous copies
-// into a ring of NSTAGE shared-memory stages, issued STAGE_AHEAD + 1 rows
-// ahead; consumers read densities and collision populations from the stage
-// (needs nx and the strip width to be multiples of 4 for 16-byte aligned
-// copies). Otherwise each thread loads its column with one row of register
-// prefetch and re-reads the collision row from L1. In both variants the four
-// halo lanes load the two columns beyond each strip edge with one row of
-// register prefetch.
-// Per-thread diagnostic accumulators of the states read.
-template <typename real>
-struct Acc {
-    double mass, J;
-    real macc;
-    int mcount;
-    real tmin, tmax, pmin, pmax;
-    bool bad;
-    __device__ __forceinline__ void reset()
-    {
-        mass = 0.0; J = 0.0; macc = real(0); mcount = 0;
-        tmin = pmin = real(INFINITY); tmax = pmax = real(-INFINITY);
-        bad = false;
-    }
-};
-
-// Static shared-memory working set of a CTA: the 8-row stencil ring (density,
-// EOS potential, Laplacian; strip plus two halo columns per side) and the
-// reduction scratch.
-template <typename real, int BLOCK>
-struct Smem {
-    real rho[RING][BLOCK + 4];
-    real phi[RING][BLOCK + 4];
-    real lap[RING][BLOCK + 4];
-    double red[BLOCK / 32][2];
-    real ext[BLOCK / 32][4];
-    int bad;
-};
-
-// One segment: strip s (columns s*W ..) of the lattice G, fluid rows ya .. yb-1.
-// Every thread of the CTA calls it with the same arguments.
-template <typename real, bool WALLS, bool PRES, int MODE, int BLOCK, bool STAGED>
+// Each thread owns CP adjacent columns (c0 = CP tid). STAGED: the strip's
+// populations of each stencil row (9 plane segments of xw values) are
+// streamed by one producer thread with bulk asynchronous copies into a ring
+// of NSTAGE shared-memory stages, issued STAGE_AHEAD + 1 rows ahead; consumers
+// read densities and collision populations from the stage (needs nx and the
+// strip width to be multiples of 4 for 16-byte aligned copies, so pairs are
+// always complete and a pressure column's interior neighbour is the other
+// column of its own pair). Otherwise (CP = 1) each thread loads its column
+// with one row of register prefetch and re-reads the collision row from L1.
+// In both variants four halo lanes load the two columns beyond each strip
+// edge with one row of register prefetch.
+template <typename real, bool WALLS, bool PRES, int MODE, int BLOCK, bool STAGED, int CP>
 __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<real> &G, int s, int ya, int yb,
                                             Smem<real, BLOCK> &S, real *stages, uint64_t *bars,
-                                            RingPos &ring_next, Acc<real> &acc, bool &lost)
+                                            RingPos &ring_next, Acc<real, CP> &acc, bool &lost)
 {
-    constexpr int SW = BLOCK + 4;
+    using V = typename Pack<real, CP>::T;
+    constexpr int SW = STRIP + 4;
+    constexpr int NW = BLOCK / 32;
     constexpr int PRODUCER = BLOCK - 1;  // no halo duty
-    constexpr int SP = stage_pitch<BLOCK>();
+    constexpr int SP = stage_pitch();
+    static_assert(CP * BLOCK == STRIP, "a CTA covers one strip");
+    static_assert(CP == 1 || STAGED, "column pairs need the staged kernel");
+    static_assert(NW == 2 || NW >= 4, "halo lanes: two warps or four and more");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const real third = real(1.0 / 3.0), twelfth = real(1.0 / 12.0), sixth = real(1.0 / 6.0);
+    const real third = real(1.0 / 3.0);
     const int nx = G.nx, ny = G.ny;
     const int rstride = 9 * nx;  // row stride of the population layout f[y][i][x]
     // push targets of directions 1..8 relative to the source slot index
     const int o1 = nx + 1, o2 = rstride + 2 * nx, o3 = 3 * nx - 1, o4 = 4 * nx - rstride;
     const int o5 = rstride + 5 * nx + 1, o6 = rstride + 6 * nx - 1, o7 = 7 * nx - rstride - 1;
     const int o8 = 8 * nx - rstride + 1;
-    real b_rho1 = 0, b_v1 = 0, t_v2 = 0;  // wall-pair carries (rows 1 -> 2, ny-3 -> ny-2)
+    real b_rho1[CP], b_v1[CP], t_v2[CP];  // wall-pair carries (rows 1 -> 2, ny-3 -> ny-2)
+#pragma unroll
+    for (int k = 0; k < CP; ++k) b_rho1[k] = b_v1[k] = t_v2[k] = real(0);
 
     const int x0 = s * G.W;
     const int xw = min(G.W, nx - x0);
-    const bool active = tid < xw;
-    const int x = x0 + tid;
-    const bool pin = PRES && active && x == 0;
-    const bool pout = PRES && active && x == nx - 1;
-    const bool pcol = pin || pout;
-    const int xc = pin ? 1 : (pout ? nx - 2 : x);  // column whose populations this thread loads
-    const int ccol = xc - x0 + 2;                  // its shared-memory column
+    const int c0 = CP * tid;  // first local column of this thread
+    const bool active = c0 < xw;
+    const int xa = x0 + c0;   // its global column
+    // pressure columns: with pairs, x = 0 is element 0 and x = nx-1 element 1
+    const bool pin = PRES && active && xa == 0;
+    const bool pout = PRES && active && xa + CP - 1 == nx - 1;
+    const bool anyp = pin || pout;
+    // CP = 1: a pressure column sums and collides its interior neighbour's column
+    const int scol = (CP == 1) ? ((pin ? 1 : (pout ? nx - 2 : xa)) - x0) : c0;  // stage column
+    const int ccol = scol + 2;                                                   // ring column
     // pushes never wrap or leave the lattice in x
-    const bool x_inner = !pcol && (PRES || (x >= 1 && x <= nx - 2));
+    const bool x_inner = !anyp && (PRES || (xa >= 1 && xa + CP - 1 <= nx - 2));
 
-    // Halo columns (lane 0 of warps 0..3): local -2, -1, xw, xw+1.
-    // hmode 1: density of column hx; 2 / 3: inlet / outlet column density
-    // derived from column hx = 1 / nx-2 (clamp beyond the pressure columns).
+    // Halo columns local -2, -1, xw, xw+1 (four lanes: lane 0 of warps 0..3,
+    // or lanes 0 and 1 of two warps). hmode 1: density of column hx; 2 / 3:
+    // inlet / outlet column density derived from column hx = 1 / nx-2 (clamp
+    // beyond the pressure columns).
+    int hidx = -1;
+    if (NW >= 4) { if (lane == 0 && warp < 4) hidx = warp; }
+    else if (lane < 2) hidx = 2 * warp + lane;
     int hmode = 0, hx = 0, hcol = 0;
-    if (lane == 0 && warp < 4) {
-        const int hloc = (warp < 2) ? (warp - 2) : (xw + warp - 2);
+    if (hidx >= 0) {
+        const int hloc = (hidx < 2) ? (hidx - 2) : (xw + hidx - 2);
         hcol = hloc + 2;
         const int gxh = x0 + hloc;
         if (PRES) {
@@ -373,29 +640,33 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
         }
     }
     // Laplacian of the two halo columns next to the strip (local -1, xw)
-    const int lhalo = (lane == 1 && warp == 1) ? 1 : ((lane == 1 && warp == 2) ? xw + 2 : -1);
+    int lhalo = -1;
+    if (NW >= 4) lhalo = (lane == 1 && warp == 1) ? 1 : ((lane == 1 && warp == 2) ? xw + 2 : -1);
+    else if (lane == 2) lhalo = warp == 0 ? 1 : xw + 2;
 
-    const real *__restrict__ col_in = G.fin + xc;
+    const real *__restrict__ col_in = G.fin + x0 + scol;
     const real *__restrict__ hal_in = G.fin + hx;
-    const int scol = xc - x0;            // this thread's column inside a stage
-    const int nrows = yb - ya + 4;       // stencil rows ya-2 .. yb+1
-    real pf[9], hf[9];
+    const int nrows = yb - ya + 4;  // stencil rows ya-2 .. yb+1
+    V pf[9];
+    real hf[9];
     real add_next = real(0);  // wetting offset of the next stencil row (mirrored wall ghost)
     // halo (and, without staging, own-column) loads of stencil row yy
     auto prefetch = [&](int yy) {
         bool mir;
         const int row = map_row<WALLS>(yy, ny, mir) * rstride;
         add_next = mir ? A.wet : real(0);
-        if (!STAGED && active) {
+        if constexpr (!STAGED) {
+            if (active) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) pf[i] = __ldg(col_in + row + i * nx);
+                for (int i = 0; i < 9; ++i) pf[i] = __ldg(col_in + row + i * nx);
+            }
         }
         if (hmode) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) hf[i] = __ldg(hal_in + row + i * nx);
         }
     };
-    // producer: stream stencil row j of this segment into stage position ip
+    // producer: stream stencil row j of this segment into the next stage
     RingPos ring_issue = ring_next;
     auto issue = [&](int j) {
         if (j < nrows) {
@@ -417,7 +688,7 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
     RingPos ring_coll = ring_next;
     for (int k = 0; k < NSTAGE - 3; ++k) ring_coll.advance();
 #pragma unroll
-    for (int i = 0; i < 9; ++i) { pf[i] = real(0); hf[i] = real(0); }
+    for (int i = 0; i < 9; ++i) { pf[i] = bc<V>(0.0); hf[i] = real(0); }
     prefetch(ya - 2);
     if constexpr (STAGED) {
         for (int j = 0; j <= STAGE_AHEAD; ++j) issue(j);
@@ -430,14 +701,16 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
         const int r = yy - 3;
         const int j = yy - (ya - 2);
         const bool collide = r >= ya && r < yb;  // uniform over the CTA
-        const uint32_t st_cons = ring_next.s, ph_cons = ring_next.ph, st_coll = ring_coll.s;
+        const uint32_t st_cons = ring_next.s, st_coll = ring_coll.s;
 
         // (1) populations of the collision row (read from HBM three iterations ago)
-        real f[9];
-        if (!STAGED && collide && active) {
-            const real *src = col_in + r * rstride;
+        V f[9];
+        if constexpr (!STAGED) {
+            if (collide && active) {
+                const real *src = col_in + r * rstride;
 #pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] = __ldg(src + i * nx);
+                for (int i = 0; i < 9; ++i) f[i] = __ldg(src + i * nx);
+            }
         }
 
         // (2) density and EOS potential of stencil row yy (staged: its
@@ -445,44 +718,56 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
         if (yy <= yb + 1) {
             const real add = add_next;
             const int rs = yy & (RING - 1);
-            real rho_own = real(0), rho_h = real(0);
+            V rho_own = bc<V>(0.0);
+            real rho_h = real(0);
             if constexpr (STAGED) {
-                (void)ph_cons;
-                const real *stg = stages + (size_t)st_cons * 9 * SP;
+                const real *stg = stages + (size_t)st_cons * 9 * SP + scol;
                 if (active) {
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) pf[i] = stg[i * SP + scol];
+                    for (int i = 0; i < 9; ++i) pf[i] = ldp<V>(stg + i * SP);
                 }
             }
             if (active) {
-                real sum = ((pf[0] + pf[1]) + (pf[2] + pf[3])) + ((pf[4] + pf[5]) + (pf[6] + pf[7])) + pf[8];
-                rho_own = (pcol ? column_density(A, G, pout, sum) : sum) + add;
+                V sum = add_(add_(add_(pf[0], pf[1]), add_(pf[2], pf[3])), add_(add_(pf[4], pf[5]), add_(pf[6], pf[7])));
+                sum = add_(sum, pf[8]);
+                if (anyp) {
+                    if constexpr (CP == 1) {
+                        set_el(sum, 0, column_density(A, G, pout, el(sum, 0)));
+                    } else {
+                        // the pair (0, 1) or (nx-2, nx-1): the column takes the other element's sum
+                        if (pin) set_el(sum, 0, column_density(A, G, false, el(sum, 1)));
+                        if (pout) set_el(sum, CP - 1, column_density(A, G, true, el(sum, CP - 2)));
+                    }
+                }
+                rho_own = add_(sum, bcr<V>(add));
             }
             if (hmode) {
-                real sum = ((hf[0] + hf[1]) + (hf[2] + hf[3])) + ((hf[4] + hf[5]) + (hf[6] + hf[7])) + hf[8];
-                rho_h = (hmode == 1 ? sum : column_density(A, G, hmode == 3, sum)) + add;
+                real sum = add_(add_(add_(hf[0], hf[1]), add_(hf[2], hf[3])), add_(add_(hf[4], hf[5]), add_(hf[6], hf[7])));
+                sum = add_(sum, hf[8]);
+                rho_h = add_(hmode == 1 ? sum : column_density(A, G, hmode == 3, sum), add);
             }
             if (yy + 1 <= yb + 1) prefetch(yy + 1);
             if (active) {
-                S.rho[rs][tid + 2] = rho_own;
-                S.phi[rs][tid + 2] = eos_phi(A, rho_own);
+                stp<V>(&S.rho[rs][c0 + 2], rho_own);
+                stp<V>(&S.phi[rs][c0 + 2], eos_phi<V>(A, rho_own));
             }
             if (hmode) {
                 S.rho[rs][hcol] = rho_h;
-                S.phi[rs][hcol] = eos_phi(A, rho_h);
+                S.phi[rs][hcol] = eos_phi<real>(A, rho_h);
             }
         }
 
         // (3) Laplacian of row yy-2 on local columns -1 .. xw
         if (yy >= ya + 1) {
             const int lr = (yy - 2) & (RING - 1), lm = (yy - 3) & (RING - 1), lp = (yy - 1) & (RING - 1);
-            auto lap_at = [&](int c) {
-                const real edges = (S.rho[lr][c - 1] + S.rho[lr][c + 1]) + (S.rho[lm][c] + S.rho[lp][c]);
-                const real corners = (S.rho[lm][c - 1] + S.rho[lm][c + 1]) + (S.rho[lp][c - 1] + S.rho[lp][c + 1]);
-                S.lap[lr][c] = (real(4) * edges + corners - real(20) * S.rho[lr][c]) * sixth;
-            };
-            if (active) lap_at(tid + 2);
-            if (lhalo >= 0) lap_at(lhalo);
+            if (active) {
+                const V L = lap9<V>(row3<real, CP, SW>(S.rho, lm, c0 + 2), row3<real, CP, SW>(S.rho, lr, c0 + 2),
+                                    row3<real, CP, SW>(S.rho, lp, c0 + 2));
+                stp<V>(&S.lap[lr][c0 + 2], L);
+            }
+            if (lhalo >= 0)
+                S.lap[lr][lhalo] = lap9<real>(row3<real, 1, SW>(S.rho, lm, lhalo), row3<real, 1, SW>(S.rho, lr, lhalo),
+                                              row3<real, 1, SW>(S.rho, lp, lhalo));
         }
         if constexpr (STAGED) {
             // one thread waits for the next stencil row's stage; the
@@ -508,123 +793,159 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
             if constexpr (STAGED) {
                 const real *sp = stages + (size_t)st_coll * 9 * SP + scol;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) f[i] = sp[i * SP];
+                for (int i = 0; i < 9; ++i) f[i] = ldp<V>(sp + i * SP);
             }
             const int q0 = r & (RING - 1), qm = (r - 1) & (RING - 1), qp = (r + 1) & (RING - 1);
-            const int c = ccol;
-            real gpx, gpy, glx, gly;
-            grad12<real, SW>(S.phi, qm, q0, qp, c, gpx, gpy);
-            grad12<real, SW>(S.lap, qm, q0, qp, c, glx, gly);
-            const real rho = S.rho[q0][c];
-            const real kr = A.kappa * rho;
-            const real Fx = (kr * glx - gpx) * twelfth + A.gx;
-            const real Fy = (kr * gly - gpy) * twelfth + A.gy;
-            const real jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-            const real jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-            const real irho = rcp_(rho);
-            const real ux = jx * irho, uy = jy * irho;
-            const real hFi = real(0.5) * irho;
-            const real vx = ux + hFi * Fx, vy = uy + hFi * Fy;
+            V ngpx, ngpy, glx, gly;
+            ngrad12<V>(row3<real, CP, SW>(S.phi, qm, ccol), row3<real, CP, SW>(S.phi, q0, ccol),
+                       row3<real, CP, SW>(S.phi, qp, ccol), ngpx, ngpy);
+            grad12<V>(row3<real, CP, SW>(S.lap, qm, ccol), row3<real, CP, SW>(S.lap, q0, ccol),
+                      row3<real, CP, SW>(S.lap, qp, ccol), glx, gly);
+            const V rho = ldp<V>(&S.rho[q0][ccol]);
+            const V kr = mul_(bcr<V>(A.kappa), rho);
+            const V Fx = add_(mulk(fma_(kr, glx, ngpx), 1.0 / 12.0), bcr<V>(A.gx));
+            const V Fy = add_(mulk(fma_(kr, gly, ngpy), 1.0 / 12.0), bcr<V>(A.gy));
+            const V jx = add_(add_(sub_(f[1], f[3]), sub_(f[5], f[6])), sub_(f[8], f[7]));
+            const V jy = sub_(add_(sub_(f[2], f[4]), add_(f[5], f[6])), add_(f[7], f[8]));
+            const V irho = rcp_(rho);
+            const V ux = mul_(jx, irho), uy = mul_(jy, irho);
+            const V hFi = mul_(irho, bc<V>(0.5));
+            const V vx = fma_(hFi, Fx, ux), vy = fma_(hFi, Fy, uy);
+            // own-column density (a pressure column's own is rho_b)
+            const V rho_own = (CP == 1 && anyp) ? bcr<V>(S.rho[q0][tid + 2]) : rho;
 
             if (MODE == MODE_STEP) {
-                real fs[9];
-                if (!pcol) {
-                    const real tFi = A.tau * irho;
-                    real fe[9];
-                    feq_pairs<real>(rho, ux + tFi * Fx, uy + tFi * Fy, fe);
+                V fs[9];
+                {
+                    // shifted equilibrium: momentum j + ushift F, velocity (j + ushift F) / rho
+                    const V mx = fma_(bcr<V>(A.ushift), Fx, jx), my = fma_(bcr<V>(A.ushift), Fy, jy);
+                    V fe[9];
+                    feq_pairs<V>(rho, mul_(mx, irho), mul_(my, irho), mx, my, fe);
+                    if (A.mrt) {
+                        mrt_relax<V, real>(A, f, fe, fs);
+                    } else {
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) fs[i] = f[i] + (fe[i] - f[i]) * A.inv_tau;
-                } else {
-                    // non-equilibrium extrapolation from the interior neighbour:
-                    // f_eq(rho_b, v) = (rho_b / rho_f) f_eq(rho_f, v)
-                    const real rho_b = S.rho[q0][tid + 2];
-                    real ff[9];
-                    feq_pairs<real>(rho, vx, vy, ff);
-                    const real sc = rho_b * irho;
+                        for (int i = 0; i < 9; ++i) fs[i] = fma_(sub_(fe[i], f[i]), bcr<V>(A.inv_tau), f[i]);
+                    }
+                }
+                if (anyp) {
+                    // pressure column: extrapolate from the interior neighbour
+                    // (CP = 1: this thread's values are the neighbour's; pairs:
+                    // the other element of the pair)
+                    const int kc = pin ? 0 : CP - 1, kf = (CP == 1) ? 0 : (pin ? 1 : CP - 2);
+                    real ff[9], fsc[9];
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) fs[i] = sc * ff[i] + A.omb * (f[i] - ff[i]);
+                    for (int i = 0; i < 9; ++i) ff[i] = el(f[i], kf);
+                    // momentum of the neighbour's v = (j + F/2) / rho
+                    const real mvx = fma_(real(0.5), el(Fx, kf), el(jx, kf));
+                    const real mvy = fma_(real(0.5), el(Fy, kf), el(jy, kf));
+                    column_extrapolate<real>(A, el(rho_own, kc), el(rho, kf), el(vx, kf), el(vy, kf), mvx, mvy, ff,
+                                             fsc);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) set_el(fs[i], kc, fsc[i]);
                 }
                 real *const out = G.fout;
-                const int oi = r * rstride + x;  // slot of (x, r) in plane 0
+                const int oi = r * rstride + xa;  // slot of (xa, r) in plane 0
                 const bool y_inner = WALLS ? (r >= 2 && r <= ny - 3) : (r >= 1 && r <= ny - 2);
                 if (x_inner && y_inner) {
-                    out[oi] = fs[0];
-                    out[oi + o1] = fs[1];
-                    out[oi + o2] = fs[2];
-                    out[oi + o3] = fs[3];
-                    out[oi + o4] = fs[4];
-                    out[oi + o5] = fs[5];
-                    out[oi + o6] = fs[6];
-                    out[oi + o7] = fs[7];
-                    out[oi + o8] = fs[8];
+                    if constexpr (CP == 1) {
+                        out[oi] = fs[0];
+                        out[oi + o1] = fs[1];
+                        out[oi + o2] = fs[2];
+                        out[oi + o3] = fs[3];
+                        out[oi + o4] = fs[4];
+                        out[oi + o5] = fs[5];
+                        out[oi + o6] = fs[6];
+                        out[oi + o7] = fs[7];
+                        out[oi + o8] = fs[8];
+                    } else {
+                        // directions without an x component keep the pair together
+                        stp<V>(out + oi, fs[0]);
+                        stp<V>(out + oi + o2, fs[2]);
+                        stp<V>(out + oi + o4, fs[4]);
+                        out[oi + o1] = el(fs[1], 0); out[oi + o1 + 1] = el(fs[1], 1);
+                        out[oi + o3] = el(fs[3], 0); out[oi + o3 + 1] = el(fs[3], 1);
+                        out[oi + o5] = el(fs[5], 0); out[oi + o5 + 1] = el(fs[5], 1);
+                        out[oi + o6] = el(fs[6], 0); out[oi + o6 + 1] = el(fs[6], 1);
+                        out[oi + o7] = el(fs[7], 0); out[oi + o7 + 1] = el(fs[7], 1);
+                        out[oi + o8] = el(fs[8], 0); out[oi + o8 + 1] = el(fs[8], 1);
+                    }
                 } else {
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        const int ty = r + ey_(i);
-                        if (WALLS && (ty == 0 || ty == ny - 1)) {
-                            // half-way bounce-back into the opposite slot of this node
-                            out[oi + opp_(i) * nx] = fs[i];
-                        } else {
-                            int tx = x + ex_(i);
-                            if (PRES) {
-                                if (tx < 0 || tx >= nx) continue;  // leaves through the column
+                    for (int k = 0; k < CP; ++k) {
+                        const int xk = xa + k, ok = oi + k;
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) {
+                            const int ty = r + ey_(i);
+                            if (WALLS && (ty == 0 || ty == ny - 1)) {
+                                // half-way bounce-back into the opposite slot of this node
+                                out[ok + opp_(i) * nx] = el(fs[i], k);
                             } else {
-                                tx = tx < 0 ? tx + nx : (tx >= nx ? tx - nx : tx);
+                                int tx = xk + ex_(i);
+                                if (PRES) {
+                                    if (tx < 0 || tx >= nx) continue;  // leaves through the column
+                                } else {
+                                    tx = tx < 0 ? tx + nx : (tx >= nx ? tx - nx : tx);
+                                }
+                                int tyw = ty;
+                                if (!WALLS) tyw = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
+                                out[tyw * rstride + i * nx + tx] = el(fs[i], k);
                             }
-                            int tyw = ty;
-                            if (!WALLS) tyw = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
-                            out[tyw * rstride + i * nx + tx] = fs[i];
                         }
                     }
                 }
-                const real mrho = pcol ? S.rho[q0][tid + 2] : rho;
-                if (sizeof(real) == 8) acc.mass += (double)mrho;
-                else {
-                    acc.macc += mrho;
-                    if (++acc.mcount == 16) { acc.mass += (double)acc.macc; acc.macc = real(0); acc.mcount = 0; }
+                acc.macc = add_(acc.macc, rho_own);
+                if (++acc.mcount == 16) acc.flush();
+#pragma unroll
+                for (int k = 0; k < CP; ++k) {
+                    const real rk = el(rho, k);
+                    if (!(rk > real(0)) || !(rk < real(1e30))) acc.bad = true;
                 }
-                if (!(rho > real(0)) || !(rho < real(1e30))) acc.bad = true;
             } else {
-                const long long oi = (long long)r * nx + x;
-                A.o_rho[oi] = pcol ? S.rho[q0][tid + 2] : rho;
-                A.o_vx[oi] = vx;
-                A.o_vy[oi] = vy;
+#pragma unroll
+                for (int k = 0; k < CP; ++k) {
+                    const bool pk = (k == 0 && pin) || (k == CP - 1 && pout);
+                    const int kv = (CP == 1 || !pk) ? k : (k == 0 ? 1 : CP - 2);  // a column reports v_f
+                    const long long oi = (long long)r * nx + xa + k;
+                    A.o_rho[oi] = el(rho_own, k);
+                    A.o_vx[oi] = el(vx, kv);
+                    A.o_vy[oi] = el(vy, kv);
+                }
             }
 
-            if (WALLS && !pcol && (r <= 2 || r >= ny - 3)) {
+            if (WALLS && (r <= 2 || r >= ny - 3)) {
                 // wall shear: quadratic through v = 0 on the half-way plane and
                 // v at distances 1/2 and 3/2; wall pressure: Eq. 2.4 in mesh units
-                auto pwall = [&]() {
-                    real grx, gry;
-                    grad12<real, SW>(S.rho, qm, q0, qp, c, grx, gry);
-                    grx *= twelfth;
-                    gry *= twelfth;
-                    return S.phi[q0][c] + rho * third - A.kappa * rho * S.lap[q0][c]
-                           - real(0.5) * A.kappa * (grx * grx + gry * gry);
-                };
-                if (r == 1) {
-                    b_rho1 = rho;
-                    b_v1 = vx;
-                    const real pw = pwall();
-                    if (MODE == MODE_STEP) { acc.pmin = fmin(acc.pmin, pw); acc.pmax = fmax(acc.pmax, pw); }
-                    else A.o_pw[x] = pw;
-                }
-                if (r == ny - 3) t_v2 = vx;
-                if (r == 2) {
-                    const real tw = b_rho1 * A.nu * (real(9) * b_v1 - vx) * third;
-                    if (MODE == MODE_STEP) { acc.J += (double)tw; acc.tmin = fmin(acc.tmin, tw); acc.tmax = fmax(acc.tmax, tw); }
-                    else A.o_tw[x] = tw;
-                }
-                if (r == ny - 2) {
-                    const real tw = rho * A.nu * (real(9) * vx - t_v2) * third;
-                    const real pw = pwall();
-                    if (MODE == MODE_STEP) {
-                        acc.J += (double)tw;
-                        acc.tmin = fmin(acc.tmin, tw); acc.tmax = fmax(acc.tmax, tw);
-                        acc.pmin = fmin(acc.pmin, pw); acc.pmax = fmax(acc.pmax, pw);
-                    } else {
-                        A.o_tw[nx + x] = tw;
-                        A.o_pw[nx + x] = pw;
+#pragma unroll
+                for (int k = 0; k < CP; ++k) {
+                    const bool pk = (k == 0 && pin) || (k == CP - 1 && pout);
+                    if (pk) continue;
+                    const int cc = ccol + k, xk = xa + k;
+                    const real rk = el(rho, k), vk = el(vx, k);
+                    if (r == 1) {
+                        b_rho1[k] = rk;
+                        b_v1[k] = vk;
+                        const real pw = wall_pressure<real, SW>(A, S.rho, S.phi, S.lap, qm, q0, qp, cc, rk);
+                        if (MODE == MODE_STEP) { acc.pmin = fmin(acc.pmin, pw); acc.pmax = fmax(acc.pmax, pw); }
+                        else A.o_pw[xk] = pw;
+                    }
+                    if (r == ny - 3) t_v2[k] = vk;
+                    if (r == 2) {
+                        const real tw = mul_(mul_(b_rho1[k], A.nu), mul_(fma_(real(9), b_v1[k], -vk), third));
+                        if (MODE == MODE_STEP) { acc.J += (double)tw; acc.tmin = fmin(acc.tmin, tw); acc.tmax = fmax(acc.tmax, tw); }
+                        else A.o_tw[xk] = tw;
+                    }
+                    if (r == ny - 2) {
+                        const real tw = mul_(mul_(rk, A.nu), mul_(fma_(real(9), vk, -t_v2[k]), third));
+                        const real pw = wall_pressure<real, SW>(A, S.rho, S.phi, S.lap, qm, q0, qp, cc, rk);
+                        if (MODE == MODE_STEP) {
+                            acc.J += (double)tw;
+                            acc.tmin = fmin(acc.tmin, tw); acc.tmax = fmax(acc.tmax, tw);
+                            acc.pmin = fmin(acc.pmin, pw); acc.pmax = fmax(acc.pmax, pw);
+                        } else {
+                            A.o_tw[nx + xk] = tw;
+                            A.o_pw[nx + xk] = pw;
+                        }
                     }
                 }
             }
@@ -635,14 +956,12 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
 }
 
 // Fixed-order CTA reduction of the accumulators; thread 0 receives the totals.
-template <typename real, int BLOCK>
-__device__ __forceinline__ void cta_reduce(Acc<real> &acc, Smem<real, BLOCK> &S, double &m, double &j,
+template <typename real, int BLOCK, int CP>
+__device__ __forceinline__ void cta_reduce(Acc<real, CP> &acc, Smem<real, BLOCK> &S, double &m, double &j,
                                            real (&e)[4], bool &anybad)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    acc.mass += (double)acc.macc;
-    acc.macc = real(0);
-    acc.mcount = 0;
+    acc.flush();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         acc.mass += __shfl_xor_sync(0xffffffffu, acc.mass, o);
@@ -677,11 +996,14 @@ __device__ __forceinline__ void cta_reduce(Acc<real> &acc, Smem<real, BLOCK> &S,
     __syncthreads();
 }
 
-template <typename real, bool WALLS, bool PRES, int MODE, int BLOCK, bool STAGED>
-__global__ void __launch_bounds__(BLOCK, MinBlocks<real, BLOCK>::value) step_kernel(const KArgs<real> A)
+template <typename real, bool WALLS, bool PRES, int MODE, bool STAGED>
+__global__ void __launch_bounds__(threads_per_cta<real, STAGED>(),
+                                  MinBlocks<real, threads_per_cta<real, STAGED>()>::value)
+    step_kernel(const KArgs<real> A)
 {
-    static_assert(BLOCK % 32 == 0 && BLOCK >= 128, "the four halo columns take one warp each");
-    constexpr int SP = stage_pitch<BLOCK>();
+    constexpr int CP = cols_per_thread<real, STAGED>();
+    constexpr int BLOCK = threads_per_cta<real, STAGED>();
+    constexpr int SP = stage_pitch();
     extern __shared__ __align__(128) unsigned char dsm[];
     real *const stages = reinterpret_cast<real *>(dsm);
     uint64_t *const bars = reinterpret_cast<uint64_t *>(dsm + (size_t)NSTAGE * 9 * SP * sizeof(real));
@@ -693,7 +1015,7 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real, BLOCK>::value) step_ker
     const long long u1 = cut_units<WALLS>(A, cta + 1);
     const Geom<real> G{A.fin, A.fout, A.nx, A.ny, A.W, A.rho_in_g, A.rho_in_l, A.rho_out_g, A.rho_out_l};
 
-    Acc<real> acc;
+    Acc<real, CP> acc;
     acc.reset();
     RingPos ring_next;  // stage of the next stencil row to consume (uniform)
     bool lost = false;  // a bounded wait gave up
@@ -712,8 +1034,8 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real, BLOCK>::value) step_ker
         const long long ue = min(u1, (long long)(s + 1) * A.nyf);
         const int yb = ya + (int)(ue - u);
         u = ue;
-        run_segment<real, WALLS, PRES, MODE, BLOCK, STAGED>(A, G, s, ya, yb, S, stages, bars, ring_next, acc,
-                                                           lost);
+        run_segment<real, WALLS, PRES, MODE, BLOCK, STAGED, CP>(A, G, s, ya, yb, S, stages, bars, ring_next, acc,
+                                                               lost);
     }
 
     if (STAGED && lost) atomicOr(A.err, 2);
@@ -722,7 +1044,7 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real, BLOCK>::value) step_ker
     double m, j;
     real e[4];
     bool anybad;
-    cta_reduce<real, BLOCK>(acc, S, m, j, e, anybad);
+    cta_reduce<real, BLOCK, CP>(acc, S, m, j, e, anybad);
     if (tid == 0) {
         A.mass_part[cta] = m;
         A.J_acc[cta] += j;
@@ -752,13 +1074,16 @@ struct BatchSeg {
     int chan, strip, ya, yb;
 };
 
-template <typename real, bool WALLS, bool PRES, int BLOCK, bool STAGED>
-__global__ void __launch_bounds__(BLOCK, MinBlocks<real, BLOCK>::value)
+template <typename real, bool WALLS, bool PRES, bool STAGED>
+__global__ void __launch_bounds__(threads_per_cta<real, STAGED>(),
+                                  MinBlocks<real, threads_per_cta<real, STAGED>()>::value)
     batch_step_kernel(const KArgs<real> A, const BatchChan<real> *__restrict__ chans,
                       const BatchSeg *__restrict__ segs, const int *__restrict__ cta_begin,
                       double *__restrict__ seg_mass, double *__restrict__ seg_J, real *__restrict__ seg_ext)
 {
-    constexpr int SP = stage_pitch<BLOCK>();
+    constexpr int CP = cols_per_thread<real, STAGED>();
+    constexpr int BLOCK = threads_per_cta<real, STAGED>();
+    constexpr int SP = stage_pitch();
     extern __shared__ __align__(128) unsigned char dsm[];
     real *const stages = reinterpret_cast<real *>(dsm);
     uint64_t *const bars = reinterpret_cast<uint64_t *>(dsm + (size_t)NSTAGE * 9 * SP * sizeof(real));
@@ -780,14 +1105,14 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<real, BLOCK>::value)
         const BatchChan<real> ch = chans[sg.chan];
         const Geom<real> G{A.fin + ch.off, A.fout + ch.off, ch.nx, ch.ny, ch.W,
                            ch.rho_in_g, ch.rho_in_l, ch.rho_out_g, ch.rho_out_l};
-        Acc<real> acc;
+        Acc<real, CP> acc;
         acc.reset();
-        run_segment<real, WALLS, PRES, MODE_STEP, BLOCK, STAGED>(A, G, sg.strip, sg.ya, sg.yb, S, stages, bars,
-                                                                ring_next, acc, lost);
+        run_segment<real, WALLS, PRES, MODE_STEP, BLOCK, STAGED, CP>(A, G, sg.strip, sg.ya, sg.yb, S, stages,
+                                                                    bars, ring_next, acc, lost);
         double m, j;
         real e[4];
         bool anybad;
-        cta_reduce<real, BLOCK>(acc, S, m, j, e, anybad);
+        cta_reduce<real, BLOCK, CP>(acc, S, m, j, e, anybad);
         if (tid == 0) {
             seg_mass[k] = m;
             seg_J[k] += j;
@@ -832,7 +1157,7 @@ __global__ void init_kernel(const double *__restrict__ rho0, real *__restrict__ 
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int y = k / nx, x = k - y * nx;
         real fe[9];
-        feq_pairs<real>((real)rho0[k], real(0), real(0), fe);
+        feq_pairs<real>((real)rho0[k], real(0), real(0), real(0), real(0), fe);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             fa[(9 * y + i) * nx + x] = fe[i];

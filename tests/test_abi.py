@@ -137,3 +137,18 @@ def test_adjoint_rejects_bad_arguments_before_touching_the_gpu(lbm):
     g = (C.c_double * 3)()
     assert lbm.lib().lbm_adjoint_backward(None, 1.0, 0.0, None, g) == lbm.LBM_ERR_ARG
     lbm.lib().lbm_adjoint_free(None)  # NULL-safe
+
+
+def test_collision_setter_validates_before_touching_the_gpu(lbm):
+    import ctypes as C
+    mrt = lbm.lbm_collision(lbm.LBM_COLL_MRT, 1.64, 1.54, 1.0, 1.7, 0.0)
+    assert lbm.lib().lbm_set_collision(None, C.byref(mrt)) == lbm.LBM_ERR_ARG
+
+
+def test_pr_coexistence_helper_matches_oracle(lbm, orc):
+    for tr in (0.5, 0.6, 0.8):
+        Tc, g, l, p = lbm.lbm_coexistence(lbm.lbm_eos(2 / 49, 2 / 21, 1.0, tr, 1.0, 0.5, lbm.LBM_EOS_PR, 0.344))
+        s = orc.Setup(nx=4, ny=4, eos="pr", a=2 / 49, b=2 / 21, T_over_Tc=tr)
+        g2, l2, p2 = s.coexistence()
+        assert abs(Tc / (s.T / tr) - 1) < 1e-12
+        assert abs(g / g2 - 1) < 1e-10 and abs(l / l2 - 1) < 1e-12 and abs(p / p2 - 1) < 1e-10

@@ -42,6 +42,17 @@ CASES = {
     "ragged129x20": dict(nx=129, ny=20, kw=dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=2e-4)),
     # walls, periodic x, wetting offset
     "wet96x40": dict(nx=96, ny=40, kw=dict(walls=True, T_over_Tc=0.8, kappa=0.5, wet=0.01)),
+    # Peng-Robinson water (Eq. 2.18) droplet, BGK, tau = 1.2
+    "pr_droplet96": dict(nx=96, ny=96, kw=dict(eos="pr", a=2 / 49, b=2 / 21, T_over_Tc=0.8, k=1.0, kappa=0.01,
+                                               tau=1.2)),
+    # the same with MRT collision (Eq. 2.1; s_q and s_j at 1/tau, see the MRT pins)
+    "mrt_pr_droplet96": dict(nx=96, ny=96, kw=dict(eos="pr", a=2 / 49, b=2 / 21, T_over_Tc=0.8, k=1.0, kappa=0.01,
+                                                   tau=1.2, collision="mrt", s_e=1.64, s_eps=1.54, s_q=1 / 1.2,
+                                                   s_j=1 / 1.2)),
+    # MRT airway channel with pressure columns
+    "mrt_airway256x64": dict(nx=256, ny=64, kw=dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, tau=1.2,
+                                                   dp=1e-3, collision="mrt", s_e=1 / 1.2, s_eps=1.54,
+                                                   s_q=1 / 1.2, s_j=1 / 1.2)),
     # the paper's drive: body force along the channel, ends at one pressure
     "bodyforce256x64": dict(nx=256, ny=64, kw=dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=0.0,
                                                   gx=1e-6)),
@@ -62,8 +73,10 @@ def _rho0(orc, name, c):
         return synth.airway_rho0(nx, ny, 3, 40, 20, l, g)
     if name == "wet96x40":
         return synth.disk_rho0(nx, ny, 14, l, g, centre=(48.0, 0.5))
-    if name == "bodyforce256x64":
+    if name == "bodyforce256x64" or name == "mrt_airway256x64":
         return synth.airway_rho0(nx, ny, 5, 64, 32, l, g, noise=1e-3, seed=2)
+    if name.endswith("droplet96"):
+        return synth.disk_rho0(nx, ny, 24, l, g, noise=1e-3, seed=1)
     raise KeyError(name)
 
 
