@@ -82,6 +82,7 @@ struct lbm_ctx {
     int64_t step = 0;
     int W = STRIP, nstrips = 0, yf0 = 0, nyf = 0;
     long long units = 0;
+    int band = 0;  // rows per band of the work-unit order
     int nctas = 0;
     int ctas_per_sm_opt = 0;
     int reverse = 0;
@@ -126,6 +127,7 @@ lbm::KArgs<real> make_args(const lbm_ctx *ctx)
     A.yf0 = ctx->yf0;
     A.nyf = ctx->nyf;
     A.units = ctx->units;
+    A.band = ctx->band;
     A.nctas = ctx->nctas;
     A.reverse = ctx->reverse;
     const double k = ctx->eos.k;
@@ -198,6 +200,20 @@ size_t dyn_smem(const lbm_ctx *ctx)
                                      : lbm::staged_smem_bytes<float>();
 }
 
+// Band height of the work-unit order: about one CTA's share of rows, so that
+// consecutive CTAs hold neighbouring strips of one band (at least 8 rows; the
+// whole column, i.e. strip-major order, when there are fewer CTAs than
+// strips). With walls no band boundary may fall between fluid rows 1|2 or
+// ny-3|ny-2 (fluid offsets 1 and nyf-1).
+int band_rows(int nyf, int nstrips, int nctas, int walls)
+{
+    const long long share = ((long long)nyf * nstrips + nctas - 1) / nctas;
+    int band = (int)std::min<long long>(nyf, std::max<long long>(8, share));
+    if (walls)
+        while (band < nyf && (nyf - 1) % band == 0) ++band;
+    return std::max(1, band);
+}
+
 // Strip partition and the CTA count of the step grid.
 lbm_status plan_launch(lbm_ctx *ctx)
 {
@@ -234,6 +250,7 @@ lbm_status plan_launch(lbm_ctx *ctx)
     n = std::min<long long>(n, std::max<long long>(1, ctx->units / 2));
     n = std::min<long long>(n, lbm::MAX_CTAS);
     ctx->nctas = (int)std::max<long long>(1, n);
+    ctx->band = band_rows(ctx->nyf, ctx->nstrips, ctx->nctas, ctx->grid.walls);
     return LBM_OK;
 }
 
@@ -768,6 +785,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_grid *grid, const lbm_eos *eos,
     if (plan_launch(&c) != LBM_OK) return LBM_ERR_CUDA;
     if (ctas > 0) c.nctas = (int)std::min<long long>(ctas, std::max<long long>(1, c.units / 2));
     c.nctas = std::min(c.nctas, NOALLOC_MAX_CTAS);
+    c.band = band_rows(c.nyf, c.nstrips, c.nctas, c.grid.walls);
     return grid->precision == 64 ? noalloc_launch<double>(&c, sc, f_in, f_out, diag_out)
                                  : noalloc_launch<float>(&c, sc, f_in, f_out, diag_out);
 }

@@ -352,6 +352,7 @@ lbm_status chan_fields(lbm_batch *b, int ci, void *rho, void *ux, void *uy, void
     A.yf0 = c.yf0;
     A.nyf = c.nyf;
     A.units = c.units;
+    A.band = c.nyf;  // strip-major
     A.rho_in_g = (real)c.rho_in;
     A.rho_in_l = (real)c.rho_in_l;
     A.rho_out_g = (real)c.rho_out;

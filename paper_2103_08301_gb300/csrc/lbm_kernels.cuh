@@ -47,6 +47,7 @@ struct KArgs {
     int nstrips;
     int yf0, nyf;     // first fluid row and number of fluid rows
     long long units;  // nstrips * nyf
+    int band;         // rows per band of the unit order (>= nyf: strip-major)
     int nctas;        // logical CTAs of the schedule
     int reverse;      // launch the logical CTAs in reverse order
     real RT, a, b4, k2, kappa, tau, inv_tau, omb, gx, gy, wet, nu;
@@ -288,15 +289,40 @@ __device__ __forceinline__ int map_row(int yy, int ny, bool &mirror)
     return r < 0 ? r + ny : r;
 }
 
+// Work units are (strip, fluid row) pairs, enumerated band by band: rows are
+// cut into bands of A.band rows and, within a band, strip by strip. Logical
+// CTAs take consecutive runs of units, so neighbouring CTAs hold neighbouring
+// strips of one band and march through the same rows at the same time: the
+// halo columns one strip reads from its neighbours are then recent in L2.
+// unit_run gives the strip s, the row y of unit u and the end of its
+// (strip, band) run.
+template <typename real>
+__device__ __forceinline__ void unit_run(const KArgs<real> &A, long long u, int &s, int &y, long long &run_end)
+{
+    const long long per_band = (long long)A.band * A.nstrips;
+    const int b = (int)(u / per_band);
+    const long long ub = (long long)b * per_band;
+    const int y0 = b * A.band;
+    const int hb = min(A.band, A.nyf - y0);
+    const long long r = u - ub;
+    s = (int)(r / hb);
+    const int off = (int)(r - (long long)s * hb);
+    y = A.yf0 + y0 + off;
+    run_end = ub + (long long)(s + 1) * hb;
+}
+
 // Boundary c of the balanced split of work units over logical CTAs. A cut
-// never separates rows 1|2 or ny-3|ny-2, so each wall-shear pair of rows is
-// processed by one CTA in one sweep.
+// never separates rows 1|2 or ny-3|ny-2 (nor does a band boundary: the host
+// picks the band height), so each wall-shear pair of rows is processed by one
+// CTA in one sweep.
 template <bool WALLS, typename real>
 __device__ __forceinline__ long long cut_units(const KArgs<real> &A, int c)
 {
     long long u = ((long long)c * A.units) / A.nctas;
     if (WALLS && u > 0 && u < A.units) {
-        int y = A.yf0 + (int)(u % A.nyf);
+        int s, y;
+        long long e;
+        unit_run(A, u, s, y, e);
         if (y == 2 || y == A.ny - 2) u -= 1;
     }
     return u;
@@ -329,6 +355,14 @@ __host__ __device__ constexpr int threads_per_cta()
 
 // Register allocation is held to LBM_FP32_THREADS_PER_SM resident FP32
 // threads per SM (256 for FP64, which carries twice the state per thread).
+// Halo duty: LBM_HALO_ONE_WARP puts the four halo columns on lanes 0..3 of
+// warp 0 (and the two halo Laplacians on lanes 0..1 of the last warp), so the
+// divergent halo path is issued by one warp per row instead of four.
+#ifndef LBM_HALO_ONE_WARP
+#define LBM_HALO_ONE_WARP 1
+#endif
+
+
 #ifndef LBM_FP32_THREADS_PER_SM
 #define LBM_FP32_THREADS_PER_SM 512
 #endif
@@ -342,7 +376,7 @@ struct MinBlocks {
 // j+STAGE_AHEAD are in flight, and row j+STAGE_AHEAD+1 is issued into the
 // stage freed by row j-4: STAGE_AHEAD + 5 stages.
 #ifndef LBM_STAGE_AHEAD
-#define LBM_STAGE_AHEAD 1
+#define LBM_STAGE_AHEAD 2
 #endif
 constexpr int STAGE_AHEAD = LBM_STAGE_AHEAD;
 // the wait for row j+1 comes before the barrier of iteration j, so that row
@@ -623,7 +657,8 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
     // inlet / outlet column density derived from column hx = 1 / nx-2 (clamp
     // beyond the pressure columns).
     int hidx = -1;
-    if (NW >= 4) { if (lane == 0 && warp < 4) hidx = warp; }
+    if (LBM_HALO_ONE_WARP) { if (warp == 0 && lane < 4) hidx = lane; }
+    else if (NW >= 4) { if (lane == 0 && warp < 4) hidx = warp; }
     else if (lane < 2) hidx = 2 * warp + lane;
     int hmode = 0, hx = 0, hcol = 0;
     if (hidx >= 0) {
@@ -641,7 +676,8 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
     }
     // Laplacian of the two halo columns next to the strip (local -1, xw)
     int lhalo = -1;
-    if (NW >= 4) lhalo = (lane == 1 && warp == 1) ? 1 : ((lane == 1 && warp == 2) ? xw + 2 : -1);
+    if (LBM_HALO_ONE_WARP) { if (warp == NW - 1 && lane < 2) lhalo = lane == 0 ? 1 : xw + 2; }
+    else if (NW >= 4) lhalo = (lane == 1 && warp == 1) ? 1 : ((lane == 1 && warp == 2) ? xw + 2 : -1);
     else if (lane == 2) lhalo = warp == 0 ? 1 : xw + 2;
 
     const real *__restrict__ col_in = G.fin + x0 + scol;
@@ -1029,9 +1065,10 @@ __global__ void __launch_bounds__(threads_per_cta<real, STAGED>(),
     }
 
     while (u < u1) {
-        const int s = (int)(u / A.nyf);
-        const int ya = A.yf0 + (int)(u - (long long)s * A.nyf);
-        const long long ue = min(u1, (long long)(s + 1) * A.nyf);
+        int s, ya;
+        long long run_end;
+        unit_run(A, u, s, ya, run_end);
+        const long long ue = min(u1, run_end);
         const int yb = ya + (int)(ue - u);
         u = ue;
         run_segment<real, WALLS, PRES, MODE, BLOCK, STAGED, CP>(A, G, s, ya, yb, S, stages, bars, ring_next, acc,

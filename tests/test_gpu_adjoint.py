@@ -203,13 +203,16 @@ def test_airway_workload_gradients_2000_steps(adjm, orc):
     # the airway workload: 512 x 128 channel, film 6, plug 48 at x = 128,
     # 0.85 Tc, dp = 1e-3, noise 1e-3, 2000 FP64 steps. J is smooth in film
     # thickness and plug length; central differences of the oracle (step 1e-3)
-    # are the reference.
+    # are the reference. In dp the column phase weight's clamp leaves kinks
+    # (differences move by ~1e-3 between steps 1e-6 and 1e-7), so the dp
+    # reference is the difference at step 1e-7 and the bound is the 1e-3 the
+    # method targets.
     nx, ny, steps = 512, 128, 2000
     kw = dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5)
-    s = orc.Setup(nx=nx, ny=ny, dp=1e-3, **kw)
-    g, l, _ = s.coexistence()
+    g, l, _ = orc.Setup(nx=nx, ny=ny, dp=1e-3, **kw).coexistence()
 
-    def J(film=6.0, plug=48.0):
+    def J(film=6.0, plug=48.0, dp=1e-3):
+        s = orc.Setup(nx=nx, ny=ny, dp=dp, **kw)
         r0 = synth.airway_rho0(nx, ny, film, 128, plug, l, g, noise=1e-3, seed=1)
         _, d = orc.run(s, orc.init(s, r0), steps)
         return np.array([d["J"], d["Jp"]])
@@ -225,8 +228,11 @@ def test_airway_workload_gradients_2000_steps(adjm, orc):
     h = 1e-3
     fd_film = (J(film=6.0 + h) - J(film=6.0 - h)) / (2 * h)
     fd_plug = (J(plug=48.0 + h) - J(plug=48.0 - h)) / (2 * h)
+    fd_dp = (J(dp=1e-3 + 1e-7) - J(dp=1e-3 - 1e-7)) / 2e-7
     for k in range(2):
         gr = grads[k][0]
         got_f, got_p = float((gr * d_film).sum()), float((gr * d_plug).sum())
         assert abs(got_f - fd_film[k]) <= 1e-3 * abs(fd_film[k]), ("film", k, got_f, fd_film[k])
         assert abs(got_p - fd_plug[k]) <= 1e-3 * abs(fd_plug[k]), ("plug", k, got_p, fd_plug[k])
+        got_dp = grads[k][1]["dp"]
+        assert abs(got_dp - fd_dp[k]) <= 1e-3 * abs(fd_dp[k]), ("dp", k, got_dp, fd_dp[k])
