@@ -48,12 +48,13 @@ typedef struct lbm_ctx lbm_ctx; /* opaque, owned by the library */
 typedef enum {
     LBM_OK = 0,
     LBM_ERR_ARG = 1,   /* NULL pointer, bad size or flag, buffer too small */
-    LBM_ERR_PARAM = 2, /* tau <= 1/2; T >= Tc without explicit p_ref; boundary
-                          pressure off the gas branch; kappa < 0; k <= 0 */
+    LBM_ERR_PARAM = 2, /* tau <= 1/2; T >= Tc without explicit p_ref;
+                          kappa < 0; k <= 0; unknown EOS kind */
     LBM_ERR_CUDA = 3,  /* a CUDA runtime call failed (lbm_last_error has the text) */
     LBM_ERR_OOM = 4,   /* device or host allocation failed */
     LBM_ERR_NAN = 5,   /* a step met a non-finite or non-positive density */
-    LBM_ERR_STATE = 6  /* checkpoint of another geometry or precision */
+    LBM_ERR_STATE = 6, /* checkpoint of another geometry or precision */
+    LBM_ERR_TIMEOUT = 7 /* a bounded wait for a staged population row gave up */
 } lbm_status;
 
 /* Lattice and geometry (Sec. 2.2: straight rigid channel of the airway model).

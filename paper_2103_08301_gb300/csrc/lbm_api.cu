@@ -38,7 +38,7 @@ Layout layout_of(int nx, int ny, int precision)
 {
     Layout L{};
     const size_t sz = precision == 64 ? 8 : 4;
-    L.pops = align_up((size_t)9 * nx * ny * sz);
+    L.pops = align_up((size_t)9 * lbm::pitch_of(nx) * ny * sz);
     size_t o = 0;
     L.f0 = o; o += L.pops;
     L.f1 = o; o += L.pops;
@@ -59,7 +59,7 @@ bool grid_ok(const lbm_grid *g)
     if (g->bc_x != 0 && g->bc_x != 1) return false;
     if (g->nx < (g->bc_x ? 4 : 1) || g->ny < (g->walls ? 4 : 1)) return false;
     // 32-bit population indices: 9 nx ny < 2^31 (up to ~238 million nodes)
-    if (9ll * g->nx * g->ny >= (1ll << 31)) return false;
+    if (9ll * lbm::pitch_of(g->nx) * g->ny >= (1ll << 31)) return false;
     return true;
 }
 
@@ -81,6 +81,7 @@ struct lbm_ctx {
     int cur = 0;          // which population array holds the current state
     int64_t step = 0;
     int W = STRIP, nstrips = 0, yf0 = 0, nyf = 0;
+    int pitch = 0;  // plane pitch of the population rows (>= nx)
     long long units = 0;
     int band = 0;  // rows per band of the work-unit order
     int nctas = 0;
@@ -122,6 +123,7 @@ lbm::KArgs<real> make_args(const lbm_ctx *ctx)
     A.plane = (long long)ctx->grid.nx * ctx->grid.ny;
     A.nx = ctx->grid.nx;
     A.ny = ctx->grid.ny;
+    A.pitch = ctx->pitch;
     A.W = ctx->W;
     A.nstrips = ctx->nstrips;
     A.yf0 = ctx->yf0;
@@ -218,15 +220,10 @@ int band_rows(int nyf, int nstrips, int nctas, int walls)
 lbm_status plan_launch(lbm_ctx *ctx)
 {
     const int nx = ctx->grid.nx;
-    int W = std::min(ctx->W > 0 ? ctx->W : STRIP, STRIP);
-    // the outlet column must not open a strip (its stencil reaches two columns back)
-    if (ctx->grid.bc_x && nx > W && nx % W == 1) {
-        for (int w = W - 1; w >= 2; --w)
-            if (nx % w != 1) { W = w; break; }
-    }
+    const int W = lbm::strip_width(nx, std::min(ctx->W > 0 ? ctx->W : STRIP, STRIP), ctx->grid.bc_x);
     ctx->W = W;
     // bulk-copy staging needs 16-byte aligned row segments
-    ctx->staged = ctx->allow_staged && (nx % 4 == 0) && (W % 4 == 0);
+    ctx->staged = ctx->allow_staged && (ctx->pitch % 4 == 0) && (W % 4 == 0);
     ctx->nstrips = (nx + W - 1) / W;
     ctx->yf0 = ctx->grid.walls ? 1 : 0;
     ctx->nyf = ctx->grid.walls ? ctx->grid.ny - 2 : ctx->grid.ny;
@@ -312,19 +309,20 @@ void reset_acc(lbm_ctx *ctx)
         (real *)(ctx->ws + ctx->L.ext), (int *)(ctx->ws + ctx->L.err), lbm::MAX_CTAS);
 }
 
-// The library stores populations row-interleaved, f[y][i][x]; the ABI
-// exchanges plane-major f[i][y][x]. One strided 2D copy per plane converts.
+// The library stores populations row-interleaved, f[y][i][x] with plane
+// pitch P >= nx; the ABI exchanges plane-major f[i][y][x]. One strided 2D
+// copy per plane converts.
 cudaError_t copy_planes(const lbm_ctx *ctx, void *dst, const void *src, bool to_abi)
 {
     const size_t sz = ctx->grid.precision == 64 ? 8 : 4;
-    const size_t nx = ctx->grid.nx, ny = ctx->grid.ny, row = nx * sz;
+    const size_t nx = ctx->grid.nx, ny = ctx->grid.ny, row = nx * sz, prow = (size_t)ctx->pitch * sz;
     for (int i = 0; i < 9; ++i) {
         cudaError_t e;
         if (to_abi)
-            e = cudaMemcpy2DAsync((char *)dst + i * nx * ny * sz, row, (const char *)src + i * row, 9 * row,
+            e = cudaMemcpy2DAsync((char *)dst + i * nx * ny * sz, row, (const char *)src + i * prow, 9 * prow,
                                   row, ny, cudaMemcpyDefault, ctx->stream);
         else
-            e = cudaMemcpy2DAsync((char *)dst + i * row, 9 * row, (const char *)src + i * nx * ny * sz, row,
+            e = cudaMemcpy2DAsync((char *)dst + i * prow, 9 * prow, (const char *)src + i * nx * ny * sz, row,
                                   row, ny, cudaMemcpyDefault, ctx->stream);
         if (e != cudaSuccess) return e;
     }
@@ -352,6 +350,7 @@ const char *lbm_status_string(lbm_status s)
     case LBM_ERR_OOM: return "out of memory";
     case LBM_ERR_NAN: return "non-finite or non-positive density";
     case LBM_ERR_STATE: return "incompatible checkpoint";
+    case LBM_ERR_TIMEOUT: return "a bounded wait for staged data gave up";
     }
     return "unknown status";
 }
@@ -404,6 +403,7 @@ lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, double
     }
 
     ctx->L = layout_of(grid->nx, grid->ny, grid->precision);
+    ctx->pitch = lbm::pitch_of(grid->nx);
     if (workspace) {
         if (ws_bytes < ctx->L.total || ((uintptr_t)workspace % ALIGN) != 0) {
             lbm_free(ctx);
@@ -441,11 +441,13 @@ lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, double
         const int blocks = (int)std::min<size_t>((N + 255) / 256, (size_t)ctx->sms * 8);
         if (grid->precision == 64) {
             lbm::init_kernel<double><<<blocks, 256, 0, ctx->stream>>>(
-                d_rho0, (double *)(ctx->ws + ctx->L.f0), (double *)(ctx->ws + ctx->L.f1), grid->nx, (int)N);
+                d_rho0, (double *)(ctx->ws + ctx->L.f0), (double *)(ctx->ws + ctx->L.f1), grid->nx, ctx->pitch,
+                grid->ny);
             reset_acc<double>(ctx);
         } else {
             lbm::init_kernel<float><<<blocks, 256, 0, ctx->stream>>>(
-                d_rho0, (float *)(ctx->ws + ctx->L.f0), (float *)(ctx->ws + ctx->L.f1), grid->nx, (int)N);
+                d_rho0, (float *)(ctx->ws + ctx->L.f0), (float *)(ctx->ws + ctx->L.f1), grid->nx, ctx->pitch,
+                grid->ny);
             reset_acc<float>(ctx);
         }
         e = cudaGetLastError();
@@ -467,7 +469,9 @@ lbm_status lbm_step(lbm_ctx *ctx, int64_t n)
     lbm_status flag = LBM_OK;
     if (ctx->err_pending && cudaEventQuery(ctx->err_ev) == cudaSuccess) {
         ctx->err_pending = false;
-        if (*ctx->h_err) flag = LBM_ERR_NAN;
+        // bit 0: bad density; bit 1: a bounded stage wait gave up
+        if (*ctx->h_err & 1) flag = LBM_ERR_NAN;
+        else if (*ctx->h_err) flag = LBM_ERR_TIMEOUT;
     }
     if (n == 0) return flag;
     lbm_status s = ctx->grid.precision == 64 ? do_steps<double>(ctx, n) : do_steps<float>(ctx, n);
@@ -765,6 +769,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_grid *grid, const lbm_eos *eos,
     // Launch plan and physics on the host stack only (no workspace).
     lbm_ctx c;
     c.grid = *grid;
+    c.pitch = grid->nx;  // caller buffers: rows of 9 nx values
     c.eos = *eos;
     if (drive) c.drive = *drive;
     else { c.drive.dp = 0; c.drive.p_ref = NAN; c.drive.gx = c.drive.gy = 0; }

@@ -33,6 +33,7 @@ struct ChanHost {
     lbm_drive drive;
     double rho_in = 0, rho_out = 0, rho_in_l = 0, rho_out_l = 0;
     long long off = 0;  // element offset in the packed buffers
+    int pitch = 0;      // plane pitch of the channel's population rows
     int W = STRIP, nstrips = 0, yf0 = 0, nyf = 0;
     long long units = 0, unit_base = 0;
 };
@@ -163,10 +164,7 @@ lbm_status batch_plan(lbm_batch *b)
     bool all4 = true;
     for (auto &c : b->ch) {
         const int nx = c.grid.nx;
-        int W = std::min(b->W_opt > 0 ? b->W_opt : STRIP, STRIP);
-        if (b->bc_x && nx > W && nx % W == 1)
-            for (int w = W - 1; w >= 2; --w)
-                if (nx % w != 1) { W = w; break; }
+        const int W = lbm::strip_width(nx, std::min(b->W_opt > 0 ? b->W_opt : STRIP, STRIP), b->bc_x);
         c.W = W;
         c.nstrips = (nx + W - 1) / W;
         c.yf0 = b->walls ? 1 : 0;
@@ -174,7 +172,7 @@ lbm_status batch_plan(lbm_batch *b)
         c.units = (long long)c.nstrips * c.nyf;
         c.unit_base = U;
         U += c.units;
-        all4 = all4 && (nx % 4 == 0) && (W % 4 == 0);
+        all4 = all4 && (c.pitch % 4 == 0) && (W % 4 == 0);
     }
     b->staged = b->allow_staged && all4;
     const size_t smem = staged_bytes(b, b->staged);
@@ -311,7 +309,7 @@ void fill_chan_table(const lbm_batch *b, std::vector<unsigned char> &buf)
     auto *t = reinterpret_cast<lbm::BatchChan<real> *>(buf.data());
     for (int i = 0; i < b->n; ++i) {
         const ChanHost &c = b->ch[i];
-        t[i] = lbm::BatchChan<real>{c.off, c.grid.nx, c.grid.ny, c.W, 0, (real)c.rho_in, (real)c.rho_in_l,
+        t[i] = lbm::BatchChan<real>{c.off, c.grid.nx, c.grid.ny, c.W, c.pitch, (real)c.rho_in, (real)c.rho_in_l,
                                     (real)c.rho_out, (real)c.rho_out_l};
     }
 }
@@ -347,6 +345,7 @@ lbm_status chan_fields(lbm_batch *b, int ci, void *rho, void *ux, void *uy, void
     A.plane = (long long)N;
     A.nx = c.grid.nx;
     A.ny = c.grid.ny;
+    A.pitch = c.pitch;
     A.W = c.W;
     A.nstrips = c.nstrips;
     A.yf0 = c.yf0;
@@ -358,7 +357,7 @@ lbm_status chan_fields(lbm_batch *b, int ci, void *rho, void *ux, void *uy, void
     A.rho_out_g = (real)c.rho_out;
     A.rho_out_l = (real)c.rho_out_l;
     A.o_rho = d_rho; A.o_vx = d_vx; A.o_vy = d_vy; A.o_tw = d_tw; A.o_pw = d_pw;
-    const bool st = b->allow_staged && nx % 4 == 0 && c.W % 4 == 0;
+    const bool st = b->allow_staged && c.pitch % 4 == 0 && c.W % 4 == 0;
     void *fn = st ? fields_kernel_ptr<real, true>(b->walls, b->bc_x) : fields_kernel_ptr<real, false>(b->walls, b->bc_x);
     const size_t smem = staged_bytes(b, st);
     BCK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attribute");
@@ -422,8 +421,9 @@ lbm_status lbm_batch_init(int32_t n, const lbm_grid *grids, const lbm_eos *eos, 
             c.rho_in = ct.rho_in; c.rho_out = ct.rho_out;
             c.rho_in_l = ct.rho_in_l; c.rho_out_l = ct.rho_out_l;
         }
+        c.pitch = lbm::pitch_of(c.grid.nx);
         c.off = (long long)off;
-        off += align_elems((size_t)9 * c.grid.nx * c.grid.ny);
+        off += align_elems((size_t)9 * c.pitch * c.grid.ny);
     }
     b->pop_elems = off;
     b->stream = (cudaStream_t)stream;
@@ -459,13 +459,15 @@ lbm_status lbm_batch_init(int32_t n, const lbm_grid *grids, const lbm_eos *eos, 
         const int N = c.grid.nx * c.grid.ny;
         e = cudaMemcpyAsync(d_rho0, rho0s[i], (size_t)N * sizeof(double), cudaMemcpyHostToDevice, b->stream);
         if (e != cudaSuccess) break;
-        const int blocks = std::min((N + 255) / 256, b->sms * 8);
+        const int blocks = std::min((c.pitch * c.grid.ny + 255) / 256, b->sms * 8);
         if (b->precision == 64)
             lbm::init_kernel<double><<<blocks, 256, 0, b->stream>>>(d_rho0, (double *)b->pop[0] + c.off,
-                                                                   (double *)b->pop[1] + c.off, c.grid.nx, N);
+                                                                   (double *)b->pop[1] + c.off, c.grid.nx,
+                                                                   c.pitch, c.grid.ny);
         else
             lbm::init_kernel<float><<<blocks, 256, 0, b->stream>>>(d_rho0, (float *)b->pop[0] + c.off,
-                                                                  (float *)b->pop[1] + c.off, c.grid.nx, N);
+                                                                  (float *)b->pop[1] + c.off, c.grid.nx,
+                                                                  c.pitch, c.grid.ny);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // d_rho0 is reused
     }
@@ -488,7 +490,9 @@ lbm_status lbm_batch_step(lbm_batch *b, int64_t n)
     lbm_status flag = LBM_OK;
     if (b->err_pending && cudaEventQuery(b->err_ev) == cudaSuccess) {
         b->err_pending = false;
-        if (*b->h_err) flag = LBM_ERR_NAN;
+        // bit 0: bad density; bit 1: a bounded stage wait gave up
+        if (*b->h_err & 1) flag = LBM_ERR_NAN;
+        else if (*b->h_err) flag = LBM_ERR_TIMEOUT;
     }
     while (n > 0) {
         if (b->graph_steps > 0 && n >= b->graph_steps && b->cur == 0) {
@@ -553,10 +557,10 @@ lbm_status lbm_batch_populations(lbm_batch *b, int32_t channel, void *dst)
 {
     if (!b || !dst || channel < 0 || channel >= b->n) return LBM_ERR_ARG;
     const ChanHost &c = b->ch[channel];
-    const size_t sz = sz_of(b), nx = c.grid.nx, ny = c.grid.ny, row = nx * sz;
+    const size_t sz = sz_of(b), nx = c.grid.nx, ny = c.grid.ny, row = nx * sz, prow = (size_t)c.pitch * sz;
     const char *src = (const char *)b->pop[b->cur] + c.off * sz;
     for (int i = 0; i < 9; ++i)
-        BCK(cudaMemcpy2DAsync((char *)dst + i * nx * ny * sz, row, src + i * row, 9 * row, row, ny,
+        BCK(cudaMemcpy2DAsync((char *)dst + i * nx * ny * sz, row, src + i * prow, 9 * prow, row, ny,
                               cudaMemcpyDefault, b->stream), "populations copy");
     BCK(cudaStreamSynchronize(b->stream), "populations sync");
     return LBM_OK;

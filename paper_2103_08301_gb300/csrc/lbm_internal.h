@@ -45,4 +45,22 @@ struct ChannelThermo {
 int channel_thermo(const lbm_eos &e, const lbm_drive &d, bool bc_x, ChannelThermo *out);
 double node_noise(uint64_t seed, uint64_t node, double amp);
 
+// Row pitch of a population plane: nx rounded up to 4 columns, so that every
+// row segment of the bulk-copy staged kernel is 16-byte aligned.
+inline int pitch_of(int nx) { return (nx + 3) & ~3; }
+
+// Strip width for an nx-column channel: the widest up to w_max, except that
+// the outlet column must not open a strip (its stencil reaches two columns
+// back); widths that keep 16-byte alignment (multiples of 4) are preferred.
+inline int strip_width(int nx, int w_max, bool bc_x)
+{
+    int W = w_max;
+    if (!(bc_x && nx > W && nx % W == 1)) return W;
+    for (int w = (W - 1) & ~3; w >= 4; w -= 4)
+        if (nx % w != 1) return w;
+    for (int w = W - 1; w >= 2; --w)
+        if (nx % w != 1) return w;
+    return W;
+}
+
 } // namespace lbm

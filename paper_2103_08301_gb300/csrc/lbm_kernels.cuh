@@ -43,6 +43,7 @@ struct KArgs {
     real *__restrict__ fout;
     long long plane;  // nx * ny (nodes per lattice)
     int nx, ny;
+    int pitch;        // row pitch of a population plane (>= nx, a multiple of 4 when staged)
     int W;            // strip width in columns (<= STRIP)
     int nstrips;
     int yf0, nyf;     // first fluid row and number of fluid rows
@@ -256,7 +257,7 @@ template <typename real>
 struct Geom {
     const real *fin;
     real *fout;
-    int nx, ny, W;
+    int nx, ny, W, pitch;
     real rho_in_g, rho_in_l, rho_out_g, rho_out_l;
 };
 
@@ -549,29 +550,44 @@ __device__ __forceinline__ real wall_pressure(const KArgs<real> &A, const real (
     return fma_(fma_(grx, grx, mul_(gry, gry)), mul_(real(-0.5), A.kappa), t);
 }
 
-// Per-thread diagnostic accumulators of the states read.
+// Per-thread diagnostic accumulators of the states read. The density sum is
+// kept in the working precision and flushed to FP64 every 16 rows (at most 16
+// terms per flush); the density range is tracked with min / max, and a
+// non-finite density shows up in the mass sum (min / max ignore NaN).
 template <typename real, int CP>
 struct Acc {
     using V = typename Pack<real, CP>::T;
     double mass, J;
-    V macc;
-    int mcount;
+    V macc, rmin, rmax;
     real tmin, tmax, pmin, pmax;
-    bool bad;
     __device__ __forceinline__ void reset()
     {
-        mass = 0.0; J = 0.0; macc = bc<V>(0.0); mcount = 0;
+        mass = 0.0; J = 0.0; macc = bc<V>(0.0);
+        rmin = bc<V>(INFINITY); rmax = bc<V>(-INFINITY);
         tmin = pmin = real(INFINITY); tmax = pmax = real(-INFINITY);
-        bad = false;
     }
     __device__ __forceinline__ void flush()
     {
 #pragma unroll
         for (int k = 0; k < CP; ++k) mass += (double)el(macc, k);
         macc = bc<V>(0.0);
-        mcount = 0;
+    }
+    // a density that is not in (0, 1e30) or a non-finite mass
+    __device__ __forceinline__ bool bad() const
+    {
+        bool b = !(mass - mass == 0.0);
+#pragma unroll
+        for (int k = 0; k < CP; ++k) b = b || !(el(rmin, k) > real(0)) || !(el(rmax, k) < real(1e30));
+        return b;
     }
 };
+
+__device__ __forceinline__ float vmin_(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ float vmax_(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double vmin_(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ double vmax_(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float2 vmin_(float2 a, float2 b) { return make_float2(fminf(a.x, b.x), fminf(a.y, b.y)); }
+__device__ __forceinline__ float2 vmax_(float2 a, float2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
 
 // Static shared-memory working set of a CTA: the 8-row stencil ring (density,
 // EOS potential, Laplacian; strip plus two halo columns per side) and the
@@ -628,11 +644,12 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const real third = real(1.0 / 3.0);
     const int nx = G.nx, ny = G.ny;
-    const int rstride = 9 * nx;  // row stride of the population layout f[y][i][x]
+    const int P = G.pitch;       // plane pitch; columns nx .. P-1 are padding
+    const int rstride = 9 * P;   // row stride of the population layout f[y][i][x]
     // push targets of directions 1..8 relative to the source slot index
-    const int o1 = nx + 1, o2 = rstride + 2 * nx, o3 = 3 * nx - 1, o4 = 4 * nx - rstride;
-    const int o5 = rstride + 5 * nx + 1, o6 = rstride + 6 * nx - 1, o7 = 7 * nx - rstride - 1;
-    const int o8 = 8 * nx - rstride + 1;
+    const int o1 = P + 1, o2 = rstride + 2 * P, o3 = 3 * P - 1, o4 = 4 * P - rstride;
+    const int o5 = rstride + 5 * P + 1, o6 = rstride + 6 * P - 1, o7 = 7 * P - rstride - 1;
+    const int o8 = 8 * P - rstride + 1;
     real b_rho1[CP], b_v1[CP], t_v2[CP];  // wall-pair carries (rows 1 -> 2, ny-3 -> ny-2)
 #pragma unroll
     for (int k = 0; k < CP; ++k) b_rho1[k] = b_v1[k] = t_v2[k] = real(0);
@@ -694,12 +711,12 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
         if constexpr (!STAGED) {
             if (active) {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) pf[i] = __ldg(col_in + row + i * nx);
+                for (int i = 0; i < 9; ++i) pf[i] = __ldg(col_in + row + i * P);
             }
         }
         if (hmode) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) hf[i] = __ldg(hal_in + row + i * nx);
+            for (int i = 0; i < 9; ++i) hf[i] = __ldg(hal_in + row + i * P);
         }
     };
     // producer: stream stencil row j of this segment into the next stage
@@ -712,10 +729,11 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
                 const uint32_t st = ring_issue.s;
                 real *dst = stages + (size_t)st * 9 * SP;
                 const real *src = G.fin + row + x0;
-                const uint32_t bytes = (uint32_t)(xw * sizeof(real));
+                // whole 16-byte groups: a ragged last strip also copies padding columns
+                const uint32_t bytes = (uint32_t)(((xw + 3) & ~3) * sizeof(real));
                 mbar_arrive_expect_tx(&bars[st], 9 * bytes);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) bulk_copy_g2s(dst + i * SP, src + i * nx, bytes, &bars[st]);
+                for (int i = 0; i < 9; ++i) bulk_copy_g2s(dst + i * SP, src + i * P, bytes, &bars[st]);
             }
             ring_issue.advance();
         }
@@ -745,7 +763,7 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
             if (collide && active) {
                 const real *src = col_in + r * rstride;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) f[i] = __ldg(src + i * nx);
+                for (int i = 0; i < 9; ++i) f[i] = __ldg(src + i * P);
             }
         }
 
@@ -915,7 +933,7 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
                             const int ty = r + ey_(i);
                             if (WALLS && (ty == 0 || ty == ny - 1)) {
                                 // half-way bounce-back into the opposite slot of this node
-                                out[ok + opp_(i) * nx] = el(fs[i], k);
+                                out[ok + opp_(i) * P] = el(fs[i], k);
                             } else {
                                 int tx = xk + ex_(i);
                                 if (PRES) {
@@ -925,18 +943,14 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
                                 }
                                 int tyw = ty;
                                 if (!WALLS) tyw = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
-                                out[tyw * rstride + i * nx + tx] = el(fs[i], k);
+                                out[tyw * rstride + i * P + tx] = el(fs[i], k);
                             }
                         }
                     }
                 }
                 acc.macc = add_(acc.macc, rho_own);
-                if (++acc.mcount == 16) acc.flush();
-#pragma unroll
-                for (int k = 0; k < CP; ++k) {
-                    const real rk = el(rho, k);
-                    if (!(rk > real(0)) || !(rk < real(1e30))) acc.bad = true;
-                }
+                acc.rmin = vmin_(acc.rmin, rho);
+                acc.rmax = vmax_(acc.rmax, rho);
             } else {
 #pragma unroll
                 for (int k = 0; k < CP; ++k) {
@@ -987,6 +1001,7 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
             }
         }
         ring_coll.advance();
+        if ((j & 15) == 15) acc.flush();  // uniform: every thread added at most 16 densities
     }
     __syncthreads();  // ring and stage reuse by the next segment
 }
@@ -1007,7 +1022,7 @@ __device__ __forceinline__ void cta_reduce(Acc<real, CP> &acc, Smem<real, BLOCK>
         acc.pmin = fmin(acc.pmin, __shfl_xor_sync(0xffffffffu, acc.pmin, o));
         acc.pmax = fmax(acc.pmax, __shfl_xor_sync(0xffffffffu, acc.pmax, o));
     }
-    const bool wbad = __any_sync(0xffffffffu, acc.bad);
+    const bool wbad = __any_sync(0xffffffffu, acc.bad());
     if (tid == 0) S.bad = 0;
     __syncthreads();
     if (lane == 0) {
@@ -1049,7 +1064,7 @@ __global__ void __launch_bounds__(threads_per_cta<real, STAGED>(),
     const int cta = A.reverse ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
     long long u = cut_units<WALLS>(A, cta);
     const long long u1 = cut_units<WALLS>(A, cta + 1);
-    const Geom<real> G{A.fin, A.fout, A.nx, A.ny, A.W, A.rho_in_g, A.rho_in_l, A.rho_out_g, A.rho_out_l};
+    const Geom<real> G{A.fin, A.fout, A.nx, A.ny, A.W, A.pitch, A.rho_in_g, A.rho_in_l, A.rho_out_g, A.rho_out_l};
 
     Acc<real, CP> acc;
     acc.reset();
@@ -1103,7 +1118,7 @@ __global__ void __launch_bounds__(threads_per_cta<real, STAGED>(),
 template <typename real>
 struct BatchChan {
     long long off;  // element offset of the channel in the packed population buffers
-    int nx, ny, W, pad;
+    int nx, ny, W, pitch;
     real rho_in_g, rho_in_l, rho_out_g, rho_out_l;
 };
 
@@ -1140,7 +1155,7 @@ __global__ void __launch_bounds__(threads_per_cta<real, STAGED>(),
     for (int k = cta_begin[cta]; k < cta_begin[cta + 1]; ++k) {
         const BatchSeg sg = segs[k];
         const BatchChan<real> ch = chans[sg.chan];
-        const Geom<real> G{A.fin + ch.off, A.fout + ch.off, ch.nx, ch.ny, ch.W,
+        const Geom<real> G{A.fin + ch.off, A.fout + ch.off, ch.nx, ch.ny, ch.W, ch.pitch,
                            ch.rho_in_g, ch.rho_in_l, ch.rho_out_g, ch.rho_out_l};
         Acc<real, CP> acc;
         acc.reset();
@@ -1186,19 +1201,21 @@ __global__ void batch_diag_kernel(const double *__restrict__ seg_mass, const dou
     }
 }
 
-// f = f_eq(rho0, 0) at every node.
+// f = f_eq(rho0, 0) at every node (rho0: nx x ny; populations with plane
+// pitch P). Padding columns are zeroed.
 template <typename real>
 __global__ void init_kernel(const double *__restrict__ rho0, real *__restrict__ fa,
-                            real *__restrict__ fb, int nx, int n)
+                            real *__restrict__ fb, int nx, int P, int ny)
 {
+    const int n = P * ny;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const int y = k / nx, x = k - y * nx;
+        const int y = k / P, x = k - y * P;
         real fe[9];
-        feq_pairs<real>((real)rho0[k], real(0), real(0), real(0), real(0), fe);
+        feq_pairs<real>(x < nx ? (real)rho0[(long long)y * nx + x] : real(0), real(0), real(0), real(0), real(0), fe);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            fa[(9 * y + i) * nx + x] = fe[i];
-            fb[(9 * y + i) * nx + x] = fe[i];
+            fa[(9 * y + i) * P + x] = fe[i];
+            fb[(9 * y + i) * P + x] = fe[i];
         }
     }
 }

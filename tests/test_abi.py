@@ -39,8 +39,9 @@ def test_library_exports_every_declared_symbol(lbm):
 
 
 def test_status_strings(lbm):
-    for s in range(7):
+    for s in range(8):
         assert lbm.status_string(s)
+    assert "wait" in lbm.status_string(lbm.LBM_ERR_TIMEOUT)
     assert lbm.status_string(0) == "ok"
 
 

@@ -185,13 +185,16 @@ def test_reverse_cta_order_is_bitwise_identical(orc, lbm):
 
 
 @pytest.mark.parametrize("precision", [32, 64])
-def test_staged_and_register_paths_agree_bitwise(orc, lbm, precision):
+@pytest.mark.parametrize("nx", [512, 301, 129])
+def test_staged_and_register_paths_agree_bitwise(orc, lbm, precision, nx):
     """The bulk-copy staged kernel and the register-prefetch kernel do the same
-    arithmetic on the same values."""
-    rho0 = _airway(orc, 512, 96, 6, 200, 48)
+    arithmetic on the same values. Widths that are not multiples of 4 are
+    staged through padded row pitches (129: the outlet rule also narrows the
+    strips to 124 columns)."""
+    rho0 = _airway(orc, nx, 96, 6, nx // 3, 48)
     out = []
     for staged in (1, 0):
-        with lbm.Lattice(512, 96, rho0, walls=True, bc_x=True, precision=precision, T_over_Tc=0.85,
+        with lbm.Lattice(nx, 96, rho0, walls=True, bc_x=True, precision=precision, T_over_Tc=0.85,
                          kappa=0.5, dp=1e-3) as lat:
             lat.set_option(lbm.LBM_OPT_STAGED, staged)
             assert lat.launch_info()["staged"] == bool(staged)
@@ -280,3 +283,46 @@ def test_full_size_one_step_sampled_against_oracle(orc, lbm):
         sub = np.abs(f1[:, b, 1:-1].astype(np.float64) - f1_ref[:, b, 1:-1])
         assert sub.max() <= 2e-6 * np.abs(f1_ref[:, b, 1:-1]).max(), b
     del f1_ref
+
+
+def test_maximum_size_grid_windows_against_oracle(orc, lbm):
+    """Largest grid the 32-bit population indices allow (9 nx ny just below
+    2^31; 2 x 8.6 GB of FP32 populations). One GPU step depends only on the
+    state within three nodes, so the oracle stepping a periodic window of the
+    GPU's input state reproduces the window's interior exactly; windows at the
+    highest row and column indices, the middle and the origin are checked."""
+    import ctypes as C
+    import torch
+    nx, ny = 16384, 14563
+    assert 9 * nx * ny < 2**31 <= 9 * nx * (ny + 1)
+    kw = dict(T_over_Tc=0.8, kappa=0.5)
+    s = orc.Setup(nx=8, ny=8, **kw)
+    g, l, _ = s.coexistence()
+    # liquid slabs every 512 columns whose half-width varies smoothly and
+    # periodically along y (the profile is continuous across both periodic
+    # seams), plus seeded noise
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float32)
+    half = 100.0 + 20.0 * np.sin(2 * np.pi * y / ny)
+    d = np.abs((x % 512) - 256.0) - half
+    rho0 = (g + (l - g) * 0.5 * (1 - np.tanh(2 * d / 4.0))).astype(np.float64)
+    del x, y, d, half
+    rho0 += synth.node_noise(nx, ny, 1e-3, 7)
+    with lbm.Lattice(nx, ny, rho0, precision=32, **kw) as lat:
+        del rho0
+        lat.step(3)
+        f0 = torch.empty((9, ny, nx), dtype=torch.float32, device="cuda")
+        assert lbm.lib().lbm_populations(lat.ctx, C.c_void_p(f0.data_ptr())) == lbm.LBM_OK
+        lat.step(1)
+        f1 = torch.empty_like(f0)
+        assert lbm.lib().lbm_populations(lat.ctx, C.c_void_p(f1.data_ptr())) == lbm.LBM_OK
+    h = w = 24
+    for y0, x0 in [(ny - h, nx - w), (ny - h - 5, 0), (ny // 2, nx // 2 + 3), (0, 0)]:
+        ys = torch.arange(y0 - 3, y0 + h + 3, device="cuda") % ny
+        xs = torch.arange(x0 - 3, x0 + w + 3, device="cuda") % nx
+        win0 = f0[:, ys][:, :, xs].double().cpu().numpy()
+        got = f1[:, ys[3:-3]][:, :, xs[3:-3]].double().cpu().numpy()
+        sw = orc.Setup(nx=w + 6, ny=h + 6, **kw)
+        ref, _ = orc.step(sw, np.ascontiguousarray(win0))
+        err = np.abs(got - ref[:, 3:-3, 3:-3]).max() / np.abs(ref).max()
+        assert err <= 2e-6, (y0, x0, err)
+    del f0, f1
