@@ -151,6 +151,57 @@ def _lattice_kw(precision):
                 kappa=PHYS["kappa"], tau=PHYS["tau"], dp=PHYS["dp"])
 
 
+def _timed_steps(lat, stream, steps):
+    """Milliseconds per step of lat over `steps` steps (CUDA events on its stream)."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat.step(5)
+    torch.cuda.synchronize()
+    a.record(stream)
+    lat.step(steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def _extras(stream):
+    """Throughput of the other scope rows on the same GPU: the FP64 step and
+    the Peng-Robinson + MRT step on the 16384 x 2048 channel, and the adjoint
+    (forward with checkpoints, backward) on the 512 x 128 airway over 2000 FP64
+    steps. Not part of the headline value."""
+    import paper_2103_08301_gb300 as lbm
+    out = {}
+    nodes = NX * NY
+    rho0 = _rho0()
+    with lbm.Lattice(NX, NY, rho0, stream=stream, **_lattice_kw(64)) as lat:
+        ms = _timed_steps(lat, stream, 100)
+    out["fp64_step"] = {"ms_per_step": ms, "mlups": nodes / ms / 1e3,
+                        "hbm_gbs": BYTES_PER_NODE[64] * nodes / ms / 1e6}
+    pr = dict(walls=True, bc_x=True, precision=32, eos="pr", a=2 / 49, b=2 / 21, T_over_Tc=0.8, k=1.0,
+              kappa=0.01, tau=1.2, dp=1e-4, collision="mrt", s_e=1.64, s_eps=1.54, s_q=1 / 1.2, s_j=1 / 1.2)
+    _, g, l, _ = lbm.lbm_coexistence(lbm.lbm_eos(2 / 49, 2 / 21, 1.0, 0.8, 1.0, 0.01, lbm.LBM_EOS_PR, 0.344))
+    rho_pr = lbm.lbm_airway_rho0(NX, NY, 64, 4096, 1024, l, g)
+    with lbm.Lattice(NX, NY, rho_pr, stream=stream, **pr) as lat:
+        ms = _timed_steps(lat, stream, 100)
+        nan = lat.diag()["nan_detected"]
+    out["pr_mrt_fp32_step"] = {"ms_per_step": ms, "mlups": nodes / ms / 1e3, "nan": bool(nan),
+                               "workload": "same channel, Peng-Robinson water 0.8 Tc, MRT, tau 1.2"}
+    from paper_2103_08301_gb300 import adjoint as adjm
+    nx, ny, steps = 512, 128, 2000
+    _, g, l, _ = lbm.lbm_coexistence(lbm.lbm_eos(1.0, 4.0, 1.0, 0.85, 1.0, 0.5))
+    r0 = lbm.lbm_airway_rho0(nx, ny, 6.0, 128, 48.0, l, g, 4.0, 1e-3, 1)
+    with adjm.Adjoint(nx, ny, steps, walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5) as adj:
+        t0 = time.perf_counter()
+        adj.forward(r0, dp=1e-3)
+        t1 = time.perf_counter()
+        adj.backward(1.0, 1.0)
+        t2 = time.perf_counter()
+    out["adjoint"] = {"workload": "512x128 airway, 2000 FP64 steps, checkpoints every 45",
+                      "forward_s": t1 - t0, "backward_s": t2 - t1,
+                      "reverse_mlups": nx * ny * steps / (t2 - t1) / 1e6}
+    return out
+
+
 def _cpu_baseline(budget_s=15.0):
     """The oracle, as it stands, on a bounded sample of the workload: a window of
     the same channel (full 2048-row height, 1024 columns with the plug inside),
@@ -306,6 +357,7 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_sweep:
         from paper_2103_08301_gb300 import sweep_bench
         sweep = sweep_bench.run(steps=200)
+    extras = _extras(stream) if (rank == 0 and world == 1 and not args.no_sweep) else None
 
     if rank == 0:
         cpu = _cpu_baseline() if world == 1 else None
@@ -330,6 +382,7 @@ def run_ours(args, world, rank, local):
             "cpu_baseline": cpu,
             "diag": {"mass": d["mass"], "wall_shear_sum": d["wall_shear_sum"], "nan": d["nan_detected"]},
             "batched_sweep": sweep,
+            "extras": extras,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -285,6 +285,8 @@ lbm_status lbm_batch_fields(lbm_batch *b, int32_t channel, void *rho, void *ux, 
                             void *p_wall);
 lbm_status lbm_batch_diag(lbm_batch *b, int32_t channel, lbm_diag_t *out);
 lbm_status lbm_batch_populations(lbm_batch *b, int32_t channel, void *dst);
+/* Collision operator of every channel, as lbm_set_collision (NULL: BGK). */
+lbm_status lbm_batch_set_collision(lbm_batch *b, const lbm_collision *c);
 /* Options as lbm_set_option plus LBM_OPT_GRAPH_STEPS. Changing the launch
  * plan resets the diagnostic accumulators. */
 lbm_status lbm_batch_set_option(lbm_batch *b, lbm_option opt, int64_t value);
@@ -383,6 +385,11 @@ lbm_status lbm_adjoint_init(const lbm_grid *grid, const lbm_eos *eos, double tau
 lbm_status lbm_adjoint_forward(lbm_adjoint *adj, const lbm_drive *drive, const double *rho0, double *J);
 lbm_status lbm_adjoint_backward(lbm_adjoint *adj, double w_tau, double w_p, double *grad_rho0,
                                 double *grad_drive);
+/* Collision operator of the differentiated step, as lbm_set_collision (NULL:
+ * BGK); the MRT relaxation is symmetric, so its transpose is itself. Takes
+ * effect at the next forward; a backward before that forward returns
+ * LBM_ERR_STATE. Errors: LBM_ERR_ARG as lbm_set_collision. */
+lbm_status lbm_adjoint_set_collision(lbm_adjoint *adj, const lbm_collision *c);
 const char *lbm_adjoint_last_error(const lbm_adjoint *adj);
 void lbm_adjoint_free(lbm_adjoint *adj);
 

@@ -86,6 +86,7 @@ _SIGS = {
     "lbm_batch_diag": (C.c_int, [_P, C.c_int32, C.POINTER(lbm_diag_t)]),
     "lbm_batch_populations": (C.c_int, [_P, C.c_int32, _P]),
     "lbm_batch_set_option": (C.c_int, [_P, C.c_int, C.c_int64]),
+    "lbm_batch_set_collision": (C.c_int, [_P, C.POINTER(lbm_collision)]),
     "lbm_batch_launch_info": (C.c_int, [_P] + [C.POINTER(C.c_int64)] * 4),
     "lbm_batch_autotune": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                      C.POINTER(C.c_double)]),
@@ -109,6 +110,7 @@ _SIGS = {
                                    C.c_int64, C.c_int64, _P, C.POINTER(_P)]),
     "lbm_adjoint_forward": (C.c_int, [_P, C.POINTER(lbm_drive), _P, C.POINTER(C.c_double)]),
     "lbm_adjoint_backward": (C.c_int, [_P, C.c_double, C.c_double, _P, C.POINTER(C.c_double)]),
+    "lbm_adjoint_set_collision": (C.c_int, [_P, C.POINTER(lbm_collision)]),
     "lbm_adjoint_last_error": (C.c_char_p, [_P]),
     "lbm_adjoint_free": (None, [_P]),
 }
@@ -403,6 +405,10 @@ class Batch:
 
     def set_option(self, opt, value):
         self._chk(lib().lbm_batch_set_option(self.h, int(opt), int(value)))
+
+    def set_collision(self, coll):
+        """lbm_batch_set_collision with an lbm_collision (None: BGK)."""
+        self._chk(lib().lbm_batch_set_collision(self.h, C.byref(coll) if coll is not None else None))
 
     def launch_info(self):
         v = [C.c_int64() for _ in range(4)]

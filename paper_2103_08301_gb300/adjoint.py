@@ -20,8 +20,8 @@ import math
 
 import numpy as np
 
-from . import (LBM_OK, LBMError, _check, lbm_airway_rho0, lbm_airway_rho0_tangent, lbm_drive, lbm_eos,
-               lbm_grid, lib)
+from . import (LBM_COLL_MRT, LBM_EOS_CS, LBM_EOS_PR, LBM_OK, LBMError, _check, lbm_airway_rho0,
+               lbm_airway_rho0_tangent, lbm_collision, lbm_drive, lbm_eos, lbm_grid, lib)
 
 _P = C.c_void_p
 
@@ -42,10 +42,11 @@ class Adjoint:
     """
 
     def __init__(self, nx, ny, nsteps, *, walls=True, bc_x=True, a=1.0, b=4.0, R=1.0, T_over_Tc=0.85,
-                 k=1.0, kappa=0.5, tau=1.0, wetting=0.0, p_ref=None, block_steps=0, stream=None):
+                 k=1.0, kappa=0.5, tau=1.0, wetting=0.0, p_ref=None, eos="cs", omega=0.344, collision="bgk",
+                 s_e=1.64, s_eps=1.54, s_j=1.0, s_q=1.7, s_nu=None, block_steps=0, stream=None):
         self.nx, self.ny, self.nsteps = nx, ny, nsteps
         self.grid = lbm_grid(nx, ny, int(walls), int(bc_x), 64)
-        self.eos = lbm_eos(a, b, R, T_over_Tc, k, kappa)
+        self.eos = lbm_eos(a, b, R, T_over_Tc, k, kappa, {"cs": LBM_EOS_CS, "pr": LBM_EOS_PR}[eos], omega)
         self.p_ref = math.nan if p_ref is None else p_ref
         self._stream = stream
         h = _P()
@@ -53,6 +54,11 @@ class Adjoint:
                                       int(nsteps), int(block_steps),
                                       _P(stream.cuda_stream) if stream is not None else None, C.byref(h)))
         self.h = h
+        if collision != "bgk":
+            if collision != "mrt":
+                raise ValueError(collision)
+            coll = lbm_collision(LBM_COLL_MRT, s_e, s_eps, s_j, s_q, 0.0 if s_nu is None else s_nu)
+            self._chk(lib().lbm_adjoint_set_collision(self.h, C.byref(coll)))
         self.generation = 0      # forward runs so far (guards stale backward calls)
         self._rho0_like = None
 

@@ -10,7 +10,7 @@
 //   lambda^n = (d f^{n+1} / d f^n)^T lambda^{n+1} + (d J_n / d f^n)^T,
 // the exact transpose of the linearised step that lbm_step takes: moments,
 // ghost densities, EOS potential, Laplacian, force (Eq. 2.17), velocity-shift
-// BGK collision, pressure columns, bounce-back streaming. Where the pressure
+// BGK or MRT collision, pressure columns, bounce-back streaming. Where the pressure
 // column's phase weight is clamped its derivative is taken as zero (the
 // derivative almost everywhere). Gradients:
 //   dJ/drho0(x) = sum_i w_i lambda^0_i(x)          (f^0 = f_eq(rho0, 0)),
@@ -48,7 +48,36 @@ struct AdjGeo {
     double bpr, aalpha;           // PR: b and a alpha(T)
     double g_in, l_in, g_out, l_out, ph_g, inv_dph;  // inv_dph = 0: single phase, no blend
     double w_tau, w_p;
+    // collision: BGK (mrt = 0) or MRT with rates over the squared row norms of
+    // the moment basis (mrate[k] = s_k / |M_k|^2); the equilibrium velocity is
+    // u + ushift F / rho with ushift = tau (BGK) or 1 / s_j (MRT)
+    int mrt;
+    double ushift, mrate[9];
 };
+
+// Lallemand-Luo moment basis (rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy)
+// over the D2Q9 velocities.
+__device__ __constant__ const int Mrow[9][9] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1},      {-4, -1, -1, -1, -1, 2, 2, 2, 2}, {4, -2, -2, -2, -2, 1, 1, 1, 1},
+    {0, 1, 0, -1, 0, 1, -1, -1, 1},   {0, -2, 0, 2, 0, 1, -1, -1, 1},   {0, 0, 1, 0, -1, 1, 1, -1, -1},
+    {0, 0, -2, 0, 2, 1, 1, -1, -1},   {0, 1, -1, 1, -1, 0, 0, 0, 0},    {0, 0, 0, 0, 0, 1, -1, 1, -1}};
+
+// v -> K v with K = M^-1 S M = M^T diag(s_k / |M_k|^2) M. K is symmetric, so
+// the same map transposes the MRT relaxation f* = f - K (f - f_eq).
+__device__ __forceinline__ void mrt_apply(const AdjGeo &g, const double (&v)[9], double (&out)[9])
+{
+    double m[9];
+    for (int k = 0; k < 9; ++k) {
+        double t = 0.0;
+        for (int i = 0; i < 9; ++i) t += Mrow[k][i] * v[i];
+        m[k] = t * g.mrate[k];
+    }
+    for (int i = 0; i < 9; ++i) {
+        double t = 0.0;
+        for (int k = 0; k < 9; ++k) t += Mrow[k][i] * m[k];
+        out[i] = t;
+    }
+}
 
 __device__ __forceinline__ bool solid_row(const AdjGeo &g, int y) { return g.walls && (y == 0 || y == g.ny - 1); }
 __device__ __forceinline__ bool pcol(const AdjGeo &g, int x) { return g.bc_x && (x == 0 || x == g.nx - 1); }
@@ -258,21 +287,27 @@ __global__ void adj_local(AdjGeo g, const double *__restrict__ lam_in,
         gb[i] = lam_in[i * n + ty * g.nx + tx];
     }
 
-    // collision f*_i = (1 - 1/tau) f_i + (1/tau) f_eq_i(rho, u_eq), u_eq = (j + tau F) / rho
-    double lam[9];
-    const double uex = (jX + g.tau * FX) / r, uey = (jY + g.tau * FY) / r;
+    // collision f* = f - K (f - f_eq(rho, u_eq)), u_eq = (j + ushift F) / rho,
+    // K = I / tau (BGK) or M^-1 S M (MRT): f-bar = g - K g, f_eq-bar = K g
+    double lam[9], kg[9];
+    if (g.mrt) {
+        mrt_apply(g, gb, kg);
+    } else {
+        for (int i = 0; i < 9; ++i) kg[i] = gb[i] / g.tau;
+    }
+    const double uex = (jX + g.ushift * FX) / r, uey = (jY + g.ushift * FY) / r;
     const double usq = uex * uex + uey * uey;
     double rb = 0.0, ubx = 0.0, uby = 0.0;
     for (int i = 0; i < 9; ++i) {
-        lam[i] = omt * gb[i];
-        const double eb = gb[i] / g.tau;
+        lam[i] = gb[i] - kg[i];
+        const double eb = kg[i];
         const double eu = ex_(i) * uex + ey_(i) * uey;
         rb += eb * wq(i) * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
         ubx += eb * wq(i) * r * (3.0 * ex_(i) + 9.0 * eu * ex_(i) - 3.0 * uex);
         uby += eb * wq(i) * r * (3.0 * ey_(i) + 9.0 * eu * ey_(i) - 3.0 * uey);
     }
     double jbx = ubx / r, jby = uby / r;
-    double ax = g.tau * ubx / r, ay = g.tau * uby / r;
+    double ax = g.ushift * ubx / r, ay = g.ushift * uby / r;
     rb -= (ubx * uex + uby * uey) / r;
 
     // wall objective terms (interior columns; a row may serve both walls on
@@ -535,6 +570,7 @@ struct lbm_adjoint {
     cudaStream_t stream = nullptr;
     lbm_ctx *ctx = nullptr;
     bool have_drive = false, forward_done = false;
+    lbm_collision coll{};  // BGK unless set
     AdjGeo geo{};
     double dgin = 0, dlin = 0, dgout = 0, dlout = 0;  // d rho_column / d dp
     // device buffers
@@ -639,6 +675,7 @@ lbm_status adj_setup_drive(lbm_adjoint *a, const lbm_drive *drive)
     std::vector<double> one((size_t)a->grid.nx * a->grid.ny, 0.1);
     lbm_status s = lbm_init(&a->grid, &a->eos, a->tau, a->wet, &d, one.data(), nullptr, 0, a->stream, &a->ctx);
     if (s != LBM_OK) { a->err = std::string("forward context: ") + lbm_status_string(s); a->ctx = nullptr; return s; }
+    if ((s = lbm_set_collision(a->ctx, &a->coll)) != LBM_OK) return ctx_status(a, s, "collision");
     a->drive = d;
     a->have_drive = true;
     lbm_diag_t dg;
@@ -653,6 +690,14 @@ lbm_status adj_setup_drive(lbm_adjoint *a, const lbm_drive *drive)
     g.eos_kind = th.kind; g.bpr = th.b; g.aalpha = th.aalpha;
     g.RT = a->eos.R * dg.T; g.a = a->eos.a; g.b4 = 0.25 * a->eos.b; g.k2 = a->eos.k * a->eos.k;
     g.kappa = a->eos.kappa; g.tau = a->tau; g.nu = (a->tau - 0.5) / 3.0; g.wet = a->wet;
+    g.mrt = a->coll.kind == LBM_COLL_MRT;
+    g.ushift = g.mrt ? 1.0 / a->coll.s_j : a->tau;
+    if (g.mrt) {
+        const double s_nu = a->coll.s_nu > 0 ? a->coll.s_nu : 1.0 / a->tau;
+        const double r[9] = {0.0, a->coll.s_e / 36.0, a->coll.s_eps / 36.0, a->coll.s_j / 6.0, a->coll.s_q / 12.0,
+                             a->coll.s_j / 6.0, a->coll.s_q / 12.0, s_nu / 4.0, s_nu / 4.0};
+        for (int k = 0; k < 9; ++k) g.mrate[k] = r[k];
+    }
     g.gx = d.gx; g.gy = d.gy;
     g.g_in = dg.rho_in; g.l_in = dg.rho_in_l; g.g_out = dg.rho_out; g.l_out = dg.rho_out_l;
     g.ph_g = dg.rho_g;
@@ -795,6 +840,26 @@ lbm_status lbm_adjoint_backward(lbm_adjoint *a, double w_tau, double w_p, double
     grad_drive[0] = h[2] * a->dgin + h[3] * a->dlin + h[4] * a->dgout + h[5] * a->dlout;
     grad_drive[1] = h[6];
     grad_drive[2] = h[7];
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_set_collision(lbm_adjoint *a, const lbm_collision *c)
+{
+    if (!a) return LBM_ERR_ARG;
+    const lbm_collision prev = a->coll;
+    a->coll = c ? *c : lbm_collision{};
+    if (a->ctx) {
+        lbm_status s = lbm_set_collision(a->ctx, &a->coll);
+        if (s != LBM_OK) { a->coll = prev; return s; }
+    } else if (a->coll.kind == LBM_COLL_MRT) {
+        for (double r : {a->coll.s_e, a->coll.s_eps, a->coll.s_j, a->coll.s_q})
+            if (!(r > 0.0 && r < 2.0)) { a->coll = prev; return LBM_ERR_ARG; }
+    } else if (a->coll.kind != LBM_COLL_BGK) {
+        a->coll = prev;
+        return LBM_ERR_ARG;
+    }
+    a->have_drive = false;    // rebuild the geometry with the new collision
+    a->forward_done = false;  // earlier checkpoints belong to the old operator
     return LBM_OK;
 }
 

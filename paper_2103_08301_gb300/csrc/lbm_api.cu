@@ -169,30 +169,41 @@ lbm::KArgs<real> make_args(const lbm_ctx *ctx)
     return A;
 }
 
-template <typename real, int MODE, bool STAGED>
+template <typename real, int MODE, bool STAGED, bool PADDED>
 void *kernel_ptr(bool walls, bool pres)
 {
     using namespace lbm;
-    if (walls && pres) return (void *)step_kernel<real, true, true, MODE, STAGED>;
-    if (walls) return (void *)step_kernel<real, true, false, MODE, STAGED>;
-    if (pres) return (void *)step_kernel<real, false, true, MODE, STAGED>;
-    return (void *)step_kernel<real, false, false, MODE, STAGED>;
+    if (walls && pres) return (void *)step_kernel<real, true, true, MODE, STAGED, PADDED>;
+    if (walls) return (void *)step_kernel<real, true, false, MODE, STAGED, PADDED>;
+    if (pres) return (void *)step_kernel<real, false, true, MODE, STAGED, PADDED>;
+    return (void *)step_kernel<real, false, false, MODE, STAGED, PADDED>;
 }
 
 template <typename real, int MODE>
-void *kernel_ptr(bool walls, bool pres, bool staged)
+void *kernel_ptr(bool walls, bool pres, bool staged, bool padded)
 {
-    return staged ? kernel_ptr<real, MODE, true>(walls, pres) : kernel_ptr<real, MODE, false>(walls, pres);
+    if (staged)
+        return padded ? kernel_ptr<real, MODE, true, true>(walls, pres) : kernel_ptr<real, MODE, true, false>(walls, pres);
+    return padded ? kernel_ptr<real, MODE, false, true>(walls, pres) : kernel_ptr<real, MODE, false, false>(walls, pres);
 }
+
+}  // namespace
+
+void *lbm_step_kernel_ptr(int precision, int mode, bool walls, bool pres, bool staged, bool padded)
+{
+    if (precision == 64)
+        return mode == lbm::MODE_STEP ? kernel_ptr<double, lbm::MODE_STEP>(walls, pres, staged, padded)
+                                      : kernel_ptr<double, lbm::MODE_FIELDS>(walls, pres, staged, padded);
+    return mode == lbm::MODE_STEP ? kernel_ptr<float, lbm::MODE_STEP>(walls, pres, staged, padded)
+                                  : kernel_ptr<float, lbm::MODE_FIELDS>(walls, pres, staged, padded);
+}
+
+namespace {
 
 void *step_kernel_ptr(const lbm_ctx *ctx, int mode)
 {
-    const bool w = ctx->grid.walls, p = ctx->grid.bc_x, st = ctx->staged;
-    if (ctx->grid.precision == 64)
-        return mode == lbm::MODE_STEP ? kernel_ptr<double, lbm::MODE_STEP>(w, p, st)
-                                      : kernel_ptr<double, lbm::MODE_FIELDS>(w, p, st);
-    return mode == lbm::MODE_STEP ? kernel_ptr<float, lbm::MODE_STEP>(w, p, st)
-                                  : kernel_ptr<float, lbm::MODE_FIELDS>(w, p, st);
+    return lbm_step_kernel_ptr(ctx->grid.precision, mode, ctx->grid.walls, ctx->grid.bc_x, ctx->staged,
+                               ctx->pitch != ctx->grid.nx);
 }
 
 size_t dyn_smem(const lbm_ctx *ctx)

@@ -47,6 +47,7 @@ struct lbm_batch {
     lbm_eos eos{};
     double tau = 1.0, wet = 0.0, T = 0, Tc = 0, rho_g = 0, rho_l = 0, p_sat = 0;
     lbm::Thermo th{};  // EOS at the working temperature
+    lbm_collision coll{};  // BGK unless lbm_batch_set_collision chose MRT
     std::vector<ChanHost> ch;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -111,16 +112,6 @@ void *batch_kernel(const lbm_batch *b)
     return b->staged ? batch_kernel_ptr<float, true>(w, p) : batch_kernel_ptr<float, false>(w, p);
 }
 
-template <typename real, bool STAGED>
-void *fields_kernel_ptr(bool walls, bool pres)
-{
-    using namespace lbm;
-    if (walls && pres) return (void *)step_kernel<real, true, true, MODE_FIELDS, STAGED>;
-    if (walls) return (void *)step_kernel<real, true, false, MODE_FIELDS, STAGED>;
-    if (pres) return (void *)step_kernel<real, false, true, MODE_FIELDS, STAGED>;
-    return (void *)step_kernel<real, false, false, MODE_FIELDS, STAGED>;
-}
-
 size_t staged_bytes(const lbm_batch *b, bool staged)
 {
     if (!staged) return 0;
@@ -146,8 +137,14 @@ lbm::KArgs<real> physics_args(const lbm_batch *b)
     A.eos_kind = b->th.kind;
     A.bpr = (real)b->th.b;
     A.aalpha = (real)b->th.aalpha;
-    A.mrt = 0;  // batched channels use BGK
-    A.ushift = (real)b->tau;
+    const lbm_collision &cl = b->coll;
+    A.mrt = cl.kind == LBM_COLL_MRT;
+    A.ushift = A.mrt ? (real)(1.0 / cl.s_j) : (real)b->tau;
+    if (A.mrt) {
+        const double s_nu = cl.s_nu > 0 ? cl.s_nu : 1.0 / b->tau;
+        A.m_e = (real)(cl.s_e / 36.0); A.m_eps = (real)(cl.s_eps / 36.0);
+        A.m_j = (real)(cl.s_j / 6.0); A.m_q = (real)(cl.s_q / 12.0); A.m_nu = (real)(s_nu / 4.0);
+    }
     A.ph_g = (real)b->rho_g;
     A.inv_dph = b->rho_l > b->rho_g ? (real)(1.0 / (b->rho_l - b->rho_g)) : real(0);
     A.err = b->d_err;
@@ -358,7 +355,7 @@ lbm_status chan_fields(lbm_batch *b, int ci, void *rho, void *ux, void *uy, void
     A.rho_out_l = (real)c.rho_out_l;
     A.o_rho = d_rho; A.o_vx = d_vx; A.o_vy = d_vy; A.o_tw = d_tw; A.o_pw = d_pw;
     const bool st = b->allow_staged && c.pitch % 4 == 0 && c.W % 4 == 0;
-    void *fn = st ? fields_kernel_ptr<real, true>(b->walls, b->bc_x) : fields_kernel_ptr<real, false>(b->walls, b->bc_x);
+    void *fn = lbm_step_kernel_ptr(b->precision, lbm::MODE_FIELDS, b->walls, b->bc_x, st, c.pitch != c.grid.nx);
     const size_t smem = staged_bytes(b, st);
     BCK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attribute");
     A.nctas = (int)std::max<long long>(1, std::min<long long>((long long)b->sms * 4, c.units / 2));
@@ -563,6 +560,23 @@ lbm_status lbm_batch_populations(lbm_batch *b, int32_t channel, void *dst)
         BCK(cudaMemcpy2DAsync((char *)dst + i * nx * ny * sz, row, src + i * prow, 9 * prow, row, ny,
                               cudaMemcpyDefault, b->stream), "populations copy");
     BCK(cudaStreamSynchronize(b->stream), "populations sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_collision(lbm_batch *b, const lbm_collision *c)
+{
+    if (!b) return LBM_ERR_ARG;
+    const lbm_collision next = c ? *c : lbm_collision{};
+    if (next.kind == LBM_COLL_MRT) {
+        for (double r : {next.s_e, next.s_eps, next.s_j, next.s_q})
+            if (!(r > 0.0 && r < 2.0)) return LBM_ERR_ARG;
+        if (std::isnan(next.s_nu) || !(next.s_nu <= 0.0 || next.s_nu < 2.0)) return LBM_ERR_ARG;
+    } else if (next.kind != LBM_COLL_BGK) {
+        return LBM_ERR_ARG;
+    }
+    b->coll = next;
+    // the captured graph holds the old kernel arguments
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
     return LBM_OK;
 }
 

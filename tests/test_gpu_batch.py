@@ -100,3 +100,23 @@ def test_graph_reverse_and_autotune_keep_results(orc, lbm):
             outs.append(np.concatenate([b.populations(c).ravel() for c in range(len(chans))]))
     for o in outs[1:]:
         assert np.array_equal(o.view(np.uint32), outs[0].view(np.uint32))
+
+
+def test_batch_mrt_matches_single_channels_bitwise(orc, lbm):
+    # MRT collision (Eq. 2.1) set on the batch after it was built (the CUDA
+    # graph is re-captured with the new arguments)
+    chans = _channels(orc, STAGED_SPECS[:3])
+    rates = dict(s_e=1 / 1.2, s_eps=1.54, s_j=1 / 1.2, s_q=1 / 1.2, s_nu=None)
+    coll = lbm.lbm_collision(lbm.LBM_COLL_MRT, rates["s_e"], rates["s_eps"], rates["s_j"], rates["s_q"], 0.0)
+    with lbm.Batch(chans, precision=32, tau=1.2, **KW) as b:
+        b.step(70)  # BGK steps, graph captured
+        b.set_collision(coll)
+        b.step(80)
+        got = [b.populations(c) for c in range(len(chans))]
+    for c, ch in enumerate(chans):
+        with lbm.Lattice(ch["nx"], ch["ny"], ch["rho0"], precision=32, dp=ch["dp"], tau=1.2, **KW) as lat:
+            lat.step(70)
+            lat.set_collision(coll)
+            lat.step(80)
+            ref = lat.populations()
+        assert np.array_equal(got[c].view(np.uint32), ref.view(np.uint32)), f"channel {c}"
