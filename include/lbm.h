@@ -209,13 +209,19 @@ lbm_status lbm_set_collision(lbm_ctx *ctx, const lbm_collision *c);
  *   LBM_OPT_STAGED       nonzero (default): stream population rows through
  *                        shared memory with bulk asynchronous copies when nx
  *                        and the strip width are multiples of 4; zero: per-
- *                        thread register prefetch. Both give identical results. */
+ *                        thread register prefetch. Both give identical results.
+ *   LBM_OPT_ROWS2        nonzero (default): the staged FP32 step gives each
+ *                        thread two rows of its column per iteration (paired
+ *                        FP32 instructions) where it applies (staged, and nx a
+ *                        multiple of 4 unless x has pressure columns); zero:
+ *                        one row per iteration. Both give identical results. */
 typedef enum {
     LBM_OPT_CTAS_PER_SM = 1,
     LBM_OPT_REVERSE = 2,
     LBM_OPT_STRIP = 3,
     LBM_OPT_STAGED = 4,
-    LBM_OPT_GRAPH_STEPS = 5 /* batches only: steps per CUDA graph replay (even, 0 = no graph) */
+    LBM_OPT_GRAPH_STEPS = 5, /* batches only: steps per CUDA graph replay (even, 0 = no graph) */
+    LBM_OPT_ROWS2 = 6
 } lbm_option;
 lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value);
 /* Launch geometry of the step kernel: CTAs, threads per CTA, work units and

@@ -90,6 +90,8 @@ struct lbm_ctx {
     int sms = 0;
     bool allow_staged = true;  // LBM_OPT_STAGED
     bool staged = false;       // bulk-copy staged kernel selected for this grid
+    bool allow_rows2 = true;   // LBM_OPT_ROWS2
+    bool rows2 = false;        // row-pair FP32 step kernel selected for this grid
     // fields scratch (allocated on first host-pointer lbm_fields)
     unsigned char *fscratch = nullptr;
     // non-blocking NaN check
@@ -200,17 +202,37 @@ void *lbm_step_kernel_ptr(int precision, int mode, bool walls, bool pres, bool s
 
 namespace {
 
-void *step_kernel_ptr(const lbm_ctx *ctx, int mode)
+template <bool PADDED>
+void *rows2_kernel_ptr(bool walls, bool pres)
 {
-    return lbm_step_kernel_ptr(ctx->grid.precision, mode, ctx->grid.walls, ctx->grid.bc_x, ctx->staged,
-                               ctx->pitch != ctx->grid.nx);
+    using namespace lbm;
+    if (walls && pres) return (void *)step_kernel_rows2<true, true, PADDED>;
+    if (walls) return (void *)step_kernel_rows2<true, false, PADDED>;
+    if (pres) return (void *)step_kernel_rows2<false, true, PADDED>;
+    return (void *)step_kernel_rows2<false, false, PADDED>;
 }
 
-size_t dyn_smem(const lbm_ctx *ctx)
+void *step_kernel_ptr(const lbm_ctx *ctx, int mode)
+{
+    const bool padded = ctx->pitch != ctx->grid.nx;
+    if (mode == lbm::MODE_STEP && ctx->rows2)
+        return padded ? rows2_kernel_ptr<true>(ctx->grid.walls, ctx->grid.bc_x)
+                      : rows2_kernel_ptr<false>(ctx->grid.walls, ctx->grid.bc_x);
+    return lbm_step_kernel_ptr(ctx->grid.precision, mode, ctx->grid.walls, ctx->grid.bc_x, ctx->staged, padded);
+}
+
+size_t dyn_smem(const lbm_ctx *ctx, int mode)
 {
     if (!ctx->staged) return 0;
+    if (mode == lbm::MODE_STEP && ctx->rows2) return lbm::rows2_smem_bytes();
     return ctx->grid.precision == 64 ? lbm::staged_smem_bytes<double>()
                                      : lbm::staged_smem_bytes<float>();
+}
+
+int threads_of(const lbm_ctx *ctx, int mode)
+{
+    if (mode == lbm::MODE_STEP && ctx->rows2) return lbm::STRIP;
+    return cta_threads(ctx->grid.precision, ctx->staged);
 }
 
 // Band height of the work-unit order: about one CTA's share of rows, so that
@@ -235,22 +257,27 @@ lbm_status plan_launch(lbm_ctx *ctx)
     ctx->W = W;
     // bulk-copy staging needs 16-byte aligned row segments
     ctx->staged = ctx->allow_staged && (ctx->pitch % 4 == 0) && (W % 4 == 0);
+    // row pairs: FP32 staged grids; with periodic x the wrapped halo columns
+    // are copied as one 16-byte group, which needs nx a multiple of 4
+    ctx->rows2 = ctx->allow_rows2 && ctx->staged && ctx->grid.precision == 32 &&
+                 lbm::cols_per_thread<float, true>() == 1 && (ctx->grid.bc_x || nx % 4 == 0);
     ctx->nstrips = (nx + W - 1) / W;
     ctx->yf0 = ctx->grid.walls ? 1 : 0;
     ctx->nyf = ctx->grid.walls ? ctx->grid.ny - 2 : ctx->grid.ny;
     ctx->units = (long long)ctx->nstrips * ctx->nyf;
 
-    const size_t smem = dyn_smem(ctx);
     for (int mode : {lbm::MODE_STEP, lbm::MODE_FIELDS}) {
         cudaError_t e = cudaFuncSetAttribute(step_kernel_ptr(ctx, mode),
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)dyn_smem(ctx, mode));
         if (e != cudaSuccess) return cuda_fail(ctx, e, "smem attribute");
     }
     int per_sm = ctx->ctas_per_sm_opt;
     if (per_sm <= 0) {
         int occ = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ, step_kernel_ptr(ctx, lbm::MODE_STEP), cta_threads(ctx->grid.precision, ctx->staged), smem);
+            &occ, step_kernel_ptr(ctx, lbm::MODE_STEP), threads_of(ctx, lbm::MODE_STEP),
+            dyn_smem(ctx, lbm::MODE_STEP));
         if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy");
         per_sm = std::max(1, occ);
     }
@@ -267,8 +294,8 @@ cudaError_t launch(lbm_ctx *ctx, const lbm::KArgs<real> &A)
 {
     void *fn = step_kernel_ptr(ctx, MODE);
     void *args[] = {(void *)&A};
-    return cudaLaunchKernel(fn, dim3(ctx->nctas), dim3(cta_threads(ctx->grid.precision, ctx->staged)), args,
-                            dyn_smem(ctx), ctx->stream);
+    return cudaLaunchKernel(fn, dim3(ctx->nctas), dim3(threads_of(ctx, MODE)), args, dyn_smem(ctx, MODE),
+                            ctx->stream);
 }
 
 template <typename real>
@@ -646,6 +673,9 @@ lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
     case LBM_OPT_STAGED:
         ctx->allow_staged = value != 0;
         break;
+    case LBM_OPT_ROWS2:
+        ctx->allow_rows2 = value != 0;
+        break;
     default:
         return LBM_ERR_ARG;
     }
@@ -664,7 +694,7 @@ lbm_status lbm_launch_info(const lbm_ctx *ctx, int64_t *ctas, int64_t *threads, 
 {
     if (!ctx) return LBM_ERR_ARG;
     if (ctas) *ctas = ctx->nctas;
-    if (threads) *threads = cta_threads(ctx->grid.precision, ctx->staged);
+    if (threads) *threads = threads_of(ctx, lbm::MODE_STEP);
     if (units) *units = ctx->units;
     if (staged) *staged = ctx->staged ? 1 : 0;
     return LBM_OK;

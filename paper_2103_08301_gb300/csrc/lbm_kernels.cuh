@@ -535,10 +535,11 @@ __device__ __forceinline__ void column_extrapolate(const KArgs<real> &A, real rh
 }
 
 // Wall pressure (Eq. 2.4 in mesh units) at ring column cc of row q0:
-// k^2 p0 - kappa rho lap rho - (kappa/2)|grad rho|^2, with k^2 p0 = phi + rho/3.
+// k^2 p0 - kappa rho lap rho - (kappa/2)|grad rho|^2, with k^2 p0 = phi + rho/3
+// and lap rho = lap (the node's Laplacian).
 template <typename real, int SW>
 __device__ __forceinline__ real wall_pressure(const KArgs<real> &A, const real (*R)[SW], const real (*P)[SW],
-                                              const real (*L)[SW], int qm, int q0, int qp, int cc, real rho)
+                                              real lap, int qm, int q0, int qp, int cc, real rho)
 {
     real grx, gry;
     grad12<real>(row3<real, 1, SW>(R, qm, cc), row3<real, 1, SW>(R, q0, cc), row3<real, 1, SW>(R, qp, cc), grx,
@@ -546,7 +547,7 @@ __device__ __forceinline__ real wall_pressure(const KArgs<real> &A, const real (
     grx = mulk(grx, 1.0 / 12.0);
     gry = mulk(gry, 1.0 / 12.0);
     const real k2p0 = add_(P[q0][cc], mulk(rho, 1.0 / 3.0));
-    const real t = fma_(mul_(A.kappa, rho), -L[q0][cc], k2p0);
+    const real t = fma_(mul_(A.kappa, rho), -lap, k2p0);
     return fma_(fma_(grx, grx, mul_(gry, gry)), mul_(real(-0.5), A.kappa), t);
 }
 
@@ -975,7 +976,7 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
                     if (r == 1) {
                         b_rho1[k] = rk;
                         b_v1[k] = vk;
-                        const real pw = wall_pressure<real, SW>(A, S.rho, S.phi, S.lap, qm, q0, qp, cc, rk);
+                        const real pw = wall_pressure<real, SW>(A, S.rho, S.phi, S.lap[q0][cc], qm, q0, qp, cc, rk);
                         if (MODE == MODE_STEP) { acc.pmin = fmin(acc.pmin, pw); acc.pmax = fmax(acc.pmax, pw); }
                         else A.o_pw[xk] = pw;
                     }
@@ -987,7 +988,7 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
                     }
                     if (r == ny - 2) {
                         const real tw = mul_(mul_(rk, A.nu), mul_(fma_(real(9), vk, -t_v2[k]), third));
-                        const real pw = wall_pressure<real, SW>(A, S.rho, S.phi, S.lap, qm, q0, qp, cc, rk);
+                        const real pw = wall_pressure<real, SW>(A, S.rho, S.phi, S.lap[q0][cc], qm, q0, qp, cc, rk);
                         if (MODE == MODE_STEP) {
                             acc.J += (double)tw;
                             acc.tmin = fmin(acc.tmin, tw); acc.tmax = fmax(acc.tmax, tw);
@@ -1277,3 +1278,5 @@ __global__ void reset_acc_kernel(double *mass_part, double *J_acc, real *ext, in
 }
 
 } // namespace lbm
+
+#include "lbm_rows2.cuh"

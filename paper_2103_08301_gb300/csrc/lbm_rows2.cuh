@@ -1,0 +1,420 @@
+// Row-pair variant of the FP32 staged step (MODE_STEP): each thread owns one
+// column and takes two consecutive rows per iteration, the pair held in a
+// float2 and computed with the paired FP32 instructions (__ffma2_rn and
+// friends), which round every element exactly as the scalar operations do.
+// The arithmetic is the same pack code as the one-row kernel's, so the two
+// kernels give identical bits; only the schedule differs:
+//   - the loop bookkeeping, barriers and stage waits of an iteration are
+//     shared by two nodes per thread, and the method's arithmetic issues one
+//     instruction per two nodes;
+//   - the stage holds each stencil row with a four-column margin on both sides
+//     (columns x0-4 .. x0+W+3), so the halo densities are summed from shared
+//     memory: no halo registers, no halo loads from global memory;
+//   - every thread waits on the stage's mbarrier itself, so a pair issued
+//     half an iteration before it is read needs no publishing barrier; three
+//     pair slots (six rows) suffice.
+// Iteration k handles stencil rows yy0 = ya-2+2k and yy0+1:
+//   (1) wait for their stage; density and phi of both rows (own and halo
+//       columns) into the 8-row ring;                      --- barrier A ---
+//   (2) issue the pair k+1 into the slot of pair k-2; Laplacian of rows
+//       yy0-1, yy0 on local columns -1 .. xw;              --- barrier B ---
+//   (3) force, collision, boundaries and push of rows yy0-2, yy0-1 (pair k-1,
+//       k >= 2; the second row only if it is below yb).
+// Restricted to strips and pitches that are multiples of 4 and, with periodic
+// x, to nx a multiple of 4 (the wrapped halo columns are copied as one
+// 16-byte group from each end of the row).
+#pragma once
+
+namespace lbm {
+
+constexpr int R2_SLOTS = 3;            // pair slots of the stage ring
+constexpr int R2_SP = STRIP + 8;       // stage row pitch: strip plus 4 margin columns per side
+constexpr int R2_ROW = 9 * R2_SP;      // one stencil row of nine planes
+constexpr int R2_SLOT = 2 * R2_ROW;    // one pair of rows
+
+constexpr size_t rows2_smem_bytes()
+{
+    return (size_t)R2_SLOTS * R2_SLOT * sizeof(float) + R2_SLOTS * sizeof(uint64_t);
+}
+
+// Position in the pair-slot ring (slot and mbarrier phase parity).
+struct RingPos2 {
+    uint32_t s = 0, ph = 0;
+    __device__ __forceinline__ void advance()
+    {
+        if (++s == R2_SLOTS) { s = 0; ph ^= 1u; }
+    }
+};
+
+// West, centre and east float2 packs (rows ra, rb) of ring column c.
+template <int SW>
+__device__ __forceinline__ Row3<float2> row3p(const float (*S)[SW], int ra, int rb, int c)
+{
+    Row3<float2> r;
+    r.w = make_float2(S[ra][c - 1], S[rb][c - 1]);
+    r.c = make_float2(S[ra][c], S[rb][c]);
+    r.e = make_float2(S[ra][c + 1], S[rb][c + 1]);
+    return r;
+}
+
+// Both rows of a slot at stage column sc, plane i.
+__device__ __forceinline__ float2 stage_pair(const float *slot, int i, int sc)
+{
+    return make_float2(slot[i * R2_SP + sc], slot[R2_ROW + i * R2_SP + sc]);
+}
+
+
+// One segment (strip s, fluid rows ya .. yb-1) of the row-pair step; see the
+// file comment for the schedule. The ring rows of rho / phi / lap are indexed
+// by y & (RING - 1) as in the one-row kernel.
+template <bool WALLS, bool PRES, bool PADDED>
+__device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom<float> &G, int s, int ya, int yb,
+                                               Smem<float, STRIP> &S, float *stages, uint64_t *bars,
+                                               RingPos2 &ring_next, Acc<float, 1> &acc, bool &lost)
+{
+    using V = float2;
+    constexpr int SW = STRIP + 4;
+    constexpr int NW = STRIP / 32;
+    constexpr int PRODUCER = STRIP - 1;  // no halo duty
+    constexpr int RM = RING - 1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float third = 1.0f / 3.0f;
+    const int nx = G.nx, ny = G.ny;
+    const int P = PADDED ? G.pitch : G.nx;  // plane pitch; columns nx .. P-1 are padding
+    const int rstride = 9 * P;
+    const int o1 = P + 1, o2 = rstride + 2 * P, o3 = 3 * P - 1, o4 = 4 * P - rstride;
+    const int o5 = rstride + 5 * P + 1, o6 = rstride + 6 * P - 1, o7 = 7 * P - rstride - 1;
+    const int o8 = 8 * P - rstride + 1;
+    float b_rho1 = 0.f, b_v1 = 0.f, t_v2 = 0.f;  // wall-pair carries (rows 1 -> 2, ny-3 -> ny-2)
+
+    const int x0 = s * G.W;
+    const int xw = min(G.W, nx - x0);
+    const int c0 = tid;
+    const bool active = c0 < xw;
+    const int xa = x0 + c0;
+    const bool pin = PRES && active && xa == 0;
+    const bool pout = PRES && active && xa == nx - 1;
+    const bool anyp = pin || pout;
+    // a pressure column sums and collides its interior neighbour's column
+    const int lcol = (pin ? 1 : (pout ? nx - 2 : xa)) - x0;
+    const int scol = lcol + 4;  // stage column
+    const int ccol = lcol + 2;  // ring column
+    const bool x_inner = !anyp && (PRES || (xa >= 1 && xa <= nx - 2));
+
+    // halo columns local -2, -1, xw, xw+1 on lanes 0..3 of warp 0. hmode 1:
+    // density of the column itself; 2 / 3: inlet / outlet column density
+    // derived from column 1 / nx-2 (clamp beyond the pressure columns).
+    int hmode = 0, hsc = 0, hcol = 0;
+    if (warp == 0 && lane < 4) {
+        const int hloc = (lane < 2) ? (lane - 2) : (xw + lane - 2);
+        hcol = hloc + 2;
+        const int gxh = x0 + hloc;
+        hmode = 1;
+        hsc = hloc + 4;
+        if (PRES) {
+            if (gxh <= 0) { hmode = 2; hsc = 1 - x0 + 4; }
+            else if (gxh >= nx - 1) { hmode = 3; hsc = nx - 2 - x0 + 4; }
+        }
+    }
+    // Laplacian of the two halo columns next to the strip (local -1, xw)
+    int lhalo = -1;
+    if (warp == NW - 1 && lane < 2) lhalo = lane == 0 ? 1 : xw + 2;
+
+    // stage copies: columns gx0 .. gx1-1 of each plane row, plus (periodic x)
+    // the four columns wrapped around from the other end of the row
+    const int gx0 = max(x0 - 4, 0);
+    const int gx1 = min(x0 + xw + 4, G.pitch);
+    const uint32_t mbytes = (uint32_t)((gx1 - gx0) * sizeof(float));
+    const bool wrapL = !PRES && x0 == 0, wrapR = !PRES && x0 + xw == nx;
+    const uint32_t row_bytes = 9u * (mbytes + (wrapL ? 16u : 0u) + (wrapR ? 16u : 0u));
+    const int dcol = gx0 - x0 + 4;
+    const int npairs = (yb - ya + 5) / 2;  // stencil rows ya-2 .. yb+1 in pairs
+    RingPos2 ring_issue = ring_next;
+    auto issue = [&](int q) {
+        if (q < npairs) {
+            if (tid == PRODUCER) {
+                const uint32_t st = ring_issue.s;
+                mbar_arrive_expect_tx(&bars[st], 2u * row_bytes);
+                float *slot = stages + (size_t)st * R2_SLOT;
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    bool mir;
+                    const float *src = G.fin + map_row<WALLS>(ya - 2 + 2 * q + t, ny, mir) * rstride;
+                    float *dst = slot + t * R2_ROW;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) bulk_copy_g2s(dst + i * R2_SP + dcol, src + i * P + gx0, mbytes, &bars[st]);
+                    if (wrapL) {
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) bulk_copy_g2s(dst + i * R2_SP, src + i * P + nx - 4, 16u, &bars[st]);
+                    }
+                    if (wrapR) {
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) bulk_copy_g2s(dst + i * R2_SP + xw + 4, src + i * P, 16u, &bars[st]);
+                    }
+                }
+            }
+            ring_issue.advance();
+        }
+    };
+
+    issue(0);
+    for (int k = 0; k < npairs; ++k) {
+        const int yy0 = ya - 2 + 2 * k;
+        const uint32_t cur = ring_next.s;
+        const uint32_t prev = cur == 0 ? R2_SLOTS - 1 : cur - 1;  // slot of pair k-1
+
+        // (1) density and phi of stencil rows yy0, yy0+1
+        if (!mbar_wait_bounded(&bars[cur], ring_next.ph)) lost = true;
+        {
+            const float *slot = stages + (size_t)cur * R2_SLOT;
+            bool m0, m1;
+            map_row<WALLS>(yy0, ny, m0);
+            map_row<WALLS>(yy0 + 1, ny, m1);
+            const V add = make_float2(m0 ? A.wet : 0.f, m1 ? A.wet : 0.f);  // mirrored wall ghosts
+            const int r0 = yy0 & RM, r1 = (yy0 + 1) & RM;
+            if (active) {
+                V pf[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) pf[i] = stage_pair(slot, i, scol);
+                V sum = add_(add_(add_(pf[0], pf[1]), add_(pf[2], pf[3])), add_(add_(pf[4], pf[5]), add_(pf[6], pf[7])));
+                sum = add_(sum, pf[8]);
+                if (anyp) {
+                    sum.x = column_density(A, G, pout, sum.x);
+                    sum.y = column_density(A, G, pout, sum.y);
+                }
+                const V rho_own = add_(sum, add);
+                const V ph = eos_phi<V>(A, rho_own);
+                S.rho[r0][c0 + 2] = rho_own.x; S.rho[r1][c0 + 2] = rho_own.y;
+                S.phi[r0][c0 + 2] = ph.x; S.phi[r1][c0 + 2] = ph.y;
+            }
+            if (hmode) {
+                V hf[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) hf[i] = stage_pair(slot, i, hsc);
+                V sum = add_(add_(add_(hf[0], hf[1]), add_(hf[2], hf[3])), add_(add_(hf[4], hf[5]), add_(hf[6], hf[7])));
+                sum = add_(sum, hf[8]);
+                if (hmode != 1) {
+                    sum.x = column_density(A, G, hmode == 3, sum.x);
+                    sum.y = column_density(A, G, hmode == 3, sum.y);
+                }
+                const V rho_h = add_(sum, add);
+                const V ph = eos_phi<V>(A, rho_h);
+                S.rho[r0][hcol] = rho_h.x; S.rho[r1][hcol] = rho_h.y;
+                S.phi[r0][hcol] = ph.x; S.phi[r1][hcol] = ph.y;
+            }
+        }
+        __syncthreads();  // A: density rows complete; the slot of pair k-2 is free
+
+        // (2) refill the slot of pair k-2 with pair k+1; Laplacian of rows yy0-1, yy0
+        if (tid == PRODUCER) fence_proxy_async_smem();
+        issue(k + 1);
+        if (k >= 1) {
+            const int qm = (yy0 - 2) & RM, q0 = (yy0 - 1) & RM, q1 = yy0 & RM, q2 = (yy0 + 1) & RM;
+            if (active) {
+                const V L = lap9<V>(row3p<SW>(S.rho, qm, q0, c0 + 2), row3p<SW>(S.rho, q0, q1, c0 + 2),
+                                    row3p<SW>(S.rho, q1, q2, c0 + 2));
+                S.lap[q0][c0 + 2] = L.x; S.lap[q1][c0 + 2] = L.y;
+            }
+            if (lhalo >= 0) {
+                const V L = lap9<V>(row3p<SW>(S.rho, qm, q0, lhalo), row3p<SW>(S.rho, q0, q1, lhalo),
+                                    row3p<SW>(S.rho, q1, q2, lhalo));
+                S.lap[q0][lhalo] = L.x; S.lap[q1][lhalo] = L.y;
+            }
+        }
+        __syncthreads();  // B: Laplacian rows complete
+
+        // (3) collide and stream rows b = yy0-2 and (if below yb) b+1
+        if (k >= 2 && active) {
+            const int b = yy0 - 2;
+            const bool second = b + 1 < yb;
+            const float *slot = stages + (size_t)prev * R2_SLOT;
+            V f[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = stage_pair(slot, i, scol);
+            const int qm = (b - 1) & RM, q0 = b & RM, q1 = (b + 1) & RM, q2 = (b + 2) & RM;
+            V ngpx, ngpy, glx, gly;
+            ngrad12<V>(row3p<SW>(S.phi, qm, q0, ccol), row3p<SW>(S.phi, q0, q1, ccol), row3p<SW>(S.phi, q1, q2, ccol),
+                       ngpx, ngpy);
+            grad12<V>(row3p<SW>(S.lap, qm, q0, ccol), row3p<SW>(S.lap, q0, q1, ccol), row3p<SW>(S.lap, q1, q2, ccol),
+                      glx, gly);
+            const V rho = make_float2(S.rho[q0][ccol], S.rho[q1][ccol]);
+            const V kr = mul_(bcr<V>(A.kappa), rho);
+            const V Fx = add_(mulk(fma_(kr, glx, ngpx), 1.0 / 12.0), bcr<V>(A.gx));
+            const V Fy = add_(mulk(fma_(kr, gly, ngpy), 1.0 / 12.0), bcr<V>(A.gy));
+            const V jx = add_(add_(sub_(f[1], f[3]), sub_(f[5], f[6])), sub_(f[8], f[7]));
+            const V jy = sub_(add_(sub_(f[2], f[4]), add_(f[5], f[6])), add_(f[7], f[8]));
+            const V irho = rcp_(rho);
+            const V ux = mul_(jx, irho), uy = mul_(jy, irho);
+            const V hFi = mul_(irho, bc<V>(0.5));
+            const V vx = fma_(hFi, Fx, ux), vy = fma_(hFi, Fy, uy);
+            // own-column density (a pressure column's own is rho_b)
+            const V rho_own = anyp ? make_float2(S.rho[q0][tid + 2], S.rho[q1][tid + 2]) : rho;
+
+            V fs[9];
+            {
+                // shifted equilibrium: momentum j + ushift F, velocity (j + ushift F) / rho
+                const V mx = fma_(bcr<V>(A.ushift), Fx, jx), my = fma_(bcr<V>(A.ushift), Fy, jy);
+                V fe[9];
+                feq_pairs<V>(rho, mul_(mx, irho), mul_(my, irho), mx, my, fe);
+                if (A.mrt) {
+                    mrt_relax<V, float>(A, f, fe, fs);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) fs[i] = fma_(sub_(fe[i], f[i]), bcr<V>(A.inv_tau), f[i]);
+                }
+            }
+            if (anyp) {
+                // pressure column: extrapolate from the interior neighbour, row by row
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    float ff[9], fsc[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) ff[i] = el(f[i], e);
+                    const float mvx = fma_(0.5f, el(Fx, e), el(jx, e));
+                    const float mvy = fma_(0.5f, el(Fy, e), el(jy, e));
+                    column_extrapolate<float>(A, el(rho_own, e), el(rho, e), el(vx, e), el(vy, e), mvx, mvy, ff, fsc);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) set_el(fs[i], e, fsc[i]);
+                }
+            }
+            float *const out = G.fout;
+            const int oi = b * rstride + xa;  // slot of (xa, b) in plane 0
+            const bool y_inner = WALLS ? (b >= 2 && b + 1 <= ny - 3) : (b >= 1 && b + 1 <= ny - 2);
+            if (x_inner && y_inner && second) {
+                const int oj = oi + rstride;
+                out[oi] = fs[0].x;      out[oj] = fs[0].y;
+                out[oi + o1] = fs[1].x; out[oj + o1] = fs[1].y;
+                out[oi + o2] = fs[2].x; out[oj + o2] = fs[2].y;
+                out[oi + o3] = fs[3].x; out[oj + o3] = fs[3].y;
+                out[oi + o4] = fs[4].x; out[oj + o4] = fs[4].y;
+                out[oi + o5] = fs[5].x; out[oj + o5] = fs[5].y;
+                out[oi + o6] = fs[6].x; out[oj + o6] = fs[6].y;
+                out[oi + o7] = fs[7].x; out[oj + o7] = fs[7].y;
+                out[oi + o8] = fs[8].x; out[oj + o8] = fs[8].y;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    if (e == 1 && !second) break;
+                    const int r = b + e, ok = oi + e * rstride;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const int ty = r + ey_(i);
+                        if (WALLS && (ty == 0 || ty == ny - 1)) {
+                            // half-way bounce-back into the opposite slot of this node
+                            out[ok + opp_(i) * P] = el(fs[i], e);
+                        } else {
+                            int tx = xa + ex_(i);
+                            if (PRES) {
+                                if (tx < 0 || tx >= nx) continue;  // leaves through the column
+                            } else {
+                                tx = tx < 0 ? tx + nx : (tx >= nx ? tx - nx : tx);
+                            }
+                            int tyw = ty;
+                            if (!WALLS) tyw = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
+                            out[tyw * rstride + i * P + tx] = el(fs[i], e);
+                        }
+                    }
+                }
+            }
+            // diagnostics of the state read, row by row in the one-row kernel's
+            // order (its flush follows collided row r when (r - ya + 5) % 16 == 15)
+            acc.macc = add_(acc.macc, rho_own.x);
+            acc.rmin = vmin_(acc.rmin, rho.x);
+            acc.rmax = vmax_(acc.rmax, rho.x);
+            if (((b - ya + 5) & 15) == 15) acc.flush();
+            if (second) {
+                acc.macc = add_(acc.macc, rho_own.y);
+                acc.rmin = vmin_(acc.rmin, rho.y);
+                acc.rmax = vmax_(acc.rmax, rho.y);
+                if (((b + 1 - ya + 5) & 15) == 15) acc.flush();
+            }
+
+            if (WALLS && !anyp && (b <= 2 || b + 1 >= ny - 3)) {
+                // wall shear: quadratic through v = 0 on the half-way plane and
+                // v at distances 1/2 and 3/2; wall pressure: Eq. 2.4 in mesh units
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    if (e == 1 && !second) break;
+                    const int r = b + e;
+                    const float rk = el(rho, e), vk = el(vx, e);
+                    const int pm = (r - 1) & RM, pz = r & RM, pp = (r + 1) & RM;
+                    if (r == 1) {
+                        b_rho1 = rk;
+                        b_v1 = vk;
+                        const float pw = wall_pressure<float, SW>(A, S.rho, S.phi, S.lap[pz][ccol], pm, pz, pp, ccol, rk);
+                        acc.pmin = fmin(acc.pmin, pw); acc.pmax = fmax(acc.pmax, pw);
+                    }
+                    if (r == ny - 3) t_v2 = vk;
+                    if (r == 2) {
+                        const float tw = mul_(mul_(b_rho1, A.nu), mul_(fma_(9.0f, b_v1, -vk), third));
+                        acc.J += (double)tw; acc.tmin = fmin(acc.tmin, tw); acc.tmax = fmax(acc.tmax, tw);
+                    }
+                    if (r == ny - 2) {
+                        const float tw = mul_(mul_(rk, A.nu), mul_(fma_(9.0f, vk, -t_v2), third));
+                        const float pw = wall_pressure<float, SW>(A, S.rho, S.phi, S.lap[pz][ccol], pm, pz, pp, ccol, rk);
+                        acc.J += (double)tw;
+                        acc.tmin = fmin(acc.tmin, tw); acc.tmax = fmax(acc.tmax, tw);
+                        acc.pmin = fmin(acc.pmin, pw); acc.pmax = fmax(acc.pmax, pw);
+                    }
+                }
+            }
+        }
+        ring_next.advance();
+    }
+    __syncthreads();  // ring and stage reuse by the next segment
+}
+
+// The row-pair step kernel (FP32, staged, MODE_STEP); launched like
+// step_kernel with rows2_smem_bytes() of dynamic shared memory.
+#ifndef LBM_R2_MIN_BLOCKS
+#define LBM_R2_MIN_BLOCKS 5
+#endif
+template <bool WALLS, bool PRES, bool PADDED>
+__global__ void __launch_bounds__(STRIP, LBM_R2_MIN_BLOCKS) step_kernel_rows2(const KArgs<float> A)
+{
+    extern __shared__ __align__(128) unsigned char dsm[];
+    float *const stages = reinterpret_cast<float *>(dsm);
+    uint64_t *const bars = reinterpret_cast<uint64_t *>(dsm + (size_t)R2_SLOTS * R2_SLOT * sizeof(float));
+    __shared__ Smem<float, STRIP> S;
+
+    const int tid = threadIdx.x;
+    const int cta = A.reverse ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+    long long u = cut_units<WALLS>(A, cta);
+    const long long u1 = cut_units<WALLS>(A, cta + 1);
+    const Geom<float> G{A.fin, A.fout, A.nx, A.ny, A.W, A.pitch, A.rho_in_g, A.rho_in_l, A.rho_out_g, A.rho_out_l};
+
+    Acc<float, 1> acc;
+    acc.reset();
+    RingPos2 ring_next;
+    bool lost = false;  // a bounded wait gave up
+    if (tid == 0) {
+        for (int st = 0; st < R2_SLOTS; ++st) mbar_init(&bars[st], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+
+    while (u < u1) {
+        int s, ya;
+        long long run_end;
+        unit_run(A, u, s, ya, run_end);
+        const long long ue = min(u1, run_end);
+        const int yb = ya + (int)(ue - u);
+        u = ue;
+        run_segment_r2<WALLS, PRES, PADDED>(A, G, s, ya, yb, S, stages, bars, ring_next, acc, lost);
+    }
+    if (lost) atomicOr(A.err, 2);
+
+    double m, j;
+    float e[4];
+    bool anybad;
+    cta_reduce<float, STRIP, 1>(acc, S, m, j, e, anybad);
+    if (tid == 0) {
+        A.mass_part[cta] = m;
+        A.J_acc[cta] += j;
+        float *ex = A.ext + 4 * cta;
+        ex[0] = fmin(ex[0], e[0]); ex[1] = fmax(ex[1], e[1]);
+        ex[2] = fmin(ex[2], e[2]); ex[3] = fmax(ex[3], e[3]);
+        if (anybad) atomicOr(A.err, 1);
+    }
+}
+}  // namespace lbm
