@@ -39,8 +39,8 @@ BYTES_PER_NODE = {32: 72, 64: 144}  # 9 populations read + 9 written
 METRIC = "MLUPS and % of HBM roofline (FP32 D2Q9 EOS step, 1xGB300) vs FP64 CPU oracle"
 WORKLOAD = "airway channel 16384x2048, FP32, CS EOS T=0.85Tc, dp=1e-3 (roofline stress)"
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SRC = os.path.join(ROOT, "paper_2103_08301_gb300", "csrc", "lbm_kernels.cuh")
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_fp32_16384x2048.md")
+KERNEL_SRC = [os.path.join(ROOT, "paper_2103_08301_gb300", "csrc", f) for f in ("lbm_kernels.cuh", "lbm_rows2.cuh")]
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_rows2_fp32_16384x2048.md")
 
 
 def _dist_env():
@@ -65,7 +65,10 @@ def _hbm_peak():
 
 def _kernel_hash():
     import hashlib
-    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in KERNEL_SRC:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
 
 
 def _profiled_traffic():
