@@ -58,6 +58,7 @@ struct lbm_batch {
     // launch plan and device tables
     int sms = 0, nctas = 0, nseg = 0, ctas_per_sm_opt = 0, W_opt = 0, reverse = 0;
     bool allow_staged = true, staged = false;
+    bool allow_rows2 = true, rows2 = false;  // LBM_OPT_ROWS2: row-pair FP32 step
     void *d_chan = nullptr;
     lbm::BatchSeg *d_segs = nullptr;
     int *d_cta_begin = nullptr;
@@ -107,6 +108,13 @@ void *batch_kernel_ptr(bool walls, bool pres)
 void *batch_kernel(const lbm_batch *b)
 {
     const bool w = b->walls, p = b->bc_x;
+    if (b->rows2) {
+        using namespace lbm;
+        if (w && p) return (void *)batch_step_kernel_rows2<true, true>;
+        if (w) return (void *)batch_step_kernel_rows2<true, false>;
+        if (p) return (void *)batch_step_kernel_rows2<false, true>;
+        return (void *)batch_step_kernel_rows2<false, false>;
+    }
     if (b->precision == 64)
         return b->staged ? batch_kernel_ptr<double, true>(w, p) : batch_kernel_ptr<double, false>(w, p);
     return b->staged ? batch_kernel_ptr<float, true>(w, p) : batch_kernel_ptr<float, false>(w, p);
@@ -117,6 +125,10 @@ size_t staged_bytes(const lbm_batch *b, bool staged)
     if (!staged) return 0;
     return b->precision == 64 ? lbm::staged_smem_bytes<double>() : lbm::staged_smem_bytes<float>();
 }
+
+// dynamic shared memory and threads of the batch step kernel
+size_t step_smem(const lbm_batch *b) { return b->rows2 ? lbm::rows2_smem_bytes() : staged_bytes(b, b->staged); }
+int step_threads(const lbm_batch *b) { return b->rows2 ? lbm::STRIP : cta_threads(b->precision, b->staged); }
 
 // Shared physics of every channel, in the kernel argument block.
 template <typename real>
@@ -158,7 +170,7 @@ lbm::KArgs<real> physics_args(const lbm_batch *b)
 lbm_status batch_plan(lbm_batch *b)
 {
     long long U = 0;
-    bool all4 = true;
+    bool all4 = true, rows2 = b->allow_rows2;
     for (auto &c : b->ch) {
         const int nx = c.grid.nx;
         const int W = lbm::strip_width(nx, std::min(b->W_opt > 0 ? b->W_opt : STRIP, STRIP), b->bc_x);
@@ -170,16 +182,17 @@ lbm_status batch_plan(lbm_batch *b)
         c.unit_base = U;
         U += c.units;
         all4 = all4 && (c.pitch % 4 == 0) && (W % 4 == 0);
+        rows2 = rows2 && (b->bc_x || nx % 4 == 0);  // wrapped halo columns need nx % 4 == 0
     }
     b->staged = b->allow_staged && all4;
-    const size_t smem = staged_bytes(b, b->staged);
+    b->rows2 = rows2 && b->staged && b->precision == 32 && lbm::cols_per_thread<float, true>() == 1;
+    const size_t smem = step_smem(b);
     cudaError_t e = cudaFuncSetAttribute(batch_kernel(b), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return bfail(b, e, "smem attribute");
     int per_sm = b->ctas_per_sm_opt;
     if (per_sm <= 0) {
         int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(b), cta_threads(b->precision, b->staged),
-                                                          smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(b), step_threads(b), smem);
         if (e != cudaSuccess) return bfail(b, e, "occupancy");
         per_sm = std::max(1, occ);
     }
@@ -265,9 +278,7 @@ cudaError_t batch_launch(lbm_batch *b)
     real *ext = static_cast<real *>(b->d_seg_ext);
     void *args[] = {(void *)&A, (void *)&chans, (void *)&b->d_segs, (void *)&b->d_cta_begin,
                     (void *)&b->d_seg_mass, (void *)&b->d_seg_J, (void *)&ext};
-    return cudaLaunchKernel(batch_kernel(b), dim3(b->nctas), dim3(cta_threads(b->precision, b->staged)), args,
-                            staged_bytes(b, b->staged),
-                            b->stream);
+    return cudaLaunchKernel(batch_kernel(b), dim3(b->nctas), dim3(step_threads(b)), args, step_smem(b), b->stream);
 }
 
 cudaError_t one_step(lbm_batch *b)
@@ -598,6 +609,9 @@ lbm_status lbm_batch_set_option(lbm_batch *b, lbm_option opt, int64_t value)
         break;
     case LBM_OPT_STAGED:
         b->allow_staged = value != 0;
+        break;
+    case LBM_OPT_ROWS2:
+        b->allow_rows2 = value != 0;
         break;
     case LBM_OPT_GRAPH_STEPS:
         if (value < 0 || (value & 1)) return LBM_ERR_ARG;

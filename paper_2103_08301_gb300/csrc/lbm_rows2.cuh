@@ -417,4 +417,52 @@ __global__ void __launch_bounds__(STRIP, LBM_R2_MIN_BLOCKS) step_kernel_rows2(co
         if (anybad) atomicOr(A.err, 1);
     }
 }
+
+// Batched channels with the row-pair step: as batch_step_kernel, every
+// segment of the work list through run_segment_r2 (padded-pitch body, since
+// the channels of a batch mix pitches), one reduction slot per segment.
+template <bool WALLS, bool PRES>
+__global__ void __launch_bounds__(STRIP, LBM_R2_MIN_BLOCKS)
+    batch_step_kernel_rows2(const KArgs<float> A, const BatchChan<float> *__restrict__ chans,
+                            const BatchSeg *__restrict__ segs, const int *__restrict__ cta_begin,
+                            double *__restrict__ seg_mass, double *__restrict__ seg_J, float *__restrict__ seg_ext)
+{
+    extern __shared__ __align__(128) unsigned char dsm[];
+    float *const stages = reinterpret_cast<float *>(dsm);
+    uint64_t *const bars = reinterpret_cast<uint64_t *>(dsm + (size_t)R2_SLOTS * R2_SLOT * sizeof(float));
+    __shared__ Smem<float, STRIP> S;
+
+    const int tid = threadIdx.x;
+    const int cta = A.reverse ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+    RingPos2 ring_next;
+    bool lost = false;
+    if (tid == 0) {
+        for (int st = 0; st < R2_SLOTS; ++st) mbar_init(&bars[st], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    for (int k = cta_begin[cta]; k < cta_begin[cta + 1]; ++k) {
+        const BatchSeg sg = segs[k];
+        const BatchChan<float> ch = chans[sg.chan];
+        const Geom<float> G{A.fin + ch.off, A.fout + ch.off, ch.nx, ch.ny, ch.W, ch.pitch,
+                            ch.rho_in_g, ch.rho_in_l, ch.rho_out_g, ch.rho_out_l};
+        Acc<float, 1> acc;
+        acc.reset();
+        run_segment_r2<WALLS, PRES, true>(A, G, sg.strip, sg.ya, sg.yb, S, stages, bars, ring_next, acc, lost);
+        double m, j;
+        float e[4];
+        bool anybad;
+        cta_reduce<float, STRIP, 1>(acc, S, m, j, e, anybad);
+        if (tid == 0) {
+            seg_mass[k] = m;
+            seg_J[k] += j;
+            float *ex = seg_ext + 4 * (long long)k;
+            ex[0] = fmin(ex[0], e[0]); ex[1] = fmax(ex[1], e[1]);
+            ex[2] = fmin(ex[2], e[2]); ex[3] = fmax(ex[3], e[3]);
+            if (anybad) atomicOr(A.err, 1);
+        }
+    }
+    if (lost) atomicOr(A.err, 2);
+}
+
 }  // namespace lbm
