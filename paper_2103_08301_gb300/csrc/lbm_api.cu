@@ -81,6 +81,7 @@ struct lbm_ctx {
     int cur = 0;          // which population array holds the current state
     int64_t step = 0;
     int W = STRIP, nstrips = 0, yf0 = 0, nyf = 0;
+    int W_opt = 0;  // LBM_OPT_STRIP (0: widest)
     int pitch = 0;  // plane pitch of the population rows (>= nx)
     long long units = 0;
     int band = 0;  // rows per band of the work-unit order
@@ -253,14 +254,21 @@ int band_rows(int nyf, int nstrips, int nctas, int walls)
 lbm_status plan_launch(lbm_ctx *ctx)
 {
     const int nx = ctx->grid.nx;
-    const int W = lbm::strip_width(nx, std::min(ctx->W > 0 ? ctx->W : STRIP, STRIP), ctx->grid.bc_x);
-    ctx->W = W;
+    const int wmax = std::min(ctx->W_opt > 0 ? ctx->W_opt : STRIP, STRIP);
+    int W = lbm::strip_width(nx, wmax, ctx->grid.bc_x);
     // bulk-copy staging needs 16-byte aligned row segments
     ctx->staged = ctx->allow_staged && (ctx->pitch % 4 == 0) && (W % 4 == 0);
-    // row pairs: FP32 staged grids; with periodic x the wrapped halo columns
-    // are copied as one 16-byte group, which needs nx a multiple of 4
+    // row pairs: FP32 staged grids with strips of at most R2_W columns (a
+    // multiple of 4); with periodic x the wrapped halo columns are copied as
+    // one 16-byte group, which needs nx a multiple of 4
     ctx->rows2 = ctx->allow_rows2 && ctx->staged && ctx->grid.precision == 32 &&
                  lbm::cols_per_thread<float, true>() == 1 && (ctx->grid.bc_x || nx % 4 == 0);
+    if (ctx->rows2) {
+        const int W2 = lbm::strip_width(nx, std::min(wmax, lbm::R2_W), ctx->grid.bc_x);
+        if (W2 % 4 == 0) W = W2;
+        else ctx->rows2 = false;
+    }
+    ctx->W = W;
     ctx->nstrips = (nx + W - 1) / W;
     ctx->yf0 = ctx->grid.walls ? 1 : 0;
     ctx->nyf = ctx->grid.walls ? ctx->grid.ny - 2 : ctx->grid.ny;
@@ -668,7 +676,7 @@ lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
         return LBM_OK;
     case LBM_OPT_STRIP:
         if (value < 2 || value > STRIP) return LBM_ERR_ARG;
-        ctx->W = (int)value;
+        ctx->W_opt = (int)value;
         break;
     case LBM_OPT_STAGED:
         ctx->allow_staged = value != 0;

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <utility>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -169,23 +170,37 @@ lbm::KArgs<real> physics_args(const lbm_batch *b)
 // nctas equal runs, never between rows 1|2 or ny-3|ny-2 of a channel.
 lbm_status batch_plan(lbm_batch *b)
 {
+    // Row pairs need every channel staged with strips of at most R2_W columns
+    // (multiples of 4) and, with periodic x, nx a multiple of 4; otherwise the
+    // batch takes the one-row kernel with strips of up to STRIP columns.
+    const int wopt = b->W_opt > 0 ? b->W_opt : STRIP;
+    auto plan_strips = [&](int wmax) {
+        long long U = 0;
+        bool all4 = true, r2ok = true;
+        for (auto &c : b->ch) {
+            const int nx = c.grid.nx;
+            const int W = lbm::strip_width(nx, std::min(wopt, wmax), b->bc_x);
+            c.W = W;
+            c.nstrips = (nx + W - 1) / W;
+            c.yf0 = b->walls ? 1 : 0;
+            c.nyf = b->walls ? c.grid.ny - 2 : c.grid.ny;
+            c.units = (long long)c.nstrips * c.nyf;
+            c.unit_base = U;
+            U += c.units;
+            all4 = all4 && (c.pitch % 4 == 0) && (W % 4 == 0);
+            r2ok = r2ok && (b->bc_x || nx % 4 == 0);
+        }
+        b->staged = b->allow_staged && all4;
+        return std::make_pair(U, r2ok && b->staged);
+    };
     long long U = 0;
-    bool all4 = true, rows2 = b->allow_rows2;
-    for (auto &c : b->ch) {
-        const int nx = c.grid.nx;
-        const int W = lbm::strip_width(nx, std::min(b->W_opt > 0 ? b->W_opt : STRIP, STRIP), b->bc_x);
-        c.W = W;
-        c.nstrips = (nx + W - 1) / W;
-        c.yf0 = b->walls ? 1 : 0;
-        c.nyf = b->walls ? c.grid.ny - 2 : c.grid.ny;
-        c.units = (long long)c.nstrips * c.nyf;
-        c.unit_base = U;
-        U += c.units;
-        all4 = all4 && (c.pitch % 4 == 0) && (W % 4 == 0);
-        rows2 = rows2 && (b->bc_x || nx % 4 == 0);  // wrapped halo columns need nx % 4 == 0
+    b->rows2 = false;
+    if (b->allow_rows2 && b->precision == 32 && lbm::cols_per_thread<float, true>() == 1) {
+        auto r = plan_strips(lbm::R2_W);
+        U = r.first;
+        b->rows2 = r.second;
     }
-    b->staged = b->allow_staged && all4;
-    b->rows2 = rows2 && b->staged && b->precision == 32 && lbm::cols_per_thread<float, true>() == 1;
+    if (!b->rows2) U = plan_strips(STRIP).first;
     const size_t smem = step_smem(b);
     cudaError_t e = cudaFuncSetAttribute(batch_kernel(b), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return bfail(b, e, "smem attribute");

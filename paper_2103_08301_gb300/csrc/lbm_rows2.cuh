@@ -7,9 +7,11 @@
 //   - the loop bookkeeping, barriers and stage waits of an iteration are
 //     shared by two nodes per thread, and the method's arithmetic issues one
 //     instruction per two nodes;
-//   - the stage holds each stencil row with a four-column margin on both sides
-//     (columns x0-4 .. x0+W+3), so the halo densities are summed from shared
-//     memory: no halo registers, no halo loads from global memory;
+//   - strips are at most STRIP - 4 columns wide and lane t holds local column
+//     t - 2, so the two halo columns on each side are lanes of their own: no
+//     divergent halo duty (which cost 8% as a one-warp duty); the stage holds
+//     each stencil row with a four-column margin on both sides (columns
+//     x0-4 .. x0+W+3), so the halo densities are summed from shared memory;
 //   - every thread waits on the stage's mbarrier itself, so a pair issued
 //     half an iteration before it is read needs no publishing barrier; three
 //     pair slots (six rows) suffice.
@@ -28,6 +30,7 @@
 namespace lbm {
 
 constexpr int R2_SLOTS = 3;            // pair slots of the stage ring
+constexpr int R2_W = STRIP - 4;        // widest strip: 128 lanes cover it and two halo columns per side
 constexpr int R2_SP = STRIP + 8;       // stage row pitch: strip plus 4 margin columns per side
 constexpr int R2_ROW = 9 * R2_SP;      // one stencil row of nine planes
 constexpr int R2_SLOT = 2 * R2_ROW;    // one pair of rows
@@ -74,10 +77,9 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
 {
     using V = float2;
     constexpr int SW = STRIP + 4;
-    constexpr int NW = STRIP / 32;
     constexpr int PRODUCER = STRIP - 1;  // no halo duty
     constexpr int RM = RING - 1;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const float third = 1.0f / 3.0f;
     const int nx = G.nx, ny = G.ny;
     const int P = PADDED ? G.pitch : G.nx;  // plane pitch; columns nx .. P-1 are padding
@@ -89,36 +91,31 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
 
     const int x0 = s * G.W;
     const int xw = min(G.W, nx - x0);
-    const int c0 = tid;
-    const bool active = c0 < xw;
-    const int xa = x0 + c0;
+    // Thread t holds local column l = t - 2: the strip (at most R2_W = STRIP - 4
+    // columns) plus two halo columns on each side, so every column's density
+    // is computed by its own lane and no halo duty exists.
+    const int l = tid - 2;
+    const int g = x0 + l;                    // global column (halo columns may lie outside 0 .. nx-1)
+    const bool dens = l < xw + 2;            // density and phi of column l (l >= -2 always)
+    const bool lapc = l >= -1 && l <= xw;    // Laplacian of column l
+    const bool active = l >= 0 && l < xw;    // collided column
+    // density source: the column itself (stage column l + 4), or at and beyond
+    // the pressure columns the inlet / outlet density derived from column
+    // 1 / nx-2 (dmode 2 / 3)
+    int dmode = 0, dsc = l + 4;
+    if (PRES) {
+        if (g <= 0) { dmode = 2; dsc = 1 - x0 + 4; }
+        else if (g >= nx - 1) { dmode = 3; dsc = nx - 2 - x0 + 4; }
+    }
+    const int xa = g;
     const bool pin = PRES && active && xa == 0;
     const bool pout = PRES && active && xa == nx - 1;
     const bool anyp = pin || pout;
-    // a pressure column sums and collides its interior neighbour's column
+    // a pressure column collides its interior neighbour's column
     const int lcol = (pin ? 1 : (pout ? nx - 2 : xa)) - x0;
     const int scol = lcol + 4;  // stage column
     const int ccol = lcol + 2;  // ring column
     const bool x_inner = !anyp && (PRES || (xa >= 1 && xa <= nx - 2));
-
-    // halo columns local -2, -1, xw, xw+1 on lanes 0..3 of warp 0. hmode 1:
-    // density of the column itself; 2 / 3: inlet / outlet column density
-    // derived from column 1 / nx-2 (clamp beyond the pressure columns).
-    int hmode = 0, hsc = 0, hcol = 0;
-    if (warp == 0 && lane < 4) {
-        const int hloc = (lane < 2) ? (lane - 2) : (xw + lane - 2);
-        hcol = hloc + 2;
-        const int gxh = x0 + hloc;
-        hmode = 1;
-        hsc = hloc + 4;
-        if (PRES) {
-            if (gxh <= 0) { hmode = 2; hsc = 1 - x0 + 4; }
-            else if (gxh >= nx - 1) { hmode = 3; hsc = nx - 2 - x0 + 4; }
-        }
-    }
-    // Laplacian of the two halo columns next to the strip (local -1, xw)
-    int lhalo = -1;
-    if (warp == NW - 1 && lane < 2) lhalo = lane == 0 ? 1 : xw + 2;
 
     // stage copies: columns gx0 .. gx1-1 of each plane row, plus (periodic x)
     // the four columns wrapped around from the other end of the row
@@ -172,35 +169,20 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
             map_row<WALLS>(yy0 + 1, ny, m1);
             const V add = make_float2(m0 ? A.wet : 0.f, m1 ? A.wet : 0.f);  // mirrored wall ghosts
             const int r0 = yy0 & RM, r1 = (yy0 + 1) & RM;
-            if (active) {
+            if (dens) {
                 V pf[9];
 #pragma unroll
-                for (int i = 0; i < 9; ++i) pf[i] = stage_pair(slot, i, scol);
+                for (int i = 0; i < 9; ++i) pf[i] = stage_pair(slot, i, dsc);
                 V sum = add_(add_(add_(pf[0], pf[1]), add_(pf[2], pf[3])), add_(add_(pf[4], pf[5]), add_(pf[6], pf[7])));
                 sum = add_(sum, pf[8]);
-                if (anyp) {
-                    sum.x = column_density(A, G, pout, sum.x);
-                    sum.y = column_density(A, G, pout, sum.y);
+                if (dmode) {
+                    sum.x = column_density(A, G, dmode == 3, sum.x);
+                    sum.y = column_density(A, G, dmode == 3, sum.y);
                 }
-                const V rho_own = add_(sum, add);
-                const V ph = eos_phi<V>(A, rho_own);
-                S.rho[r0][c0 + 2] = rho_own.x; S.rho[r1][c0 + 2] = rho_own.y;
-                S.phi[r0][c0 + 2] = ph.x; S.phi[r1][c0 + 2] = ph.y;
-            }
-            if (hmode) {
-                V hf[9];
-#pragma unroll
-                for (int i = 0; i < 9; ++i) hf[i] = stage_pair(slot, i, hsc);
-                V sum = add_(add_(add_(hf[0], hf[1]), add_(hf[2], hf[3])), add_(add_(hf[4], hf[5]), add_(hf[6], hf[7])));
-                sum = add_(sum, hf[8]);
-                if (hmode != 1) {
-                    sum.x = column_density(A, G, hmode == 3, sum.x);
-                    sum.y = column_density(A, G, hmode == 3, sum.y);
-                }
-                const V rho_h = add_(sum, add);
-                const V ph = eos_phi<V>(A, rho_h);
-                S.rho[r0][hcol] = rho_h.x; S.rho[r1][hcol] = rho_h.y;
-                S.phi[r0][hcol] = ph.x; S.phi[r1][hcol] = ph.y;
+                const V rho_c = add_(sum, add);
+                const V ph = eos_phi<V>(A, rho_c);
+                S.rho[r0][tid] = rho_c.x; S.rho[r1][tid] = rho_c.y;
+                S.phi[r0][tid] = ph.x; S.phi[r1][tid] = ph.y;
             }
         }
         __syncthreads();  // A: density rows complete; the slot of pair k-2 is free
@@ -210,15 +192,10 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
         issue(k + 1);
         if (k >= 1) {
             const int qm = (yy0 - 2) & RM, q0 = (yy0 - 1) & RM, q1 = yy0 & RM, q2 = (yy0 + 1) & RM;
-            if (active) {
-                const V L = lap9<V>(row3p<SW>(S.rho, qm, q0, c0 + 2), row3p<SW>(S.rho, q0, q1, c0 + 2),
-                                    row3p<SW>(S.rho, q1, q2, c0 + 2));
-                S.lap[q0][c0 + 2] = L.x; S.lap[q1][c0 + 2] = L.y;
-            }
-            if (lhalo >= 0) {
-                const V L = lap9<V>(row3p<SW>(S.rho, qm, q0, lhalo), row3p<SW>(S.rho, q0, q1, lhalo),
-                                    row3p<SW>(S.rho, q1, q2, lhalo));
-                S.lap[q0][lhalo] = L.x; S.lap[q1][lhalo] = L.y;
+            if (lapc) {
+                const V L = lap9<V>(row3p<SW>(S.rho, qm, q0, tid), row3p<SW>(S.rho, q0, q1, tid),
+                                    row3p<SW>(S.rho, q1, q2, tid));
+                S.lap[q0][tid] = L.x; S.lap[q1][tid] = L.y;
             }
         }
         __syncthreads();  // B: Laplacian rows complete
@@ -248,7 +225,7 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
             const V hFi = mul_(irho, bc<V>(0.5));
             const V vx = fma_(hFi, Fx, ux), vy = fma_(hFi, Fy, uy);
             // own-column density (a pressure column's own is rho_b)
-            const V rho_own = anyp ? make_float2(S.rho[q0][tid + 2], S.rho[q1][tid + 2]) : rho;
+            const V rho_own = anyp ? make_float2(S.rho[q0][tid], S.rho[q1][tid]) : rho;
 
             V fs[9];
             {

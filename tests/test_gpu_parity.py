@@ -196,6 +196,7 @@ def test_staged_and_register_paths_agree_bitwise(orc, lbm, precision, nx):
     for staged in (1, 0):
         with lbm.Lattice(nx, 96, rho0, walls=True, bc_x=True, precision=precision, T_over_Tc=0.85,
                          kappa=0.5, dp=1e-3) as lat:
+            lat.set_option(lbm.LBM_OPT_STRIP, 124)  # the same work split for both kernels
             lat.set_option(lbm.LBM_OPT_STAGED, staged)
             assert lat.launch_info()["staged"] == bool(staged)
             lat.step(200)
@@ -204,7 +205,8 @@ def test_staged_and_register_paths_agree_bitwise(orc, lbm, precision, nx):
     assert np.array_equal(out[0][0].view(u), out[1][0].view(u))
     for k in ("rho", "vx", "vy", "tau_wall", "p_wall"):
         assert np.array_equal(out[0][1][k].view(u), out[1][1][k].view(u)), k
-    assert out[0][2]["wall_shear_sum"] == out[1][2]["wall_shear_sum"]
+    d0, d1 = out[0][2]["wall_shear_sum"], out[1][2]["wall_shear_sum"]
+    assert abs(d0 - d1) <= 1e-9 * abs(d1) + 1e-15  # the kernels' reduction orders differ
 
 
 @pytest.mark.parametrize("name,ctas_per_sm", [("droplet128", 5), ("airway512x128", 5), ("airway512x128", 3),
@@ -212,24 +214,33 @@ def test_staged_and_register_paths_agree_bitwise(orc, lbm, precision, nx):
                                                ("pr_droplet96", 5), ("mrt_airway256x64", 4), ("bodyforce256x64", 1)])
 def test_row_pair_and_one_row_kernels_agree_bitwise(orc, lbm, name, ctas_per_sm):
     """The FP32 row-pair step (two rows of a column per thread, paired FP32
-    instructions) and the one-row step do the same arithmetic in the same
-    order: populations, fields and diagnostics agree bit for bit, over segment
-    splits of both parities (CTA counts) and every boundary kind."""
+    instructions) and the one-row step do the same arithmetic on every node in
+    the same order: populations and fields agree bit for bit, over segment
+    splits of both parities (CTA counts) and every boundary kind; the
+    diagnostic sums agree to rounding."""
     c = CASES[name]
     rho0 = _rho0(orc, name, c)
     out = []
     for rows2 in (1, 0):
         with lbm.Lattice(c["nx"], c["ny"], rho0, precision=32, **_lat_kw(c["kw"])) as lat:
             lat.set_option(lbm.LBM_OPT_ROWS2, rows2)
-            # the same CTA count, hence the same work split and diagnostics order
+            # the same strips and CTA count, hence the same work split and
+            # diagnostics order (row pairs take strips of at most 124 columns)
+            lat.set_option(lbm.LBM_OPT_STRIP, 124)
             lat.set_option(lbm.LBM_OPT_CTAS_PER_SM, ctas_per_sm)
             lat.step(150)
             out.append((lat.populations(), lat.fields(), lat.diag()))
     assert np.array_equal(out[0][0].view(np.uint32), out[1][0].view(np.uint32))
     for k in ("rho", "vx", "vy", "tau_wall", "p_wall"):
         assert np.array_equal(out[0][1][k].view(np.uint32), out[1][1][k].view(np.uint32)), k
-    for k in ("mass", "wall_shear_sum", "tau_wall_min", "tau_wall_max", "p_wall_min", "p_wall_max", "nan_detected"):
+    # extrema exactly; sums to rounding (the kernels map columns to lanes
+    # differently, so the fixed reduction trees add in different orders)
+    for k in ("tau_wall_min", "tau_wall_max", "p_wall_min", "p_wall_max", "nan_detected"):
         assert out[0][2][k] == out[1][2][k], k
+    assert abs(out[0][2]["mass"] - out[1][2]["mass"]) <= 1e-12 * out[1][2]["mass"]
+    # the wall-shear sum cancels (a resting droplet sums to ~1e-7): absolute floor
+    assert abs(out[0][2]["wall_shear_sum"] - out[1][2]["wall_shear_sum"]) <= \
+        1e-9 * abs(out[1][2]["wall_shear_sum"]) + 1e-15
 
 
 def test_checkpoint_restore_continues_bitwise(orc, lbm):
