@@ -14,11 +14,12 @@
 //     converts); a step reads buffer A and pushes post-collision values into
 //     buffer B; all indices are 32-bit (9 nx ny < 2^31);
 //   - each CTA owns a strip of up to STRIP = 128 columns and marches along y
-//     over a contiguous range of rows; each thread owns one column, or (FP32
-//     staged kernel) a pair of adjacent columns computed with the paired
-//     FP32 instructions; population rows are streamed into a shared-memory
-//     stage ring by bulk asynchronous copies (or, unstaged, prefetched into
-//     registers one row ahead);
+//     over a contiguous range of rows; in this file each thread owns one
+//     column (or, built with LBM_FP32_PAIR=2, a pair of adjacent columns) and
+//     one row per iteration; the default FP32 staged step, in lbm_rows2.cuh,
+//     gives each thread two rows per iteration; population rows are streamed
+//     into a shared-memory stage ring by bulk asynchronous copies (or,
+//     unstaged, prefetched into registers one row ahead);
 //   - rho, phi = k^2 p0(rho) - rho/3 and lap(rho) of the rows in flight sit
 //     in an 8-row shared-memory ring that covers the strip plus two halo
 //     columns per side; the halo densities are summed from the neighbouring
