@@ -43,6 +43,7 @@ __device__ __forceinline__ double wq(int i) { return lbm::w_<double>(i); }
 
 struct AdjGeo {
     int nx, ny, walls, bc_x;
+    int fp;                       // plane pitch of a stored state: rows of nine planes, f[(y * 9 + i) * fp + x]
     int eos_kind;                 // 0 Carnahan-Starling, 1 Peng-Robinson
     double RT, a, b4, k2, kappa, tau, nu, wet, gx, gy;
     double bpr, aalpha;           // PR: b and a alpha(T)
@@ -161,10 +162,11 @@ __global__ void adj_moments(AdjGeo g, const double *__restrict__ f, double *rho,
     if (c >= n) return;
     const int x = c % g.nx, y = c / g.nx;
     if (solid_row(g, y)) { rho[c] = jx[c] = jy[c] = 0.0; return; }
+    const double *fr = f + (size_t)y * 9 * g.fp;  // row y of the state
     if (pcol(g, x)) {
-        const int cf = y * g.nx + (x == 0 ? 1 : g.nx - 2);
+        const int xf = x == 0 ? 1 : g.nx - 2;
         double rf = 0.0;
-        for (int i = 0; i < 9; ++i) rf += f[i * n + cf];
+        for (int i = 0; i < 9; ++i) rf += fr[i * g.fp + xf];
         double dth;
         const double th = col_theta(g, rf, dth);
         const double gg = x == 0 ? g.g_in : g.g_out, ll = x == 0 ? g.l_in : g.l_out;
@@ -174,7 +176,7 @@ __global__ void adj_moments(AdjGeo g, const double *__restrict__ f, double *rho,
     }
     double r = 0.0, X = 0.0, Y = 0.0;
     for (int i = 0; i < 9; ++i) {
-        const double fi = f[i * n + c];
+        const double fi = fr[i * g.fp + x];
         r += fi;
         X += ex_(i) * fi;
         Y += ey_(i) * fi;
@@ -540,11 +542,13 @@ __global__ void adj_reduce_col(const double *__restrict__ colp, int ny, double *
     }
 }
 
-__global__ void adj_init_f(const double *__restrict__ rho0, int n, double *f)
+// the resting equilibrium of rho0, in the state layout (padding columns stay as set)
+__global__ void adj_init_f(AdjGeo g, const double *__restrict__ rho0, double *f)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
-    for (int i = 0; i < 9; ++i) f[i * n + c] = wq(i) * rho0[c];
+    if (c >= g.nx * g.ny) return;
+    const int x = c % g.nx, y = c / g.nx;
+    for (int i = 0; i < 9; ++i) f[((size_t)y * 9 + i) * g.fp + x] = wq(i) * rho0[c];
 }
 
 __global__ void adj_grad_rho0(const double *__restrict__ lam, int n, double *g)
@@ -607,6 +611,8 @@ lbm_status adj_alloc(lbm_adjoint *a, double **p, size_t count)
 }
 
 size_t npop(const lbm_adjoint *a) { return (size_t)9 * a->grid.nx * a->grid.ny; }
+// one stored state in the forward context's own layout (plane pitch pitch_of(nx))
+size_t spop(const lbm_adjoint *a) { return (size_t)9 * lbm::pitch_of(a->grid.nx) * a->grid.ny; }
 
 lbm_status adj_fields(lbm_adjoint *a, const double *f)
 {
@@ -684,6 +690,7 @@ lbm_status adj_setup_drive(lbm_adjoint *a, const lbm_drive *drive)
 
     AdjGeo &g = a->geo;
     g.nx = a->grid.nx; g.ny = a->grid.ny; g.walls = a->grid.walls; g.bc_x = a->grid.bc_x;
+    g.fp = lbm::pitch_of(a->grid.nx);
     lbm::Thermo th{};
     double tc;
     if (lbm::thermo_of(a->eos, &th, &tc)) { a->err = "equation of state"; return LBM_ERR_PARAM; }
@@ -745,10 +752,10 @@ lbm_status lbm_adjoint_init(const lbm_grid *grid, const lbm_eos *eos, double tau
     a->stream = (cudaStream_t)stream;
 
     const size_t n = (size_t)grid->nx * grid->ny, m1 = (size_t)(grid->nx + 2) * (grid->ny + 2),
-                 m2 = (size_t)(grid->nx + 4) * (grid->ny + 4), P = npop(a);
+                 m2 = (size_t)(grid->nx + 4) * (grid->ny + 4), P = npop(a), PS = spop(a);
     lbm_status s = LBM_OK;
     struct { double **p; size_t count; } bufs[] = {
-        {&a->ckpt, P * a->nblocks}, {&a->blk, P * a->K}, {&a->lam0, P}, {&a->lam1, P},
+        {&a->ckpt, PS * a->nblocks}, {&a->blk, PS * a->K}, {&a->lam0, P}, {&a->lam1, P},
         {&a->rho, n}, {&a->jx, n}, {&a->jy, n}, {&a->Fx, n}, {&a->Fy, n}, {&a->L1, m1},
         {&a->Ax, 2 * n}, {&a->Jbx, n}, {&a->Jby, n}, {&a->R, n}, {&a->Ls, n}, {&a->Cx, n}, {&a->Cy, n},
         {&a->Lb1, m1}, {&a->Pb1, m1}, {&a->Eb2, m2}, {&a->tw, 4 * (size_t)grid->nx},
@@ -773,22 +780,19 @@ lbm_status lbm_adjoint_forward(lbm_adjoint *a, const lbm_drive *drive, const dou
     lbm_status s = adj_setup_drive(a, drive);
     if (s != LBM_OK) return s;
     const long long n = (long long)a->grid.nx * a->grid.ny;
-    const size_t P = npop(a);
+    const size_t PS = spop(a);
     ACK(cudaMemcpyAsync(a->rho0, rho0, n * sizeof(double), cudaMemcpyDefault, a->stream), "rho0 copy");
-    adj_init_f<<<blocks(n), TPB, 0, a->stream>>>(a->rho0, (int)n, a->ckpt);
+    ACK(cudaMemsetAsync(a->ckpt, 0, PS * sizeof(double), a->stream), "adjoint memset");  // padding columns
+    adj_init_f<<<blocks(n), TPB, 0, a->stream>>>(a->geo, a->rho0, a->ckpt);
     ACK(cudaGetLastError(), "adjoint init kernel");
     ACK(cudaMemsetAsync(a->acc, 0, 8 * sizeof(double), a->stream), "adjoint memset");
-    s = lbm_load_populations(a->ctx, a->ckpt);
-    if (s != LBM_OK) return ctx_status(a, s, "load initial state");
+    // everything below is enqueued on the context's stream: no host round trip per step
+    ACK(lbm_ctx_load_state(a->ctx, a->ckpt), "load initial state");
     for (int64_t t = 0; t < a->nsteps; ++t) {
-        double *state = a->blk;
-        if (t % a->K == 0) {
-            state = a->ckpt + (size_t)(t / a->K) * P;
-            if (t > 0 && (s = lbm_populations(a->ctx, state)) != LBM_OK) return ctx_status(a, s, "checkpoint");
-        } else if ((s = lbm_populations(a->ctx, state)) != LBM_OK) {
-            return ctx_status(a, s, "state copy");
-        }
-        if ((s = adj_objective(a, state)) != LBM_OK) return s;
+        if (t > 0 && t % a->K == 0)
+            ACK(lbm_ctx_copy_state(a->ctx, a->ckpt + (size_t)(t / a->K) * PS), "checkpoint");
+        // the objective reads the state in the context's own buffer
+        if ((s = adj_objective(a, static_cast<const double *>(lbm_ctx_state(a->ctx)))) != LBM_OK) return s;
         if (t + 1 < a->nsteps && (s = lbm_step(a->ctx, 1)) != LBM_OK) return ctx_status(a, s, "forward step");
     }
     double h[2];
@@ -808,24 +812,23 @@ lbm_status lbm_adjoint_backward(lbm_adjoint *a, double w_tau, double w_p, double
     a->geo.w_tau = w_tau;
     a->geo.w_p = w_p;
     const long long n = (long long)a->grid.nx * a->grid.ny;
-    const size_t P = npop(a);
+    const size_t P = npop(a), PS = spop(a);
     ACK(cudaMemsetAsync(a->acc, 0, 8 * sizeof(double), a->stream), "adjoint memset");
     ACK(cudaMemsetAsync(a->lam1, 0, P * sizeof(double), a->stream), "adjoint memset");
     double *lin = a->lam1, *lout = a->lam0;
     lbm_status s;
     for (int64_t b = a->nblocks - 1; b >= 0; --b) {
         const int64_t n0 = b * a->K, n1 = std::min(a->nsteps, n0 + a->K);
-        const double *ck = a->ckpt + (size_t)b * P;
+        const double *ck = a->ckpt + (size_t)b * PS;
         if (n1 - n0 > 1) {
-            if ((s = lbm_load_populations(a->ctx, ck)) != LBM_OK) return ctx_status(a, s, "load checkpoint");
+            ACK(lbm_ctx_load_state(a->ctx, ck), "load checkpoint");
             for (int64_t m = 1; m < n1 - n0; ++m) {
                 if ((s = lbm_step(a->ctx, 1)) != LBM_OK) return ctx_status(a, s, "recompute step");
-                if ((s = lbm_populations(a->ctx, a->blk + (size_t)m * P)) != LBM_OK)
-                    return ctx_status(a, s, "recompute copy");
+                ACK(lbm_ctx_copy_state(a->ctx, a->blk + (size_t)m * PS), "recompute copy");
             }
         }
         for (int64_t t = n1 - 1; t >= n0; --t) {
-            const double *state = t == n0 ? ck : a->blk + (size_t)(t - n0) * P;
+            const double *state = t == n0 ? ck : a->blk + (size_t)(t - n0) * PS;
             if ((s = adj_reverse_step(a, state, lin, lout)) != LBM_OK) return s;
             std::swap(lin, lout);
         }

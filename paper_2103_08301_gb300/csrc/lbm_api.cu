@@ -192,6 +192,29 @@ void *kernel_ptr(bool walls, bool pres, bool staged, bool padded)
 
 }  // namespace
 
+namespace {
+size_t state_bytes(const lbm_ctx *ctx)
+{
+    return (size_t)9 * ctx->pitch * ctx->grid.ny * (ctx->grid.precision == 64 ? 8 : 4);
+}
+}  // namespace
+
+cudaError_t lbm_ctx_copy_state(lbm_ctx *ctx, void *dst)
+{
+    return cudaMemcpyAsync(dst, ctx->ws + (ctx->cur ? ctx->L.f1 : ctx->L.f0), state_bytes(ctx),
+                           cudaMemcpyDeviceToDevice, ctx->stream);
+}
+
+const void *lbm_ctx_state(const lbm_ctx *ctx) { return ctx->ws + (ctx->cur ? ctx->L.f1 : ctx->L.f0); }
+
+cudaError_t lbm_ctx_load_state(lbm_ctx *ctx, const void *src)
+{
+    const size_t bytes = state_bytes(ctx);
+    cudaError_t e = cudaMemcpyAsync(ctx->ws + ctx->L.f0, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->ws + ctx->L.f1, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    return e;
+}
+
 void *lbm_step_kernel_ptr(int precision, int mode, bool walls, bool pres, bool staged, bool padded)
 {
     if (precision == 64)

@@ -65,6 +65,17 @@ inline int strip_width(int nx, int w_max, bool bc_x)
 
 } // namespace lbm
 
+// The current population state of a context in its own layout (rows of nine
+// planes, plane pitch pitch_of(nx), 9 * pitch * ny values): an asynchronous
+// device copy out of it / into both of its buffers, on the context's stream
+// and without synchronising (the public lbm_populations / lbm_load_populations
+// convert to the plane-major ABI layout and synchronise). lbm_api.cu.
+#ifdef __CUDACC__
+cudaError_t lbm_ctx_copy_state(lbm_ctx *ctx, void *dst);
+const void *lbm_ctx_state(const lbm_ctx *ctx);  // the current state buffer itself (device)
+cudaError_t lbm_ctx_load_state(lbm_ctx *ctx, const void *src);
+#endif
+
 // Launchable step kernel (lbm_api.cu) for a precision (32/64), a mode
 // (lbm::MODE_STEP or MODE_FIELDS), the boundary set, the staged variant and a
 // row pitch above nx (padded).
