@@ -193,15 +193,72 @@ def _extras(stream):
     nx, ny, steps = 512, 128, 2000
     _, g, l, _ = lbm.lbm_coexistence(lbm.lbm_eos(1.0, 4.0, 1.0, 0.85, 1.0, 0.5))
     r0 = lbm.lbm_airway_rho0(nx, ny, 6.0, 128, 48.0, l, g, 4.0, 1e-3, 1)
-    with adjm.Adjoint(nx, ny, steps, walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5) as adj:
+    with adjm.Adjoint(nx, ny, steps, walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, block_steps=100) as adj:
         t0 = time.perf_counter()
         adj.forward(r0, dp=1e-3)
         t1 = time.perf_counter()
         adj.backward(1.0, 1.0)
         t2 = time.perf_counter()
-    out["adjoint"] = {"workload": "512x128 airway, 2000 FP64 steps, checkpoints every 45",
+    out["adjoint"] = {"workload": "512x128 airway, 2000 FP64 steps, checkpoints every 100",
                       "forward_s": t1 - t0, "backward_s": t2 - t1,
                       "reverse_mlups": nx * ny * steps / (t2 - t1) / 1e6}
+    out["configs"] = _configs(stream)
+    return out
+
+
+def _oracle_mlups(s, f, budget_s):
+    """Oracle MLUPS on as many steps of state f as fit in about budget_s seconds."""
+    import oracle
+    t0 = time.perf_counter()
+    f, _ = oracle.run(s, f, 1)
+    one = time.perf_counter() - t0
+    steps = max(1, int(budget_s / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    oracle.run(s, f, steps)
+    dt = time.perf_counter() - t0
+    return s.nx * s.ny * steps / dt / 1e6, steps
+
+
+def _configs(stream, budget_s=2.0):
+    """The two single-lattice workloads not timed above, on the GPU and with the
+    oracle on all host cores and on one core (bounded samples of the same
+    state): the 128 x 128 periodic droplet (FP64, 10000 steps) and the
+    2048 x 256 airway channel (FP32, 20000 of its 100000 steps; its 38 MB state
+    sits in L2, so its GB/s is algorithmic traffic, not DRAM)."""
+    import oracle
+    import synth
+    import paper_2103_08301_gb300 as lbm
+    peak, _ = _hbm_peak()
+    out = {}
+    cases = [
+        ("droplet_128x128_fp64", 128, 128, 64, 10000,
+         dict(walls=False, bc_x=False, T_over_Tc=0.8, k=1.0, kappa=0.5, tau=1.0)),
+        ("airway_2048x256_fp32", 2048, 256, 32, 20000,
+         dict(walls=True, bc_x=True, T_over_Tc=0.85, k=1.0, kappa=0.5, tau=1.0, dp=1e-3)),
+    ]
+    for name, nx, ny, prec, steps, kw in cases:
+        s = oracle.Setup(nx=nx, ny=ny, **kw)
+        g, l, _ = s.coexistence()
+        if name.startswith("droplet"):
+            rho0 = synth.disk_rho0(nx, ny, 30, l, g, noise=1e-3, seed=1)
+        else:
+            rho0 = synth.airway_rho0(nx, ny, 8.0, 512.0, 128.0, l, g)
+        with lbm.Lattice(nx, ny, rho0, precision=prec, stream=stream, **kw) as lat:
+            ms = _timed_steps(lat, stream, steps)
+        mlups = nx * ny / ms / 1e3
+        gbs = BYTES_PER_NODE[prec] * nx * ny / ms / 1e6
+        f0 = oracle.init(s, rho0)
+        ncores = oracle.num_threads()
+        o_all, n_all = _oracle_mlups(s, f0, budget_s)
+        oracle.set_num_threads(1)
+        try:
+            o_one, n_one = _oracle_mlups(s, f0, budget_s)
+        finally:
+            oracle.set_num_threads(ncores)
+        out[name] = {"gpu_mlups": mlups, "gpu_gbs": gbs, "roofline_frac_of_measured": gbs / peak,
+                     "gpu_steps": steps, "oracle_mlups": o_all, "oracle_cores": ncores,
+                     "oracle_mlups_1core": o_one,
+                     "oracle_sample": f"{n_all} steps on {ncores} cores, {n_one} steps on 1 core"}
     return out
 
 

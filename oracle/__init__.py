@@ -107,6 +107,8 @@ def lib():
         L.orc_fields.argtypes = [C.POINTER(Params), _PD, _PD, _PD, _PD, _PD, _PD]
         L.orc_force.argtypes = [C.POINTER(Params), _PD, _PD, _PD]
         L.orc_num_threads.restype = C.c_int
+        L.orc_set_num_threads.argtypes = [C.c_int]
+        L.orc_set_num_threads.restype = None
         _lib = L
     return _lib
 
@@ -385,3 +387,8 @@ def force(setup: Setup, f: np.ndarray):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops (for timing it on one core)."""
+    lib().orc_set_num_threads(int(n))

@@ -967,3 +967,13 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads of the parallel loops (n >= 1); for timing the oracle on one core. */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
