@@ -255,7 +255,7 @@ size_t dyn_smem(const lbm_ctx *ctx, int mode)
 
 int threads_of(const lbm_ctx *ctx, int mode)
 {
-    if (mode == lbm::MODE_STEP && ctx->rows2) return lbm::STRIP;
+    if (mode == lbm::MODE_STEP && ctx->rows2) return lbm::R2_BLOCK;
     return cta_threads(ctx->grid.precision, ctx->staged);
 }
 

@@ -129,7 +129,7 @@ size_t staged_bytes(const lbm_batch *b, bool staged)
 
 // dynamic shared memory and threads of the batch step kernel
 size_t step_smem(const lbm_batch *b) { return b->rows2 ? lbm::rows2_smem_bytes() : staged_bytes(b, b->staged); }
-int step_threads(const lbm_batch *b) { return b->rows2 ? lbm::STRIP : cta_threads(b->precision, b->staged); }
+int step_threads(const lbm_batch *b) { return b->rows2 ? lbm::R2_BLOCK : cta_threads(b->precision, b->staged); }
 
 // Shared physics of every channel, in the kernel argument block.
 template <typename real>

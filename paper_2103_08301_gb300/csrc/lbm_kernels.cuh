@@ -1009,9 +1009,9 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
 }
 
 // Fixed-order CTA reduction of the accumulators; thread 0 receives the totals.
-template <typename real, int BLOCK, int CP>
-__device__ __forceinline__ void cta_reduce(Acc<real, CP> &acc, Smem<real, BLOCK> &S, double &m, double &j,
-                                           real (&e)[4], bool &anybad)
+template <typename real, int BLOCK, int CP, typename SM>
+__device__ __forceinline__ void cta_reduce(Acc<real, CP> &acc, SM &S, double &m, double &j, real (&e)[4],
+                                           bool &anybad)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     acc.flush();

@@ -7,7 +7,7 @@
 //   - the loop bookkeeping, barriers and stage waits of an iteration are
 //     shared by two nodes per thread, and the method's arithmetic issues one
 //     instruction per two nodes;
-//   - strips are at most STRIP - 4 columns wide and lane t holds local column
+//   - strips are at most R2_BLOCK - 4 columns wide and lane t holds local column
 //     t - 2, so the two halo columns on each side are lanes of their own: no
 //     divergent halo duty (which cost 8% as a one-warp duty); the stage holds
 //     each stencil row with a four-column margin on both sides (columns
@@ -30,8 +30,14 @@
 namespace lbm {
 
 constexpr int R2_SLOTS = 3;            // pair slots of the stage ring
-constexpr int R2_W = STRIP - 4;        // widest strip: 128 lanes cover it and two halo columns per side
-constexpr int R2_SP = STRIP + 8;       // stage row pitch: strip plus 4 margin columns per side
+// Threads of a row-pair CTA (one column each).
+#ifndef LBM_R2_BLOCK
+#define LBM_R2_BLOCK 128
+#endif
+constexpr int R2_BLOCK = LBM_R2_BLOCK;
+static_assert(R2_BLOCK % 32 == 0 && R2_BLOCK <= STRIP, "whole warps, at most STRIP lanes");
+constexpr int R2_W = R2_BLOCK - 4;     // widest strip: the lanes cover it and two halo columns per side
+constexpr int R2_SP = R2_BLOCK + 8;    // stage row pitch: strip plus 4 margin columns per side
 constexpr int R2_ROW = 9 * R2_SP;      // one stencil row of nine planes
 constexpr int R2_SLOT = 2 * R2_ROW;    // one pair of rows
 
@@ -60,6 +66,17 @@ __device__ __forceinline__ Row3<float2> row3p(const float (*S)[SW], int ra, int 
     return r;
 }
 
+// Static shared memory of a row-pair CTA: the 8-row rings of density, phi
+// and Laplacian (one column per lane) and the reduction scratch.
+struct SmemR2 {
+    __align__(16) float rho[RING][R2_BLOCK + 4];
+    __align__(16) float phi[RING][R2_BLOCK + 4];
+    __align__(16) float lap[RING][R2_BLOCK + 4];
+    double red[R2_BLOCK / 32][2];
+    float ext[R2_BLOCK / 32][4];
+    int bad;
+};
+
 // Both rows of a slot at stage column sc, plane i.
 __device__ __forceinline__ float2 stage_pair(const float *slot, int i, int sc)
 {
@@ -72,12 +89,12 @@ __device__ __forceinline__ float2 stage_pair(const float *slot, int i, int sc)
 // by y & (RING - 1) as in the one-row kernel.
 template <bool WALLS, bool PRES, bool PADDED>
 __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom<float> &G, int s, int ya, int yb,
-                                               Smem<float, STRIP> &S, float *stages, uint64_t *bars,
+                                               SmemR2 &S, float *stages, uint64_t *bars,
                                                RingPos2 &ring_next, Acc<float, 1> &acc, bool &lost)
 {
     using V = float2;
-    constexpr int SW = STRIP + 4;
-    constexpr int PRODUCER = STRIP - 1;  // no halo duty
+    constexpr int SW = R2_BLOCK + 4;
+    constexpr int PRODUCER = R2_BLOCK - 1;  // no halo duty
     constexpr int RM = RING - 1;
     const int tid = threadIdx.x;
     const float third = 1.0f / 3.0f;
@@ -91,7 +108,7 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
 
     const int x0 = s * G.W;
     const int xw = min(G.W, nx - x0);
-    // Thread t holds local column l = t - 2: the strip (at most R2_W = STRIP - 4
+    // Thread t holds local column l = t - 2: the strip (at most R2_W = R2_BLOCK - 4
     // columns) plus two halo columns on each side, so every column's density
     // is computed by its own lane and no halo duty exists.
     const int l = tid - 2;
@@ -344,15 +361,15 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
 // The row-pair step kernel (FP32, staged, MODE_STEP); launched like
 // step_kernel with rows2_smem_bytes() of dynamic shared memory.
 #ifndef LBM_R2_MIN_BLOCKS
-#define LBM_R2_MIN_BLOCKS 5
+#define LBM_R2_MIN_BLOCKS (640 / LBM_R2_BLOCK)
 #endif
 template <bool WALLS, bool PRES, bool PADDED>
-__global__ void __launch_bounds__(STRIP, LBM_R2_MIN_BLOCKS) step_kernel_rows2(const KArgs<float> A)
+__global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS) step_kernel_rows2(const KArgs<float> A)
 {
     extern __shared__ __align__(128) unsigned char dsm[];
     float *const stages = reinterpret_cast<float *>(dsm);
     uint64_t *const bars = reinterpret_cast<uint64_t *>(dsm + (size_t)R2_SLOTS * R2_SLOT * sizeof(float));
-    __shared__ Smem<float, STRIP> S;
+    __shared__ SmemR2 S;
 
     const int tid = threadIdx.x;
     const int cta = A.reverse ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
@@ -384,7 +401,7 @@ __global__ void __launch_bounds__(STRIP, LBM_R2_MIN_BLOCKS) step_kernel_rows2(co
     double m, j;
     float e[4];
     bool anybad;
-    cta_reduce<float, STRIP, 1>(acc, S, m, j, e, anybad);
+    cta_reduce<float, R2_BLOCK, 1>(acc, S, m, j, e, anybad);
     if (tid == 0) {
         A.mass_part[cta] = m;
         A.J_acc[cta] += j;
@@ -399,7 +416,7 @@ __global__ void __launch_bounds__(STRIP, LBM_R2_MIN_BLOCKS) step_kernel_rows2(co
 // segment of the work list through run_segment_r2 (padded-pitch body, since
 // the channels of a batch mix pitches), one reduction slot per segment.
 template <bool WALLS, bool PRES>
-__global__ void __launch_bounds__(STRIP, LBM_R2_MIN_BLOCKS)
+__global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS)
     batch_step_kernel_rows2(const KArgs<float> A, const BatchChan<float> *__restrict__ chans,
                             const BatchSeg *__restrict__ segs, const int *__restrict__ cta_begin,
                             double *__restrict__ seg_mass, double *__restrict__ seg_J, float *__restrict__ seg_ext)
@@ -407,7 +424,7 @@ __global__ void __launch_bounds__(STRIP, LBM_R2_MIN_BLOCKS)
     extern __shared__ __align__(128) unsigned char dsm[];
     float *const stages = reinterpret_cast<float *>(dsm);
     uint64_t *const bars = reinterpret_cast<uint64_t *>(dsm + (size_t)R2_SLOTS * R2_SLOT * sizeof(float));
-    __shared__ Smem<float, STRIP> S;
+    __shared__ SmemR2 S;
 
     const int tid = threadIdx.x;
     const int cta = A.reverse ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
@@ -429,7 +446,7 @@ __global__ void __launch_bounds__(STRIP, LBM_R2_MIN_BLOCKS)
         double m, j;
         float e[4];
         bool anybad;
-        cta_reduce<float, STRIP, 1>(acc, S, m, j, e, anybad);
+        cta_reduce<float, R2_BLOCK, 1>(acc, S, m, j, e, anybad);
         if (tid == 0) {
             seg_mass[k] = m;
             seg_J[k] += j;
