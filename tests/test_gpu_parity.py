@@ -152,6 +152,30 @@ def test_tiny_and_degenerate_grids_fp64(orc, lbm, nx, ny, walls, bc_x):
     assert abs(d["mass"] - d_ref["mass"]) <= 1e-12 * d_ref["mass"]
 
 
+@pytest.mark.parametrize("nx,ny,walls,bc_x", [(4, 4, True, True), (4, 4, False, False), (8, 6, True, False),
+                                              (12, 5, False, False), (5, 7, True, True), (130, 5, True, True),
+                                              (128, 9, False, False)])
+def test_tiny_grids_fp32_row_pairs(orc, lbm, nx, ny, walls, bc_x):
+    """Tiny and single-strip grids through the FP32 row-pair kernel (periodic x
+    exercises the wrapped halo copies from both ends of a row): against the
+    oracle at the FP32 tolerance, and bit for bit against the one-row kernel."""
+    kw = dict(walls=walls, bc_x=bc_x, T_over_Tc=0.85, kappa=0.5, dp=1e-4 if bc_x else 0.0)
+    s = orc.Setup(nx=nx, ny=ny, **kw)
+    g, l, _ = s.coexistence()
+    rng = np.random.default_rng(nx * 100 + ny + 7)
+    rho0 = g + (l - g) * rng.random((ny, nx)) * 0.3
+    f_ref, _ = orc.run(s, orc.init(s, rho0), 200)
+    ref = orc.fields(s, f_ref)["rho"]
+    out = []
+    for rows2 in (1, 0):
+        with lbm.Lattice(nx, ny, rho0, precision=32, **kw) as lat:
+            lat.set_option(lbm.LBM_OPT_ROWS2, rows2)
+            lat.step(200)
+            out.append((lat.fields()["rho"].astype(np.float64), lat.populations()))
+    assert np.abs(out[0][0] - ref).max() <= 1e-4 * np.abs(ref).max()
+    assert np.array_equal(out[0][1].view(np.uint32), out[1][1].view(np.uint32))
+
+
 def test_single_step_populations_bitwise_structure(orc, lbm):
     """One FP64 step from a random state: every population slot the step writes
     matches the oracle, and slots it never writes keep their value."""
