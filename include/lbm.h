@@ -231,9 +231,9 @@ lbm_status lbm_launch_info(const lbm_ctx *ctx, int64_t *ctas, int64_t *threads, 
 
 /* One time step from f_in to f_out without allocating any device memory.
  * No counterpart in the paper: this is a deployment form of lbm_step for
- * callers that cannot allocate at the point where they step (code running
- * inside another framework's memory pool, hosts that size every buffer up
- * front, work about to be recorded into a CUDA graph).
+ * callers that cannot call cudaMalloc where they step: code running inside
+ * another framework's memory pool (a raw allocation would bypass the pool's
+ * accounting and limits), or a host that sizes every device buffer up front.
  *   grid, eos, tau, wetting, drive: as for lbm_init (drive may be NULL).
  *   f_in, f_out: distinct caller-owned device arrays of 9*nx*ny values of the
  *            grid precision in the library's row-interleaved layout f[y][i][x]
@@ -250,8 +250,8 @@ lbm_status lbm_launch_info(const lbm_ctx *ctx, int64_t *ctas, int64_t *threads, 
  * Scratch: the per-CTA partials live in one static device array (about
  * 192 KB) that the library holds on every device it is used on until the
  * process exits. Every call reuses and first clears it, so calls whose work
- * overlaps on the GPU (different streams, or graphs replayed concurrently)
- * race on it; serialise them. The first call on a device resolves the
+ * overlaps on the GPU (for instance on different streams) race on it;
+ * serialise them. The first call on a device resolves the
  * array's device address (cudaGetSymbolAddress) and should come before any
  * stream capture.
  * Errors: LBM_ERR_ARG (bad grid, NULL or equal buffers, ctas outside

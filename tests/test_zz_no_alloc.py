@@ -1,9 +1,9 @@
 """The allocation-free step (lbm_step_noalloc) against the ordinary context path.
 
-lbm_step_noalloc serves callers that cannot allocate device memory when they
-step the lattice (a framework that owns the memory pool, a host that sizes all
-buffers up front, work recorded into a CUDA graph): it steps between two
-caller-owned buffers and keeps its per-CTA scratch in a fixed device array.
+lbm_step_noalloc serves callers that cannot call cudaMalloc when they step the
+lattice (code inside a framework that owns the memory pool, a host that sizes
+all buffers up front): it steps between two caller-owned buffers and keeps its
+per-CTA scratch in a fixed device array.
 Here the test allocates the buffers itself (with torch) and checks two calls
 in a row against two lbm_step calls on a context. This file is collected last
 so a failure here comes after every other test has run.
