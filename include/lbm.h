@@ -360,7 +360,7 @@ typedef struct {
 lbm_status lbm_plug_analysis(int32_t nx, int32_t ny, const double *rho, double rho_mid, lbm_plug_state *out);
 
 /* ------------------------------------------------------------------------ */
-/* Discrete adjoint (precision-64 channels)                                  */
+/* Discrete adjoint                                                          */
 /* ------------------------------------------------------------------------ */
 /* Gradients of the time-integrated wall loads of Sec. 3 (Figs. 10-12),
  * summed over the states n = 0 .. nsteps-1 that nsteps steps read and over the
@@ -370,11 +370,15 @@ lbm_status lbm_plug_analysis(int32_t nx, int32_t ny, const double *rho, double r
  * exact transpose of the linearised step of lbm_step (a pressure column's
  * clamped phase weight contributes no derivative), run backwards over blocks
  * of block_steps steps recomputed from checkpoints kept in device memory
- * (9 nx ny doubles per checkpoint: ceil(nsteps/K) checkpoints plus K states
- * of one block; K = block_steps, or ceil(sqrt(nsteps)) if 0).
+ * (one state, 9 pitch ny values of the forward precision with pitch = nx
+ * rounded up to a multiple of 4, per checkpoint: ceil(nsteps/K) checkpoints
+ * plus K states of one block; K = block_steps, or ceil(sqrt(nsteps)) if 0).
  *
- * lbm_adjoint_init: grid->precision must be 64 (LBM_ERR_ARG otherwise);
- *   nsteps >= 1. Allocates on the current device; stream as in lbm_init.
+ * lbm_adjoint_init: grid->precision is the precision of the forward steps and
+ *   checkpoints, 64 or 32 (LBM_ERR_ARG otherwise); the reverse sweep is FP64
+ *   either way, on the stored states widened to FP64, so with 32 the result is
+ *   the gradient of the FP64 step along the FP32 trajectory. nsteps >= 1.
+ *   Allocates on the current device; stream as in lbm_init.
  * lbm_adjoint_forward: runs nsteps steps from f0 = f_eq(rho0, 0) under
  *   `drive` (NULL: no drive), keeping checkpoints, and returns J (host,
  *   2 doubles). rho0: nx*ny doubles, host or device. Synchronises the stream.

@@ -10,8 +10,10 @@ Binding of the ``lbm_adjoint_*`` entry points of ``include/lbm.h`` plus two
 - ``AirwayProfile``: (film, plug_len) -> rho0, the initial airway density of
   ``lbm_airway_rho0``, with its exact tangent from ``lbm_airway_rho0_tangent``.
 
-Chained, they give dJ/d(pressure drop, film thickness, plug length). Only
-precision-64 channels are differentiated.
+Chained, they give dJ/d(pressure drop, film thickness, plug length). The
+forward steps and checkpoints run in FP64 (precision=64) or FP32
+(precision=32, half the checkpoint memory); the reverse sweep is FP64 either
+way, on the stored states widened to FP64.
 """
 from __future__ import annotations
 
@@ -43,9 +45,9 @@ class Adjoint:
 
     def __init__(self, nx, ny, nsteps, *, walls=True, bc_x=True, a=1.0, b=4.0, R=1.0, T_over_Tc=0.85,
                  k=1.0, kappa=0.5, tau=1.0, wetting=0.0, p_ref=None, eos="cs", omega=0.344, collision="bgk",
-                 s_e=1.64, s_eps=1.54, s_j=1.0, s_q=1.7, s_nu=None, block_steps=0, stream=None):
+                 s_e=1.64, s_eps=1.54, s_j=1.0, s_q=1.7, s_nu=None, block_steps=0, precision=64, stream=None):
         self.nx, self.ny, self.nsteps = nx, ny, nsteps
-        self.grid = lbm_grid(nx, ny, int(walls), int(bc_x), 64)
+        self.grid = lbm_grid(nx, ny, int(walls), int(bc_x), int(precision))
         self.eos = lbm_eos(a, b, R, T_over_Tc, k, kappa, {"cs": LBM_EOS_CS, "pr": LBM_EOS_PR}[eos], omega)
         self.p_ref = math.nan if p_ref is None else p_ref
         self._stream = stream

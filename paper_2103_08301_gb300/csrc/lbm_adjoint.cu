@@ -155,18 +155,20 @@ __device__ __forceinline__ double col_theta(const AdjGeo &g, double rf, double &
 
 // ---- forward recompute of the fields of one state ---------------------------
 
-__global__ void adj_moments(AdjGeo g, const double *__restrict__ f, double *rho, double *jx, double *jy)
+// S: the stored state's type (double, or float for an FP32 forward; widened here)
+template <typename S>
+__global__ void adj_moments(AdjGeo g, const S *__restrict__ f, double *rho, double *jx, double *jy)
 {
     const int n = g.nx * g.ny;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
     const int x = c % g.nx, y = c / g.nx;
     if (solid_row(g, y)) { rho[c] = jx[c] = jy[c] = 0.0; return; }
-    const double *fr = f + (size_t)y * 9 * g.fp;  // row y of the state
+    const S *fr = f + (size_t)y * 9 * g.fp;  // row y of the state
     if (pcol(g, x)) {
         const int xf = x == 0 ? 1 : g.nx - 2;
         double rf = 0.0;
-        for (int i = 0; i < 9; ++i) rf += fr[i * g.fp + xf];
+        for (int i = 0; i < 9; ++i) rf += (double)fr[i * g.fp + xf];
         double dth;
         const double th = col_theta(g, rf, dth);
         const double gg = x == 0 ? g.g_in : g.g_out, ll = x == 0 ? g.l_in : g.l_out;
@@ -176,7 +178,7 @@ __global__ void adj_moments(AdjGeo g, const double *__restrict__ f, double *rho,
     }
     double r = 0.0, X = 0.0, Y = 0.0;
     for (int i = 0; i < 9; ++i) {
-        const double fi = fr[i * g.fp + x];
+        const double fi = (double)fr[i * g.fp + x];
         r += fi;
         X += ex_(i) * fi;
         Y += ey_(i) * fi;
@@ -543,12 +545,13 @@ __global__ void adj_reduce_col(const double *__restrict__ colp, int ny, double *
 }
 
 // the resting equilibrium of rho0, in the state layout (padding columns stay as set)
-__global__ void adj_init_f(AdjGeo g, const double *__restrict__ rho0, double *f)
+template <typename S>
+__global__ void adj_init_f(AdjGeo g, const double *__restrict__ rho0, S *f)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.nx * g.ny) return;
     const int x = c % g.nx, y = c / g.nx;
-    for (int i = 0; i < 9; ++i) f[((size_t)y * 9 + i) * g.fp + x] = wq(i) * rho0[c];
+    for (int i = 0; i < 9; ++i) f[((size_t)y * 9 + i) * g.fp + x] = (S)(wq(i) * rho0[c]);
 }
 
 __global__ void adj_grad_rho0(const double *__restrict__ lam, int n, double *g)
@@ -613,19 +616,25 @@ lbm_status adj_alloc(lbm_adjoint *a, double **p, size_t count)
 size_t npop(const lbm_adjoint *a) { return (size_t)9 * a->grid.nx * a->grid.ny; }
 // one stored state in the forward context's own layout (plane pitch pitch_of(nx))
 size_t spop(const lbm_adjoint *a) { return (size_t)9 * lbm::pitch_of(a->grid.nx) * a->grid.ny; }
+// bytes of one stored state (the forward precision), and state k of an array of them
+size_t sbytes(const lbm_adjoint *a) { return spop(a) * (a->grid.precision == 32 ? 4 : 8); }
+void *state_at(double *base, size_t k, size_t bytes) { return (char *)base + k * bytes; }
 
-lbm_status adj_fields(lbm_adjoint *a, const double *f)
+lbm_status adj_fields(lbm_adjoint *a, const void *f)
 {
     const AdjGeo &g = a->geo;
     const long long n = (long long)g.nx * g.ny, m1 = (long long)(g.nx + 2) * (g.ny + 2);
-    adj_moments<<<blocks(n), TPB, 0, a->stream>>>(g, f, a->rho, a->jx, a->jy);
+    if (a->grid.precision == 32)
+        adj_moments<float><<<blocks(n), TPB, 0, a->stream>>>(g, (const float *)f, a->rho, a->jx, a->jy);
+    else
+        adj_moments<double><<<blocks(n), TPB, 0, a->stream>>>(g, (const double *)f, a->rho, a->jx, a->jy);
     adj_lap<<<blocks(m1), TPB, 0, a->stream>>>(g, a->rho, a->L1);
     adj_force<<<blocks(n), TPB, 0, a->stream>>>(g, a->rho, a->L1, a->Fx, a->Fy);
     ACK(cudaGetLastError(), "adjoint field kernels");
     return LBM_OK;
 }
 
-lbm_status adj_objective(lbm_adjoint *a, const double *f)
+lbm_status adj_objective(lbm_adjoint *a, const void *f)
 {
     lbm_status s = adj_fields(a, f);
     if (s != LBM_OK) return s;
@@ -637,7 +646,7 @@ lbm_status adj_objective(lbm_adjoint *a, const double *f)
     return LBM_OK;
 }
 
-lbm_status adj_reverse_step(lbm_adjoint *a, const double *f, const double *lam_in, double *lam_out)
+lbm_status adj_reverse_step(lbm_adjoint *a, const void *f, const double *lam_in, double *lam_out)
 {
     lbm_status s = adj_fields(a, f);
     if (s != LBM_OK) return s;
@@ -736,7 +745,8 @@ lbm_status lbm_adjoint_init(const lbm_grid *grid, const lbm_eos *eos, double tau
 {
     if (!out) return LBM_ERR_ARG;
     *out = nullptr;
-    if (!grid || !eos || grid->precision != 64 || nsteps < 1 || block_steps < 0) return LBM_ERR_ARG;
+    if (!grid || !eos || (grid->precision != 64 && grid->precision != 32) || nsteps < 1 || block_steps < 0)
+        return LBM_ERR_ARG;
     if (grid->nx < 1 || grid->ny < 1 || 9ll * grid->nx * grid->ny >= (1ll << 31)) return LBM_ERR_ARG;
     if (!(tau > 0.5) || !std::isfinite(wetting)) return LBM_ERR_PARAM;
     lbm_adjoint *a = new (std::nothrow) lbm_adjoint();
@@ -752,10 +762,11 @@ lbm_status lbm_adjoint_init(const lbm_grid *grid, const lbm_eos *eos, double tau
     a->stream = (cudaStream_t)stream;
 
     const size_t n = (size_t)grid->nx * grid->ny, m1 = (size_t)(grid->nx + 2) * (grid->ny + 2),
-                 m2 = (size_t)(grid->nx + 4) * (grid->ny + 4), P = npop(a), PS = spop(a);
+                 m2 = (size_t)(grid->nx + 4) * (grid->ny + 4), P = npop(a);
+    const size_t SD = (sbytes(a) + 7) / 8;  // one stored state, in doubles
     lbm_status s = LBM_OK;
     struct { double **p; size_t count; } bufs[] = {
-        {&a->ckpt, PS * a->nblocks}, {&a->blk, PS * a->K}, {&a->lam0, P}, {&a->lam1, P},
+        {&a->ckpt, SD * a->nblocks}, {&a->blk, SD * a->K}, {&a->lam0, P}, {&a->lam1, P},
         {&a->rho, n}, {&a->jx, n}, {&a->jy, n}, {&a->Fx, n}, {&a->Fy, n}, {&a->L1, m1},
         {&a->Ax, 2 * n}, {&a->Jbx, n}, {&a->Jby, n}, {&a->R, n}, {&a->Ls, n}, {&a->Cx, n}, {&a->Cy, n},
         {&a->Lb1, m1}, {&a->Pb1, m1}, {&a->Eb2, m2}, {&a->tw, 4 * (size_t)grid->nx},
@@ -780,19 +791,22 @@ lbm_status lbm_adjoint_forward(lbm_adjoint *a, const lbm_drive *drive, const dou
     lbm_status s = adj_setup_drive(a, drive);
     if (s != LBM_OK) return s;
     const long long n = (long long)a->grid.nx * a->grid.ny;
-    const size_t PS = spop(a);
+    const size_t SB = sbytes(a);
     ACK(cudaMemcpyAsync(a->rho0, rho0, n * sizeof(double), cudaMemcpyDefault, a->stream), "rho0 copy");
-    ACK(cudaMemsetAsync(a->ckpt, 0, PS * sizeof(double), a->stream), "adjoint memset");  // padding columns
-    adj_init_f<<<blocks(n), TPB, 0, a->stream>>>(a->geo, a->rho0, a->ckpt);
+    ACK(cudaMemsetAsync(a->ckpt, 0, SB, a->stream), "adjoint memset");  // padding columns
+    if (a->grid.precision == 32)
+        adj_init_f<float><<<blocks(n), TPB, 0, a->stream>>>(a->geo, a->rho0, (float *)a->ckpt);
+    else
+        adj_init_f<double><<<blocks(n), TPB, 0, a->stream>>>(a->geo, a->rho0, a->ckpt);
     ACK(cudaGetLastError(), "adjoint init kernel");
     ACK(cudaMemsetAsync(a->acc, 0, 8 * sizeof(double), a->stream), "adjoint memset");
     // everything below is enqueued on the context's stream: no host round trip per step
     ACK(lbm_ctx_load_state(a->ctx, a->ckpt), "load initial state");
     for (int64_t t = 0; t < a->nsteps; ++t) {
         if (t > 0 && t % a->K == 0)
-            ACK(lbm_ctx_copy_state(a->ctx, a->ckpt + (size_t)(t / a->K) * PS), "checkpoint");
+            ACK(lbm_ctx_copy_state(a->ctx, state_at(a->ckpt, (size_t)(t / a->K), SB)), "checkpoint");
         // the objective reads the state in the context's own buffer
-        if ((s = adj_objective(a, static_cast<const double *>(lbm_ctx_state(a->ctx)))) != LBM_OK) return s;
+        if ((s = adj_objective(a, lbm_ctx_state(a->ctx))) != LBM_OK) return s;
         if (t + 1 < a->nsteps && (s = lbm_step(a->ctx, 1)) != LBM_OK) return ctx_status(a, s, "forward step");
     }
     double h[2];
@@ -812,23 +826,23 @@ lbm_status lbm_adjoint_backward(lbm_adjoint *a, double w_tau, double w_p, double
     a->geo.w_tau = w_tau;
     a->geo.w_p = w_p;
     const long long n = (long long)a->grid.nx * a->grid.ny;
-    const size_t P = npop(a), PS = spop(a);
+    const size_t P = npop(a), SB = sbytes(a);
     ACK(cudaMemsetAsync(a->acc, 0, 8 * sizeof(double), a->stream), "adjoint memset");
     ACK(cudaMemsetAsync(a->lam1, 0, P * sizeof(double), a->stream), "adjoint memset");
     double *lin = a->lam1, *lout = a->lam0;
     lbm_status s;
     for (int64_t b = a->nblocks - 1; b >= 0; --b) {
         const int64_t n0 = b * a->K, n1 = std::min(a->nsteps, n0 + a->K);
-        const double *ck = a->ckpt + (size_t)b * PS;
+        const void *ck = state_at(a->ckpt, (size_t)b, SB);
         if (n1 - n0 > 1) {
             ACK(lbm_ctx_load_state(a->ctx, ck), "load checkpoint");
             for (int64_t m = 1; m < n1 - n0; ++m) {
                 if ((s = lbm_step(a->ctx, 1)) != LBM_OK) return ctx_status(a, s, "recompute step");
-                ACK(lbm_ctx_copy_state(a->ctx, a->blk + (size_t)m * PS), "recompute copy");
+                ACK(lbm_ctx_copy_state(a->ctx, state_at(a->blk, (size_t)m, SB)), "recompute copy");
             }
         }
         for (int64_t t = n1 - 1; t >= n0; --t) {
-            const double *state = t == n0 ? ck : a->blk + (size_t)(t - n0) * PS;
+            const void *state = t == n0 ? ck : state_at(a->blk, (size_t)(t - n0), SB);
             if ((s = adj_reverse_step(a, state, lin, lout)) != LBM_OK) return s;
             std::swap(lin, lout);
         }

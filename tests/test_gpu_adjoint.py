@@ -205,31 +205,42 @@ def test_autograd_chain_film_plug_and_pressure_drop(adjm, orc):
         assert abs(t.grad.item() - ref) <= 1e-6 * abs(ref) + 1e-9 * np.abs(fd).max(), (p, t.grad.item(), ref)
 
 
-def test_airway_workload_gradients_2000_steps(adjm, orc):
+_AIRWAY_J = {}
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_airway_workload_gradients_2000_steps(adjm, orc, precision):
     # the airway workload: 512 x 128 channel, film 6, plug 48 at x = 128,
     # 0.85 Tc, dp = 1e-3, noise 1e-3, 2000 FP64 steps. J is smooth in film
     # thickness and plug length; central differences of the oracle (step 1e-3)
     # are the reference. In dp the column phase weight's clamp leaves kinks
     # (differences move by ~1e-3 between steps 1e-6 and 1e-7), so the dp
     # reference is the difference at step 1e-7 and the bound is the 1e-3 the
-    # method targets.
+    # method targets. precision = 32: FP32 forward and checkpoints (every 100
+    # steps), FP64 reverse; J within 1e-5 of the FP64 oracle's, gradients within
+    # the same 1e-3 of its central differences.
     nx, ny, steps = 512, 128, 2000
     kw = dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5)
     g, l, _ = orc.Setup(nx=nx, ny=ny, dp=1e-3, **kw).coexistence()
 
-    def J(film=6.0, plug=48.0, dp=1e-3):
-        s = orc.Setup(nx=nx, ny=ny, dp=dp, **kw)
-        r0 = synth.airway_rho0(nx, ny, film, 128, plug, l, g, noise=1e-3, seed=1)
-        _, d = orc.run(s, orc.init(s, r0), steps)
-        return np.array([d["J"], d["Jp"]])
+    def J(film=6.0, plug=48.0, dp=1e-3):  # the oracle's (J_tau, J_p), cached over both precisions
+        key = (film, plug, dp)
+        if key not in _AIRWAY_J:
+            s = orc.Setup(nx=nx, ny=ny, dp=dp, **kw)
+            r0 = synth.airway_rho0(nx, ny, film, 128, plug, l, g, noise=1e-3, seed=1)
+            _, d = orc.run(s, orc.init(s, r0), steps)
+            _AIRWAY_J[key] = np.array([d["J"], d["Jp"]])
+        return _AIRWAY_J[key]
 
     import paper_2103_08301_gb300 as lbm
-    with adjm.Adjoint(nx, ny, steps, **kw) as adj:
+    block = 100 if precision == 32 else 0
+    with adjm.Adjoint(nx, ny, steps, precision=precision, block_steps=block, **kw) as adj:
         r0 = synth.airway_rho0(nx, ny, 6.0, 128, 48.0, l, g, noise=1e-3, seed=1)
         Jg = adj.forward(r0, dp=1e-3)
         grads = [adj.backward(1.0, 0.0), adj.backward(0.0, 1.0)]
     ref = J()
-    assert abs(Jg[0] / ref[0] - 1) < 1e-9 and abs(Jg[1] / ref[1] - 1) < 1e-11
+    tol = (1e-9, 1e-11) if precision == 64 else (1e-5, 1e-5)
+    assert abs(Jg[0] / ref[0] - 1) < tol[0] and abs(Jg[1] / ref[1] - 1) < tol[1], (Jg, ref)
     d_film, d_plug = lbm.lbm_airway_rho0_tangent(nx, ny, 6.0, 128, 48.0, l, g)
     h = 1e-3
     fd_film = (J(film=6.0 + h) - J(film=6.0 - h)) / (2 * h)
