@@ -214,14 +214,18 @@ lbm_status lbm_set_collision(lbm_ctx *ctx, const lbm_collision *c);
  *                        thread two rows of its column per iteration (paired
  *                        FP32 instructions) where it applies (staged, and nx a
  *                        multiple of 4 unless x has pressure columns); zero:
- *                        one row per iteration. Both give identical results. */
+ *                        one row per iteration. Both give identical results.
+ *   LBM_OPT_TMA          nonzero (default): the row-pair kernel stages each
+ *                        stencil row with one 2-D tensor (TMA) load; zero:
+ *                        nine bulk copies per row. Identical results. */
 typedef enum {
     LBM_OPT_CTAS_PER_SM = 1,
     LBM_OPT_REVERSE = 2,
     LBM_OPT_STRIP = 3,
     LBM_OPT_STAGED = 4,
     LBM_OPT_GRAPH_STEPS = 5, /* batches only: steps per CUDA graph replay (even, 0 = no graph) */
-    LBM_OPT_ROWS2 = 6
+    LBM_OPT_ROWS2 = 6,
+    LBM_OPT_TMA = 7
 } lbm_option;
 lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value);
 /* Launch geometry of the step kernel: CTAs, threads per CTA, work units and

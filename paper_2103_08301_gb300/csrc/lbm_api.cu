@@ -3,6 +3,9 @@
 // device workspace, kernel launches on the context stream, diagnostics and
 // checkpoints. Every step of the method runs in the kernels of lbm_kernels.cuh.
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled (fetched at run time; no link to the driver library)
+
+#include <mutex>
 
 #include <algorithm>
 #include <cmath>
@@ -93,6 +96,9 @@ struct lbm_ctx {
     bool staged = false;       // bulk-copy staged kernel selected for this grid
     bool allow_rows2 = true;   // LBM_OPT_ROWS2
     bool rows2 = false;        // row-pair FP32 step kernel selected for this grid
+    bool allow_tma = true;     // LBM_OPT_TMA
+    bool tma_ok = false;       // tmap[] encoded (FP32, pitch a multiple of 4)
+    CUtensorMap tmap[2];       // 2-D views of the two population buffers for the row-pair stage
     // fields scratch (allocated on first host-pointer lbm_fields)
     unsigned char *fscratch = nullptr;
     // non-blocking NaN check
@@ -253,6 +259,43 @@ size_t dyn_smem(const lbm_ctx *ctx, int mode)
                                      : lbm::staged_smem_bytes<float>();
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    static std::mutex m;
+    std::lock_guard<std::mutex> lock(m);
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// The 2-D view of one FP32 population buffer that the row-pair stage reads:
+// x = column (pitch wide, stride 4 pitch bytes per y), y = 9 * row + plane;
+// boxes of R2_SP columns by 9 planes (one stencil row), zero fill outside.
+bool encode_population_map(CUtensorMap *map, void *base, int pitch, int ny)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || pitch % 4 != 0) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)9 * (cuuint64_t)ny};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)lbm::R2_SP, 9u};
+    const cuuint32_t elem[2] = {1u, 1u};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int threads_of(const lbm_ctx *ctx, int mode)
 {
     if (mode == lbm::MODE_STEP && ctx->rows2) return lbm::R2_BLOCK;
@@ -324,6 +367,16 @@ template <typename real, int MODE>
 cudaError_t launch(lbm_ctx *ctx, const lbm::KArgs<real> &A)
 {
     void *fn = step_kernel_ptr(ctx, MODE);
+    if (MODE == lbm::MODE_STEP && ctx->rows2) {
+        // the row-pair kernel also takes the tensor map of its source buffer
+        static const CUtensorMap unused{};
+        lbm::KArgs<real> B = A;
+        B.tma = ctx->tma_ok && ctx->allow_tma;
+        const CUtensorMap *m = B.tma ? &ctx->tmap[ctx->cur] : &unused;
+        void *args[] = {(void *)&B, (void *)m};
+        return cudaLaunchKernel(fn, dim3(ctx->nctas), dim3(threads_of(ctx, MODE)), args, dyn_smem(ctx, MODE),
+                                ctx->stream);
+    }
     void *args[] = {(void *)&A};
     return cudaLaunchKernel(fn, dim3(ctx->nctas), dim3(threads_of(ctx, MODE)), args, dyn_smem(ctx, MODE),
                             ctx->stream);
@@ -499,6 +552,9 @@ lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, double
 
     lbm_status st = plan_launch(ctx);
     if (st != LBM_OK) { lbm_free(ctx); return st; }
+    if (grid->precision == 32)
+        ctx->tma_ok = encode_population_map(&ctx->tmap[0], ctx->ws + ctx->L.f0, ctx->pitch, grid->ny) &&
+                      encode_population_map(&ctx->tmap[1], ctx->ws + ctx->L.f1, ctx->pitch, grid->ny);
 
     // Initial state f = f_eq(rho0, 0) in both arrays.
     const size_t N = (size_t)grid->nx * grid->ny;
@@ -707,6 +763,9 @@ lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
     case LBM_OPT_ROWS2:
         ctx->allow_rows2 = value != 0;
         break;
+    case LBM_OPT_TMA:
+        ctx->allow_tma = value != 0;
+        return LBM_OK;
     default:
         return LBM_ERR_ARG;
     }
@@ -755,7 +814,6 @@ void lbm_free(lbm_ctx *ctx)
 // needs - the per-CTA diagnostic partials - in a fixed device array that the
 // library declares at file scope. Nothing is allocated per call.
 // ---------------------------------------------------------------------------
-#include <mutex>
 
 namespace {
 

@@ -628,6 +628,8 @@ lbm_status lbm_batch_set_option(lbm_batch *b, lbm_option opt, int64_t value)
     case LBM_OPT_ROWS2:
         b->allow_rows2 = value != 0;
         break;
+    case LBM_OPT_TMA:
+        return LBM_OK;  // batches stage with bulk copies (one tensor map per channel would be needed)
     case LBM_OPT_GRAPH_STEPS:
         if (value < 0 || (value & 1)) return LBM_ERR_ARG;
         b->graph_steps = (int)value;

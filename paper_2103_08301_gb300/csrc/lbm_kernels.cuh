@@ -28,6 +28,7 @@
 //     launch is a balanced split of (strip, row) units over the CTAs.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the type only; nothing of the driver library is linked)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -63,6 +64,9 @@ struct KArgs {
     // ushift = tau (BGK) or 1/s_j (MRT)
     int mrt;
     real ushift, m_e, m_eps, m_j, m_q, m_nu;
+    // row-pair staged step: 1 = stage rows through the tensor-map kernel
+    // parameter (one 2-D TMA load per row), 0 = plain bulk copies per plane
+    int tma;
     // pressure columns: gas / liquid branch densities at the inlet and outlet
     // pressures, and the phase indicator theta = clamp((rho_f - ph_g) * inv_dph, 0, 1)
     real rho_in_g, rho_in_l, rho_out_g, rho_out_l, ph_g, inv_dph;

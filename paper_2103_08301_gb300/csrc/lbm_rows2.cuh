@@ -38,13 +38,29 @@ constexpr int R2_BLOCK = LBM_R2_BLOCK;
 static_assert(R2_BLOCK % 32 == 0 && R2_BLOCK <= STRIP, "whole warps, at most STRIP lanes");
 constexpr int R2_W = R2_BLOCK - 4;     // widest strip: the lanes cover it and two halo columns per side
 constexpr int R2_SP = R2_BLOCK + 8;    // stage row pitch: strip plus 4 margin columns per side
-constexpr int R2_ROW = 9 * R2_SP;      // one stencil row of nine planes
+// one stencil row of nine planes, padded to a 128-byte multiple so that every
+// row of every slot starts on a 128-byte boundary (tensor copy destinations)
+constexpr int R2_ROW = (9 * R2_SP + 31) / 32 * 32;
 constexpr int R2_SLOT = 2 * R2_ROW;    // one pair of rows
 
 constexpr size_t rows2_smem_bytes()
 {
     return (size_t)R2_SLOTS * R2_SLOT * sizeof(float) + R2_SLOTS * sizeof(uint64_t);
 }
+
+// 2-D tiled tensor load (TMA) of box (x, y) of the tensor map into shared
+// memory, completing on the mbarrier's transaction count. The population
+// maps are 2-D views of a buffer: x = column (pitch wide), y = 9 * row + plane;
+// the box is R2_SP columns by 9 planes, so one load brings a stencil row.
+// Columns outside the array (x < 0 or beyond the pitch) read as zero.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+constexpr uint32_t R2_TMA_ROW_BYTES = 9u * R2_SP * sizeof(float);  // one box
 
 // Position in the pair-slot ring (slot and mbarrier phase parity).
 struct RingPos2 {
@@ -90,7 +106,8 @@ __device__ __forceinline__ float2 stage_pair(const float *slot, int i, int sc)
 template <bool WALLS, bool PRES, bool PADDED>
 __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom<float> &G, int s, int ya, int yb,
                                                SmemR2 &S, float *stages, uint64_t *bars,
-                                               RingPos2 &ring_next, Acc<float, 1> &acc, bool &lost)
+                                               RingPos2 &ring_next, const CUtensorMap *tmap, Acc<float, 1> &acc,
+                                               bool &lost)
 {
     using V = float2;
     constexpr int SW = R2_BLOCK + 4;
@@ -144,9 +161,23 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
     const int dcol = gx0 - x0 + 4;
     const int npairs = (yb - ya + 5) / 2;  // stencil rows ya-2 .. yb+1 in pairs
     RingPos2 ring_issue = ring_next;
+    // tensor loads: the box starts 4 columns left of the strip; strips that
+    // need wrapped halo columns (periodic x, first or last strip) keep the
+    // bulk copies, whose wrap copies would race with a box's zero fill
+    const bool use_tma = tmap != nullptr && !wrapL && !wrapR;
     auto issue = [&](int q) {
         if (q < npairs) {
-            if (tid == PRODUCER) {
+            if (tid == PRODUCER && use_tma) {
+                const uint32_t st = ring_issue.s;
+                mbar_arrive_expect_tx(&bars[st], 2u * R2_TMA_ROW_BYTES);
+                float *slot = stages + (size_t)st * R2_SLOT;
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    bool mir;
+                    const int row = map_row<WALLS>(ya - 2 + 2 * q + t, ny, mir);
+                    tma_load_2d(slot + t * R2_ROW, tmap, x0 - 4, 9 * row, &bars[st]);
+                }
+            } else if (tid == PRODUCER) {
                 const uint32_t st = ring_issue.s;
                 mbar_arrive_expect_tx(&bars[st], 2u * row_bytes);
                 float *slot = stages + (size_t)st * R2_SLOT;
@@ -363,8 +394,10 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
 #ifndef LBM_R2_MIN_BLOCKS
 #define LBM_R2_MIN_BLOCKS (640 / LBM_R2_BLOCK)
 #endif
+// tmap: 2-D tensor map of A.fin (used when A.tma is set)
 template <bool WALLS, bool PRES, bool PADDED>
-__global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS) step_kernel_rows2(const KArgs<float> A)
+__global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS)
+    step_kernel_rows2(const KArgs<float> A, const __grid_constant__ CUtensorMap tmap)
 {
     extern __shared__ __align__(128) unsigned char dsm[];
     float *const stages = reinterpret_cast<float *>(dsm);
@@ -394,7 +427,8 @@ __global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS) step_kernel_rows2
         const long long ue = min(u1, run_end);
         const int yb = ya + (int)(ue - u);
         u = ue;
-        run_segment_r2<WALLS, PRES, PADDED>(A, G, s, ya, yb, S, stages, bars, ring_next, acc, lost);
+        run_segment_r2<WALLS, PRES, PADDED>(A, G, s, ya, yb, S, stages, bars, ring_next, A.tma ? &tmap : nullptr,
+                                            acc, lost);
     }
     if (lost) atomicOr(A.err, 2);
 
@@ -442,7 +476,8 @@ __global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS)
                             ch.rho_in_g, ch.rho_in_l, ch.rho_out_g, ch.rho_out_l};
         Acc<float, 1> acc;
         acc.reset();
-        run_segment_r2<WALLS, PRES, true>(A, G, sg.strip, sg.ya, sg.yb, S, stages, bars, ring_next, acc, lost);
+        run_segment_r2<WALLS, PRES, true>(A, G, sg.strip, sg.ya, sg.yb, S, stages, bars, ring_next, nullptr, acc,
+                                          lost);
         double m, j;
         float e[4];
         bool anybad;

@@ -267,6 +267,28 @@ def test_row_pair_and_one_row_kernels_agree_bitwise(orc, lbm, name, ctas_per_sm)
         1e-9 * abs(out[1][2]["wall_shear_sum"]) + 1e-15
 
 
+@pytest.mark.parametrize("case", ["airway", "periodic"])
+def test_tensor_map_stage_matches_bulk_copies_bitwise(orc, lbm, case):
+    """The row-pair stage loaded by 2-D tensor (TMA) loads and by per-plane
+    bulk copies: the same populations bit for bit. Periodic x: the interior
+    strips take tensor loads, the two end strips (wrapped halos) bulk copies."""
+    if case == "airway":
+        nx, ny, kw = 512, 128, dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=1e-3)
+        rho0 = _airway(orc, nx, ny, 6, 128, 48)
+    else:
+        nx, ny, kw = 512, 64, dict(walls=False, bc_x=False, T_over_Tc=0.8, kappa=0.5)
+        g, l, _ = orc.Setup(nx=nx, ny=ny, **kw).coexistence()
+        rho0 = synth.disk_rho0(nx, ny, 20, l, g, noise=1e-3, seed=4, centre=(125.0, 30.0))
+    out = []
+    for tma in (1, 0):
+        with lbm.Lattice(nx, ny, rho0, precision=32, **kw) as lat:
+            lat.set_option(lbm.LBM_OPT_TMA, tma)
+            lat.step(150)
+            out.append((lat.populations(), lat.diag()))
+    assert np.array_equal(out[0][0].view(np.uint32), out[1][0].view(np.uint32))
+    assert out[0][1]["mass"] == out[1][1]["mass"]
+
+
 def test_checkpoint_restore_continues_bitwise(orc, lbm):
     rho0 = _airway(orc, 320, 64, 5, 100, 40)
     kw = dict(walls=True, bc_x=True, precision=32, T_over_Tc=0.85, kappa=0.5, dp=1e-3)
