@@ -12,6 +12,12 @@
 //     divergent halo duty (which cost 8% as a one-warp duty); the stage holds
 //     each stencil row with a four-column margin on both sides (columns
 //     x0-4 .. x0+W+3), so the halo densities are summed from shared memory;
+//   - one producer thread stages each stencil row with a single 2-D tensor
+//     (TMA) load of 132 columns by 9 planes (cp.async.bulk.tensor through
+//     the tensor-map kernel parameter); strips whose halo wraps around a
+//     periodic x take nine plane copies and the wrap copies instead (plain
+//     cp.async.bulk), and so does the batch kernel. Nine copies per row in
+//     place of one load cost 7% of the step;
 //   - every thread waits on the stage's mbarrier itself, so a pair issued
 //     half an iteration before it is read needs no publishing barrier; three
 //     pair slots (six rows) suffice.
