@@ -215,9 +215,10 @@ lbm_status lbm_set_collision(lbm_ctx *ctx, const lbm_collision *c);
  *                        FP32 instructions) where it applies (staged, and nx a
  *                        multiple of 4 unless x has pressure columns); zero:
  *                        one row per iteration. Both give identical results.
- *   LBM_OPT_TMA          nonzero (default): the row-pair kernel stages each
- *                        stencil row with one 2-D tensor (TMA) load; zero:
- *                        nine bulk copies per row. Identical results. */
+ *   LBM_OPT_TMA          nonzero (default for contexts, zero for batches):
+ *                        the row-pair kernel stages each stencil row with one
+ *                        2-D tensor (TMA) load; zero: nine bulk copies per
+ *                        row. Identical results. */
 typedef enum {
     LBM_OPT_CTAS_PER_SM = 1,
     LBM_OPT_REVERSE = 2,

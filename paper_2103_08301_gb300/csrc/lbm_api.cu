@@ -460,6 +460,12 @@ struct CkptHeader {
 
 } // namespace
 
+bool lbm_encode_population_map(CUtensorMap *map, void *base, int pitch, int ny)
+{
+    return encode_population_map(map, base, pitch, ny);
+}
+
+
 extern "C" {
 
 const char *lbm_status_string(lbm_status s)

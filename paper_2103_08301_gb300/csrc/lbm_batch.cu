@@ -60,6 +60,10 @@ struct lbm_batch {
     int sms = 0, nctas = 0, nseg = 0, ctas_per_sm_opt = 0, W_opt = 0, reverse = 0;
     bool allow_staged = true, staged = false;
     bool allow_rows2 = true, rows2 = false;  // LBM_OPT_ROWS2: row-pair FP32 step
+    // LBM_OPT_TMA (off by default for batches: reading 2n maps from device
+    // memory made the 64-channel sweep 4% slower than plane copies); d_tmaps encoded
+    bool allow_tma = false, tma_ok = false;
+    CUtensorMap *d_tmaps = nullptr;          // [2][n]: tensor maps of each buffer's channels (FP32)
     void *d_chan = nullptr;
     lbm::BatchSeg *d_segs = nullptr;
     int *d_cta_begin = nullptr;
@@ -291,8 +295,10 @@ cudaError_t batch_launch(lbm_batch *b)
     A.fout = reinterpret_cast<real *>(b->pop[1 - b->cur]);
     const lbm::BatchChan<real> *chans = static_cast<const lbm::BatchChan<real> *>(b->d_chan);
     real *ext = static_cast<real *>(b->d_seg_ext);
+    // the row-pair kernel takes one more argument: the source buffer's tensor maps
+    const CUtensorMap *tm = b->tma_ok && b->allow_tma ? b->d_tmaps + (size_t)b->cur * b->n : nullptr;
     void *args[] = {(void *)&A, (void *)&chans, (void *)&b->d_segs, (void *)&b->d_cta_begin,
-                    (void *)&b->d_seg_mass, (void *)&b->d_seg_J, (void *)&ext};
+                    (void *)&b->d_seg_mass, (void *)&b->d_seg_J, (void *)&ext, b->rows2 ? (void *)&tm : nullptr};
     return cudaLaunchKernel(batch_kernel(b), dim3(b->nctas), dim3(step_threads(b)), args, step_smem(b), b->stream);
 }
 
@@ -500,6 +506,23 @@ lbm_status lbm_batch_init(int32_t n, const lbm_grid *grids, const lbm_eos *eos, 
         lbm_batch_free(b);
         return s;
     }
+    if (b->precision == 32) {
+        // tensor maps of every channel in both buffers, for the row-pair stage
+        std::vector<CUtensorMap> maps((size_t)2 * n);
+        bool ok = true;
+        for (int k = 0; k < 2 && ok; ++k)
+            for (int i = 0; i < n && ok; ++i) {
+                const ChanHost &c = b->ch[i];
+                ok = lbm_encode_population_map(&maps[(size_t)k * n + i], (float *)b->pop[k] + c.off, c.pitch,
+                                               c.grid.ny);
+            }
+        if (ok && cudaMalloc((void **)&b->d_tmaps, maps.size() * sizeof(CUtensorMap)) == cudaSuccess &&
+            cudaMemcpy(b->d_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice) ==
+                cudaSuccess)
+            b->tma_ok = true;
+        else
+            cudaGetLastError();  // plane copies instead
+    }
     lbm_status s = batch_plan(b);
     if (s == LBM_OK) s = upload_chan_table(b);
     if (s != LBM_OK) { lbm_batch_free(b); return s; }
@@ -629,7 +652,9 @@ lbm_status lbm_batch_set_option(lbm_batch *b, lbm_option opt, int64_t value)
         b->allow_rows2 = value != 0;
         break;
     case LBM_OPT_TMA:
-        return LBM_OK;  // batches stage with bulk copies (one tensor map per channel would be needed)
+        b->allow_tma = value != 0;
+        if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }  // captured arguments
+        return LBM_OK;
     case LBM_OPT_GRAPH_STEPS:
         if (value < 0 || (value & 1)) return LBM_ERR_ARG;
         b->graph_steps = (int)value;
@@ -729,6 +754,7 @@ void lbm_batch_free(lbm_batch *b)
     if (b->graph) cudaGraphExecDestroy(b->graph);
     cudaFree(b->pop[0]);
     cudaFree(b->pop[1]);
+    cudaFree(b->d_tmaps);
     cudaFree(b->d_chan);
     cudaFree(b->d_segs);
     cudaFree(b->d_cta_begin);

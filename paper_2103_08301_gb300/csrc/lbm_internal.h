@@ -1,6 +1,10 @@
 // Declarations shared by the host translation units of the solver library.
 #pragma once
 
+#ifdef __CUDACC__
+#include <cuda.h>  // CUtensorMap
+#endif
+
 #include <cstdint>
 
 #include "lbm.h"
@@ -71,6 +75,10 @@ inline int strip_width(int nx, int w_max, bool bc_x)
 // and without synchronising (the public lbm_populations / lbm_load_populations
 // convert to the plane-major ABI layout and synchronise). lbm_api.cu.
 #ifdef __CUDACC__
+// 2-D tensor map of one FP32 population array (pitch wide, 9 * ny plane-rows)
+// in the form the row-pair stage loads it (lbm_api.cu); false if the driver
+// entry point is unavailable or the layout does not qualify.
+bool lbm_encode_population_map(CUtensorMap *map, void *base, int pitch, int ny);
 cudaError_t lbm_ctx_copy_state(lbm_ctx *ctx, void *dst);
 const void *lbm_ctx_state(const lbm_ctx *ctx);  // the current state buffer itself (device)
 cudaError_t lbm_ctx_load_state(lbm_ctx *ctx, const void *src);

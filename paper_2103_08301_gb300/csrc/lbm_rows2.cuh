@@ -16,7 +16,9 @@
 //     (TMA) load of 132 columns by 9 planes (cp.async.bulk.tensor through
 //     the tensor-map kernel parameter); strips whose halo wraps around a
 //     periodic x take nine plane copies and the wrap copies instead (plain
-//     cp.async.bulk), and so does the batch kernel. Nine copies per row in
+//     cp.async.bulk). The batch kernel can read its channels' maps from
+//     device memory, but by default it takes the plane copies (faster there:
+//     58.9k against 56.3k MLUPS on the 64-channel sweep). Nine copies per row in
 //     place of one load cost 7% of the step;
 //   - every thread waits on the stage's mbarrier itself, so a pair issued
 //     half an iteration before it is read needs no publishing barrier; three
@@ -455,11 +457,14 @@ __global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS)
 // Batched channels with the row-pair step: as batch_step_kernel, every
 // segment of the work list through run_segment_r2 (padded-pitch body, since
 // the channels of a batch mix pitches), one reduction slot per segment.
+// tmaps: NULL (plane copies) or the tensor maps of the source buffer, one per
+// channel, in device memory (written by the host before the launch).
 template <bool WALLS, bool PRES>
 __global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS)
     batch_step_kernel_rows2(const KArgs<float> A, const BatchChan<float> *__restrict__ chans,
                             const BatchSeg *__restrict__ segs, const int *__restrict__ cta_begin,
-                            double *__restrict__ seg_mass, double *__restrict__ seg_J, float *__restrict__ seg_ext)
+                            double *__restrict__ seg_mass, double *__restrict__ seg_J, float *__restrict__ seg_ext,
+                            const CUtensorMap *__restrict__ tmaps)
 {
     extern __shared__ __align__(128) unsigned char dsm[];
     float *const stages = reinterpret_cast<float *>(dsm);
@@ -482,8 +487,8 @@ __global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS)
                             ch.rho_in_g, ch.rho_in_l, ch.rho_out_g, ch.rho_out_l};
         Acc<float, 1> acc;
         acc.reset();
-        run_segment_r2<WALLS, PRES, true>(A, G, sg.strip, sg.ya, sg.yb, S, stages, bars, ring_next, nullptr, acc,
-                                          lost);
+        run_segment_r2<WALLS, PRES, true>(A, G, sg.strip, sg.ya, sg.yb, S, stages, bars, ring_next,
+                                          tmaps ? tmaps + sg.chan : nullptr, acc, lost);
         double m, j;
         float e[4];
         bool anybad;

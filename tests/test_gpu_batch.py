@@ -153,3 +153,23 @@ def test_batch_row_pair_kernel_matches_one_row_kernel(orc, lbm, specs, kw):
         assert abs(m0 - m1) <= 1e-12 * m1, c
         j0, j1 = outs[0][c][1]["wall_shear_sum"], outs[1][c][1]["wall_shear_sum"]
         assert abs(j0 - j1) <= 1e-9 * abs(j1) + 1e-15, c
+
+
+@pytest.mark.parametrize("specs,kw", [(RAGGED_SPECS, KW),
+                                      (PERIODIC_SPECS, dict(walls=True, bc_x=False, T_over_Tc=0.85, kappa=0.5))])
+def test_batch_tensor_map_stage_matches_bulk_copies(orc, lbm, specs, kw):
+    """The batch's row-pair stage through per-channel tensor maps and through
+    plane copies: populations and diagnostics bit for bit (same kernel body,
+    same work list)."""
+    chans = _channels(orc, specs)
+    for ch in chans:
+        ch["gx"] = 2e-6 if not kw["bc_x"] else 0.0
+    outs = []
+    for tma in (1, 0):
+        with lbm.Batch(chans, precision=32, **kw) as b:
+            b.set_option(lbm.LBM_OPT_TMA, tma)
+            b.step(130)
+            outs.append([(b.populations(c), b.diag(c)) for c in range(len(chans))])
+    for c in range(len(chans)):
+        assert np.array_equal(outs[0][c][0].view(np.uint32), outs[1][c][0].view(np.uint32)), f"channel {c}"
+        assert outs[0][c][1]["mass"] == outs[1][c][1]["mass"], c
