@@ -45,7 +45,10 @@ constexpr int R2_SLOTS = 3;            // pair slots of the stage ring
 constexpr int R2_BLOCK = LBM_R2_BLOCK;
 static_assert(R2_BLOCK % 32 == 0 && R2_BLOCK <= STRIP, "whole warps, at most STRIP lanes");
 constexpr int R2_W = R2_BLOCK - 4;     // widest strip: the lanes cover it and two halo columns per side
-constexpr int R2_SP = R2_BLOCK + 8;    // stage row pitch: strip plus 4 margin columns per side
+// stage row pitch and tensor box width: columns x0-4 .. x0+R2_BLOCK-1, i.e. a
+// strip of up to R2_W columns with 4 margin columns on each side (the bulk
+// path's right wrap copy ends at xw + 7 <= R2_BLOCK + 3)
+constexpr int R2_SP = R2_BLOCK + 4;
 // one stencil row of nine planes, padded to a 128-byte multiple so that every
 // row of every slot starts on a 128-byte boundary (tensor copy destinations)
 constexpr int R2_ROW = (9 * R2_SP + 31) / 32 * 32;
