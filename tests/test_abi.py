@@ -153,3 +153,24 @@ def test_pr_coexistence_helper_matches_oracle(lbm, orc):
         g2, l2, p2 = s.coexistence()
         assert abs(Tc / (s.T / tr) - 1) < 1e-12
         assert abs(g / g2 - 1) < 1e-10 and abs(l / l2 - 1) < 1e-12 and abs(p / p2 - 1) < 1e-10
+
+
+def test_binding_constants_match_header_enums(lbm):
+    """Every enumerator of include/lbm.h that the binding exports has the
+    header's value (options, statuses, EOS and collision kinds)."""
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "lbm.h")).read(), flags=re.S)
+    found = 0
+    for body in re.findall(r"typedef\s+enum\s*\{(.*?)\}", text, flags=re.S):
+        value = -1
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            m = re.match(r"(LBM_[A-Z0-9_]+)\s*(?:=\s*(-?\d+))?$", item)
+            assert m, item
+            value = int(m.group(2)) if m.group(2) is not None else value + 1
+            if hasattr(lbm, m.group(1)):
+                assert getattr(lbm, m.group(1)) == value, m.group(1)
+                found += 1
+    assert found >= 15
+    assert (lbm.LBM_OPT_ROWS2, lbm.LBM_OPT_TMA) == (6, 7)
