@@ -12,6 +12,9 @@ in the C source.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 (closed forms, library routines, physics laws); none is "parity unpinned".
+The boundary arithmetic (pressure-column branch roots, spinodal saturation,
+the column density blend and extrapolation, the kappa terms of the wall
+pressure, the wetting offset) is pinned in ``tests/test_oracle_boundaries.py``.
 """
 from __future__ import annotations
 
