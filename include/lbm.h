@@ -239,31 +239,38 @@ lbm_status lbm_launch_info(const lbm_ctx *ctx, int64_t *ctas, int64_t *threads, 
  * callers that cannot call cudaMalloc where they step: code running inside
  * another framework's memory pool (a raw allocation would bypass the pool's
  * accounting and limits), or a host that sizes every device buffer up front.
+ * The collision is always BGK (the lbm_init default); MRT needs a context.
  *   grid, eos, tau, wetting, drive: as for lbm_init (drive may be NULL).
  *   f_in, f_out: distinct caller-owned device arrays of 9*nx*ny values of the
  *            grid precision in the library's row-interleaved layout f[y][i][x]
- *            (index (9*y + i)*nx + x). f_out receives the next state;
- *            slots no population reaches (solid rows, the inflow slots of
- *            pressure columns) are left untouched, so initialise f_out from
- *            f_in if those must be defined.
+ *            (index (9*y + i)*nx + x), each aligned to its element size
+ *            (LBM_ERR_ARG otherwise). Buffers that start on a 16-byte boundary
+ *            (and nx a multiple of 4) take the staged kernels; others take
+ *            the register-prefetch kernel, with identical results.
+ *            f_out receives the next state; slots no population reaches
+ *            (solid rows, the inflow slots of pressure columns) are left
+ *            untouched, so initialise f_out from f_in if those must be defined.
  *   ctas:    CTAs of the step grid, 0 = as lbm_step chooses; at most 4096.
- *   diag_out: NULL or a device array of 7 doubles receiving, for the state
- *            f_in: mass, wall-shear sum, tau_w min/max, p_w min/max, and a
- *            nonzero flag if a bad density was met.
+ *   diag_out: NULL or a device array of 7 doubles (8-byte aligned) receiving,
+ *            for the state f_in: mass, wall-shear sum, tau_w min/max,
+ *            p_w min/max, and the error word of the step (below).
+ *   err_out: NULL or a device int32 receiving the error word of the step:
+ *            bit 0 = a bad (non-finite or non-positive) density was met,
+ *            bit 1 = a bounded wait for a staged population row gave up
+ *            (f_out is then not valid). Written asynchronously on `stream`.
  *   stream:  cudaStream_t (NULL = legacy default stream); the call only
  *            enqueues work and does not synchronise.
- * Scratch: the per-CTA partials live in one static device array (about
- * 192 KB) that the library holds on every device it is used on until the
- * process exits. Every call reuses and first clears it, so calls whose work
- * overlaps on the GPU (for instance on different streams) race on it;
- * serialise them. The first call on a device resolves the
- * array's device address (cudaGetSymbolAddress) and should come before any
- * stream capture.
- * Errors: LBM_ERR_ARG (bad grid, NULL or equal buffers, ctas outside
- * 0..4096), LBM_ERR_PARAM, LBM_ERR_CUDA. */
+ * Scratch: the per-CTA partials and the error word live in one static device
+ * array (about 192 KB) that the library holds on every device it is used on
+ * until the process exits. Every call reuses and first clears it, so calls
+ * whose work overlaps on the GPU (for instance on different streams) race on
+ * it; serialise them. The first call on a device resolves the array's device
+ * address (cudaGetSymbolAddress) and should come before any stream capture.
+ * Errors: LBM_ERR_ARG (bad grid, NULL, equal or misaligned buffers, ctas
+ * outside 0..4096), LBM_ERR_PARAM, LBM_ERR_CUDA. */
 lbm_status lbm_step_noalloc(const lbm_grid *grid, const lbm_eos *eos, double tau, double wetting,
                             const lbm_drive *drive, const void *f_in, void *f_out, int64_t ctas,
-                            double *diag_out, void *stream);
+                            double *diag_out, int32_t *err_out, void *stream);
 
 /* Release everything the library allocated. NULL-safe. */
 void lbm_free(lbm_ctx *ctx);

@@ -79,7 +79,7 @@ _SIGS = {
     "lbm_set_collision": (C.c_int, [_P, C.POINTER(lbm_collision)]),
     "lbm_launch_info": (C.c_int, [_P] + [C.POINTER(C.c_int64)] * 4),
     "lbm_step_noalloc": (C.c_int, [C.POINTER(lbm_grid), C.POINTER(lbm_eos), C.c_double, C.c_double,
-                                   C.POINTER(lbm_drive), _P, _P, C.c_int64, _P, _P]),
+                                   C.POINTER(lbm_drive), _P, _P, C.c_int64, _P, _P, _P]),
     "lbm_batch_init": (C.c_int, [C.c_int32, C.POINTER(lbm_grid), C.POINTER(lbm_eos), C.c_double, C.c_double,
                                  C.POINTER(lbm_drive), C.POINTER(C.POINTER(C.c_double)), _P, C.POINTER(_P)]),
     "lbm_batch_step": (C.c_int, [_P, C.c_int64]),
@@ -180,12 +180,13 @@ def lbm_step(ctx, n: int) -> int:
 
 
 def lbm_step_noalloc(grid, eos, tau, wetting, drive, f_in_ptr, f_out_ptr, ctas=0, diag_ptr=None,
-                     stream=None) -> int:
+                     stream=None, err_ptr=None) -> int:
     """One step between caller-owned device buffers (raw pointers); returns the status."""
     return int(lib().lbm_step_noalloc(C.byref(grid), C.byref(eos), float(tau), float(wetting),
                                       C.byref(drive) if drive is not None else None,
                                       _P(f_in_ptr), _P(f_out_ptr), int(ctas),
-                                      _P(diag_ptr) if diag_ptr else None, _P(stream) if stream else None))
+                                      _P(diag_ptr) if diag_ptr else None, _P(err_ptr) if err_ptr else None,
+                                      _P(stream) if stream else None))
 
 
 class lbm_plug_state(C.Structure):

@@ -813,12 +813,13 @@ void lbm_free(lbm_ctx *ctx)
 // Allocation-free single step.
 //
 // Some callers cannot allocate device memory at the point where they step the
-// lattice: code running inside another framework's memory pool, an
-// embedded host that pre-sizes every buffer up front, or a caller about to
-// record its work into a CUDA graph. This entry point performs one step
-// between two caller-owned population buffers and keeps the only scratch it
-// needs - the per-CTA diagnostic partials - in a fixed device array that the
-// library declares at file scope. Nothing is allocated per call.
+// lattice: code running inside another framework's memory pool (a raw
+// allocation would bypass the pool's accounting and limits), or an embedded
+// host that sizes every device buffer up front. This entry point performs one
+// step between two caller-owned population buffers and keeps the only scratch
+// it needs - the per-CTA diagnostic partials and the error word - in a fixed
+// device array that the library declares at file scope. Nothing is allocated
+// per call.
 // ---------------------------------------------------------------------------
 
 namespace {
@@ -866,7 +867,8 @@ cudaError_t noalloc_scratch(NoallocScratch **out)
 }
 
 template <typename real>
-lbm_status noalloc_launch(lbm_ctx *c, NoallocScratch *sc, const void *f_in, void *f_out, double *diag_out)
+lbm_status noalloc_launch(lbm_ctx *c, NoallocScratch *sc, const void *f_in, void *f_out, double *diag_out,
+                          int32_t *err_out)
 {
     real *ext = reinterpret_cast<real *>(sc->ext);
     lbm::reset_acc_kernel<real><<<(c->nctas + 255) / 256, 256, 0, c->stream>>>(sc->mass, sc->J, ext, &sc->err,
@@ -883,6 +885,8 @@ lbm_status noalloc_launch(lbm_ctx *c, NoallocScratch *sc, const void *f_in, void
     if (diag_out)
         lbm::diag_kernel<real><<<1, 256, 0, c->stream>>>(sc->mass, sc->J, ext, &sc->err, c->nctas, diag_out);
     e = cudaGetLastError();
+    if (e == cudaSuccess && err_out)
+        e = cudaMemcpyAsync(err_out, &sc->err, sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
     return e == cudaSuccess ? LBM_OK : cuda_fail(nullptr, e, "noalloc launch");
 }
 
@@ -890,10 +894,16 @@ lbm_status noalloc_launch(lbm_ctx *c, NoallocScratch *sc, const void *f_in, void
 
 extern "C" lbm_status lbm_step_noalloc(const lbm_grid *grid, const lbm_eos *eos, double tau,
                                        double wetting, const lbm_drive *drive, const void *f_in,
-                                       void *f_out, int64_t ctas, double *diag_out, void *stream)
+                                       void *f_out, int64_t ctas, double *diag_out, int32_t *err_out,
+                                       void *stream)
 {
     if (!grid_ok(grid) || !eos || !f_in || !f_out || f_in == f_out) return LBM_ERR_ARG;
     if (ctas < 0 || ctas > NOALLOC_MAX_CTAS) return LBM_ERR_ARG;
+    // buffers must hold whole values of the grid precision; the staged kernels
+    // also need 16-byte aligned rows (checked below)
+    const uintptr_t esz = grid->precision == 64 ? 8 : 4;
+    if (((uintptr_t)f_in | (uintptr_t)f_out) % esz != 0) return LBM_ERR_ARG;
+    if (((uintptr_t)diag_out) % 8 != 0 || ((uintptr_t)err_out) % 4 != 0) return LBM_ERR_ARG;
     if (!(tau > 0.5) || !(eos->k > 0) || !(eos->kappa >= 0) || !(eos->a > 0) || !(eos->b > 0) ||
         !(eos->R > 0) || !(eos->T_over_Tc > 0) || !std::isfinite(wetting))
         return LBM_ERR_PARAM;
@@ -912,6 +922,11 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_grid *grid, const lbm_eos *eos,
     c.tau = tau;
     c.wet = wetting;
     c.stream = static_cast<cudaStream_t>(stream);
+    // The staged kernels copy population rows with bulk asynchronous copies,
+    // which need 16-byte aligned addresses: a caller buffer that does not start
+    // on a 16-byte boundary (a view with an element offset) takes the register-
+    // prefetch kernel, which gives identical results.
+    if (((uintptr_t)f_in | (uintptr_t)f_out) % 16 != 0) c.allow_staged = false;
     lbm::ChannelThermo ct;
     if (lbm::channel_thermo(*eos, c.drive, grid->bc_x, &ct)) return LBM_ERR_PARAM;
     c.th = ct.th;
@@ -927,6 +942,6 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_grid *grid, const lbm_eos *eos,
     if (ctas > 0) c.nctas = (int)std::min<long long>(ctas, std::max<long long>(1, c.units / 2));
     c.nctas = std::min(c.nctas, NOALLOC_MAX_CTAS);
     c.band = band_rows(c.nyf, c.nstrips, c.nctas, c.grid.walls);
-    return grid->precision == 64 ? noalloc_launch<double>(&c, sc, f_in, f_out, diag_out)
-                                 : noalloc_launch<float>(&c, sc, f_in, f_out, diag_out);
+    return grid->precision == 64 ? noalloc_launch<double>(&c, sc, f_in, f_out, diag_out, err_out)
+                                 : noalloc_launch<float>(&c, sc, f_in, f_out, diag_out, err_out);
 }

@@ -174,3 +174,17 @@ def test_binding_constants_match_header_enums(lbm):
                 found += 1
     assert found >= 15
     assert (lbm.LBM_OPT_ROWS2, lbm.LBM_OPT_TMA) == (6, 7)
+
+
+def test_noalloc_rejects_misaligned_buffers_without_a_launch(lbm):
+    # pointers that do not hold whole values of the grid precision are refused
+    # during argument checking, before any CUDA call (this runs without a GPU)
+    g = lbm.lbm_grid(64, 32, 1, 0, 32)
+    g64 = lbm.lbm_grid(64, 32, 1, 0, 64)
+    e = lbm.lbm_eos(1.0, 4.0, 1.0, 0.8, 1.0, 0.5)
+    good, bad2, bad4 = 0x10000, 0x20002, 0x30004
+    assert lbm.lbm_step_noalloc(g, e, 1.0, 0.0, None, bad2, good, 0) == lbm.LBM_ERR_ARG
+    assert lbm.lbm_step_noalloc(g, e, 1.0, 0.0, None, good, bad2, 0) == lbm.LBM_ERR_ARG
+    assert lbm.lbm_step_noalloc(g64, e, 1.0, 0.0, None, bad4, good, 0) == lbm.LBM_ERR_ARG
+    assert lbm.lbm_step_noalloc(g, e, 1.0, 0.0, None, good, 0x40000, 0, diag_ptr=bad4) == lbm.LBM_ERR_ARG
+    assert lbm.lbm_step_noalloc(g, e, 1.0, 0.0, None, good, 0x40000, 0, err_ptr=bad2) == lbm.LBM_ERR_ARG
