@@ -51,7 +51,7 @@ class Params(C.Structure):
                 ("gx", C.c_double), ("gy", C.c_double),
                 ("eos_kind", C.c_int32), ("collision", C.c_int32), ("aalpha", C.c_double),
                 ("s_e", C.c_double), ("s_eps", C.c_double), ("s_j", C.c_double), ("s_q", C.c_double),
-                ("s_nu", C.c_double)]
+                ("s_nu", C.c_double), ("mask", C.c_void_p)]
 
 
 class Eos(C.Structure):
@@ -288,6 +288,7 @@ class Setup:
     s_q: float = 1.7
     s_j: float = 1.0
     s_nu: float | None = None
+    mask: np.ndarray | None = None  # (ny, nx), nonzero = solid node (general wall geometry)
     T: float = field(init=False)
     aalpha: float = field(init=False, default=0.0)
     rho_in: float = field(init=False, default=0.0)    # gas-branch column densities
@@ -301,6 +302,9 @@ class Setup:
         return Eos(EOS_KINDS[self.eos], self.a, self.b, self.R, self.T, self.aalpha)
 
     def __post_init__(self):
+        if self.mask is not None:
+            self.mask = np.ascontiguousarray(np.asarray(self.mask) != 0, dtype=np.uint8)
+            assert self.mask.shape == (self.ny, self.nx)
         Tc, _ = eos_critical(self.eos, self.a, self.b, self.R)
         self.T = self.T_over_Tc * Tc
         if self.eos == "pr":
@@ -333,7 +337,8 @@ class Setup:
                       self.T, self.k, self.kappa, self.tau, self.wet, self.rho_in, self.rho_in_l,
                       self.rho_out, self.rho_out_l, self.ph_g, self.ph_l, self.gx, self.gy,
                       EOS_KINDS[self.eos], int(self.collision == "mrt"), self.aalpha,
-                      self.s_e, self.s_eps, self.s_j, self.s_q, s_nu)
+                      self.s_e, self.s_eps, self.s_j, self.s_q, s_nu,
+                      None if self.mask is None else self.mask.ctypes.data)
 
 
 def init(setup: Setup, rho0: np.ndarray) -> np.ndarray:

@@ -19,6 +19,7 @@
  *   6. collision      BGK with u_eq = u + tau F / rho                  (Eq. 2.2, Sec. 2.1)
  *   7. pressure cols  non-equilibrium extrapolation at rho_b           (Sec. 2.2)
  *   8. streaming      f_i(x + e_i) = f*_i(x), half-way bounce-back     (Eq. 2.1, Sec. 2.2)
+ *                     at wall rows and at the nodes of an optional solid mask
  *   9. diagnostics    mass, wall shear, wall pressure (Eq. 2.4)        (Sec. 3, Fig. 3)
  *
  * Where the paper is silent or garbled, the reading taken is written next to
@@ -70,6 +71,11 @@ typedef struct {
      * shifts the equilibrium velocity by F / (s_j rho), so the relaxed
      * momentum gains F per step; s_j = 1/tau with every rate 1/tau is BGK. */
     double s_e, s_eps, s_j, s_q, s_nu;
+    /* Optional per-node solid mask (nx*ny bytes, 1 = solid), the general wall
+     * geometry of the library's lbm_init; NULL: only the rows that 'walls'
+     * makes solid. With a mask, stencil reads of solid points take the ghost
+     * densities of mask_ghost() below. */
+    const uint8_t *mask;
 } orc_params;
 
 typedef struct {
@@ -546,6 +552,75 @@ static int is_pressure_col(const orc_params *p, int x)
     return p->bc_x && (x == 0 || x == p->nx - 1);
 }
 
+/* Solid lattice node: a wall row, or a node the mask marks. */
+static int is_solid(const orc_params *p, int x, int y)
+{
+    return is_solid_row(p, y) || (p->mask && p->mask[(long)y * p->nx + x]);
+}
+
+/* Maps an integer point onto the lattice (periodic axes wrap, x beyond a
+ * pressure column clamps to the column); returns 0 for rows outside a walled
+ * lattice, which count as solid. */
+static int map_point(const orc_params *p, int *x, int *y)
+{
+    if (p->bc_x) { if (*x < 0) *x = 0; if (*x > p->nx - 1) *x = p->nx - 1; }
+    else *x = (int)pmod(*x, p->nx);
+    if (p->walls) { if (*y < 0 || *y > p->ny - 1) return 0; }
+    else *y = (int)pmod(*y, p->ny);
+    return 1;
+}
+
+static int fluid_point(const orc_params *p, int x, int y)
+{
+    return map_point(p, &x, &y) && !is_solid(p, x, y);
+}
+
+/* Ghost density of a solid point (x, y) for the stencils of nearby fluid
+ * nodes, with a mask (the paper gives no rule for general geometry; this is
+ * the mirror rule of flat walls, generalised):
+ *   - along the four axis directions n, the depth d of the first fluid point
+ *     x + d n, d <= 2; the directions of least depth each give one mirror
+ *     source: x + (2d - 1) n (the point as deep in front of the wall as x is
+ *     behind it) if it is fluid, else x + d n;
+ *   - no axis direction within depth 2: the four diagonals, likewise;
+ *   - none either: the fluid points at knight offsets (1, 2), (2, 1), ...;
+ *   - ghost = mean of the sources' densities + the wetting offset 'wet'.
+ * A flat wall reduces to the channel rule: depth 1 mirrors the first fluid
+ * row, depth 2 the second. Points with no fluid point within Chebyshev
+ * distance 2 feed no fluid node's stencil and read 0. */
+static double mask_ghost(const orc_params *p, const double *rho, int x, int y)
+{
+    static const int axis[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
+    static const int diag[4][2] = {{1, 1}, {-1, 1}, {-1, -1}, {1, -1}};
+    static const int knight[8][2] = {{1, 2}, {2, 1}, {-1, 2}, {-2, 1}, {-1, -2}, {-2, -1}, {1, -2}, {2, -1}};
+    double sum = 0.0;
+    int n = 0;
+    for (int set = 0; set < 2 && n == 0; ++set) {
+        const int (*dir)[2] = set == 0 ? axis : diag;
+        for (int d = 1; d <= 2 && n == 0; ++d)
+            for (int k = 0; k < 4; ++k) {
+                int dx = dir[k][0], dy = dir[k][1];
+                if (!fluid_point(p, x + d * dx, y + d * dy)) continue;
+                if (d == 2 && fluid_point(p, x + dx, y + dy)) continue;
+                int sx = x + (2 * d - 1) * dx, sy = y + (2 * d - 1) * dy;
+                if (!fluid_point(p, sx, sy)) { sx = x + d * dx; sy = y + d * dy; }
+                map_point(p, &sx, &sy);
+                sum += rho[(long)sy * p->nx + sx];
+                n += 1;
+            }
+    }
+    if (n == 0)
+        for (int k = 0; k < 8; ++k) {
+            int sx = x + knight[k][0], sy = y + knight[k][1];
+            if (!fluid_point(p, sx, sy)) continue;
+            map_point(p, &sx, &sy);
+            sum += rho[(long)sy * p->nx + sx];
+            n += 1;
+        }
+    if (n == 0) return 0.0;
+    return sum / n + p->wet;
+}
+
 /* Density of a pressure column at a row whose interior neighbour has density
  * rho_f (see orc_params). */
 static double column_density(const orc_params *p, int outlet, double rho_f)
@@ -573,6 +648,11 @@ static double rho_ghost(const orc_params *p, const double *rho, int x, int y)
 {
     int nx = p->nx, ny = p->ny;
     double add = 0.0;
+    if (p->mask) {
+        int mx = x, my = y;
+        if (map_point(p, &mx, &my) && !is_solid(p, mx, my)) return rho[(long)my * nx + mx];
+        return mask_ghost(p, rho, x, y);
+    }
     if (p->walls) {
         if (y <= 0) { y = 1 - y; add = p->wet; }
         else if (y >= ny - 1) { y = 2 * ny - 3 - y; add = p->wet; }
@@ -631,7 +711,7 @@ static void fields_and_force(const orc_params *p, const double *f, orc_work *w)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             long c = (long)y * nx + x;
-            if (is_solid_row(p, y)) { w->rho[c] = 0.0; w->ux[c] = w->uy[c] = 0.0; continue; }
+            if (is_solid(p, x, y)) { w->rho[c] = 0.0; w->ux[c] = w->uy[c] = 0.0; continue; }
             double r = 0.0, jx = 0.0, jy = 0.0;
             for (int i = 0; i < Q; ++i) {
                 double fi = f[i * n + c];
@@ -679,7 +759,7 @@ static void fields_and_force(const orc_params *p, const double *f, orc_work *w)
         for (int x = 0; x < nx; ++x) {
             long c = (long)y * nx + x;
             long ce = (long)(y + 2) * sx + (x + 2);
-            if (is_solid_row(p, y) || is_pressure_col(p, x)) { w->Fx[c] = w->Fy[c] = 0.0; continue; }
+            if (is_solid(p, x, y) || is_pressure_col(p, x)) { w->Fx[c] = w->Fy[c] = 0.0; continue; }
             double gpx, gpy, glx, gly;
             grad_ext(w->P, sx, ce, &gpx, &gpy);
             grad_ext(w->L, sx, ce, &glx, &gly);
@@ -722,6 +802,7 @@ static void wall_fields(const orc_params *p, const orc_work *w, double *tw, doub
             pw[side * nx + x] = 0.0;
             if (!p->walls || is_pressure_col(p, x)) continue;
             int y1 = side ? ny - 2 : 1, y2 = side ? ny - 3 : 2;
+            if (is_solid(p, x, y1) || is_solid(p, x, y2)) continue; /* wall column covered by an obstacle */
             long c1 = (long)y1 * nx + x, c2 = (long)y2 * nx + x;
             double r1 = w->rho[c1], r2 = w->rho[c2];
             double v1 = w->ux[c1] + w->Fx[c1] / (2.0 * r1);
@@ -744,6 +825,7 @@ static void diag_of(const orc_params *p, const orc_work *w, orc_diag *d)
     for (int y = 0; y < ny; ++y) {
         if (is_solid_row(p, y)) continue;
         for (int x = 0; x < nx; ++x) {
+            if (is_solid(p, x, y)) continue;
             double v = w->rho[(long)y * nx + x];
             double t = s + v;
             if (fabs(s) >= fabs(v)) comp += (s - t) + v; else comp += (v - t) + s;
@@ -762,6 +844,8 @@ static void diag_of(const orc_params *p, const orc_work *w, orc_diag *d)
     for (int side = 0; side < 2; ++side)
         for (int x = 0; x < nx; ++x) {
             if (is_pressure_col(p, x)) continue;
+            int y1 = side ? ny - 2 : 1, y2 = side ? ny - 3 : 2;
+            if (is_solid(p, x, y1) || is_solid(p, x, y2)) continue;
             double t = tw[side * nx + x], q = pw[side * nx + x];
             d->J += t;
             d->Jp += q;
@@ -814,7 +898,7 @@ int orc_step(const orc_params *p, const double *fin, double *fout, orc_diag *d)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             long c = (long)y * nx + x;
-            if (is_solid_row(p, y) || is_pressure_col(p, x)) continue;
+            if (is_solid(p, x, y) || is_pressure_col(p, x)) continue;
             double r = w.rho[c];
             /* velocity shift: tau F / rho for BGK, F / (s_j rho) for MRT */
             const double shift = p->collision ? 1.0 / p->s_j : p->tau;
@@ -865,7 +949,7 @@ int orc_step(const orc_params *p, const double *fin, double *fout, orc_diag *d)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 long c = (long)y * nx + x;
-                if (is_solid_row(p, y)) continue;
+                if (is_solid(p, x, y)) continue;
                 int tx = x + ex[i], ty = y + ey[i];
                 if (p->walls && (ty == 0 || ty == ny - 1)) {
                     fout[opp[i] * n + c] = fs[i * n + c];
@@ -874,6 +958,11 @@ int orc_step(const orc_params *p, const double *fin, double *fout, orc_diag *d)
                 if (!p->walls) ty = (int)pmod(ty, ny);
                 if (p->bc_x) { if (tx < 0 || tx >= nx) continue; }
                 else tx = (int)pmod(tx, nx);
+                if (p->mask && p->mask[(long)ty * nx + tx]) {
+                    /* half-way bounce-back at an obstacle's link */
+                    fout[opp[i] * n + c] = fs[i * n + c];
+                    continue;
+                }
                 fout[i * n + (long)ty * nx + tx] = fs[i * n + c];
             }
 
@@ -925,7 +1014,7 @@ int orc_fields(const orc_params *p, const double *f, double *rho, double *vx, do
         for (int x = 0; x < nx; ++x) {
             long c = (long)y * nx + x;
             double r = w.rho[c], X = 0.0, Y = 0.0;
-            if (is_solid_row(p, y)) r = 0.0;
+            if (is_solid(p, x, y)) r = 0.0;
             else if (is_pressure_col(p, x)) { X = w.ux[c]; Y = w.uy[c]; }
             else { X = w.ux[c] + w.Fx[c] / (2.0 * r); Y = w.uy[c] + w.Fy[c] / (2.0 * r); }
             if (rho) rho[c] = r;
