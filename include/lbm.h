@@ -59,8 +59,7 @@ typedef enum {
 
 /* Lattice and geometry (Sec. 2.2: straight rigid channel of the airway model).
  * walls: 0 = periodic in y; 1 = rows 0 and ny-1 are solid no-slip walls (the
- *        channel walls; this is the ABI's wall mask, which the paper's
- *        geometry reduces to).
+ *        channel walls; lbm_init's wall_mask adds solid nodes anywhere).
  * bc_x:  0 = periodic in x; 1 = column 0 is the pressure inlet and column
  *        nx-1 the pressure outlet.
  * Limits: nx, ny >= 4 (>= 1 for a periodic axis), 9*nx*ny < 2^31 (32-bit
@@ -133,6 +132,24 @@ size_t lbm_workspace_bytes(const lbm_grid *grid);
 /* Create a context.
  *   grid, eos, drive: copied. drive may be NULL (no drive).
  *   tau:      BGK relaxation time, > 1/2.
+ *   wall_mask: NULL, or a host array of nx*ny bytes (node y*nx + x), nonzero =
+ *             solid node; copied. General geometry for the no-slip walls of
+ *             Sec. 2.2: half-way bounce-back on every link into a solid node,
+ *             and ghost densities at solid points for the stencils of Eq. 2.17:
+ *             the flat-wall mirror rule generalised (along the axis directions
+ *             of least depth d <= 2 to fluid, the point (2d-1) nodes out, or d
+ *             nodes out if that is solid; else the diagonals likewise; else the
+ *             fluid points at knight offsets; the mean of those densities plus
+ *             `wetting`). Solid nodes keep their populations and report zero
+ *             fields. With grid->walls = 1 rows 0 and ny-1 are solid whatever
+ *             the mask says; with bc_x = 1 columns 0, 1, nx-2 and nx-1 must be
+ *             fluid outside the wall rows (LBM_ERR_ARG otherwise). A mask that
+ *             adds no solid node to the wall rows runs the channel kernels; any
+ *             other runs the general-geometry kernels, whose device tables
+ *             (about 13 bytes per node plus the ghost table) the library
+ *             allocates even when `workspace` is given. Wall shear and wall
+ *             pressure count the wall columns whose two rows next to the wall
+ *             are fluid.
  *   wetting:  ghost-density offset added to mirrored wall densities
  *             (0 = neutral wetting, 90-degree contact angle).
  *   rho0:     host array of nx*ny doubles, the initial density; the
@@ -144,8 +161,8 @@ size_t lbm_workspace_bytes(const lbm_grid *grid);
  *   stream:   cudaStream_t to issue all work on; NULL = legacy default stream.
  *   out:      receives the context; *out is NULL on failure.
  * Errors: LBM_ERR_ARG, LBM_ERR_PARAM, LBM_ERR_OOM, LBM_ERR_CUDA. */
-lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, double wetting,
-                    const lbm_drive *drive, const double *rho0, void *workspace,
+lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, const uint8_t *wall_mask,
+                    double wetting, const lbm_drive *drive, const double *rho0, void *workspace,
                     size_t ws_bytes, void *stream, lbm_ctx **out);
 
 /* Advance n >= 0 time steps (one fused kernel launch each), asynchronously.
@@ -218,7 +235,15 @@ lbm_status lbm_set_collision(lbm_ctx *ctx, const lbm_collision *c);
  *   LBM_OPT_TMA          nonzero (default for contexts, zero for batches):
  *                        the row-pair kernel stages each stencil row with one
  *                        2-D tensor (TMA) load; zero: nine bulk copies per
- *                        row. Identical results. */
+ *                        row. Identical results.
+ *   LBM_OPT_PREFETCH     0..4: the row-pair kernel, where it stages with
+ *                        tensor loads, prefetches into L2 the stencil rows
+ *                        this many row pairs ahead of the pair it stages into
+ *                        shared memory (0 = none). Identical results.
+ *   LBM_OPT_GENERAL      nonzero: run the general-geometry kernels even when
+ *                        the wall mask adds no solid node (identical
+ *                        populations; diagnostic sums to rounding); zero: the
+ *                        channel kernels wherever the geometry allows. */
 typedef enum {
     LBM_OPT_CTAS_PER_SM = 1,
     LBM_OPT_REVERSE = 2,
@@ -226,7 +251,9 @@ typedef enum {
     LBM_OPT_STAGED = 4,
     LBM_OPT_GRAPH_STEPS = 5, /* batches only: steps per CUDA graph replay (even, 0 = no graph) */
     LBM_OPT_ROWS2 = 6,
-    LBM_OPT_TMA = 7
+    LBM_OPT_TMA = 7,
+    LBM_OPT_PREFETCH = 8,
+    LBM_OPT_GENERAL = 9
 } lbm_option;
 lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value);
 /* Launch geometry of the step kernel: CTAs, threads per CTA, work units and

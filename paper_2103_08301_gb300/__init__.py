@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "liblbm.so")
 LBM_OK, LBM_ERR_ARG, LBM_ERR_PARAM, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_NAN, LBM_ERR_STATE, LBM_ERR_TIMEOUT = range(8)
 LBM_OPT_CTAS_PER_SM, LBM_OPT_REVERSE, LBM_OPT_STRIP, LBM_OPT_STAGED, LBM_OPT_GRAPH_STEPS, LBM_OPT_ROWS2, LBM_OPT_TMA = \
     1, 2, 3, 4, 5, 6, 7
+LBM_OPT_PREFETCH, LBM_OPT_GENERAL = 8, 9
 
 
 class lbm_grid(C.Structure):
@@ -64,7 +65,7 @@ class lbm_diag_t(C.Structure):
 _P = C.c_void_p
 _SIGS = {
     "lbm_workspace_bytes": (C.c_size_t, [C.POINTER(lbm_grid)]),
-    "lbm_init": (C.c_int, [C.POINTER(lbm_grid), C.POINTER(lbm_eos), C.c_double, C.c_double,
+    "lbm_init": (C.c_int, [C.POINTER(lbm_grid), C.POINTER(lbm_eos), C.c_double, _P, C.c_double,
                            C.POINTER(lbm_drive), C.POINTER(C.c_double), _P, C.c_size_t, _P,
                            C.POINTER(_P)]),
     "lbm_step": (C.c_int, [_P, C.c_int64]),
@@ -163,10 +164,17 @@ def lbm_workspace_bytes(grid: lbm_grid) -> int:
     return int(lib().lbm_workspace_bytes(C.byref(grid)))
 
 
-def lbm_init(grid, eos, tau, wetting, drive, rho0, workspace=None, ws_bytes=0, stream=None):
+def lbm_init(grid, eos, tau, wetting, drive, rho0, workspace=None, ws_bytes=0, stream=None, wall_mask=None):
+    """lbm_init; wall_mask: None or an (ny, nx) array, nonzero = solid node."""
     rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+    mask = None
+    if wall_mask is not None:
+        mask = np.ascontiguousarray(np.asarray(wall_mask) != 0, dtype=np.uint8)
+        if mask.shape != (grid.ny, grid.nx):
+            raise ValueError(f"wall_mask shape {mask.shape} != {(grid.ny, grid.nx)}")
     ctx = _P()
-    st = lib().lbm_init(C.byref(grid), C.byref(eos), float(tau), float(wetting),
+    st = lib().lbm_init(C.byref(grid), C.byref(eos), float(tau),
+                        _P(mask.ctypes.data) if mask is not None else None, float(wetting),
                         C.byref(drive) if drive is not None else None,
                         rho0.ctypes.data_as(C.POINTER(C.c_double)),
                         _P(workspace) if workspace else None, int(ws_bytes),
@@ -241,7 +249,8 @@ def lbm_disk_rho0(nx, ny, cx, cy, r0, rho_l, rho_g, width=4.0, noise=0.0, seed=1
 class Lattice:
     """One channel (or periodic box) resident on the current CUDA device.
 
-    Parameters mirror lbm_init. ``workspace`` may be a CUDA torch tensor of at
+    Parameters mirror lbm_init; ``mask`` is the wall mask, an (ny, nx) array
+    with nonzero entries at solid nodes. ``workspace`` may be a CUDA torch tensor of at
     least ``lbm_workspace_bytes`` bytes (kept alive by this object); by default
     the library allocates. ``stream`` is a torch.cuda.Stream or None.
     """
@@ -249,7 +258,7 @@ class Lattice:
     def __init__(self, nx, ny, rho0, *, walls=False, bc_x=False, precision=32, a=1.0, b=4.0,
                  R=1.0, T_over_Tc=0.8, k=1.0, kappa=0.5, tau=1.0, wetting=0.0, dp=0.0,
                  p_ref=None, gx=0.0, gy=0.0, eos="cs", omega=0.344, collision="bgk", s_e=1.64,
-                 s_eps=1.54, s_j=1.0, s_q=1.7, s_nu=None, workspace=None, stream=None):
+                 s_eps=1.54, s_j=1.0, s_q=1.7, s_nu=None, workspace=None, stream=None, mask=None):
         self.grid = lbm_grid(nx, ny, int(walls), int(bc_x), int(precision))
         self.eos = lbm_eos(a, b, R, T_over_Tc, k, kappa, {"cs": LBM_EOS_CS, "pr": LBM_EOS_PR}[eos], omega)
         self.drive = lbm_drive(dp, math.nan if p_ref is None else p_ref, gx, gy)
@@ -261,7 +270,8 @@ class Lattice:
         if workspace is not None:
             ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
         sptr = stream.cuda_stream if stream is not None else None
-        self.ctx = lbm_init(self.grid, self.eos, tau, wetting, self.drive, rho0, ws_ptr, ws_bytes, sptr)
+        self.ctx = lbm_init(self.grid, self.eos, tau, wetting, self.drive, rho0, ws_ptr, ws_bytes, sptr,
+                            wall_mask=mask)
         if collision != "bgk":
             if collision != "mrt":
                 raise ValueError(collision)

@@ -1,9 +1,10 @@
 """Build the solver's shared library (liblbm.so) in-tree for sm_103a.
 
-Four translation units, compiled in parallel and linked with nvcc:
+Five translation units, compiled in parallel and linked with nvcc:
   csrc/lbm_api.cu     - single-channel C ABI and the step kernels (nvcc, -gencode sm_103a)
   csrc/lbm_batch.cu   - batched multi-channel sweep (nvcc)
   csrc/lbm_adjoint.cu - discrete adjoint with checkpoint-and-recompute (nvcc)
+  csrc/lbm_mask.cu    - general wall geometry (per-node solid mask) step kernels (nvcc)
   csrc/lbm_host.cpp   - host FP64 thermodynamics, initial profiles, plug analysis (g++)
 Run as ``python -m paper_2103_08301_gb300.build`` or call ``build()``.
 """
@@ -23,7 +24,8 @@ LIB = os.path.join(HERE, "liblbm.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["lbm_api.cu", "lbm_batch.cu", "lbm_adjoint.cu", "lbm_host.cpp", "lbm_kernels.cuh", "lbm_rows2.cuh", "lbm_internal.h"]
+SOURCES = ["lbm_api.cu", "lbm_batch.cu", "lbm_adjoint.cu", "lbm_mask.cu", "lbm_host.cpp", "lbm_kernels.cuh",
+           "lbm_rows2.cuh", "lbm_internal.h"]
 
 
 def _stale() -> bool:
@@ -52,6 +54,7 @@ def build(force: bool = False, verbose: bool = False, out: str | None = None) ->
     batch_o = os.path.join(bdir, "lbm_batch.o")
     adj_o = os.path.join(bdir, "lbm_adjoint.o")
     host_o = os.path.join(bdir, "lbm_host.o")
+    mask_o = os.path.join(bdir, "lbm_mask.o")
     extra = os.environ.get("LBM_NVCC_FLAGS", "").split()  # tuning experiments, e.g. -DLBM_STAGE_AHEAD=2
 
     def nvcc(src, obj):
@@ -63,14 +66,14 @@ def build(force: bool = False, verbose: bool = False, out: str | None = None) ->
 
     gxx = ["g++", "-O2", "-std=c++17", "-fPIC", "-I", INCLUDE, "-I", CSRC, "-c",
            os.path.join(CSRC, "lbm_host.cpp"), "-o", host_o]
-    with ThreadPoolExecutor(4) as ex:
+    with ThreadPoolExecutor(5) as ex:
         outs = list(ex.map(_run, [nvcc("lbm_api.cu", api_o), nvcc("lbm_batch.cu", batch_o),
-                                  nvcc("lbm_adjoint.cu", adj_o), gxx]))
+                                  nvcc("lbm_adjoint.cu", adj_o), nvcc("lbm_mask.cu", mask_o), gxx]))
     if verbose:
-        for o in outs[:3]:
+        for o in outs[:4]:
             print(o)
     tmp = lib + f".tmp{os.getpid()}"
-    _run([NVCC, *ARCH, "-shared", "-o", tmp, api_o, batch_o, adj_o, host_o, "-lcudart"])
+    _run([NVCC, *ARCH, "-shared", "-o", tmp, api_o, batch_o, adj_o, mask_o, host_o, "-lcudart"])
     os.replace(tmp, lib)
     return lib
 

@@ -688,7 +688,7 @@ lbm_status adj_setup_drive(lbm_adjoint *a, const lbm_drive *drive)
     if (a->ctx && a->have_drive && same_drive(d, a->drive)) return LBM_OK;
     if (a->ctx) { lbm_free(a->ctx); a->ctx = nullptr; }
     std::vector<double> one((size_t)a->grid.nx * a->grid.ny, 0.1);
-    lbm_status s = lbm_init(&a->grid, &a->eos, a->tau, a->wet, &d, one.data(), nullptr, 0, a->stream, &a->ctx);
+    lbm_status s = lbm_init(&a->grid, &a->eos, a->tau, nullptr, a->wet, &d, one.data(), nullptr, 0, a->stream, &a->ctx);
     if (s != LBM_OK) { a->err = std::string("forward context: ") + lbm_status_string(s); a->ctx = nullptr; return s; }
     if ((s = lbm_set_collision(a->ctx, &a->coll)) != LBM_OK) return ctx_status(a, s, "collision");
     a->drive = d;

@@ -6,6 +6,7 @@
 #include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled (fetched at run time; no link to the driver library)
 
 #include <mutex>
+#include <vector>
 
 #include <algorithm>
 #include <cmath>
@@ -97,6 +98,12 @@ struct lbm_ctx {
     bool allow_rows2 = true;   // LBM_OPT_ROWS2
     bool rows2 = false;        // row-pair FP32 step kernel selected for this grid
     bool allow_tma = true;     // LBM_OPT_TMA
+    int pf = 0;                // LBM_OPT_PREFETCH (row pairs ahead, 0 = off)
+    // general wall geometry (lbm_mask.cu): set when the mask adds solid nodes
+    // to the wall rows, or when LBM_OPT_GENERAL forces that path
+    lbm::MaskPath *mask = nullptr;
+    std::vector<uint8_t> mask_host;  // the caller's mask (empty: none)
+    bool force_general = false;
     bool tma_ok = false;       // tmap[] encoded (FP32, pitch a multiple of 4)
     CUtensorMap tmap[2];       // 2-D views of the two population buffers for the row-pair stage
     // fields scratch (allocated on first host-pointer lbm_fields)
@@ -372,6 +379,7 @@ cudaError_t launch(lbm_ctx *ctx, const lbm::KArgs<real> &A)
         static const CUtensorMap unused{};
         lbm::KArgs<real> B = A;
         B.tma = ctx->tma_ok && ctx->allow_tma;
+        B.pf = ctx->pf;
         const CUtensorMap *m = B.tma ? &ctx->tmap[ctx->cur] : &unused;
         void *args[] = {(void *)&B, (void *)m};
         return cudaLaunchKernel(fn, dim3(ctx->nctas), dim3(threads_of(ctx, MODE)), args, dyn_smem(ctx, MODE),
@@ -387,7 +395,8 @@ lbm_status do_steps(lbm_ctx *ctx, int64_t n)
 {
     for (int64_t s = 0; s < n; ++s) {
         lbm::KArgs<real> A = make_args<real>(ctx);
-        cudaError_t e = launch<real, lbm::MODE_STEP>(ctx, A);
+        cudaError_t e = ctx->mask ? lbm::mask_launch<real>(ctx->mask, A, lbm::MODE_STEP, ctx->stream)
+                                  : launch<real, lbm::MODE_STEP>(ctx, A);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
         ctx->cur = 1 - ctx->cur;
         ctx->step += 1;
@@ -411,7 +420,8 @@ lbm_status do_fields(lbm_ctx *ctx, void *rho, void *ux, void *uy, void *tw, void
     lbm::KArgs<real> A = make_args<real>(ctx);
     A.fout = nullptr;
     A.o_rho = d_rho; A.o_vx = d_vx; A.o_vy = d_vy; A.o_tw = d_tw; A.o_pw = d_pw;
-    cudaError_t le = launch<real, lbm::MODE_FIELDS>(ctx, A);
+    cudaError_t le = ctx->mask ? lbm::mask_launch<real>(ctx->mask, A, lbm::MODE_FIELDS, ctx->stream)
+                               : launch<real, lbm::MODE_FIELDS>(ctx, A);
     if (le != cudaSuccess) return cuda_fail(ctx, le, "fields launch");
     struct { void *dst; real *src; size_t n; } outs[] = {
         {rho, d_rho, N}, {ux, d_vx, N}, {uy, d_vy, N}, {tw, d_tw, 2 * nx}, {pw, d_pw, 2 * nx}};
@@ -465,6 +475,24 @@ bool lbm_encode_population_map(CUtensorMap *map, void *base, int pitch, int ny)
     return encode_population_map(map, base, pitch, ny);
 }
 
+namespace {
+
+// (Re)selects the general-geometry path: kept when the caller's mask adds
+// solid nodes to the wall rows or LBM_OPT_GENERAL forces it; the diagnostic
+// slots then follow its CTA count.
+lbm_status plan_geometry(lbm_ctx *ctx)
+{
+    lbm::mask_free(ctx->mask);
+    ctx->mask = nullptr;
+    const uint8_t *m = ctx->mask_host.empty() ? nullptr : ctx->mask_host.data();
+    lbm_status st = lbm::mask_setup(m, ctx->grid, ctx->pitch, ctx->sms, ctx->force_general, ctx->stream, &ctx->mask,
+                                    ctx->last_error, sizeof ctx->last_error);
+    if (st == LBM_OK && ctx->mask) ctx->nctas = lbm::mask_blocks(ctx->mask);
+    return st;
+}
+
+}  // namespace
+
 
 extern "C" {
 
@@ -491,8 +519,8 @@ size_t lbm_workspace_bytes(const lbm_grid *grid)
     return layout_of(grid->nx, grid->ny, grid->precision).total;
 }
 
-lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, double wetting,
-                    const lbm_drive *drive, const double *rho0, void *workspace, size_t ws_bytes,
+lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, const uint8_t *wall_mask,
+                    double wetting, const lbm_drive *drive, const double *rho0, void *workspace, size_t ws_bytes,
                     void *stream, lbm_ctx **out)
 {
     if (!out) return LBM_ERR_ARG;
@@ -557,6 +585,9 @@ lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, double
     *ctx->h_err = 0;
 
     lbm_status st = plan_launch(ctx);
+    if (st != LBM_OK) { lbm_free(ctx); return st; }
+    if (wall_mask) ctx->mask_host.assign(wall_mask, wall_mask + (size_t)grid->nx * grid->ny);
+    st = plan_geometry(ctx);
     if (st != LBM_OK) { lbm_free(ctx); return st; }
     if (grid->precision == 32)
         ctx->tma_ok = encode_population_map(&ctx->tmap[0], ctx->ws + ctx->L.f0, ctx->pitch, grid->ny) &&
@@ -772,6 +803,13 @@ lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
     case LBM_OPT_TMA:
         ctx->allow_tma = value != 0;
         return LBM_OK;
+    case LBM_OPT_PREFETCH:
+        if (value < 0 || value > 4) return LBM_ERR_ARG;
+        ctx->pf = (int)value;
+        return LBM_OK;
+    case LBM_OPT_GENERAL:
+        ctx->force_general = value != 0;
+        break;
     default:
         return LBM_ERR_ARG;
     }
@@ -779,6 +817,7 @@ lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
     // through their totals, so reset them to keep the reduction exact.
     int old = ctx->nctas;
     lbm_status s = plan_launch(ctx);
+    if (s == LBM_OK) s = plan_geometry(ctx);
     if (s == LBM_OK && old != ctx->nctas) {
         if (ctx->grid.precision == 64) reset_acc<double>(ctx); else reset_acc<float>(ctx);
     }
@@ -790,9 +829,9 @@ lbm_status lbm_launch_info(const lbm_ctx *ctx, int64_t *ctas, int64_t *threads, 
 {
     if (!ctx) return LBM_ERR_ARG;
     if (ctas) *ctas = ctx->nctas;
-    if (threads) *threads = threads_of(ctx, lbm::MODE_STEP);
-    if (units) *units = ctx->units;
-    if (staged) *staged = ctx->staged ? 1 : 0;
+    if (threads) *threads = ctx->mask ? 256 : threads_of(ctx, lbm::MODE_STEP);
+    if (units) *units = ctx->mask ? (int64_t)ctx->grid.nx * ctx->grid.ny : ctx->units;
+    if (staged) *staged = (ctx->staged && !ctx->mask) ? 1 : 0;
     return LBM_OK;
 }
 
@@ -801,6 +840,7 @@ void lbm_free(lbm_ctx *ctx)
     if (!ctx) return;
     if (ctx->stream || ctx->ws) cudaStreamSynchronize(ctx->stream);
     if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
+    lbm::mask_free(ctx->mask);
     if (ctx->fscratch) cudaFree(ctx->fscratch);
     if (ctx->h_err) cudaFreeHost(ctx->h_err);
     if (ctx->err_ev) cudaEventDestroy(ctx->err_ev);

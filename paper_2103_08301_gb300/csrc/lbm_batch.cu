@@ -63,6 +63,7 @@ struct lbm_batch {
     // LBM_OPT_TMA (off by default for batches: reading 2n maps from device
     // memory made the 64-channel sweep 4% slower than plane copies); d_tmaps encoded
     bool allow_tma = false, tma_ok = false;
+    int pf = 0;  // LBM_OPT_PREFETCH (row pairs ahead, 0 = off)
     CUtensorMap *d_tmaps = nullptr;          // [2][n]: tensor maps of each buffer's channels (FP32)
     void *d_chan = nullptr;
     lbm::BatchSeg *d_segs = nullptr;
@@ -166,6 +167,7 @@ lbm::KArgs<real> physics_args(const lbm_batch *b)
     A.inv_dph = b->rho_l > b->rho_g ? (real)(1.0 / (b->rho_l - b->rho_g)) : real(0);
     A.err = b->d_err;
     A.reverse = b->reverse;
+    A.pf = b->pf;
     return A;
 }
 
@@ -653,6 +655,11 @@ lbm_status lbm_batch_set_option(lbm_batch *b, lbm_option opt, int64_t value)
         break;
     case LBM_OPT_TMA:
         b->allow_tma = value != 0;
+        if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }  // captured arguments
+        return LBM_OK;
+    case LBM_OPT_PREFETCH:
+        if (value < 0 || value > 4) return LBM_ERR_ARG;
+        b->pf = (int)value;
         if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }  // captured arguments
         return LBM_OK;
     case LBM_OPT_GRAPH_STEPS:

@@ -82,6 +82,23 @@ bool lbm_encode_population_map(CUtensorMap *map, void *base, int pitch, int ny);
 cudaError_t lbm_ctx_copy_state(lbm_ctx *ctx, void *dst);
 const void *lbm_ctx_state(const lbm_ctx *ctx);  // the current state buffer itself (device)
 cudaError_t lbm_ctx_load_state(lbm_ctx *ctx, const void *src);
+
+namespace lbm {
+template <typename real>
+struct KArgs;
+// The general-geometry step on a lattice with a solid mask (lbm_mask.cu).
+// mask_setup validates the mask, builds the ghost table and allocates the
+// path's device tables; *out stays NULL (LBM_OK) when the mask adds no solid
+// node to the wall rows, unless `force`. mask_launch runs one step (mode
+// MODE_STEP) or the fields (MODE_FIELDS) of A.fin on `stream`.
+struct MaskPath;
+lbm_status mask_setup(const uint8_t *mask, const lbm_grid &g, int pitch, int sms, bool force, cudaStream_t stream,
+                      MaskPath **out, char *err, size_t errlen);
+void mask_free(MaskPath *m);
+int mask_blocks(const MaskPath *m);  // CTAs of the collide kernel (diagnostic slots)
+template <typename real>
+cudaError_t mask_launch(const MaskPath *m, const KArgs<real> &A, int mode, cudaStream_t stream);
+}  // namespace lbm
 #endif
 
 // Launchable step kernel (lbm_api.cu) for a precision (32/64), a mode

@@ -67,6 +67,9 @@ struct KArgs {
     // row-pair staged step: 1 = stage rows through the tensor-map kernel
     // parameter (one 2-D TMA load per row), 0 = plain bulk copies per plane
     int tma;
+    // row-pair staged step: the stencil rows of the pair this many pairs ahead
+    // of the one being staged are prefetched into L2 (0 = no prefetch)
+    int pf;
     // pressure columns: gas / liquid branch densities at the inlet and outlet
     // pressures, and the phase indicator theta = clamp((rho_f - ph_g) * inv_dph, 0, 1)
     real rho_in_g, rho_in_l, rho_out_g, rho_out_l, ph_g, inv_dph;
@@ -226,6 +229,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     for (int it = 0; it < (1 << 22); ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+// L2 prefetch of a global range (16-byte aligned, a multiple of 16 bytes) by
+// the bulk-copy unit: no shared memory and no completion to wait for.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 // Orders this thread's earlier generic-proxy accesses to shared memory before
 // later async-proxy (bulk copy) writes.

@@ -72,6 +72,12 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 constexpr uint32_t R2_TMA_ROW_BYTES = 9u * R2_SP * sizeof(float);  // one box
+// L2 prefetch of the same box (no shared memory, nothing to wait for)
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, int y)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y) : "memory");
+}
 
 // Position in the pair-slot ring (slot and mbarrier phase parity).
 struct RingPos2 {
@@ -176,7 +182,24 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
     // need wrapped halo columns (periodic x, first or last strip) keep the
     // bulk copies, whose wrap copies would race with a box's zero fill
     const bool use_tma = tmap != nullptr && !wrapL && !wrapR;
+    // L2 prefetch (tensor-load path) of stencil-row pair q: the boxes the
+    // stage loads of pair q will read
+    auto prefetch = [&](int q) {
+        if (q < npairs) {
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                bool mir;
+                tma_prefetch_2d(tmap, x0 - 4, 9 * map_row<WALLS>(ya - 2 + 2 * q + t, ny, mir));
+            }
+        }
+    };
     auto issue = [&](int q) {
+        if (A.pf > 0 && use_tma && tid == PRODUCER) {
+            // keep the pairs up to A.pf ahead of the staged one in flight to L2
+            if (q == 0)
+                for (int d = 1; d < A.pf; ++d) prefetch(d);
+            prefetch(q + A.pf);
+        }
         if (q < npairs) {
             if (tid == PRODUCER && use_tma) {
                 const uint32_t st = ring_issue.s;

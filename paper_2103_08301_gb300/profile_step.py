@@ -23,6 +23,7 @@ def main():
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--staged", type=int, default=1, help="1: bulk-copy staged kernel, 0: register prefetch")
+    ap.add_argument("--prefetch", type=int, default=-1, help="LBM_OPT_PREFETCH (row pairs ahead); -1: default")
     args = ap.parse_args()
 
     import torch
@@ -41,6 +42,8 @@ def main():
         lat.set_option(lbm.LBM_OPT_STAGED, args.staged)
         if args.ctas_per_sm:
             lat.set_option(lbm.LBM_OPT_CTAS_PER_SM, args.ctas_per_sm)
+        if args.prefetch >= 0:
+            lat.set_option(lbm.LBM_OPT_PREFETCH, args.prefetch)
         lat.step(2)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -173,7 +173,7 @@ def test_binding_constants_match_header_enums(lbm):
                 assert getattr(lbm, m.group(1)) == value, m.group(1)
                 found += 1
     assert found >= 15
-    assert (lbm.LBM_OPT_ROWS2, lbm.LBM_OPT_TMA) == (6, 7)
+    assert (lbm.LBM_OPT_ROWS2, lbm.LBM_OPT_TMA, lbm.LBM_OPT_PREFETCH, lbm.LBM_OPT_GENERAL) == (6, 7, 8, 9)
 
 
 def test_noalloc_rejects_misaligned_buffers_without_a_launch(lbm):

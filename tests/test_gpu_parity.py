@@ -289,6 +289,23 @@ def test_tensor_map_stage_matches_bulk_copies_bitwise(orc, lbm, case):
     assert out[0][1]["mass"] == out[1][1]["mass"]
 
 
+@pytest.mark.parametrize("pf", [1, 3])
+def test_l2_prefetch_changes_nothing(orc, lbm, pf):
+    """Prefetching stencil rows into L2 ahead of the stage loads moves no data
+    into the computation: populations and diagnostics stay bit-identical."""
+    nx, ny, kw = 640, 96, dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=1e-3)
+    rho0 = _airway(orc, nx, ny, 6, 200, 48)
+    out = []
+    for v in (pf, 0):
+        with lbm.Lattice(nx, ny, rho0, precision=32, **kw) as lat:
+            lat.set_option(lbm.LBM_OPT_PREFETCH, v)
+            lat.step(120)
+            out.append((lat.populations(), lat.diag()))
+    assert np.array_equal(out[0][0].view(np.uint32), out[1][0].view(np.uint32))
+    assert out[0][1]["mass"] == out[1][1]["mass"]
+    assert out[0][1]["wall_shear_sum"] == out[1][1]["wall_shear_sum"]
+
+
 def test_checkpoint_restore_continues_bitwise(orc, lbm):
     rho0 = _airway(orc, 320, 64, 5, 100, 40)
     kw = dict(walls=True, bc_x=True, precision=32, T_over_Tc=0.85, kappa=0.5, dp=1e-3)
