@@ -185,6 +185,12 @@ lbm_status lbm_fields(lbm_ctx *ctx, void *rho, void *ux, void *uy, void *tau_wal
  * them in *out (host). Synchronises the stream. */
 lbm_status lbm_diag(lbm_ctx *ctx, lbm_diag_t *out);
 
+/* Restart the diagnostic accumulators (wall-shear sum, wall shear and wall
+ * pressure extrema) so that they cover the steps issued afterwards; the step
+ * counter and the bad-density flag are kept. Asynchronous. Errors:
+ * LBM_ERR_ARG, LBM_ERR_CUDA. */
+lbm_status lbm_reset_diag(lbm_ctx *ctx);
+
 /* Raw population state: 9*nx*ny values of the context precision, layout
  * f[i][y][x]. dst / src may be host or device pointers. */
 lbm_status lbm_populations(lbm_ctx *ctx, void *dst);
@@ -330,6 +336,8 @@ lbm_status lbm_batch_fields(lbm_batch *b, int32_t channel, void *rho, void *ux, 
                             void *p_wall);
 lbm_status lbm_batch_diag(lbm_batch *b, int32_t channel, lbm_diag_t *out);
 lbm_status lbm_batch_populations(lbm_batch *b, int32_t channel, void *dst);
+/* As lbm_reset_diag, for every channel. */
+lbm_status lbm_batch_reset_diag(lbm_batch *b);
 /* Collision operator of every channel, as lbm_set_collision (NULL: BGK). */
 lbm_status lbm_batch_set_collision(lbm_batch *b, const lbm_collision *c);
 /* Options as lbm_set_option plus LBM_OPT_GRAPH_STEPS. Changing the launch
@@ -353,6 +361,23 @@ void lbm_batch_free(lbm_batch *b); /* NULL-safe */
  * T = T_over_Tc * Tc. LBM_ERR_PARAM above Tc. Any output may be NULL. */
 lbm_status lbm_coexistence(const lbm_eos *eos, double *Tc, double *rho_g, double *rho_l,
                            double *p_sat);
+
+/* The method's own coexistence (Sec. 2.1 "Verification": the densities a flat
+ * interface relaxes to, which at lattice interface widths differ from
+ * Maxwell's): a liquid slab between rows ny/4 and 3ny/4 of a periodic 4 x ny
+ * box, started from the Maxwell densities (tanh profile, width 4), stepped
+ * `steps` times on the current device with this EOS, tau and collision (NULL:
+ * BGK) at `precision` (32 or 64). Returns the bulk densities (rows 0 and
+ * ny/2) and their mesh pressures k^2 p0(rho), which agree once the slab has
+ * settled (equal mechanical pressure across a flat interface); *p_gas is the
+ * reference pressure at which a pressure column holds the method's own
+ * saturated vapour. Any output may be NULL. Synchronises `stream` (NULL:
+ * legacy default stream); allocates and frees a context of its own.
+ * Errors: LBM_ERR_ARG (ny < 16, steps < 0, bad precision), LBM_ERR_PARAM
+ * (T >= Tc or as lbm_init), LBM_ERR_NAN, LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_relaxed_coexistence(const lbm_eos *eos, double tau, const lbm_collision *coll, int32_t precision,
+                                   int32_t ny, int64_t steps, void *stream, double *rho_g, double *rho_l,
+                                   double *p_gas, double *p_liq);
 
 /* Initial density of the airway channel (Sec. 2.2, Fig. 2): wall films of
  * thickness `film` measured from the half-way wall planes and a plug

@@ -72,6 +72,8 @@ _SIGS = {
     "lbm_fields": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "lbm_diag": (C.c_int, [_P, C.POINTER(lbm_diag_t)]),
     "lbm_populations": (C.c_int, [_P, _P]),
+    "lbm_reset_diag": (C.c_int, [_P]),
+    "lbm_batch_reset_diag": (C.c_int, [_P]),
     "lbm_load_populations": (C.c_int, [_P, _P]),
     "lbm_checkpoint_bytes": (C.c_size_t, [_P]),
     "lbm_checkpoint": (C.c_int, [_P, _P, C.c_size_t]),
@@ -99,6 +101,8 @@ _SIGS = {
     "lbm_status_string": (C.c_char_p, [C.c_int]),
     "lbm_last_error": (C.c_char_p, [_P]),
     "lbm_coexistence": (C.c_int, [C.POINTER(lbm_eos)] + [C.POINTER(C.c_double)] * 4),
+    "lbm_relaxed_coexistence": (C.c_int, [C.POINTER(lbm_eos), C.c_double, C.POINTER(lbm_collision), C.c_int32,
+                                          C.c_int32, C.c_int64, _P] + [C.POINTER(C.c_double)] * 4),
     "lbm_airway_rho0": (C.c_int, [C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
                                   C.c_double, C.c_double, C.c_double, C.c_double, C.c_uint64,
                                   C.POINTER(C.c_double)]),
@@ -218,6 +222,18 @@ def lbm_coexistence(eos: lbm_eos):
     return Tc.value, g.value, l.value, p.value
 
 
+def lbm_relaxed_coexistence(eos: lbm_eos, tau=1.0, collision=None, precision=64, ny=192, steps=40000,
+                            stream=None):
+    """The method's own coexistence from a relaxed flat slab on the GPU:
+    dict(rho_g, rho_l, p_gas, p_liq) (mesh pressures k^2 p0)."""
+    v = [C.c_double() for _ in range(4)]
+    _check(lib().lbm_relaxed_coexistence(C.byref(eos), float(tau), C.byref(collision) if collision else None,
+                                         int(precision), int(ny), int(steps),
+                                         _P(stream.cuda_stream) if stream is not None else None,
+                                         *[C.byref(x) for x in v]))
+    return dict(zip(("rho_g", "rho_l", "p_gas", "p_liq"), [x.value for x in v]))
+
+
 def lbm_airway_rho0(nx, ny, film, plug_x, plug_len, rho_l, rho_g, width=4.0, noise=0.0, seed=1):
     out = np.empty((ny, nx), dtype=np.float64)
     _check(lib().lbm_airway_rho0(nx, ny, film, plug_x, plug_len, rho_l, rho_g, width, noise, seed,
@@ -311,6 +327,10 @@ class Lattice:
         d = lbm_diag_t()
         _check(lib().lbm_diag(self.ctx, C.byref(d)), self.ctx)
         return d.as_dict()
+
+    def reset_diag(self):
+        """lbm_reset_diag: the accumulators restart from the next step."""
+        _check(lib().lbm_reset_diag(self.ctx), self.ctx)
 
     def populations(self):
         f = np.empty((9, self.ny, self.nx), self.dtype)
@@ -417,6 +437,9 @@ class Batch:
 
     def set_option(self, opt, value):
         self._chk(lib().lbm_batch_set_option(self.h, int(opt), int(value)))
+
+    def reset_diag(self):
+        self._chk(lib().lbm_batch_reset_diag(self.h))
 
     def set_collision(self, coll):
         """lbm_batch_set_collision with an lbm_collision (None: BGK)."""

@@ -625,6 +625,50 @@ lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, const 
     return LBM_OK;
 }
 
+lbm_status lbm_relaxed_coexistence(const lbm_eos *eos, double tau, const lbm_collision *coll, int32_t precision,
+                                   int32_t ny, int64_t steps, void *stream, double *rho_g, double *rho_l,
+                                   double *p_gas, double *p_liq)
+{
+    if (!eos || (precision != 32 && precision != 64) || ny < 16 || steps < 0) return LBM_ERR_ARG;
+    lbm::Thermo th{};
+    double Tc = 0, g = 0, l = 0, ps = 0;
+    if (lbm::thermo_of(*eos, &th, &Tc) || lbm::maxwell(th, &g, &l, &ps)) return LBM_ERR_PARAM;
+    // a liquid slab between rows ny/4 and 3ny/4 of a periodic 4 x ny box, tanh
+    // profile of width 4 between the Maxwell densities
+    const int nx = 4;
+    std::vector<double> rho0((size_t)nx * ny);
+    for (int y = 0; y < ny; ++y) {
+        const double sl = 0.5 * (std::tanh(2.0 * (y - 0.25 * ny) / 4.0) - std::tanh(2.0 * (y - 0.75 * ny) / 4.0));
+        for (int x = 0; x < nx; ++x) rho0[(size_t)y * nx + x] = g + (l - g) * sl;
+    }
+    const lbm_grid grid{nx, ny, 0, 0, precision};
+    lbm_ctx *ctx = nullptr;
+    lbm_status st = lbm_init(&grid, eos, tau, nullptr, 0.0, nullptr, rho0.data(), nullptr, 0, stream, &ctx);
+    if (st != LBM_OK) return st;
+    if (coll) st = lbm_set_collision(ctx, coll);
+    if (st == LBM_OK) st = lbm_step(ctx, steps);
+    std::vector<double> r64((size_t)nx * ny);
+    std::vector<float> r32((size_t)nx * ny);
+    if (st == LBM_OK)
+        st = lbm_fields(ctx, precision == 64 ? (void *)r64.data() : (void *)r32.data(), nullptr, nullptr, nullptr,
+                        nullptr);
+    if (st == LBM_OK) st = lbm_step(ctx, 0);  // the bad-density flag of the last steps
+    if (st == LBM_OK) {
+        lbm_diag_t d;
+        st = lbm_diag(ctx, &d);
+        if (st == LBM_OK && d.nan_detected) st = LBM_ERR_NAN;
+    }
+    lbm_free(ctx);
+    if (st != LBM_OK) return st;
+    auto at = [&](int y) { return precision == 64 ? r64[(size_t)y * nx] : (double)r32[(size_t)y * nx]; };
+    const double rg = at(0), rl = at(ny / 2), k2 = eos->k * eos->k;
+    if (rho_g) *rho_g = rg;
+    if (rho_l) *rho_l = rl;
+    if (p_gas) *p_gas = k2 * lbm::eos_pressure(th, rg);
+    if (p_liq) *p_liq = k2 * lbm::eos_pressure(th, rl);
+    return LBM_OK;
+}
+
 lbm_status lbm_step(lbm_ctx *ctx, int64_t n)
 {
     if (!ctx || n < 0) return LBM_ERR_ARG;
@@ -685,6 +729,20 @@ lbm_status lbm_diag(lbm_ctx *ctx, lbm_diag_t *out)
     out->rho_g = ctx->rho_g; out->rho_l = ctx->rho_l; out->p_sat = ctx->p_sat;
     out->rho_in = ctx->rho_in; out->rho_out = ctx->rho_out;
     out->rho_in_l = ctx->rho_in_l; out->rho_out_l = ctx->rho_out_l;
+    return LBM_OK;
+}
+
+lbm_status lbm_reset_diag(lbm_ctx *ctx)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    double *mass = (double *)(ctx->ws + ctx->L.mass), *J = (double *)(ctx->ws + ctx->L.J);
+    if (ctx->grid.precision == 64)
+        lbm::reset_acc_kernel<double><<<(lbm::MAX_CTAS + 255) / 256, 256, 0, ctx->stream>>>(
+            mass, J, (double *)(ctx->ws + ctx->L.ext), nullptr, lbm::MAX_CTAS);
+    else
+        lbm::reset_acc_kernel<float><<<(lbm::MAX_CTAS + 255) / 256, 256, 0, ctx->stream>>>(
+            mass, J, (float *)(ctx->ws + ctx->L.ext), nullptr, lbm::MAX_CTAS);
+    CK(cudaGetLastError(), "reset diag");
     return LBM_OK;
 }
 

@@ -601,6 +601,19 @@ lbm_status lbm_batch_diag(lbm_batch *b, int32_t channel, lbm_diag_t *out)
     return LBM_OK;
 }
 
+lbm_status lbm_batch_reset_diag(lbm_batch *b)
+{
+    if (!b) return LBM_ERR_ARG;
+    if (b->precision == 64)
+        lbm::reset_acc_kernel<double><<<(b->nseg + 255) / 256, 256, 0, b->stream>>>(
+            b->d_seg_mass, b->d_seg_J, (double *)b->d_seg_ext, nullptr, b->nseg);
+    else
+        lbm::reset_acc_kernel<float><<<(b->nseg + 255) / 256, 256, 0, b->stream>>>(
+            b->d_seg_mass, b->d_seg_J, (float *)b->d_seg_ext, nullptr, b->nseg);
+    BCK(cudaGetLastError(), "reset diag");
+    return LBM_OK;
+}
+
 lbm_status lbm_batch_populations(lbm_batch *b, int32_t channel, void *dst)
 {
     if (!b || !dst || channel < 0 || channel >= b->n) return LBM_ERR_ARG;

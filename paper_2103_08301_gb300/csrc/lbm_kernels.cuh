@@ -1287,7 +1287,7 @@ __global__ void reset_acc_kernel(double *mass_part, double *J_acc, real *ext, in
         ext[4 * c + 1] = real(-INFINITY);
         ext[4 * c + 2] = real(INFINITY);
         ext[4 * c + 3] = real(-INFINITY);
-        if (c == 0) *err = 0;
+        if (c == 0 && err) *err = 0;
     }
 }
 
