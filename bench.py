@@ -5,8 +5,12 @@ path over the lattice): the airway channel scaled to 16384 x 2048 nodes
 (walls top and bottom, wall films 64 nodes thick, a liquid plug over
 x in [4096, 5120), pressure inlet/outlet with a drop of 1e-3, Carnahan-Starling
 EOS at T = 0.85 Tc, tau = 1, k = 1, kappa = 0.5), FP32 populations, synthetic
-seeded initial density. The 2.4 GB state (two population arrays) is far
-larger than L2, so no flush is needed between steps.
+seeded initial density. The channel sits at the method's own coexistence: the
+inlet column at its saturation pressure p* (p_ref = p* - dp/2, so the upstream
+vapour is saturated rather than supersaturated), films and plug at its liquid
+density in its vapour (p*, rho_g*, rho_l* from a relaxed flat slab). The 2.4 GB
+state (two population arrays) is far larger than L2, so no flush is needed
+between steps.
 
 Metric: MLUPS (million lattice-node updates per second, nx*ny*steps/t/1e6),
 whole job over N GPUs, each GPU stepping its own replica of the channel (the
@@ -37,8 +41,10 @@ FILM, PLUG_X, PLUG_LEN = 64.0, 4096.0, 1024.0
 PHYS = dict(T_over_Tc=0.85, k=1.0, kappa=0.5, tau=1.0, dp=1e-3)
 BYTES_PER_NODE = {32: 72, 64: 144}  # 9 populations read + 9 written
 METRIC = "MLUPS and % of HBM roofline (FP32 D2Q9 EOS step, 1xGB300) vs FP64 CPU oracle"
-WORKLOAD = "airway channel 16384x2048, FP32, CS EOS T=0.85Tc, dp=1e-3 (roofline stress)"
+WORKLOAD = ("airway channel 16384x2048, FP32, CS EOS T=0.85Tc, dp=1e-3, inlet at the method's coexistence "
+            "pressure (roofline stress)")
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e nominal
 KERNEL_SRC = [os.path.join(ROOT, "paper_2103_08301_gb300", "csrc", f) for f in ("lbm_kernels.cuh", "lbm_rows2.cuh")]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_rows2_fp32_16384x2048.md")
 
@@ -142,16 +148,35 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def _rho0(nx=NX, ny=NY, plug_x=PLUG_X, plug_len=PLUG_LEN, film=FILM):
+def _operating_point(stream=None):
+    """(rho_g*, rho_l*, p*): the method's own coexistence at the workload's EOS,
+    tau, k and kappa, from a relaxed flat slab on the GPU (FP64)."""
     import paper_2103_08301_gb300 as lbm
     eos = lbm.lbm_eos(1.0, 4.0, 1.0, PHYS["T_over_Tc"], PHYS["k"], PHYS["kappa"])
-    _, g, l, _ = lbm.lbm_coexistence(eos)
+    c = lbm.lbm_relaxed_coexistence(eos, PHYS["tau"], None, 64, 192, 40000, stream=stream)
+    return c["rho_g"], c["rho_l"], c["p_gas"]
+
+
+def _oracle_operating_point():
+    """The same operating point from the oracle's own relaxed slab (for the CPU legs)."""
+    import oracle
+    import synth
+    s = oracle.Setup(nx=2, ny=192, T_over_Tc=PHYS["T_over_Tc"], k=PHYS["k"], kappa=PHYS["kappa"], tau=PHYS["tau"])
+    g, l, _ = s.coexistence()
+    f, _ = oracle.run(s, oracle.init(s, synth.slab_rho0(2, 192, 48, 144, l, g, width=4)), 40000)
+    r = oracle.fields(s, f)["rho"][:, 0]
+    return r[0], r[96], PHYS["k"] ** 2 * oracle.cs_p0(s.a, s.b, s.R, s.T, r[0])
+
+
+def _rho0(op, nx=NX, ny=NY, plug_x=PLUG_X, plug_len=PLUG_LEN, film=FILM):
+    import paper_2103_08301_gb300 as lbm
+    g, l, _ = op
     return lbm.lbm_airway_rho0(nx, ny, film, plug_x, plug_len, l, g)
 
 
-def _lattice_kw(precision):
+def _lattice_kw(precision, op):
     return dict(walls=True, bc_x=True, precision=precision, T_over_Tc=PHYS["T_over_Tc"], k=PHYS["k"],
-                kappa=PHYS["kappa"], tau=PHYS["tau"], dp=PHYS["dp"])
+                kappa=PHYS["kappa"], tau=PHYS["tau"], dp=PHYS["dp"], p_ref=op[2] - 0.5 * PHYS["dp"])
 
 
 def _timed_steps(lat, stream, steps):
@@ -167,16 +192,19 @@ def _timed_steps(lat, stream, steps):
     return a.elapsed_time(b) / steps
 
 
-def _extras(stream):
+def _extras(stream, op):
     """Throughput of the other scope rows on the same GPU: the FP64 step and
-    the Peng-Robinson + MRT step on the 16384 x 2048 channel, and the adjoint
+    the Peng-Robinson + MRT step on the 16384 x 2048 channel, the adjoint
     (forward with checkpoints, backward) on the 512 x 128 airway over 2000 FP64
-    steps. Not part of the headline value."""
+    steps, the general-geometry step, the other single-lattice workloads and
+    the rupture trend sweep. Not part of the headline value."""
+    import numpy as np
+
     import paper_2103_08301_gb300 as lbm
     out = {}
     nodes = NX * NY
-    rho0 = _rho0()
-    with lbm.Lattice(NX, NY, rho0, stream=stream, **_lattice_kw(64)) as lat:
+    rho0 = _rho0(op)
+    with lbm.Lattice(NX, NY, rho0, stream=stream, **_lattice_kw(64, op)) as lat:
         ms = _timed_steps(lat, stream, 100)
     out["fp64_step"] = {"ms_per_step": ms, "mlups": nodes / ms / 1e3,
                         "hbm_gbs": BYTES_PER_NODE[64] * nodes / ms / 1e6}
@@ -205,8 +233,35 @@ def _extras(stream):
                                 f"FP64 reverse",
                     "forward_s": t1 - t0, "backward_s": t2 - t1,
                     "reverse_mlups": nx * ny * steps / (t2 - t1) / 1e6}
-    out["configs"] = _configs(stream)
+    # the same channel with a wall mask (a constriction on both walls every
+    # 2048 columns): the general-geometry kernels
+    mask = np.zeros((NY, NX), np.uint8)
+    for x0 in range(1024, NX - 512, 2048):
+        mask[1:NY // 4, x0:x0 + 64] = 1
+        mask[NY - NY // 4:NY - 1, x0:x0 + 64] = 1
+    with lbm.Lattice(NX, NY, rho0, stream=stream, mask=mask, **_lattice_kw(32, op)) as lat:
+        ms = _timed_steps(lat, stream, 50)
+        nan = lat.diag()["nan_detected"]
+    out["masked_fp32_step"] = {"ms_per_step": ms, "mlups": nodes / ms / 1e3, "nan": bool(nan),
+                               "hbm_gbs_at_72B": 72 * nodes / ms / 1e6,
+                               "workload": "same channel, constrictions on both walls every 2048 columns "
+                                           "(general-geometry kernels)"}
+    out["configs"] = _configs(stream, op)
+    out["trends"] = _trends(stream, op)
     return out
+
+
+def _trends(stream, op):
+    """Plug rupture under the paper's body-force drive on its proportions
+    (1500 x 202 lattice, R = 100, film 0.15 R, plug 1 R at x = 200), one
+    parameter varied at a time (Sec. 3.3, Figs. 10-12)."""
+    from paper_2103_08301_gb300 import trends
+    base = dict(nx=1500, ny=202, film=15, plug_len=100, force=5e-7)
+    rows = trends.sweep(base, {"force": [4e-7, 5e-7, 6e-7, 8e-7], "plug_len": [60, 80, 120], "film": [10, 20]},
+                        coex=op, max_steps=60000, every=250, window=1500, settle=1000, plug_x=200, stream=stream)
+    return {"base": base, "rows": [{"vary": n, "value": v, "rupture_step": r["rupture_step"],
+                                    "dP_wall": r["dP_wall"], "dtau_wall": r["dtau_wall"],
+                                    "droplet_mass": r["droplet_mass"], "nan": r["nan"]} for n, v, r in rows]}
 
 
 def _oracle_mlups(s, f, budget_s):
@@ -222,35 +277,51 @@ def _oracle_mlups(s, f, budget_s):
     return s.nx * s.ny * steps / dt / 1e6, steps
 
 
-def _configs(stream, budget_s=2.0):
+def _configs(stream, op, budget_s=2.0):
     """The two single-lattice workloads not timed above, on the GPU and with the
     oracle on all host cores and on one core (bounded samples of the same
     state): the 128 x 128 periodic droplet (FP64, 10000 steps) and the
-    2048 x 256 airway channel (FP32, 20000 of its 100000 steps; its 38 MB state
-    sits in L2, so its GB/s is algorithmic traffic, not DRAM)."""
+    2048 x 256 airway channel (FP32, its full 100000 steps at the method's
+    coexistence, with the plug's state at the end; its 38 MB state sits in L2,
+    so its GB/s is algorithmic traffic, not DRAM), plus that channel under the
+    paper's body-force drive (G = dp / nx, ends at p*) until its plug ruptures."""
+    import numpy as np
+
     import oracle
     import synth
     import paper_2103_08301_gb300 as lbm
+    from paper_2103_08301_gb300 import trends
     peak, _ = _hbm_peak()
     out = {}
+    rg, rl, ps = op
+    org, orl, ops = _oracle_operating_point()  # the oracle samples take the oracle's own
+    dp = 1e-3
     cases = [
         ("droplet_128x128_fp64", 128, 128, 64, 10000,
          dict(walls=False, bc_x=False, T_over_Tc=0.8, k=1.0, kappa=0.5, tau=1.0)),
-        ("airway_2048x256_fp32", 2048, 256, 32, 20000,
-         dict(walls=True, bc_x=True, T_over_Tc=0.85, k=1.0, kappa=0.5, tau=1.0, dp=1e-3)),
+        ("airway_2048x256_fp32", 2048, 256, 32, 100000,
+         dict(walls=True, bc_x=True, T_over_Tc=0.85, k=1.0, kappa=0.5, tau=1.0, dp=dp, p_ref=ps - 0.5 * dp)),
     ]
     for name, nx, ny, prec, steps, kw in cases:
         s = oracle.Setup(nx=nx, ny=ny, **kw)
         g, l, _ = s.coexistence()
         if name.startswith("droplet"):
-            rho0 = synth.disk_rho0(nx, ny, 30, l, g, noise=1e-3, seed=1)
+            rho0 = o_rho0 = synth.disk_rho0(nx, ny, 30, l, g, noise=1e-3, seed=1)
         else:
-            rho0 = synth.airway_rho0(nx, ny, 8.0, 512.0, 128.0, l, g)
+            rho0 = synth.airway_rho0(nx, ny, 8.0, 512.0, 128.0, rl, rg)
+            o_rho0 = synth.airway_rho0(nx, ny, 8.0, 512.0, 128.0, orl, org)
+            s = oracle.Setup(nx=nx, ny=ny, **dict(kw, p_ref=ops - 0.5 * dp))
+        plug = None
         with lbm.Lattice(nx, ny, rho0, precision=prec, stream=stream, **kw) as lat:
             ms = _timed_steps(lat, stream, steps)
+            if name.startswith("airway"):
+                st = lbm.lbm_plug_analysis(lat.fields()["rho"].astype(np.float64), 0.5 * (rg + rl))
+                plug = {"after_steps": steps + 5, "x_rear": st["x_rear"], "x_front": st["x_front"],
+                        "intact": st["intact"], "n_droplets": st["n_droplets"],
+                        "nan": bool(lat.diag()["nan_detected"])}
         mlups = nx * ny / ms / 1e3
         gbs = BYTES_PER_NODE[prec] * nx * ny / ms / 1e6
-        f0 = oracle.init(s, rho0)
+        f0 = oracle.init(s, o_rho0)
         ncores = oracle.num_threads()
         o_all, n_all = _oracle_mlups(s, f0, budget_s)
         oracle.set_num_threads(1)
@@ -262,6 +333,13 @@ def _configs(stream, budget_s=2.0):
                      "gpu_steps": steps, "oracle_mlups": o_all, "oracle_cores": ncores,
                      "oracle_mlups_1core": o_one,
                      "oracle_sample": f"{n_all} steps on {ncores} cores, {n_one} steps on 1 core"}
+        if plug is not None:
+            out[name]["plug_at_end"] = plug
+    r = trends.rupture_run(2048, 256, 8.0, 128.0, dp / 2048, plug_x=512, coex=op, max_steps=100000, every=500,
+                           window=1500, settle=1000, stream=stream)
+    out["airway_2048x256_body_force_rupture"] = {
+        "force": dp / 2048, "rupture_step": r["rupture_step"], "steps": r["steps"], "dP_wall": r["dP_wall"],
+        "dtau_wall": r["dtau_wall"], "droplet_mass": r["droplet_mass"], "nan": r["nan"]}
     return out
 
 
@@ -270,12 +348,12 @@ def _cpu_baseline(budget_s=15.0):
     the same channel (full 2048-row height, 1024 columns with the plug inside),
     timed for as many steps as fit in about budget_s seconds."""
     import oracle
-    nx, ny = 1024, NY
-    s = oracle.Setup(nx=nx, ny=ny, walls=True, bc_x=True, T_over_Tc=PHYS["T_over_Tc"], k=PHYS["k"],
-                     kappa=PHYS["kappa"], tau=PHYS["tau"], dp=PHYS["dp"])
-    g, l, _ = s.coexistence()
     import synth
-    f = oracle.init(s, synth.airway_rho0(nx, ny, FILM, 256.0, 256.0, l, g))
+    nx, ny = 1024, NY
+    rg, rl, ps = _oracle_operating_point()
+    s = oracle.Setup(nx=nx, ny=ny, walls=True, bc_x=True, T_over_Tc=PHYS["T_over_Tc"], k=PHYS["k"],
+                     kappa=PHYS["kappa"], tau=PHYS["tau"], dp=PHYS["dp"], p_ref=ps - 0.5 * PHYS["dp"])
+    f = oracle.init(s, synth.airway_rho0(nx, ny, FILM, 256.0, 256.0, rl, rg))
     t0 = time.perf_counter()
     f, _ = oracle.run(s, f, 1)
     one = time.perf_counter() - t0
@@ -315,9 +393,10 @@ def run_reference(args, world, rank):
     oracle.build()
     budget = 150.0
     ny = 256
+    g, l, ps = _oracle_operating_point()
+    p_ref = ps - 0.5 * PHYS["dp"]
     s_probe = oracle.Setup(nx=512, ny=ny, walls=True, bc_x=True, T_over_Tc=PHYS["T_over_Tc"], k=PHYS["k"],
-                           kappa=PHYS["kappa"], tau=PHYS["tau"], dp=PHYS["dp"])
-    g, l, _ = s_probe.coexistence()
+                           kappa=PHYS["kappa"], tau=PHYS["tau"], dp=PHYS["dp"], p_ref=p_ref)
     f = oracle.init(s_probe, synth.airway_rho0(512, ny, 8.0, 128.0, 128.0, l, g))
     t0 = time.perf_counter()
     oracle.run(s_probe, f, 3)
@@ -325,7 +404,7 @@ def run_reference(args, world, rank):
     per_step = budget / max(1, args.steps + args.warmup)
     nx = int(max(64, min(NX, rate * per_step / ny)))
     s = oracle.Setup(nx=nx, ny=ny, walls=True, bc_x=True, T_over_Tc=PHYS["T_over_Tc"], k=PHYS["k"],
-                     kappa=PHYS["kappa"], tau=PHYS["tau"], dp=PHYS["dp"])
+                     kappa=PHYS["kappa"], tau=PHYS["tau"], dp=PHYS["dp"], p_ref=p_ref)
     f = oracle.init(s, synth.airway_rho0(nx, ny, 8.0, nx / 4, nx / 8, l, g))
     f, _ = oracle.run(s, f, args.warmup)
     t0 = time.perf_counter()
@@ -361,9 +440,10 @@ def run_ours(args, world, rank, local):
         dist.barrier()
 
     precision = 32
-    rho0 = _rho0()
     stream = torch.cuda.Stream()
-    lat = lbm.Lattice(NX, NY, rho0, stream=stream, **_lattice_kw(precision))
+    op = _operating_point(stream)
+    rho0 = _rho0(op)
+    lat = lbm.Lattice(NX, NY, rho0, stream=stream, **_lattice_kw(precision, op))
     info = lat.launch_info()
     lat.step(args.warmup)
     torch.cuda.synchronize()
@@ -407,7 +487,7 @@ def run_ours(args, world, rank, local):
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
-    lat2 = lbm.Lattice(NX, NY, rho_pinned.numpy(), stream=stream, **_lattice_kw(precision))
+    lat2 = lbm.Lattice(NX, NY, rho_pinned.numpy(), stream=stream, **_lattice_kw(precision, op))
     for _ in range(args.steps):
         lat2.step(1)
         lat2.diag()
@@ -420,7 +500,7 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_sweep:
         from paper_2103_08301_gb300 import sweep_bench
         sweep = sweep_bench.run(steps=200)
-    extras = _extras(stream) if (rank == 0 and world == 1 and not args.no_sweep) else None
+    extras = _extras(stream, op) if (rank == 0 and world == 1 and not args.no_sweep) else None
 
     if rank == 0:
         cpu = _cpu_baseline() if world == 1 else None
@@ -429,10 +509,13 @@ def run_ours(args, world, rank, local):
             "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "precision": precision,
+                       "operating_point": {"rho_g": op[0], "rho_l": op[1], "p_star": op[2],
+                                           "p_ref": op[2] - 0.5 * PHYS["dp"]},
                        "l2": "state 2.4 GB > 129 MB L2 (no flush needed)",
                        "launch": info, "parallelism": f"{world} independent channel replicas"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_src,
+                         "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
                          "traffic": _profiled_traffic(),
                          "algorithmic_bytes_per_launch": bytes_per_launch,
                          "kernel_ms_mean": kmean * 1e3,

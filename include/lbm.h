@@ -117,7 +117,8 @@ typedef struct {
     double wall_shear_sum; /* sum over states and columns of tau_w(bottom) + tau_w(top) */
     double tau_wall_min, tau_wall_max; /* extrema of tau_w over walls and states */
     double p_wall_min, p_wall_max;     /* extrema of the wall pressure (Eq. 2.4) */
-    int32_t nan_detected;  /* nonzero once any step met a bad density */
+    int32_t nan_detected;  /* nonzero once any step met a bad density (a stage
+                              wait that gave up shows as LBM_ERR_TIMEOUT from lbm_step) */
     int32_t pad_;
     /* thermodynamic set-up derived by lbm_init (host FP64); rho_in / rho_out
        are the gas-branch and rho_in_l / rho_out_l the liquid-branch densities
@@ -129,7 +130,10 @@ typedef struct {
  * arrays plus diagnostics). 0 on invalid grid. */
 size_t lbm_workspace_bytes(const lbm_grid *grid);
 
-/* Create a context.
+/* Create a context. (Failure-detection tests: the environment variable
+ * LBM_FAULT=alloc makes lbm_init fail with LBM_ERR_OOM after its device
+ * allocations, releasing them; LBM_FAULT=param makes it fail with
+ * LBM_ERR_PARAM before any CUDA call.)
  *   grid, eos, drive: copied. drive may be NULL (no drive).
  *   tau:      BGK relaxation time, > 1/2.
  *   wall_mask: NULL, or a host array of nx*ny bytes (node y*nx + x), nonzero =
@@ -249,7 +253,19 @@ lbm_status lbm_set_collision(lbm_ctx *ctx, const lbm_collision *c);
  *   LBM_OPT_GENERAL      nonzero: run the general-geometry kernels even when
  *                        the wall mask adds no solid node (identical
  *                        populations; diagnostic sums to rounding); zero: the
- *                        channel kernels wherever the geometry allows. */
+ *                        channel kernels wherever the geometry allows.
+ *   LBM_OPT_FAULT_SKIP_COPY  test hook of failure detection, 0 (default) =
+ *                        off; for FP32 channels with walls, pressure columns
+ *                        and nx a multiple of 4 (LBM_ERR_ARG otherwise), run
+ *                        through a separate test build of the step kernel.
+ *                        Nonzero: the FP32 row-pair step's first CTA never
+ *                        issues the shared-memory copy of the final stencil-row
+ *                        pair of its last segment, and every stage wait polls
+ *                        at most 4096 times; the wait for that pair gives up
+ *                        and a later lbm_step reports LBM_ERR_TIMEOUT (no copy
+ *                        reuses that slot afterwards, so none is in flight when
+ *                        the CTA exits). The state is then invalid;
+ *                        lbm_restore recovers. */
 typedef enum {
     LBM_OPT_CTAS_PER_SM = 1,
     LBM_OPT_REVERSE = 2,
@@ -259,7 +275,8 @@ typedef enum {
     LBM_OPT_ROWS2 = 6,
     LBM_OPT_TMA = 7,
     LBM_OPT_PREFETCH = 8,
-    LBM_OPT_GENERAL = 9
+    LBM_OPT_GENERAL = 9,
+    LBM_OPT_FAULT_SKIP_COPY = 10
 } lbm_option;
 lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value);
 /* Launch geometry of the step kernel: CTAs, threads per CTA, work units and

@@ -33,6 +33,16 @@ constexpr uint64_t CKPT_MAGIC = 0x4C424D434B505431ull;  // "LBMCKPT1"
 
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
+// Host-side fault injection for the failure-detection tests (read at every
+// lbm_init): LBM_FAULT=alloc fails lbm_init as if its last device allocation
+// had failed, after the workspace was allocated, so the error path's clean-up
+// runs; LBM_FAULT=param fails it as if the thermodynamics had no solution.
+bool fault_is(const char *kind)
+{
+    const char *f = std::getenv("LBM_FAULT");
+    return f && std::strcmp(f, kind) == 0;
+}
+
 struct Layout {
     size_t pops;      // one population array
     size_t f0, f1, mass, J, ext, err, dout, total;
@@ -104,6 +114,7 @@ struct lbm_ctx {
     lbm::MaskPath *mask = nullptr;
     std::vector<uint8_t> mask_host;  // the caller's mask (empty: none)
     bool force_general = false;
+    bool fault_skip = false;  // LBM_OPT_FAULT_SKIP_COPY (test hook)
     bool tma_ok = false;       // tmap[] encoded (FP32, pitch a multiple of 4)
     CUtensorMap tmap[2];       // 2-D views of the two population buffers for the row-pair stage
     // fields scratch (allocated on first host-pointer lbm_fields)
@@ -380,6 +391,10 @@ cudaError_t launch(lbm_ctx *ctx, const lbm::KArgs<real> &A)
         lbm::KArgs<real> B = A;
         B.tma = ctx->tma_ok && ctx->allow_tma;
         B.pf = ctx->pf;
+        if (ctx->fault_skip) {
+            B.poll_limit = 4096;
+            fn = (void *)lbm::step_kernel_rows2<true, true, false, true>;
+        }
         const CUtensorMap *m = B.tma ? &ctx->tmap[ctx->cur] : &unused;
         void *args[] = {(void *)&B, (void *)m};
         return cudaLaunchKernel(fn, dim3(ctx->nctas), dim3(threads_of(ctx, MODE)), args, dyn_smem(ctx, MODE),
@@ -542,7 +557,10 @@ lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, const 
 
     // Thermodynamics (host FP64).
     lbm::ChannelThermo ct;
-    if (lbm::channel_thermo(*eos, ctx->drive, grid->bc_x, &ct)) { lbm_free(ctx); return LBM_ERR_PARAM; }
+    if (lbm::channel_thermo(*eos, ctx->drive, grid->bc_x, &ct) || fault_is("param")) {
+        lbm_free(ctx);
+        return LBM_ERR_PARAM;
+    }
     ctx->th = ct.th;
     ctx->T = ct.T; ctx->Tc = ct.Tc;
     ctx->rho_g = ct.rho_g; ctx->rho_l = ct.rho_l; ctx->p_sat = ct.p_sat;
@@ -577,6 +595,7 @@ lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, const 
     }
     e = cudaMallocHost((void **)&ctx->h_err, sizeof(int));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->err_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess && fault_is("alloc")) e = cudaErrorMemoryAllocation;
     if (e != cudaSuccess) {
         lbm_status s = cuda_fail(ctx, e, "host flag");
         lbm_free(ctx);
@@ -724,7 +743,7 @@ lbm_status lbm_diag(lbm_ctx *ctx, lbm_diag_t *out)
     out->tau_wall_max = any ? h[3] : 0.0;
     out->p_wall_min = any ? h[4] : 0.0;
     out->p_wall_max = any ? h[5] : 0.0;
-    out->nan_detected = h[6] != 0.0;
+    out->nan_detected = ((int)h[6] & 1) != 0;  // bit 1 (a stage wait gave up) is lbm_step's LBM_ERR_TIMEOUT
     out->T = ctx->T; out->Tc = ctx->Tc;
     out->rho_g = ctx->rho_g; out->rho_l = ctx->rho_l; out->p_sat = ctx->p_sat;
     out->rho_in = ctx->rho_in; out->rho_out = ctx->rho_out;
@@ -868,6 +887,18 @@ lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
     case LBM_OPT_GENERAL:
         ctx->force_general = value != 0;
         break;
+    case LBM_OPT_FAULT_SKIP_COPY:
+        // the test build exists for walls, pressure columns and unpadded rows
+        if (value != 0) {
+            if (!(ctx->rows2 && !ctx->mask && ctx->grid.walls && ctx->grid.bc_x && ctx->pitch == ctx->grid.nx))
+                return LBM_ERR_ARG;
+            cudaError_t e = cudaFuncSetAttribute((void *)lbm::step_kernel_rows2<true, true, false, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)lbm::rows2_smem_bytes());
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "smem attribute");
+        }
+        ctx->fault_skip = value != 0;
+        return LBM_OK;
     default:
         return LBM_ERR_ARG;
     }

@@ -595,7 +595,7 @@ lbm_status lbm_batch_diag(lbm_batch *b, int32_t channel, lbm_diag_t *out)
     out->tau_wall_max = any ? h[3] : 0.0;
     out->p_wall_min = any ? h[4] : 0.0;
     out->p_wall_max = any ? h[5] : 0.0;
-    out->nan_detected = h[6] != 0.0;
+    out->nan_detected = ((int)h[6] & 1) != 0;
     out->T = b->T; out->Tc = b->Tc; out->rho_g = b->rho_g; out->rho_l = b->rho_l; out->p_sat = b->p_sat;
     out->rho_in = c.rho_in; out->rho_out = c.rho_out; out->rho_in_l = c.rho_in_l; out->rho_out_l = c.rho_out_l;
     return LBM_OK;

@@ -70,6 +70,9 @@ struct KArgs {
     // row-pair staged step: the stencil rows of the pair this many pairs ahead
     // of the one being staged are prefetched into L2 (0 = no prefetch)
     int pf;
+    // failure-detection test build of the row-pair step (step_kernel_rows2
+    // with HOOK): every stage wait polls at most poll_limit times
+    int poll_limit;
     // pressure columns: gas / liquid branch densities at the inlet and outlet
     // pressures, and the phase indicator theta = clamp((rho_f - ph_g) * inv_dph, 0, 1)
     real rho_in_g, rho_in_l, rho_out_g, rho_out_l, ph_g, inv_dph;
@@ -224,9 +227,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 // Waits for the phase with the given parity; gives up after a bounded number
 // of polls (each poll itself suspends for a hardware-defined interval) and
 // returns false, so a lost transfer can never hang the GPU.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int limit = 1 << 22)
 {
-    for (int it = 0; it < (1 << 22); ++it)
+    for (int it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }

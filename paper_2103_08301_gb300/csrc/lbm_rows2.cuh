@@ -120,11 +120,18 @@ __device__ __forceinline__ float2 stage_pair(const float *slot, int i, int sc)
 // One segment (strip s, fluid rows ya .. yb-1) of the row-pair step; see the
 // file comment for the schedule. The ring rows of rho / phi / lap are indexed
 // by y & (RING - 1) as in the one-row kernel.
-template <bool WALLS, bool PRES, bool PADDED>
+// lost: a stage wait of this thread gave up (the step is then invalid and
+// reported so; the loop runs on with whatever the stage holds). HOOK: the
+// failure-detection test build (a separate instantiation, so the production
+// kernel's code is untouched); skip_here: its hook applies to this segment:
+// the copy of the final pair is never issued, so the wait for it gives up
+// after KArgs::poll_limit polls; no later copy reuses that slot, so nothing is
+// left in flight when the CTA exits.
+template <bool WALLS, bool PRES, bool PADDED, bool HOOK = false>
 __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom<float> &G, int s, int ya, int yb,
                                                SmemR2 &S, float *stages, uint64_t *bars,
                                                RingPos2 &ring_next, const CUtensorMap *tmap, Acc<float, 1> &acc,
-                                               bool &lost)
+                                               bool &lost, bool skip_here)
 {
     using V = float2;
     constexpr int SW = R2_BLOCK + 4;
@@ -193,6 +200,7 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
             }
         }
     };
+    const int poll = HOOK ? A.poll_limit : (1 << 22);
     auto issue = [&](int q) {
         if (A.pf > 0 && use_tma && tid == PRODUCER) {
             // keep the pairs up to A.pf ahead of the staged one in flight to L2
@@ -201,7 +209,9 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
             prefetch(q + A.pf);
         }
         if (q < npairs) {
-            if (tid == PRODUCER && use_tma) {
+            if (HOOK && skip_here && q == npairs - 1) {
+                // the test hook: the final pair's copy is never issued
+            } else if (tid == PRODUCER && use_tma) {
                 const uint32_t st = ring_issue.s;
                 mbar_arrive_expect_tx(&bars[st], 2u * R2_TMA_ROW_BYTES);
                 float *slot = stages + (size_t)st * R2_SLOT;
@@ -243,7 +253,7 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
         const uint32_t prev = cur == 0 ? R2_SLOTS - 1 : cur - 1;  // slot of pair k-1
 
         // (1) density and phi of stencil rows yy0, yy0+1
-        if (!mbar_wait_bounded(&bars[cur], ring_next.ph)) lost = true;
+        if (!mbar_wait_bounded(&bars[cur], ring_next.ph, poll)) lost = true;
         {
             const float *slot = stages + (size_t)cur * R2_SLOT;
             bool m0, m1;
@@ -428,8 +438,9 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
 #ifndef LBM_R2_MIN_BLOCKS
 #define LBM_R2_MIN_BLOCKS (640 / LBM_R2_BLOCK)
 #endif
-// tmap: 2-D tensor map of A.fin (used when A.tma is set)
-template <bool WALLS, bool PRES, bool PADDED>
+// tmap: 2-D tensor map of A.fin (used when A.tma is set). HOOK: the
+// failure-detection test build (see run_segment_r2).
+template <bool WALLS, bool PRES, bool PADDED, bool HOOK = false>
 __global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS)
     step_kernel_rows2(const KArgs<float> A, const __grid_constant__ CUtensorMap tmap)
 {
@@ -461,8 +472,9 @@ __global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS)
         const long long ue = min(u1, run_end);
         const int yb = ya + (int)(ue - u);
         u = ue;
-        run_segment_r2<WALLS, PRES, PADDED>(A, G, s, ya, yb, S, stages, bars, ring_next, A.tma ? &tmap : nullptr,
-                                            acc, lost);
+        // the test hook applies to the first CTA's last segment
+        run_segment_r2<WALLS, PRES, PADDED, HOOK>(A, G, s, ya, yb, S, stages, bars, ring_next,
+                                                  A.tma ? &tmap : nullptr, acc, lost, HOOK && cta == 0 && u == u1);
     }
     if (lost) atomicOr(A.err, 2);
 
@@ -514,7 +526,7 @@ __global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS)
         Acc<float, 1> acc;
         acc.reset();
         run_segment_r2<WALLS, PRES, true>(A, G, sg.strip, sg.ya, sg.yb, S, stages, bars, ring_next,
-                                          tmaps ? tmaps + sg.chan : nullptr, acc, lost);
+                                          tmaps ? tmaps + sg.chan : nullptr, acc, lost, false);
         double m, j;
         float e[4];
         bool anybad;

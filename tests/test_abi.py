@@ -188,3 +188,14 @@ def test_noalloc_rejects_misaligned_buffers_without_a_launch(lbm):
     assert lbm.lbm_step_noalloc(g64, e, 1.0, 0.0, None, bad4, good, 0) == lbm.LBM_ERR_ARG
     assert lbm.lbm_step_noalloc(g, e, 1.0, 0.0, None, good, 0x40000, 0, diag_ptr=bad4) == lbm.LBM_ERR_ARG
     assert lbm.lbm_step_noalloc(g, e, 1.0, 0.0, None, good, 0x40000, 0, err_ptr=bad2) == lbm.LBM_ERR_ARG
+
+
+def test_fault_injection_param_before_any_cuda_call(lbm, monkeypatch):
+    # LBM_FAULT=param fails lbm_init as if the thermodynamics had no solution;
+    # the check comes before the first CUDA call, so it runs without a GPU
+    g = lbm.lbm_grid(16, 16, 0, 0, 32)
+    e = lbm.lbm_eos(1.0, 4.0, 1.0, 0.8, 1.0, 0.5)
+    monkeypatch.setenv("LBM_FAULT", "param")
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_init(g, e, 1.0, 0.0, None, np.full((16, 16), 0.1))
+    assert ei.value.status == lbm.LBM_ERR_PARAM
