@@ -61,3 +61,14 @@ def test_airway_at_the_method_coexistence_keeps_its_gas_core(lbm):
             st = lbm.lbm_plug_analysis(r, mid)
             assert st["intact"] == 1  # the plug still closes the channel
     assert frac["maxwell"] > 0.5 and frac["method"] == 0.0, frac
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_gpu_slab_meets_maxwell_at_the_cancelling_relaxation_time(orc, lbm, precision):
+    """The GPU step's own flat interface at tau = 1.36, 0.85 Tc: both bulk
+    densities within 1% of the Maxwell construction (the oracle's, pinned to
+    scipy's equal-area solution)."""
+    eos = lbm.lbm_eos(1.0, 4.0, 1.0, 0.85, 1.0, 0.5)
+    got = lbm.lbm_relaxed_coexistence(eos, 1.36, None, precision, 192, 60000)
+    g, l, _ = orc.Setup(nx=2, ny=2, T_over_Tc=0.85, kappa=0.5).coexistence()
+    assert abs(got["rho_g"] / g - 1) < 0.01 and abs(got["rho_l"] / l - 1) < 0.01, got
