@@ -76,6 +76,10 @@ struct lbm_batch {
     // graph of graph_steps steps starting from buffer 0
     int graph_steps = DEFAULT_GRAPH_STEPS;
     cudaGraphExec_t graph = nullptr;
+    // persistent stepping (row-pair batches): one cooperative launch per chunk
+    // of steps, segments ordered by step counters (LBM_OPT_PERSISTENT)
+    bool allow_persist = true, persist = false;
+    int *d_done = nullptr, *d_abort = nullptr, *d_dep_beg = nullptr, *d_dep = nullptr;
     // fields scratch and non-blocking NaN check
     unsigned char *fscratch = nullptr;
     size_t fscratch_bytes = 0;
@@ -124,6 +128,54 @@ void *batch_kernel(const lbm_batch *b)
     if (b->precision == 64)
         return b->staged ? batch_kernel_ptr<double, true>(w, p) : batch_kernel_ptr<double, false>(w, p);
     return b->staged ? batch_kernel_ptr<float, true>(w, p) : batch_kernel_ptr<float, false>(w, p);
+}
+
+void *persist_kernel(const lbm_batch *b)
+{
+    using namespace lbm;
+    const bool w = b->walls, p = b->bc_x;
+    if (w && p) return (void *)batch_persistent_kernel_rows2<true, true>;
+    if (w) return (void *)batch_persistent_kernel_rows2<true, false>;
+    if (p) return (void *)batch_persistent_kernel_rows2<false, true>;
+    return (void *)batch_persistent_kernel_rows2<false, false>;
+}
+
+// Dependencies of each segment for persistent stepping: the segments of the
+// same channel in its own and the two neighbouring strips (wrapped for
+// periodic x) whose fluid rows meet [ya - 3, yb + 2] (wrapped for periodic y):
+// the rows its stencil reads, and the rows whose earlier readers its pushes
+// into the target buffer must not overtake. CSR: beg[nseg + 1], dep[].
+void build_deps(const lbm_batch *b, std::vector<int> &beg, std::vector<int> &dep)
+{
+    std::vector<std::vector<std::vector<int>>> by(b->n);  // [channel][strip] -> segments
+    for (int c = 0; c < b->n; ++c) by[c].resize(b->ch[c].nstrips);
+    for (int k = 0; k < b->nseg; ++k) by[b->segs[k].chan][b->segs[k].strip].push_back(k);
+    beg.assign(1, 0);
+    dep.clear();
+    for (int k = 0; k < b->nseg; ++k) {
+        const lbm::BatchSeg &g = b->segs[k];
+        const ChanHost &c = b->ch[g.chan];
+        const int ny = c.grid.ny, ns = c.nstrips;
+        const int a = g.ya - 3, z = g.yb + 2;  // inclusive row range
+        auto meets = [&](const lbm::BatchSeg &t) {
+            for (int sh : {0, -ny, ny}) {
+                if (b->walls && sh != 0) continue;
+                if (t.ya + sh <= z && t.yb - 1 + sh >= a) return true;
+            }
+            return false;
+        };
+        std::vector<int> strips;
+        for (int d = -1; d <= 1; ++d) {
+            int t = g.strip + d;
+            if (b->bc_x) { if (t < 0 || t >= ns) continue; }
+            else t = ((t % ns) + ns) % ns;
+            if (std::find(strips.begin(), strips.end(), t) == strips.end()) strips.push_back(t);
+        }
+        for (int t : strips)
+            for (int j : by[g.chan][t])
+                if (meets(b->segs[j])) dep.push_back(j);
+        beg.push_back((int)dep.size());
+    }
 }
 
 size_t staged_bytes(const lbm_batch *b, bool staged)
@@ -217,6 +269,22 @@ lbm_status batch_plan(lbm_batch *b)
         if (e != cudaSuccess) return bfail(b, e, "occupancy");
         per_sm = std::max(1, occ);
     }
+    // persistent stepping needs every CTA resident at once (cooperative launch)
+    b->persist = false;
+    if (b->rows2 && b->allow_persist) {
+        int dev = 0, coop = 0, occ = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(persist_kernel(b), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persist_kernel(b), step_threads(b), smem);
+        if (e != cudaSuccess) return bfail(b, e, "persistent kernel set-up");
+        if (coop && occ > 0) {
+            b->persist = true;
+            per_sm = std::min(per_sm, occ);
+        }
+    }
     long long G = (long long)b->sms * per_sm;
     G = std::min<long long>(G, std::max<long long>(1, U / 2));
     G = std::min<long long>(G, lbm::MAX_CTAS);
@@ -270,6 +338,25 @@ lbm_status batch_plan(lbm_batch *b)
     BCK(cudaMalloc((void **)&b->d_seg_mass, ns * sizeof(double)), "segment slots");
     BCK(cudaMalloc((void **)&b->d_seg_J, ns * sizeof(double)), "segment slots");
     BCK(cudaMalloc(&b->d_seg_ext, ns * 4 * sz_of(b)), "segment slots");
+    cudaFree(b->d_done);
+    cudaFree(b->d_abort);
+    cudaFree(b->d_dep_beg);
+    cudaFree(b->d_dep);
+    b->d_done = b->d_abort = b->d_dep_beg = b->d_dep = nullptr;
+    if (b->persist) {
+        std::vector<int> dbeg, dep;
+        build_deps(b, dbeg, dep);
+        BCK(cudaMalloc((void **)&b->d_done, ns * sizeof(int)), "step counters");
+        BCK(cudaMalloc((void **)&b->d_abort, sizeof(int)), "step counters");
+        BCK(cudaMalloc((void **)&b->d_dep_beg, dbeg.size() * sizeof(int)), "dependencies");
+        BCK(cudaMalloc((void **)&b->d_dep, std::max<size_t>(1, dep.size()) * sizeof(int)), "dependencies");
+        BCK(cudaMemcpyAsync(b->d_dep_beg, dbeg.data(), dbeg.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream),
+            "dependencies");
+        if (!dep.empty())
+            BCK(cudaMemcpyAsync(b->d_dep, dep.data(), dep.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream),
+                "dependencies");
+        BCK(cudaStreamSynchronize(b->stream), "dependencies");  // the host vectors die here
+    }
     BCK(cudaMemcpyAsync(b->d_segs, b->segs.data(), b->nseg * sizeof(lbm::BatchSeg), cudaMemcpyHostToDevice,
                         b->stream), "work list copy");
     BCK(cudaMemcpyAsync(b->d_cta_begin, begin.data(), (b->nctas + 1) * sizeof(int), cudaMemcpyHostToDevice,
@@ -302,6 +389,31 @@ cudaError_t batch_launch(lbm_batch *b)
     void *args[] = {(void *)&A, (void *)&chans, (void *)&b->d_segs, (void *)&b->d_cta_begin,
                     (void *)&b->d_seg_mass, (void *)&b->d_seg_J, (void *)&ext, b->rows2 ? (void *)&tm : nullptr};
     return cudaLaunchKernel(batch_kernel(b), dim3(b->nctas), dim3(step_threads(b)), args, step_smem(b), b->stream);
+}
+
+// Persistent stepping: `steps` steps of every channel in one cooperative launch.
+cudaError_t persistent_steps(lbm_batch *b, int steps)
+{
+    lbm::KArgs<float> A = physics_args<float>(b);
+    const lbm::BatchChan<float> *chans = static_cast<const lbm::BatchChan<float> *>(b->d_chan);
+    float *ext = static_cast<float *>(b->d_seg_ext);
+    const CUtensorMap *tm = b->tma_ok && b->allow_tma ? b->d_tmaps : nullptr;
+    float *buf0 = reinterpret_cast<float *>(b->pop[0]), *buf1 = reinterpret_cast<float *>(b->pop[1]);
+    int nchan = b->n, cur0 = b->cur;
+    cudaError_t e = cudaMemsetAsync(b->d_done, 0, (size_t)std::max(1, b->nseg) * sizeof(int), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_abort, 0, sizeof(int), b->stream);
+    if (e != cudaSuccess) return e;
+    void *args[] = {(void *)&A, (void *)&chans, (void *)&b->d_segs, (void *)&b->d_cta_begin, (void *)&b->d_seg_mass,
+                    (void *)&b->d_seg_J, (void *)&ext, (void *)&tm, (void *)&nchan, (void *)&b->d_dep_beg,
+                    (void *)&b->d_dep, (void *)&b->d_done, (void *)&b->d_abort, (void *)&buf0, (void *)&buf1,
+                    (void *)&cur0, (void *)&steps};
+    e = cudaLaunchCooperativeKernel(persist_kernel(b), dim3(b->nctas), dim3(step_threads(b)), args, step_smem(b),
+                                    b->stream);
+    if (e == cudaSuccess) {
+        b->cur ^= steps & 1;
+        b->step += steps;
+    }
+    return e;
 }
 
 cudaError_t one_step(lbm_batch *b)
@@ -542,6 +654,11 @@ lbm_status lbm_batch_step(lbm_batch *b, int64_t n)
         if (*b->h_err & 1) flag = LBM_ERR_NAN;
         else if (*b->h_err) flag = LBM_ERR_TIMEOUT;
     }
+    while (n > 0 && b->persist) {
+        const int chunk = (int)std::min<int64_t>(n, 4096);
+        BCK(persistent_steps(b, chunk), "persistent launch");
+        n -= chunk;
+    }
     while (n > 0) {
         if (b->graph_steps > 0 && n >= b->graph_steps && b->cur == 0) {
             if (!b->graph) {
@@ -675,6 +792,9 @@ lbm_status lbm_batch_set_option(lbm_batch *b, lbm_option opt, int64_t value)
         b->pf = (int)value;
         if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }  // captured arguments
         return LBM_OK;
+    case LBM_OPT_PERSISTENT:
+        b->allow_persist = value != 0;
+        break;
     case LBM_OPT_GRAPH_STEPS:
         if (value < 0 || (value & 1)) return LBM_ERR_ARG;
         b->graph_steps = (int)value;
@@ -733,9 +853,13 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int32_t trial_steps, int64_t *best_c
             b->W_opt = w;
             if (batch_plan(b) != LBM_OK) continue;
             upload_chan_table(b);
-            one_step(b);  // warm-up
+            // time the plan the way lbm_batch_step will run it
+            if (b->persist) persistent_steps(b, 2);  // warm-up
+            else one_step(b);
             cudaEventRecord(e0, b->stream);
-            for (int s = 0; s < trial_steps; ++s) one_step(b);
+            if (b->persist) persistent_steps(b, trial_steps);
+            else
+                for (int s = 0; s < trial_steps; ++s) one_step(b);
             cudaEventRecord(e1, b->stream);
             cudaEventSynchronize(e1);
             float ms = 0.f;
@@ -775,6 +899,10 @@ void lbm_batch_free(lbm_batch *b)
     cudaFree(b->pop[0]);
     cudaFree(b->pop[1]);
     cudaFree(b->d_tmaps);
+    cudaFree(b->d_done);
+    cudaFree(b->d_abort);
+    cudaFree(b->d_dep_beg);
+    cudaFree(b->d_dep);
     cudaFree(b->d_chan);
     cudaFree(b->d_segs);
     cudaFree(b->d_cta_begin);

@@ -544,3 +544,121 @@ __global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS)
 }
 
 }  // namespace lbm
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Persistent batch: one cooperative launch runs `nsteps` steps of every
+// channel. Each segment (channel, strip, rows) keeps a step counter in global
+// memory; before its step n a segment waits until every segment it depends on
+// has completed n steps: the segments of its own and the two neighbouring
+// strips of its channel whose rows meet [ya - 3, yb + 2] (the rows its stencil
+// reads from the source buffer, and the rows whose earlier readers its pushes
+// into the target buffer must not overtake; built on the host). The waits are
+// bounded; one that gives up sets error bit 1 and a global abort flag, which
+// ends every CTA's waiting, so nothing hangs. All CTAs are co-resident (a
+// cooperative launch), so a CTA only ever waits for work that can run.
+// Memory ordering: a segment's threads write the target buffer, the CTA
+// barrier orders those writes before thread 0's release of the counter, and
+// the waiter's acquire (thread 0) and CTA barrier order them before the
+// producer thread's bulk copies, behind a generic-to-async proxy fence.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ld_acquire_gpu(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+constexpr int PERSIST_POLLS = 1 << 22;  // polls (each after a short sleep) before a dependency wait gives up
+
+template <bool WALLS, bool PRES>
+__global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS)
+    batch_persistent_kernel_rows2(const KArgs<float> A, const BatchChan<float> *__restrict__ chans,
+                                  const BatchSeg *__restrict__ segs, const int *__restrict__ cta_begin,
+                                  double *__restrict__ seg_mass, double *__restrict__ seg_J,
+                                  float *__restrict__ seg_ext, const CUtensorMap *__restrict__ tmaps, int nchan,
+                                  const int *__restrict__ dep_beg, const int *__restrict__ dep, int *done,
+                                  int *abort_flag, float *buf0, float *buf1, int cur0, int nsteps)
+{
+    extern __shared__ __align__(128) unsigned char dsm[];
+    float *const stages = reinterpret_cast<float *>(dsm);
+    uint64_t *const bars = reinterpret_cast<uint64_t *>(dsm + (size_t)R2_SLOTS * R2_SLOT * sizeof(float));
+    __shared__ SmemR2 S;
+    __shared__ int s_stop;
+
+    const int tid = threadIdx.x;
+    constexpr int PRODUCER = R2_BLOCK - 1;
+    const int cta = A.reverse ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+    RingPos2 ring_next;
+    bool lost = false;
+    if (tid == 0) {
+        for (int st = 0; st < R2_SLOTS; ++st) mbar_init(&bars[st], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    for (int n = 0; n < nsteps; ++n) {
+        const int src = (cur0 + n) & 1;
+        float *const fin = src ? buf1 : buf0;
+        float *const fout = src ? buf0 : buf1;
+        for (int k = cta_begin[cta]; k < cta_begin[cta + 1]; ++k) {
+            if (tid == 0) {
+                int stop = 0;
+                for (int j = dep_beg[k]; j < dep_beg[k + 1] && !stop; ++j) {
+                    const int *c = done + dep[j];
+                    for (int it = 0; ld_acquire_gpu(c) < n; ++it) {
+                        if (it >= PERSIST_POLLS || ld_acquire_gpu(abort_flag)) {
+                            stop = 1;
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                }
+                if (stop) {
+                    atomicOr(A.err, 2);
+                    atomicExch(abort_flag, 1);
+                }
+                s_stop = stop;
+            }
+            __syncthreads();
+            if (s_stop) n = nsteps;  // uniform: leave both loops
+            if (n == nsteps) break;
+            if (tid == PRODUCER) fence_proxy_async_global();
+            const BatchSeg sg = segs[k];
+            const BatchChan<float> ch = chans[sg.chan];
+            const Geom<float> G{fin + ch.off, fout + ch.off, ch.nx, ch.ny, ch.W, ch.pitch,
+                                ch.rho_in_g, ch.rho_in_l, ch.rho_out_g, ch.rho_out_l};
+            Acc<float, 1> acc;
+            acc.reset();
+            run_segment_r2<WALLS, PRES, true>(A, G, sg.strip, sg.ya, sg.yb, S, stages, bars, ring_next,
+                                              tmaps ? tmaps + (size_t)src * nchan + sg.chan : nullptr, acc, lost,
+                                              false);
+            double m, j;
+            float e[4];
+            bool anybad;
+            cta_reduce<float, R2_BLOCK, 1>(acc, S, m, j, e, anybad);  // ends with a CTA barrier
+            if (tid == 0) {
+                seg_mass[k] = m;
+                seg_J[k] += j;
+                float *ex = seg_ext + 4 * (long long)k;
+                ex[0] = fmin(ex[0], e[0]); ex[1] = fmax(ex[1], e[1]);
+                ex[2] = fmin(ex[2], e[2]); ex[3] = fmax(ex[3], e[3]);
+                if (anybad) atomicOr(A.err, 1);
+                fence_proxy_async_global();  // this CTA's bulk reads of the source are complete
+                __threadfence();
+                st_release_gpu(done + k, n + 1);
+            }
+        }
+    }
+    if (lost) atomicOr(A.err, 2);
+}
+
+}  // namespace lbm

@@ -173,3 +173,34 @@ def test_batch_tensor_map_stage_matches_bulk_copies(orc, lbm, specs, kw):
     for c in range(len(chans)):
         assert np.array_equal(outs[0][c][0].view(np.uint32), outs[1][c][0].view(np.uint32)), f"channel {c}"
         assert outs[0][c][1]["mass"] == outs[1][c][1]["mass"], c
+
+
+@pytest.mark.parametrize("kind", ["airway", "airway_tma", "periodic"])
+def test_persistent_batch_matches_per_step_launches_bitwise(orc, lbm, kind):
+    """One cooperative launch carrying many steps (segments ordered by step
+    counters) against one launch per step: the same populations, bit for bit,
+    and the same diagnostics, over an odd number of steps (the buffers end
+    swapped) and uneven channels."""
+    if kind == "periodic":
+        kw = dict(walls=False, bc_x=False, T_over_Tc=0.8, kappa=0.5)
+        g, l, _ = orc.Setup(nx=8, ny=8, **kw).coexistence()
+        chans = [{"nx": nx, "ny": ny, "rho0": synth.disk_rho0(nx, ny, r, l, g, noise=1e-3, seed=nx,
+                                                              centre=(0.3 * nx, 0.6 * ny))}
+                 for nx, ny, r in ((256, 64, 14), (132, 40, 9), (512, 24, 7), (128, 128, 30))]
+    else:
+        kw = KW
+        chans = _channels(orc, STAGED_SPECS + [(2048, 300, 1e-3, 12, 512, 128)])
+    steps = 137
+    out = []
+    for persistent in (1, 0):
+        with lbm.Batch(chans, precision=32, **kw) as b:
+            if kind == "airway_tma":
+                b.set_option(lbm.LBM_OPT_TMA, 1)
+            b.set_option(lbm.LBM_OPT_PERSISTENT, persistent)
+            b.step(steps)
+            out.append([(b.populations(i), b.diag(i)) for i in range(len(chans))])
+    for (pa, da), (pb, db) in zip(*out):
+        assert np.array_equal(pa.view(np.uint32), pb.view(np.uint32))
+        for k in ("mass", "wall_shear_sum", "tau_wall_min", "tau_wall_max", "p_wall_min", "p_wall_max",
+                  "nan_detected"):
+            assert da[k] == db[k], k
