@@ -569,6 +569,13 @@ __device__ __forceinline__ int ld_acquire_gpu(const int *p)
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ int ld_relaxed_gpu(const int *p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ void st_release_gpu(int *p, int v)
 {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -611,17 +618,28 @@ __global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS)
         float *const fout = src ? buf0 : buf1;
         for (int k = cta_begin[cta]; k < cta_begin[cta + 1]; ++k) {
             if (tid == 0) {
+                // the counters are read in groups of up to 8 independent
+                // relaxed loads (their latencies overlap), re-read until all
+                // have reached n, then one acquire fence orders the step's reads
                 int stop = 0;
-                for (int j = dep_beg[k]; j < dep_beg[k + 1] && !stop; ++j) {
-                    const int *c = done + dep[j];
-                    for (int it = 0; ld_acquire_gpu(c) < n; ++it) {
-                        if (it >= PERSIST_POLLS || ld_acquire_gpu(abort_flag)) {
+                for (int j0 = dep_beg[k]; j0 < dep_beg[k + 1] && !stop; j0 += 8) {
+                    const int m = min(8, dep_beg[k + 1] - j0);
+                    for (int it = 0;; ++it) {
+                        int v[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) v[q] = q < m ? ld_relaxed_gpu(done + dep[j0 + q]) : n;
+                        bool ready = true;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) ready = ready && v[q] >= n;
+                        if (ready) break;
+                        if (it >= PERSIST_POLLS || ld_relaxed_gpu(abort_flag)) {
                             stop = 1;
                             break;
                         }
                         __nanosleep(64);
                     }
                 }
+                fence_acq_rel_gpu();
                 if (stop) {
                     atomicOr(A.err, 2);
                     atomicExch(abort_flag, 1);
