@@ -170,8 +170,12 @@ lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, const 
                     size_t ws_bytes, void *stream, lbm_ctx **out);
 
 /* Advance n >= 0 time steps (one fused kernel launch each), asynchronously.
- * Returns LBM_ERR_NAN if a completed earlier step met a bad density (checked
- * without blocking), LBM_ERR_CUDA on launch failure. */
+ * On a context created with a stream of its own, runs of LBM_OPT_GRAPH_STEPS
+ * steps (default 64) starting from the first population buffer are replayed
+ * from a CUDA graph captured on first use (identical results; changing an
+ * option or the collision drops it). Returns LBM_ERR_NAN if a completed
+ * earlier step met a bad density (checked without blocking), LBM_ERR_CUDA on
+ * launch failure. */
 lbm_status lbm_step(lbm_ctx *ctx, int64_t n);
 
 /* Macroscopic fields of the current state, computed on the GPU:
@@ -271,7 +275,8 @@ typedef enum {
     LBM_OPT_REVERSE = 2,
     LBM_OPT_STRIP = 3,
     LBM_OPT_STAGED = 4,
-    LBM_OPT_GRAPH_STEPS = 5, /* batches only: steps per CUDA graph replay (even, 0 = no graph) */
+    LBM_OPT_GRAPH_STEPS = 5, /* steps per CUDA graph replay (even, 0 = no graph; default 64); contexts
+                                replay only on a stream of their own (not the legacy default stream) */
     LBM_OPT_ROWS2 = 6,
     LBM_OPT_TMA = 7,
     LBM_OPT_PREFETCH = 8,

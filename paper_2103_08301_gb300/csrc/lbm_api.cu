@@ -115,6 +115,10 @@ struct lbm_ctx {
     std::vector<uint8_t> mask_host;  // the caller's mask (empty: none)
     bool force_general = false;
     bool fault_skip = false;  // LBM_OPT_FAULT_SKIP_COPY (test hook)
+    // graph replay of lbm_step: graph_steps launches captured from buffer 0
+    // (contexts with a stream of their own; LBM_OPT_GRAPH_STEPS)
+    int graph_steps = 64;
+    cudaGraphExec_t graph = nullptr;
     bool tma_ok = false;       // tmap[] encoded (FP32, pitch a multiple of 4)
     CUtensorMap tmap[2];       // 2-D views of the two population buffers for the row-pair stage
     // fields scratch (allocated on first host-pointer lbm_fields)
@@ -405,9 +409,52 @@ cudaError_t launch(lbm_ctx *ctx, const lbm::KArgs<real> &A)
                             ctx->stream);
 }
 
+void drop_graph(lbm_ctx *ctx)
+{
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+}
+
+template <typename real>
+lbm_status do_steps(lbm_ctx *ctx, int64_t n);
+
+// graph_steps steps starting from buffer 0, captured once and replayed (the
+// captured launches hold the kernel arguments of that moment: any change of
+// plan, option or collision drops the graph)
+template <typename real>
+lbm_status build_graph(lbm_ctx *ctx)
+{
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+    const int cur0 = ctx->cur;
+    const int64_t step0 = ctx->step;
+    const int keep = ctx->graph_steps;
+    ctx->graph_steps = 0;  // capture single launches
+    lbm_status st = do_steps<real>(ctx, keep);
+    ctx->graph_steps = keep;
+    cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+    ctx->cur = cur0;  // capture records; nothing ran
+    ctx->step = step0;
+    if (st != LBM_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "graph end capture");
+    cudaError_t e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { ctx->graph = nullptr; return cuda_fail(ctx, e, "graph instantiate"); }
+    return LBM_OK;
+}
+
 template <typename real>
 lbm_status do_steps(lbm_ctx *ctx, int64_t n)
 {
+    while (ctx->graph_steps > 0 && ctx->stream && n >= ctx->graph_steps && ctx->cur == 0) {
+        if (!ctx->graph) {
+            lbm_status s = build_graph<real>(ctx);
+            if (s != LBM_OK) return s;
+        }
+        CK(cudaGraphLaunch(ctx->graph, ctx->stream), "graph launch");
+        ctx->step += ctx->graph_steps;  // an even count: the state ends in buffer 0 again
+        n -= ctx->graph_steps;
+    }
     for (int64_t s = 0; s < n; ++s) {
         lbm::KArgs<real> A = make_args<real>(ctx);
         cudaError_t e = ctx->mask ? lbm::mask_launch<real>(ctx->mask, A, lbm::MODE_STEP, ctx->stream)
@@ -846,6 +893,7 @@ lbm_status lbm_restore(lbm_ctx *ctx, const void *host_buf, size_t bytes)
 lbm_status lbm_set_collision(lbm_ctx *ctx, const lbm_collision *c)
 {
     if (!ctx) return LBM_ERR_ARG;
+    drop_graph(ctx);
     if (!c) { ctx->coll = lbm_collision{}; return LBM_OK; }
     if (c->kind == LBM_COLL_BGK) { ctx->coll = *c; return LBM_OK; }
     if (c->kind != LBM_COLL_MRT) return LBM_ERR_ARG;
@@ -859,6 +907,7 @@ lbm_status lbm_set_collision(lbm_ctx *ctx, const lbm_collision *c)
 lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
 {
     if (!ctx) return LBM_ERR_ARG;
+    drop_graph(ctx);  // the captured launches hold the old arguments
     switch (opt) {
     case LBM_OPT_CTAS_PER_SM:
         if (value < 0 || value > 32) return LBM_ERR_ARG;
@@ -887,6 +936,11 @@ lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
     case LBM_OPT_GENERAL:
         ctx->force_general = value != 0;
         break;
+    case LBM_OPT_GRAPH_STEPS:
+        if (value < 0 || (value & 1) || value > 1 << 20) return LBM_ERR_ARG;
+        ctx->graph_steps = (int)value;
+        drop_graph(ctx);
+        return LBM_OK;
     case LBM_OPT_FAULT_SKIP_COPY:
         // the test build exists for walls, pressure columns and unpadded rows
         if (value != 0) {
@@ -930,6 +984,7 @@ void lbm_free(lbm_ctx *ctx)
     if (ctx->stream || ctx->ws) cudaStreamSynchronize(ctx->stream);
     if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
     lbm::mask_free(ctx->mask);
+    drop_graph(ctx);
     if (ctx->fscratch) cudaFree(ctx->fscratch);
     if (ctx->h_err) cudaFreeHost(ctx->h_err);
     if (ctx->err_ev) cudaEventDestroy(ctx->err_ev);

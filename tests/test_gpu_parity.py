@@ -306,6 +306,28 @@ def test_l2_prefetch_changes_nothing(orc, lbm, pf):
     assert out[0][1]["wall_shear_sum"] == out[1][1]["wall_shear_sum"]
 
 
+@pytest.mark.parametrize("precision", [32, 64])
+def test_graph_replayed_steps_match_single_launches(orc, lbm, precision):
+    """lbm_step replayed from a captured CUDA graph (a context with its own
+    stream) against one launch per call: identical populations and sums, over
+    an odd number of steps and across an option change that drops the graph."""
+    import torch
+    nx, ny, kw = 384, 80, dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=1e-3)
+    rho0 = _airway(orc, nx, ny, 5, 100, 40)
+    out = []
+    for graphs in (64, 0):
+        with lbm.Lattice(nx, ny, rho0, precision=precision, stream=torch.cuda.Stream(), **kw) as lat:
+            lat.set_option(lbm.LBM_OPT_GRAPH_STEPS, graphs)
+            lat.step(131)
+            lat.set_option(lbm.LBM_OPT_REVERSE, 0)
+            lat.step(1)
+            lat.step(128)
+            out.append((lat.populations(), lat.diag()))
+    u = np.uint32 if precision == 32 else np.uint64
+    assert np.array_equal(out[0][0].view(u), out[1][0].view(u))
+    assert out[0][1]["mass"] == out[1][1]["mass"] and out[0][1]["wall_shear_sum"] == out[1][1]["wall_shear_sum"]
+
+
 def test_checkpoint_restore_continues_bitwise(orc, lbm):
     rho0 = _airway(orc, 320, 64, 5, 100, 40)
     kw = dict(walls=True, bc_x=True, precision=32, T_over_Tc=0.85, kappa=0.5, dp=1e-3)
