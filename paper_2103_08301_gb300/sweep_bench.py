@@ -7,6 +7,10 @@ of uneven size (height 128-512, length 1024-4096) with seeded pressure drop in
 channel the same number of steps; throughput is total node updates per second.
 
   python -m paper_2103_08301_gb300.sweep_bench --steps 200
+  python -m paper_2103_08301_gb300.sweep_bench --batched-only --tma 1 --channels 16 --steps 5
+
+`--batched-only` steps only the batch, with its default plan (no autotune),
+tensor loads on or off (`--tma`), for profiling one batch launch.
 """
 from __future__ import annotations
 
@@ -81,12 +85,44 @@ def run(steps=200, n=64, seed=3, precision=32):
     }
 
 
+def run_batched_only(steps=5, n=16, seed=3, precision=32, tma=0):
+    import torch
+
+    import paper_2103_08301_gb300 as lbm
+    from paper_2103_08301_gb300 import build
+
+    build.build()
+    kw = dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5)
+    eos = lbm.lbm_eos(1.0, 4.0, 1.0, kw["T_over_Tc"], 1.0, kw["kappa"])
+    _, g, l, _ = lbm.lbm_coexistence(eos)
+    chans = [{"nx": s["nx"], "ny": s["ny"], "dp": s["dp"],
+              "rho0": lbm.lbm_airway_rho0(s["nx"], s["ny"], s["film"], s["plug_x"], s["plug_len"], l, g)}
+             for s in _sweep_channels(n, seed)]
+    nodes = sum(c["nx"] * c["ny"] for c in chans)
+    with lbm.Batch(chans, precision=precision, **kw) as b:
+        b.set_option(lbm.LBM_OPT_TMA, tma)
+        b.step(3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.step(steps)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        info = b.launch_info()
+    return {"channels": n, "nodes": nodes, "steps": steps, "tma": tma, "batched_mlups": nodes * steps / t / 1e6,
+            "launch": info}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--channels", type=int, default=64)
+    ap.add_argument("--batched-only", action="store_true")
+    ap.add_argument("--tma", type=int, default=0, choices=[0, 1])
     args = ap.parse_args()
-    print(json.dumps(run(steps=args.steps, n=args.channels)))
+    if args.batched_only:
+        print(json.dumps(run_batched_only(steps=args.steps, n=args.channels, tma=args.tma)))
+    else:
+        print(json.dumps(run(steps=args.steps, n=args.channels)))
 
 
 if __name__ == "__main__":

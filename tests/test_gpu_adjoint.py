@@ -253,3 +253,51 @@ def test_airway_workload_gradients_2000_steps(adjm, orc, precision):
         assert abs(got_p - fd_plug[k]) <= 1e-3 * abs(fd_plug[k]), ("plug", k, got_p, fd_plug[k])
         got_dp = grads[k][1]["dp"]
         assert abs(got_dp - fd_dp[k]) <= 1e-3 * abs(fd_dp[k]), ("dp", k, got_dp, fd_dp[k])
+
+
+def _node_fd(orc, c, s, r0, x, y, h):
+    """Central difference of the oracle's (J_tau, J_p) in the initial density of node (x, y)."""
+    def J(r):
+        _, d = orc.run(s, orc.init(s, r), c["steps"])
+        return np.array([d["J"], d["Jp"]])
+    rp, rm = r0.copy(), r0.copy()
+    rp[y, x] += h
+    rm[y, x] -= h
+    return (J(rp) - J(rm)) / (2 * h)
+
+
+@pytest.mark.parametrize("name", ["two_phase_columns", "periodic_body_force"])
+def test_per_node_density_gradient_matches_oracle(adjm, orc, name):
+    """dJ/drho0 at single nodes against Richardson-extrapolated central
+    differences of the oracle (steps 1e-5 and 2.5e-6, which agree to 1e-5, so
+    no kink lies between them): interior bulk and interface nodes, the first
+    fluid rows next to both walls, a wall-film node, the nodes next to the
+    inlet and outlet columns and the column nodes themselves (zero where
+    pressure columns overwrite them, nonzero in the periodic channel). Solid
+    wall-row nodes are ignored by the step, so both gradients are zero there."""
+    c = _case(name)
+    nx, ny = c["nx"], c["ny"]
+    adj, s, _ = _adjoint(adjm, orc, c)
+    with adj:
+        grads = [adj.backward(1.0, 0.0)[0], adj.backward(0.0, 1.0)[0]]
+    r0 = _rho0(orc, c, s)
+    interior = [(48, 20), (30, 20), (70, 3)]
+    wall_adjacent = [(48, 1), (40, ny - 2), (nx - 3, 1)]
+    column = [(1, 20), (nx - 2, 10), (0, 20), (nx - 1, 5)]
+    fd = {}
+    for (x, y) in interior + wall_adjacent + column:
+        d1 = _node_fd(orc, c, s, r0, x, y, 1e-5)
+        d2 = _node_fd(orc, c, s, r0, x, y, 2.5e-6)
+        assert np.abs(d1 - d2).max() <= 1e-5 * np.abs(d2).max() + 1e-300, ((x, y), d1, d2)
+        fd[(x, y)] = (16.0 * d2 - d1) / 15.0
+    scale = max(np.abs(v).max() for v in fd.values())
+    for (x, y), ref in fd.items():
+        for k in range(2):
+            got = grads[k][y, x]
+            assert abs(got - ref[k]) <= 1e-6 * abs(ref[k]) + 1e-9 * scale, (name, (x, y), k, got, ref[k])
+    if c["bc_x"]:
+        for k in range(2):
+            assert fd[(0, 20)][k] == 0.0 and fd[(nx - 1, 5)][k] == 0.0
+            assert np.abs(grads[k][:, 0]).max() <= 1e-12 * scale and np.abs(grads[k][:, -1]).max() <= 1e-12 * scale
+    for k in range(2):
+        assert np.abs(grads[k][0]).max() <= 1e-12 * scale and np.abs(grads[k][-1]).max() <= 1e-12 * scale
