@@ -221,16 +221,16 @@ def _extras(stream, op):
     nx, ny, steps = 512, 128, 2000
     _, g, l, _ = lbm.lbm_coexistence(lbm.lbm_eos(1.0, 4.0, 1.0, 0.85, 1.0, 0.5))
     r0 = lbm.lbm_airway_rho0(nx, ny, 6.0, 128, 48.0, l, g, 4.0, 1e-3, 1)
-    for key, prec in (("adjoint", 32), ("adjoint_fp64_forward", 64)):
+    for key, prec, rev in (("adjoint", 32, 64), ("adjoint_fp32_reverse", 32, 32), ("adjoint_fp64_forward", 64, 64)):
         with adjm.Adjoint(nx, ny, steps, walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, block_steps=100,
-                          precision=prec) as adj:
+                          precision=prec, reverse_precision=rev) as adj:
             t0 = time.perf_counter()
             adj.forward(r0, dp=1e-3)
             t1 = time.perf_counter()
             adj.backward(1.0, 1.0)
             t2 = time.perf_counter()
         out[key] = {"workload": f"512x128 airway, 2000 steps, FP{prec} forward with checkpoints every 100, "
-                                f"FP64 reverse",
+                                f"FP{rev} reverse",
                     "forward_s": t1 - t0, "backward_s": t2 - t1,
                     "reverse_mlups": nx * ny * steps / (t2 - t1) / 1e6}
     # the same channel with a wall mask (a constriction on both walls every

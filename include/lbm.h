@@ -468,8 +468,9 @@ lbm_status lbm_plug_analysis(int32_t nx, int32_t ny, const double *rho, double r
  *
  * lbm_adjoint_init: grid->precision is the precision of the forward steps and
  *   checkpoints, 64 or 32 (LBM_ERR_ARG otherwise); the reverse sweep is FP64
- *   either way, on the stored states widened to FP64, so with 32 the result is
- *   the gradient of the FP64 step along the FP32 trajectory. nsteps >= 1.
+ *   unless lbm_adjoint_set_precision says otherwise, on the stored states
+ *   widened to FP64, so with 32 the result is the gradient of the FP64 step
+ *   along the FP32 trajectory. nsteps >= 1.
  *   Allocates on the current device; stream as in lbm_init.
  * lbm_adjoint_forward: runs nsteps steps from f0 = f_eq(rho0, 0) under
  *   `drive` (NULL: no drive), keeping checkpoints, and returns J (host,
@@ -492,6 +493,14 @@ lbm_status lbm_adjoint_backward(lbm_adjoint *adj, double w_tau, double w_p, doub
  * effect at the next forward; a backward before that forward returns
  * LBM_ERR_STATE. Errors: LBM_ERR_ARG as lbm_set_collision. */
 lbm_status lbm_adjoint_set_collision(lbm_adjoint *adj, const lbm_collision *c);
+/* Arithmetic of the reverse sweep and of the objective's per-node terms:
+ * 64 (the default) or 32. With 32 the fields recomputed from each stored
+ * state, the adjoint populations and the per-step terms are FP32, on the FP32
+ * pipes; the sums over steps and nodes (J, dJ/d dp, dJ/dG) and grad_rho0 stay
+ * FP64. Meant for an FP32 forward whose gradients are wanted to a relative
+ * 1e-3 or so (FP32 rounding compounds over the reverse steps). Takes effect at
+ * the next forward or backward. Errors: LBM_ERR_ARG (adj NULL, or not 32/64). */
+lbm_status lbm_adjoint_set_precision(lbm_adjoint *adj, int32_t reverse_precision);
 const char *lbm_adjoint_last_error(const lbm_adjoint *adj);
 void lbm_adjoint_free(lbm_adjoint *adj);
 

@@ -117,6 +117,7 @@ _SIGS = {
     "lbm_adjoint_forward": (C.c_int, [_P, C.POINTER(lbm_drive), _P, C.POINTER(C.c_double)]),
     "lbm_adjoint_backward": (C.c_int, [_P, C.c_double, C.c_double, _P, C.POINTER(C.c_double)]),
     "lbm_adjoint_set_collision": (C.c_int, [_P, C.POINTER(lbm_collision)]),
+    "lbm_adjoint_set_precision": (C.c_int, [_P, C.c_int32]),
     "lbm_adjoint_last_error": (C.c_char_p, [_P]),
     "lbm_adjoint_free": (None, [_P]),
 }

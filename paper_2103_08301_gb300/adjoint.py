@@ -12,8 +12,10 @@ Binding of the ``lbm_adjoint_*`` entry points of ``include/lbm.h`` plus two
 
 Chained, they give dJ/d(pressure drop, film thickness, plug length). The
 forward steps and checkpoints run in FP64 (precision=64) or FP32
-(precision=32, half the checkpoint memory); the reverse sweep is FP64 either
-way, on the stored states widened to FP64.
+(precision=32, half the checkpoint memory); the reverse sweep is FP64
+(reverse_precision=64, on the stored states widened to FP64) or FP32
+(reverse_precision=32, for an FP32 forward: per-step arithmetic in FP32, sums
+over steps and nodes in FP64).
 """
 from __future__ import annotations
 
@@ -45,7 +47,7 @@ class Adjoint:
 
     def __init__(self, nx, ny, nsteps, *, walls=True, bc_x=True, a=1.0, b=4.0, R=1.0, T_over_Tc=0.85,
                  k=1.0, kappa=0.5, tau=1.0, wetting=0.0, p_ref=None, eos="cs", omega=0.344, collision="bgk",
-                 s_e=1.64, s_eps=1.54, s_j=1.0, s_q=1.7, s_nu=None, block_steps=0, precision=64, stream=None):
+                 s_e=1.64, s_eps=1.54, s_j=1.0, s_q=1.7, s_nu=None, block_steps=0, precision=64, reverse_precision=64, stream=None):
         self.nx, self.ny, self.nsteps = nx, ny, nsteps
         self.grid = lbm_grid(nx, ny, int(walls), int(bc_x), int(precision))
         self.eos = lbm_eos(a, b, R, T_over_Tc, k, kappa, {"cs": LBM_EOS_CS, "pr": LBM_EOS_PR}[eos], omega)
@@ -61,6 +63,8 @@ class Adjoint:
                 raise ValueError(collision)
             coll = lbm_collision(LBM_COLL_MRT, s_e, s_eps, s_j, s_q, 0.0 if s_nu is None else s_nu)
             self._chk(lib().lbm_adjoint_set_collision(self.h, C.byref(coll)))
+        if reverse_precision != 64:
+            self._chk(lib().lbm_adjoint_set_precision(self.h, int(reverse_precision)))
         self.generation = 0      # forward runs so far (guards stale backward calls)
         self._rho0_like = None
 

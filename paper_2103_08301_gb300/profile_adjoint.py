@@ -7,6 +7,7 @@ pressure columns with a drop of 1e-3, CS EOS at 0.85 Tc, kappa = 0.5, seeded
 synthetic initial density (noise 1e-3).
 
   python -m paper_2103_08301_gb300.profile_adjoint --nx 512 --ny 128 --steps 2000 [--precision 32]
+      [--reverse-precision 32]
 
 Prints the forward and backward wall times and the reverse throughput.
 """
@@ -24,6 +25,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--block-steps", type=int, default=100)
+    ap.add_argument("--reverse-precision", type=int, default=64, choices=[32, 64])
     ap.add_argument("--repeat", type=int, default=1, help="backward passes timed (the first is reported too)")
     args = ap.parse_args()
 
@@ -38,9 +40,11 @@ def main():
     _, g, l, _ = lbm.lbm_coexistence(lbm.lbm_eos(1.0, 4.0, 1.0, 0.85, 1.0, 0.5))
     plug = 48.0 if nx == 512 else nx * 3 / 32
     r0 = lbm.lbm_airway_rho0(nx, ny, 6.0, nx / 4, plug, l, g, 4.0, 1e-3, 1)
-    out = {"nx": nx, "ny": ny, "steps": args.steps, "precision": args.precision}
+    out = {"nx": nx, "ny": ny, "steps": args.steps, "precision": args.precision,
+           "reverse_precision": args.reverse_precision}
     with adjm.Adjoint(nx, ny, args.steps, walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5,
-                      block_steps=args.block_steps, precision=args.precision) as adj:
+                      block_steps=args.block_steps, precision=args.precision,
+                      reverse_precision=args.reverse_precision) as adj:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         J = adj.forward(r0, dp=1e-3)

@@ -137,6 +137,7 @@ def test_adjoint_rejects_bad_arguments_before_touching_the_gpu(lbm):
     assert st == lbm.LBM_ERR_PARAM
     g = (C.c_double * 3)()
     assert lbm.lib().lbm_adjoint_backward(None, 1.0, 0.0, None, g) == lbm.LBM_ERR_ARG
+    assert lbm.lib().lbm_adjoint_set_precision(None, 32) == lbm.LBM_ERR_ARG
     lbm.lib().lbm_adjoint_free(None)  # NULL-safe
 
 

@@ -208,8 +208,8 @@ def test_autograd_chain_film_plug_and_pressure_drop(adjm, orc):
 _AIRWAY_J = {}
 
 
-@pytest.mark.parametrize("precision", [64, 32])
-def test_airway_workload_gradients_2000_steps(adjm, orc, precision):
+@pytest.mark.parametrize("precision,reverse", [(64, 64), (32, 64), (32, 32)])
+def test_airway_workload_gradients_2000_steps(adjm, orc, precision, reverse):
     # the airway workload: 512 x 128 channel, film 6, plug 48 at x = 128,
     # 0.85 Tc, dp = 1e-3, noise 1e-3, 2000 FP64 steps. J is smooth in film
     # thickness and plug length; central differences of the oracle (step 1e-3)
@@ -218,7 +218,9 @@ def test_airway_workload_gradients_2000_steps(adjm, orc, precision):
     # reference is the difference at step 1e-7 and the bound is the 1e-3 the
     # method targets. precision = 32: FP32 forward and checkpoints (every 100
     # steps), FP64 reverse; J within 1e-5 of the FP64 oracle's, gradients within
-    # the same 1e-3 of its central differences.
+    # the same 1e-3 of its central differences. reverse = 32: the reverse sweep
+    # and the objective's per-step terms in FP32 as well (sums over steps in
+    # FP64), held to the same bounds.
     nx, ny, steps = 512, 128, 2000
     kw = dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5)
     g, l, _ = orc.Setup(nx=nx, ny=ny, dp=1e-3, **kw).coexistence()
@@ -234,7 +236,8 @@ def test_airway_workload_gradients_2000_steps(adjm, orc, precision):
 
     import paper_2103_08301_gb300 as lbm
     block = 100 if precision == 32 else 0
-    with adjm.Adjoint(nx, ny, steps, precision=precision, block_steps=block, **kw) as adj:
+    with adjm.Adjoint(nx, ny, steps, precision=precision, reverse_precision=reverse, block_steps=block,
+                      **kw) as adj:
         r0 = synth.airway_rho0(nx, ny, 6.0, 128, 48.0, l, g, noise=1e-3, seed=1)
         Jg = adj.forward(r0, dp=1e-3)
         grads = [adj.backward(1.0, 0.0), adj.backward(0.0, 1.0)]
@@ -301,3 +304,23 @@ def test_per_node_density_gradient_matches_oracle(adjm, orc, name):
             assert np.abs(grads[k][:, 0]).max() <= 1e-12 * scale and np.abs(grads[k][:, -1]).max() <= 1e-12 * scale
     for k in range(2):
         assert np.abs(grads[k][0]).max() <= 1e-12 * scale and np.abs(grads[k][-1]).max() <= 1e-12 * scale
+
+
+def test_fp32_reverse_sweep_tracks_the_fp64_one(adjm, orc):
+    """The FP32 reverse sweep on an FP32 forward against the FP64 sweep on the
+    same stored states: per-node dJ/drho0 within 1e-4 of the largest entry and
+    the drive gradients within 1e-4 relative (FP32 rounding over 200 reverse
+    steps of a two-phase channel under a body force)."""
+    c = _case("periodic_body_force")
+    s, _ = _setup(orc, c)
+    r0 = _rho0(orc, c, s)
+    out = {}
+    for rev in (64, 32):
+        with adjm.Adjoint(c["nx"], c["ny"], c["steps"], walls=True, bc_x=False, T_over_Tc=c["T_over_Tc"],
+                          kappa=c["kappa"], precision=32, reverse_precision=rev) as adj:
+            J = adj.forward(r0, gx=c["gx"])
+            out[rev] = (J, adj.backward(1.0, 0.5))
+    (J64, (g64, d64)), (J32, (g32, d32)) = out[64], out[32]
+    assert abs(J32[0] / J64[0] - 1) < 1e-5 and abs(J32[1] / J64[1] - 1) < 1e-5
+    assert np.abs(g32 - g64).max() <= 1e-4 * np.abs(g64).max()
+    assert abs(d32["gx"] / d64["gx"] - 1) < 1e-4
