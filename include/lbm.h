@@ -62,8 +62,12 @@ typedef enum {
  *        channel walls; lbm_init's wall_mask adds solid nodes anywhere).
  * bc_x:  0 = periodic in x; 1 = column 0 is the pressure inlet and column
  *        nx-1 the pressure outlet.
- * Limits: nx, ny >= 4 (>= 1 for a periodic axis), 9*nx*ny < 2^31 (32-bit
- * population indices: at most ~238 million nodes per context). */
+ * Limits: nx, ny >= 4 (>= 1 for a periodic axis); pitch*ny < 2^31 nodes and
+ * 9*ny < 2^31, with pitch = nx rounded up to a multiple of 4. A context whose
+ * 9*pitch*ny population slots reach 2^31 (above ~238 million nodes) steps
+ * with kernels that take 64-bit population offsets; the wall-mask path
+ * (wall_mask, LBM_OPT_GENERAL), the batch, lbm_step_noalloc and the adjoint
+ * keep 9*pitch*ny < 2^31 (LBM_ERR_ARG above). */
 typedef struct {
     int32_t nx, ny;
     int32_t walls;

@@ -65,16 +65,17 @@ Layout layout_of(int nx, int ny, int precision)
     return L;
 }
 
-bool grid_ok(const lbm_grid *g)
+// big: a context may take 64-bit population offsets (node indices, and the
+// 9 ny plane-rows of a tensor map, stay below 2^31); otherwise 9 pitch ny < 2^31.
+bool grid_ok(const lbm_grid *g, bool big = false)
 {
     if (!g) return false;
     if (g->precision != 32 && g->precision != 64) return false;
     if (g->walls != 0 && g->walls != 1) return false;
     if (g->bc_x != 0 && g->bc_x != 1) return false;
     if (g->nx < (g->bc_x ? 4 : 1) || g->ny < (g->walls ? 4 : 1)) return false;
-    // 32-bit population indices: 9 nx ny < 2^31 (up to ~238 million nodes)
-    if (9ll * lbm::pitch_of(g->nx) * g->ny >= (1ll << 31)) return false;
-    return true;
+    if (big) return (long long)lbm::pitch_of(g->nx) * g->ny < (1ll << 31) && 9ll * g->ny < (1ll << 31);
+    return lbm::idx32_ok(g->nx, g->ny);
 }
 
 } // namespace
@@ -97,6 +98,7 @@ struct lbm_ctx {
     int W = STRIP, nstrips = 0, yf0 = 0, nyf = 0;
     int W_opt = 0;  // LBM_OPT_STRIP (0: widest)
     int pitch = 0;  // plane pitch of the population rows (>= nx)
+    bool big = false;  // 9 pitch ny >= 2^31: kernels with 64-bit population offsets
     long long units = 0;
     int band = 0;  // rows per band of the work-unit order
     int nctas = 0;
@@ -267,6 +269,12 @@ void *rows2_kernel_ptr(bool walls, bool pres)
 void *step_kernel_ptr(const lbm_ctx *ctx, int mode)
 {
     const bool padded = ctx->pitch != ctx->grid.nx;
+    if (ctx->big) {
+        if (mode == lbm::MODE_STEP && ctx->rows2)
+            return lbm_big_rows2_kernel_ptr(ctx->grid.walls, ctx->grid.bc_x, padded);
+        return lbm_big_step_kernel_ptr(ctx->grid.precision, mode, ctx->grid.walls, ctx->grid.bc_x, ctx->staged,
+                                       padded);
+    }
     if (mode == lbm::MODE_STEP && ctx->rows2)
         return padded ? rows2_kernel_ptr<true>(ctx->grid.walls, ctx->grid.bc_x)
                       : rows2_kernel_ptr<false>(ctx->grid.walls, ctx->grid.bc_x);
@@ -547,6 +555,11 @@ lbm_status plan_geometry(lbm_ctx *ctx)
     lbm::mask_free(ctx->mask);
     ctx->mask = nullptr;
     const uint8_t *m = ctx->mask_host.empty() ? nullptr : ctx->mask_host.data();
+    if (ctx->big && (m || ctx->force_general)) {
+        std::snprintf(ctx->last_error, sizeof ctx->last_error,
+                      "the general-geometry kernels need 9 pitch ny < 2^31");
+        return LBM_ERR_ARG;
+    }
     lbm_status st = lbm::mask_setup(m, ctx->grid, ctx->pitch, ctx->sms, ctx->force_general, ctx->stream, &ctx->mask,
                                     ctx->last_error, sizeof ctx->last_error);
     if (st == LBM_OK && ctx->mask) ctx->nctas = lbm::mask_blocks(ctx->mask);
@@ -577,7 +590,7 @@ const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->last_error : 
 
 size_t lbm_workspace_bytes(const lbm_grid *grid)
 {
-    if (!grid_ok(grid)) return 0;
+    if (!grid_ok(grid, true)) return 0;
     return layout_of(grid->nx, grid->ny, grid->precision).total;
 }
 
@@ -587,7 +600,7 @@ lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, const 
 {
     if (!out) return LBM_ERR_ARG;
     *out = nullptr;
-    if (!grid_ok(grid) || !eos || !rho0) return LBM_ERR_ARG;
+    if (!grid_ok(grid, true) || !eos || !rho0) return LBM_ERR_ARG;
     if (!(tau > 0.5) || !(eos->k > 0) || !(eos->kappa >= 0) || !(eos->a > 0) || !(eos->b > 0) ||
         !(eos->R > 0) || !(eos->T_over_Tc > 0) || !std::isfinite(wetting))
         return LBM_ERR_PARAM;
@@ -625,6 +638,7 @@ lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, const 
 
     ctx->L = layout_of(grid->nx, grid->ny, grid->precision);
     ctx->pitch = lbm::pitch_of(grid->nx);
+    ctx->big = !lbm::idx32_ok(grid->nx, grid->ny);
     if (workspace) {
         if (ws_bytes < ctx->L.total || ((uintptr_t)workspace % ALIGN) != 0) {
             lbm_free(ctx);
@@ -934,6 +948,7 @@ lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
         ctx->pf = (int)value;
         return LBM_OK;
     case LBM_OPT_GENERAL:
+        if (value != 0 && ctx->big) return LBM_ERR_ARG;  // 32-bit offsets only
         ctx->force_general = value != 0;
         break;
     case LBM_OPT_GRAPH_STEPS:
@@ -944,7 +959,8 @@ lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
     case LBM_OPT_FAULT_SKIP_COPY:
         // the test build exists for walls, pressure columns and unpadded rows
         if (value != 0) {
-            if (!(ctx->rows2 && !ctx->mask && ctx->grid.walls && ctx->grid.bc_x && ctx->pitch == ctx->grid.nx))
+            if (!(ctx->rows2 && !ctx->mask && !ctx->big && ctx->grid.walls && ctx->grid.bc_x &&
+                  ctx->pitch == ctx->grid.nx))
                 return LBM_ERR_ARG;
             cudaError_t e = cudaFuncSetAttribute((void *)lbm::step_kernel_rows2<true, true, false, true>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,

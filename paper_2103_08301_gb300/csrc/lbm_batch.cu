@@ -529,7 +529,7 @@ lbm_status lbm_batch_init(int32_t n, const lbm_grid *grids, const lbm_eos *eos, 
     if (n <= 0 || !grids || !eos || !rho0s) return LBM_ERR_ARG;
     for (int i = 0; i < n; ++i) {
         const lbm_grid &g = grids[i];
-        if (lbm_workspace_bytes(&g) == 0 || !rho0s[i]) return LBM_ERR_ARG;
+        if (lbm_workspace_bytes(&g) == 0 || !lbm::idx32_ok(g.nx, g.ny) || !rho0s[i]) return LBM_ERR_ARG;
         if (g.precision != grids[0].precision || g.walls != grids[0].walls || g.bc_x != grids[0].bc_x)
             return LBM_ERR_ARG;
     }

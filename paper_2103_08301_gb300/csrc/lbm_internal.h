@@ -53,6 +53,12 @@ double node_noise(uint64_t seed, uint64_t node, double amp);
 // row segment of the bulk-copy staged kernel is 16-byte aligned.
 inline int pitch_of(int nx) { return (nx + 3) & ~3; }
 
+// Whether 32-bit population offsets address the grid: 9 pitch ny < 2^31
+// (about 238 million nodes). Larger single-channel grids take the kernels
+// with 64-bit offsets; the batch, the wall-mask path, the allocation-free
+// entry and the adjoint keep the 32-bit bound.
+inline bool idx32_ok(int nx, int ny) { return 9ll * pitch_of(nx) * ny < (1ll << 31); }
+
 // Strip width for an nx-column channel: the widest up to w_max, except that
 // the outlet column must not open a strip (its stencil reaches two columns
 // back); widths that keep 16-byte alignment (multiples of 4) are preferred.
@@ -105,3 +111,7 @@ cudaError_t mask_launch(const MaskPath *m, const KArgs<real> &A, int mode, cudaS
 // (lbm::MODE_STEP or MODE_FIELDS), the boundary set, the staged variant and a
 // row pitch above nx (padded).
 void *lbm_step_kernel_ptr(int precision, int mode, bool walls, bool pres, bool staged, bool padded);
+// The same kernels with 64-bit population offsets (lbm_big.cu), and the FP32
+// row-pair step likewise, for grids whose 9 pitch ny slots reach 2^31.
+void *lbm_big_step_kernel_ptr(int precision, int mode, bool walls, bool pres, bool staged, bool padded);
+void *lbm_big_rows2_kernel_ptr(bool walls, bool pres, bool padded);

@@ -646,7 +646,8 @@ struct Smem {
 // with one row of register prefetch and re-reads the collision row from L1.
 // In both variants four halo lanes load the two columns beyond each strip
 // edge with one row of register prefetch.
-template <typename real, bool WALLS, bool PRES, int MODE, int BLOCK, bool STAGED, int CP, bool PADDED>
+template <typename real, bool WALLS, bool PRES, int MODE, int BLOCK, bool STAGED, int CP, bool PADDED,
+          typename IX = int>
 __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<real> &G, int s, int ya, int yb,
                                             Smem<real, BLOCK> &S, real *stages, uint64_t *bars,
                                             RingPos &ring_next, Acc<real, CP> &acc, bool &lost)
@@ -724,7 +725,7 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
     // halo (and, without staging, own-column) loads of stencil row yy
     auto prefetch = [&](int yy) {
         bool mir;
-        const int row = map_row<WALLS>(yy, ny, mir) * rstride;
+        const IX row = (IX)map_row<WALLS>(yy, ny, mir) * rstride;
         add_next = mir ? A.wet : real(0);
         if constexpr (!STAGED) {
             if (active) {
@@ -743,7 +744,7 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
         if (j < nrows) {
             if (tid == PRODUCER) {
                 bool mir;
-                const int row = map_row<WALLS>(ya - 2 + j, ny, mir) * rstride;
+                const IX row = (IX)map_row<WALLS>(ya - 2 + j, ny, mir) * rstride;
                 const uint32_t st = ring_issue.s;
                 real *dst = stages + (size_t)st * 9 * SP;
                 const real *src = G.fin + row + x0;
@@ -779,7 +780,7 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
         V f[9];
         if constexpr (!STAGED) {
             if (collide && active) {
-                const real *src = col_in + r * rstride;
+                const real *src = col_in + (IX)r * rstride;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) f[i] = __ldg(src + i * P);
             }
@@ -917,7 +918,7 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
                     for (int i = 0; i < 9; ++i) set_el(fs[i], kc, fsc[i]);
                 }
                 real *const out = G.fout;
-                const int oi = r * rstride + xa;  // slot of (xa, r) in plane 0
+                const IX oi = (IX)r * rstride + xa;  // slot of (xa, r) in plane 0
                 const bool y_inner = WALLS ? (r >= 2 && r <= ny - 3) : (r >= 1 && r <= ny - 2);
                 if (x_inner && y_inner) {
                     if constexpr (CP == 1) {
@@ -945,7 +946,8 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
                 } else {
 #pragma unroll
                     for (int k = 0; k < CP; ++k) {
-                        const int xk = xa + k, ok = oi + k;
+                        const int xk = xa + k;
+                        const IX ok = oi + k;
 #pragma unroll
                         for (int i = 0; i < 9; ++i) {
                             const int ty = r + ey_(i);
@@ -961,7 +963,7 @@ __device__ __forceinline__ void run_segment(const KArgs<real> &A, const Geom<rea
                                 }
                                 int tyw = ty;
                                 if (!WALLS) tyw = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
-                                out[tyw * rstride + i * P + tx] = el(fs[i], k);
+                                out[(IX)tyw * rstride + i * P + tx] = el(fs[i], k);
                             }
                         }
                     }
@@ -1067,8 +1069,9 @@ __device__ __forceinline__ void cta_reduce(Acc<real, CP> &acc, SM &S, double &m,
 
 // PADDED: the population rows have a plane pitch above nx (taken from the
 // arguments); otherwise the pitch is nx itself, which the compiler can share
-// with the bounds arithmetic (4% faster than carrying both).
-template <typename real, bool WALLS, bool PRES, int MODE, bool STAGED, bool PADDED>
+// with the bounds arithmetic (4% faster than carrying both). IX: the type of
+// population offsets, int while 9 pitch ny < 2^31, long long above.
+template <typename real, bool WALLS, bool PRES, int MODE, bool STAGED, bool PADDED, typename IX = int>
 __global__ void __launch_bounds__(threads_per_cta<real, STAGED>(),
                                   MinBlocks<real, threads_per_cta<real, STAGED>()>::value)
     step_kernel(const KArgs<real> A)
@@ -1107,7 +1110,7 @@ __global__ void __launch_bounds__(threads_per_cta<real, STAGED>(),
         const long long ue = min(u1, run_end);
         const int yb = ya + (int)(ue - u);
         u = ue;
-        run_segment<real, WALLS, PRES, MODE, BLOCK, STAGED, CP, PADDED>(A, G, s, ya, yb, S, stages, bars, ring_next,
+        run_segment<real, WALLS, PRES, MODE, BLOCK, STAGED, CP, PADDED, IX>(A, G, s, ya, yb, S, stages, bars, ring_next,
                                                                        acc, lost);
     }
 
@@ -1223,7 +1226,7 @@ __global__ void batch_diag_kernel(const double *__restrict__ seg_mass, const dou
 }
 
 // f = f_eq(rho0, 0) at every node (rho0: nx x ny; populations with plane
-// pitch P). Padding columns are zeroed.
+// pitch P, 64-bit offsets). Padding columns are zeroed.
 template <typename real>
 __global__ void init_kernel(const double *__restrict__ rho0, real *__restrict__ fa,
                             real *__restrict__ fb, int nx, int P, int ny)
@@ -1235,8 +1238,8 @@ __global__ void init_kernel(const double *__restrict__ rho0, real *__restrict__ 
         feq_pairs<real>(x < nx ? (real)rho0[(long long)y * nx + x] : real(0), real(0), real(0), real(0), real(0), fe);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            fa[(9 * y + i) * P + x] = fe[i];
-            fb[(9 * y + i) * P + x] = fe[i];
+            fa[(long long)(9 * y + i) * P + x] = fe[i];
+            fb[(long long)(9 * y + i) * P + x] = fe[i];
         }
     }
 }

@@ -127,7 +127,7 @@ __device__ __forceinline__ float2 stage_pair(const float *slot, int i, int sc)
 // the copy of the final pair is never issued, so the wait for it gives up
 // after KArgs::poll_limit polls; no later copy reuses that slot, so nothing is
 // left in flight when the CTA exits.
-template <bool WALLS, bool PRES, bool PADDED, bool HOOK = false>
+template <bool WALLS, bool PRES, bool PADDED, bool HOOK = false, typename IX = int>
 __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom<float> &G, int s, int ya, int yb,
                                                SmemR2 &S, float *stages, uint64_t *bars,
                                                RingPos2 &ring_next, const CUtensorMap *tmap, Acc<float, 1> &acc,
@@ -228,7 +228,7 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
                     bool mir;
-                    const float *src = G.fin + map_row<WALLS>(ya - 2 + 2 * q + t, ny, mir) * rstride;
+                    const float *src = G.fin + (IX)map_row<WALLS>(ya - 2 + 2 * q + t, ny, mir) * rstride;
                     float *dst = slot + t * R2_ROW;
 #pragma unroll
                     for (int i = 0; i < 9; ++i) bulk_copy_g2s(dst + i * R2_SP + dcol, src + i * P + gx0, mbytes, &bars[st]);
@@ -347,10 +347,10 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
                 }
             }
             float *const out = G.fout;
-            const int oi = b * rstride + xa;  // slot of (xa, b) in plane 0
+            const IX oi = (IX)b * rstride + xa;  // slot of (xa, b) in plane 0
             const bool y_inner = WALLS ? (b >= 2 && b + 1 <= ny - 3) : (b >= 1 && b + 1 <= ny - 2);
             if (x_inner && y_inner && second) {
-                const int oj = oi + rstride;
+                const IX oj = oi + rstride;
                 out[oi] = fs[0].x;      out[oj] = fs[0].y;
                 out[oi + o1] = fs[1].x; out[oj + o1] = fs[1].y;
                 out[oi + o2] = fs[2].x; out[oj + o2] = fs[2].y;
@@ -364,7 +364,8 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     if (e == 1 && !second) break;
-                    const int r = b + e, ok = oi + e * rstride;
+                    const int r = b + e;
+                    const IX ok = oi + (IX)e * rstride;
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
                         const int ty = r + ey_(i);
@@ -380,7 +381,7 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
                             }
                             int tyw = ty;
                             if (!WALLS) tyw = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
-                            out[tyw * rstride + i * P + tx] = el(fs[i], e);
+                            out[(IX)tyw * rstride + i * P + tx] = el(fs[i], e);
                         }
                     }
                 }
@@ -439,8 +440,9 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
 #define LBM_R2_MIN_BLOCKS (640 / LBM_R2_BLOCK)
 #endif
 // tmap: 2-D tensor map of A.fin (used when A.tma is set). HOOK: the
-// failure-detection test build (see run_segment_r2).
-template <bool WALLS, bool PRES, bool PADDED, bool HOOK = false>
+// failure-detection test build (see run_segment_r2). IX: the type of
+// population offsets, int while 9 pitch ny < 2^31, long long above.
+template <bool WALLS, bool PRES, bool PADDED, bool HOOK = false, typename IX = int>
 __global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS)
     step_kernel_rows2(const KArgs<float> A, const __grid_constant__ CUtensorMap tmap)
 {
@@ -473,7 +475,7 @@ __global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS)
         const int yb = ya + (int)(ue - u);
         u = ue;
         // the test hook applies to the first CTA's last segment
-        run_segment_r2<WALLS, PRES, PADDED, HOOK>(A, G, s, ya, yb, S, stages, bars, ring_next,
+        run_segment_r2<WALLS, PRES, PADDED, HOOK, IX>(A, G, s, ya, yb, S, stages, bars, ring_next,
                                                   A.tma ? &tmap : nullptr, acc, lost, HOOK && cta == 0 && u == u1);
     }
     if (lost) atomicOr(A.err, 2);

@@ -53,9 +53,30 @@ def test_workspace_bytes(lbm):
     assert lbm.lbm_workspace_bytes(g64) >= 2 * 9 * 256 * 64 * 8
     for bad in [lbm.lbm_grid(0, 64, 0, 0, 32), lbm.lbm_grid(64, 3, 1, 0, 32),
                 lbm.lbm_grid(3, 64, 0, 1, 32), lbm.lbm_grid(64, 64, 0, 0, 16),
-                lbm.lbm_grid(64, 64, 2, 0, 32), lbm.lbm_grid(1 << 16, 1 << 15, 0, 0, 32),
-                lbm.lbm_grid(16384, 16384, 1, 1, 32)]:  # 9 nx ny >= 2^31
+                lbm.lbm_grid(64, 64, 2, 0, 32),
+                lbm.lbm_grid(1 << 16, 1 << 15, 0, 0, 32),  # 2^31 nodes
+                lbm.lbm_grid(1, 1 << 28, 0, 0, 32)]:       # 9 ny >= 2^31 plane-rows
         assert lbm.lbm_workspace_bytes(bad) == 0
+    # past 2^31 population slots a context takes 64-bit offsets
+    big = lbm.lbm_grid(16384, 16384, 1, 1, 32)
+    assert lbm.lbm_workspace_bytes(big) >= 2 * 9 * 16384 * 16384 * 4
+
+
+def test_paths_with_32_bit_offsets_reject_larger_grids(lbm):
+    """The batch, the allocation-free step and the adjoint keep 9 pitch ny < 2^31
+    and refuse larger grids before touching the GPU."""
+    import ctypes as C
+    big = lbm.lbm_grid(16384, 14600, 1, 1, 32)
+    e = lbm.lbm_eos(1.0, 4.0, 1.0, 0.85, 1.0, 0.5)
+    one = (C.c_double * 1)(0.1)
+    rho = (C.POINTER(C.c_double) * 1)(C.cast(one, C.POINTER(C.c_double)))
+    out = C.c_void_p()
+    assert lbm.lib().lbm_batch_init(1, C.byref(big), C.byref(e), 1.0, 0.0, None, rho, None,
+                                    C.byref(out)) == lbm.LBM_ERR_ARG
+    assert lbm.lib().lbm_step_noalloc(C.byref(big), C.byref(e), 1.0, 0.0, None, C.c_void_p(16), C.c_void_p(32),
+                                      0, None, None, None) == lbm.LBM_ERR_ARG
+    assert lbm.lib().lbm_adjoint_init(C.byref(big), C.byref(e), 1.0, 0.0, 10, 0, None,
+                                      C.byref(out)) == lbm.LBM_ERR_ARG
 
 
 def test_init_rejects_bad_arguments_before_touching_the_gpu(lbm):

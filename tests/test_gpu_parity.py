@@ -406,18 +406,32 @@ def test_full_size_one_step_sampled_against_oracle(orc, lbm):
     del f1_ref
 
 
-def test_maximum_size_grid_windows_against_oracle(orc, lbm):
-    """Largest grid the 32-bit population indices allow (9 nx ny just below
-    2^31; 2 x 8.6 GB of FP32 populations). One GPU step depends only on the
-    state within three nodes, so the oracle stepping a periodic window of the
-    GPU's input state reproduces the window's interior exactly; windows at the
-    highest row and column indices, the middle and the origin are checked."""
+BIG_GRIDS = {
+    # the largest grid 32-bit population offsets address (9 nx ny just below 2^31)
+    "periodic_below_2^31": (16384, 14563, dict(T_over_Tc=0.8, kappa=0.5)),
+    # just past it: the kernels with 64-bit offsets
+    "periodic_above_2^31": (16384, 14600, dict(T_over_Tc=0.8, kappa=0.5)),
+    "airway_above_2^31": (16384, 14600, dict(walls=True, bc_x=True, T_over_Tc=0.8, kappa=0.5, dp=1e-4)),
+}
+
+
+@pytest.mark.parametrize("name", list(BIG_GRIDS))
+def test_maximum_size_grid_windows_against_oracle(orc, lbm, name):
+    """Grids at the 32-bit population offset bound (2 x 8.6 GB of FP32
+    populations) and just past it. One GPU step depends only on the state
+    within three nodes, so the oracle stepping a periodic window of the GPU's
+    input state reproduces the window's interior exactly; windows at the
+    highest row and column indices the step reaches through its interior
+    rule, the middle and the origin are checked (with walls and pressure
+    columns, windows stay three nodes clear of them)."""
     import ctypes as C
     import torch
-    nx, ny = 16384, 14563
-    assert 9 * nx * ny < 2**31 <= 9 * nx * (ny + 1)
-    kw = dict(T_over_Tc=0.8, kappa=0.5)
-    s = orc.Setup(nx=8, ny=8, **kw)
+    nx, ny, kw = BIG_GRIDS[name]
+    if name.startswith("periodic_below"):
+        assert 9 * nx * ny < 2**31 <= 9 * nx * (ny + 1)
+    else:
+        assert 9 * nx * ny > 2**31
+    s = orc.Setup(nx=8, ny=8, T_over_Tc=kw["T_over_Tc"], kappa=kw["kappa"])
     g, l, _ = s.coexistence()
     # liquid slabs every 512 columns whose half-width varies smoothly and
     # periodically along y (the profile is continuous across both periodic
@@ -436,13 +450,19 @@ def test_maximum_size_grid_windows_against_oracle(orc, lbm):
         lat.step(1)
         f1 = torch.empty_like(f0)
         assert lbm.lib().lbm_populations(lat.ctx, C.c_void_p(f1.data_ptr())) == lbm.LBM_OK
+        assert not lat.diag()["nan_detected"]
     h = w = 24
-    for y0, x0 in [(ny - h, nx - w), (ny - h - 5, 0), (ny // 2, nx // 2 + 3), (0, 0)]:
+    if kw.get("walls"):
+        corners = [(ny - h - 6, nx - w - 6), (ny - h - 6, 6), (ny // 2, nx // 2 + 3), (6, 6)]
+    else:
+        corners = [(ny - h, nx - w), (ny - h - 5, 0), (ny // 2, nx // 2 + 3), (0, 0)]
+    okw = dict(T_over_Tc=kw["T_over_Tc"], kappa=kw["kappa"])
+    for y0, x0 in corners:
         ys = torch.arange(y0 - 3, y0 + h + 3, device="cuda") % ny
         xs = torch.arange(x0 - 3, x0 + w + 3, device="cuda") % nx
         win0 = f0[:, ys][:, :, xs].double().cpu().numpy()
         got = f1[:, ys[3:-3]][:, :, xs[3:-3]].double().cpu().numpy()
-        sw = orc.Setup(nx=w + 6, ny=h + 6, **kw)
+        sw = orc.Setup(nx=w + 6, ny=h + 6, **okw)
         ref, _ = orc.step(sw, np.ascontiguousarray(win0))
         err = np.abs(got - ref[:, 3:-3, 3:-3]).max() / np.abs(ref).max()
         assert err <= 2e-6, (y0, x0, err)
