@@ -56,6 +56,10 @@ CASES = {
     # the paper's drive: body force along the channel, ends at one pressure
     "bodyforce256x64": dict(nx=256, ny=64, kw=dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=0.0,
                                                   gx=1e-6)),
+    # full height of the benchmark channel (2048 rows) at the benchmark's CTA
+    # count: 9 strips x 2046 rows over 760 CTAs cut into ~85 bands, so band
+    # and segment boundaries fall throughout the height
+    "airway1024x2048": dict(nx=1024, ny=2048, kw=dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=1e-3)),
 }
 
 
@@ -65,6 +69,8 @@ def _rho0(orc, name, c):
     g, l, _ = s.coexistence()
     if name == "droplet128":
         return synth.disk_rho0(nx, ny, 30, l, g, noise=1e-3, seed=1)
+    if name == "airway1024x2048":
+        return synth.airway_rho0(nx, ny, 64, 256, 128, l, g, noise=1e-3, seed=3)
     if name.startswith("airway"):
         return synth.airway_rho0(nx, ny, 6, 128, 48, l, g)
     if name == "ragged200x37":
@@ -87,6 +93,9 @@ def _lat_kw(kw):
     return out
 
 
+_REF = {}
+
+
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("precision,tol", [(64, 1e-11), (32, 1e-4)])
 def test_rho_parity_after_1000_steps(orc, lbm, name, precision, tol):
@@ -94,8 +103,10 @@ def test_rho_parity_after_1000_steps(orc, lbm, name, precision, tol):
     nx, ny, kw = c["nx"], c["ny"], c["kw"]
     rho0 = _rho0(orc, name, c)
     s = orc.Setup(nx=nx, ny=ny, **kw)
-    f_ref, d_ref = orc.run(s, orc.init(s, rho0), 1000)
-    ref = orc.fields(s, f_ref)
+    if name not in _REF:  # the oracle's 1000 steps, shared by both precisions
+        f_ref, d_ref = orc.run(s, orc.init(s, rho0), 1000)
+        _REF[name] = (orc.fields(s, f_ref), d_ref)
+    ref, d_ref = _REF[name]
     with lbm.Lattice(nx, ny, rho0, precision=precision, **_lat_kw(kw)) as lat:
         lat.step(1000)
         got = lat.fields()
@@ -104,7 +115,9 @@ def test_rho_parity_after_1000_steps(orc, lbm, name, precision, tol):
     assert err <= tol, f"{name} fp{precision}: rel Linf(rho) {err:.3e}"
     vscale = max(np.abs(ref["vx"]).max(), np.abs(ref["vy"]).max(), 1e-12)
     verr = max(np.abs(got["vx"] - ref["vx"]).max(), np.abs(got["vy"] - ref["vy"]).max()) / vscale
-    assert verr <= (1e-9 if precision == 64 else 3e-2), f"velocity {verr:.3e}"
+    # FP32 bounds below: about five times the largest deviation measured over
+    # these cases on GB300 (velocity 2.0e-4, tau_w 5.6e-4, p_w 4.6e-5, J 6e-6)
+    assert verr <= (1e-9 if precision == 64 else 1e-3), f"velocity {verr:.3e}"
     # diagnostics of the 1000 states read
     # FP32: open channels exchange mass through the pressure columns, so the
     # mass follows the (slightly different) FP32 trajectory
@@ -113,17 +126,17 @@ def test_rho_parity_after_1000_steps(orc, lbm, name, precision, tol):
         J = d_ref["J"]
         # scale: the sum of |tau_w| bounds, so a J that cancels to ~0 is not over-weighted
         Jscale = max(abs(J), 1000 * 2 * nx * max(abs(d_ref["tw_min"]), abs(d_ref["tw_max"])) * 1e-3)
-        assert abs(d["wall_shear_sum"] - J) <= (1e-9 if precision == 64 else 1e-2) * Jscale
+        assert abs(d["wall_shear_sum"] - J) <= (1e-9 if precision == 64 else 3e-5) * Jscale
         for k_gpu, k_ref in [("p_wall_min", "pw_min"), ("p_wall_max", "pw_max")]:
             assert abs(d[k_gpu] - d_ref[k_ref]) <= (1e-12 if precision == 64 else 1e-5)
         for k_gpu, k_ref in [("tau_wall_min", "tw_min"), ("tau_wall_max", "tw_max")]:
             assert abs(d[k_gpu] - d_ref[k_ref]) <= (1e-12 if precision == 64 else 1e-5)
         tw_scale = max(np.abs(ref["tau_wall"]).max(), 1e-12)
-        assert np.abs(got["tau_wall"] - ref["tau_wall"]).max() <= (1e-9 if precision == 64 else 3e-2) * tw_scale
+        assert np.abs(got["tau_wall"] - ref["tau_wall"]).max() <= (1e-9 if precision == 64 else 3e-3) * tw_scale
         # FP32: the wall pressure inherits the density deviation times the stiff
         # liquid EOS, so it is bounded relative to its own scale
         pw_scale = np.abs(ref["p_wall"]).max()
-        assert np.abs(got["p_wall"] - ref["p_wall"]).max() <= (1e-13 if precision == 64 else 1e-3 * pw_scale)
+        assert np.abs(got["p_wall"] - ref["p_wall"]).max() <= (1e-13 if precision == 64 else 2e-4 * pw_scale)
 
 
 @pytest.mark.parametrize("nx,ny,walls,bc_x", [(4, 4, True, True), (5, 4, True, False), (1, 9, False, False),
