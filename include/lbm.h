@@ -326,8 +326,8 @@ lbm_status lbm_launch_info(const lbm_ctx *ctx, int64_t *ctas, int64_t *threads, 
  * whose work overlaps on the GPU (for instance on different streams) race on
  * it; serialise them. The first call on a device resolves the array's device
  * address (cudaGetSymbolAddress) and should come before any stream capture.
- * Errors: LBM_ERR_ARG (bad grid, NULL, equal or misaligned buffers, ctas
- * outside 0..4096), LBM_ERR_PARAM, LBM_ERR_CUDA. */
+ * Errors: LBM_ERR_ARG (bad grid or 9*pitch*ny >= 2^31, NULL, equal or
+ * misaligned buffers, ctas outside 0..4096), LBM_ERR_PARAM, LBM_ERR_CUDA. */
 lbm_status lbm_step_noalloc(const lbm_grid *grid, const lbm_eos *eos, double tau, double wetting,
                             const lbm_drive *drive, const void *f_in, void *f_out, int64_t ctas,
                             double *diag_out, int32_t *err_out, void *stream);
