@@ -37,6 +37,12 @@ size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 // lbm_init): LBM_FAULT=alloc fails lbm_init as if its last device allocation
 // had failed, after the workspace was allocated, so the error path's clean-up
 // runs; LBM_FAULT=param fails it as if the thermodynamics had no solution.
+// CTAs whose share of the work is under this many rows per strip take the
+// row-pair kernel that issues a segment's first three stage pairs together
+// (measured: 4096 x 512 +8.6%, 1024 x 128 +6%; 16384 x 2048, ~358 rows per
+// CTA, 0.9% slower with it)
+constexpr long long EARLY_ROWS = 128;
+
 bool fault_is(const char *kind)
 {
     const char *f = std::getenv("LBM_FAULT");
@@ -99,6 +105,7 @@ struct lbm_ctx {
     int W_opt = 0;  // LBM_OPT_STRIP (0: widest)
     int pitch = 0;  // plane pitch of the population rows (>= nx)
     bool big = false;  // 9 pitch ny >= 2^31: kernels with 64-bit population offsets
+    bool early = false;  // row-pair kernel issuing a segment's first three stage pairs together
     long long units = 0;
     int band = 0;  // rows per band of the work-unit order
     int nctas = 0;
@@ -256,15 +263,16 @@ void *lbm_step_kernel_ptr(int precision, int mode, bool walls, bool pres, bool s
 
 namespace {
 
-template <bool PADDED>
+template <bool PADDED, int EARLY>
 void *rows2_kernel_ptr(bool walls, bool pres)
 {
     using namespace lbm;
-    if (walls && pres) return (void *)step_kernel_rows2<true, true, PADDED>;
-    if (walls) return (void *)step_kernel_rows2<true, false, PADDED>;
-    if (pres) return (void *)step_kernel_rows2<false, true, PADDED>;
-    return (void *)step_kernel_rows2<false, false, PADDED>;
+    if (walls && pres) return (void *)step_kernel_rows2<true, true, PADDED, false, int, EARLY>;
+    if (walls) return (void *)step_kernel_rows2<true, false, PADDED, false, int, EARLY>;
+    if (pres) return (void *)step_kernel_rows2<false, true, PADDED, false, int, EARLY>;
+    return (void *)step_kernel_rows2<false, false, PADDED, false, int, EARLY>;
 }
+
 
 void *step_kernel_ptr(const lbm_ctx *ctx, int mode)
 {
@@ -275,9 +283,13 @@ void *step_kernel_ptr(const lbm_ctx *ctx, int mode)
         return lbm_big_step_kernel_ptr(ctx->grid.precision, mode, ctx->grid.walls, ctx->grid.bc_x, ctx->staged,
                                        padded);
     }
-    if (mode == lbm::MODE_STEP && ctx->rows2)
-        return padded ? rows2_kernel_ptr<true>(ctx->grid.walls, ctx->grid.bc_x)
-                      : rows2_kernel_ptr<false>(ctx->grid.walls, ctx->grid.bc_x);
+    if (mode == lbm::MODE_STEP && ctx->rows2) {
+        if (ctx->early)
+            return padded ? rows2_kernel_ptr<true, 3>(ctx->grid.walls, ctx->grid.bc_x)
+                          : rows2_kernel_ptr<false, 3>(ctx->grid.walls, ctx->grid.bc_x);
+        return padded ? rows2_kernel_ptr<true, 1>(ctx->grid.walls, ctx->grid.bc_x)
+                      : rows2_kernel_ptr<false, 1>(ctx->grid.walls, ctx->grid.bc_x);
+    }
     return lbm_step_kernel_ptr(ctx->grid.precision, mode, ctx->grid.walls, ctx->grid.bc_x, ctx->staged, padded);
 }
 
@@ -369,6 +381,7 @@ lbm_status plan_launch(lbm_ctx *ctx)
     ctx->yf0 = ctx->grid.walls ? 1 : 0;
     ctx->nyf = ctx->grid.walls ? ctx->grid.ny - 2 : ctx->grid.ny;
     ctx->units = (long long)ctx->nstrips * ctx->nyf;
+    ctx->early = false;  // chosen once the CTA count is known
 
     for (int mode : {lbm::MODE_STEP, lbm::MODE_FIELDS}) {
         cudaError_t e = cudaFuncSetAttribute(step_kernel_ptr(ctx, mode),
@@ -390,6 +403,13 @@ lbm_status plan_launch(lbm_ctx *ctx)
     n = std::min<long long>(n, lbm::MAX_CTAS);
     ctx->nctas = (int)std::max<long long>(1, n);
     ctx->band = band_rows(ctx->nyf, ctx->nstrips, ctx->nctas, ctx->grid.walls);
+    if (ctx->rows2 && !ctx->big && ctx->units < EARLY_ROWS * ctx->nctas) {
+        ctx->early = true;
+        cudaError_t e = cudaFuncSetAttribute(step_kernel_ptr(ctx, lbm::MODE_STEP),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)dyn_smem(ctx, lbm::MODE_STEP));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "smem attribute");
+    }
     return LBM_OK;
 }
 

@@ -36,6 +36,7 @@ struct ChanHost {
     long long off = 0;  // element offset in the packed buffers
     int pitch = 0;      // plane pitch of the channel's population rows
     int W = STRIP, nstrips = 0, yf0 = 0, nyf = 0;
+    int band = 0, nbands = 1;  // work order: bands of `band` fluid rows, strip by strip within a band
     long long units = 0, unit_base = 0;
 };
 
@@ -58,6 +59,7 @@ struct lbm_batch {
     int64_t step = 0;
     // launch plan and device tables
     int sms = 0, nctas = 0, nseg = 0, ctas_per_sm_opt = 0, W_opt = 0, reverse = 0;
+    int band_opt = 0;  // LBM_OPT_BAND: rows per band of the work order (0 = the channel's height)
     bool allow_staged = true, staged = false;
     bool allow_rows2 = true, rows2 = false;  // LBM_OPT_ROWS2: row-pair FP32 step
     // LBM_OPT_TMA (off by default for batches: reading 2n maps from device
@@ -244,6 +246,11 @@ lbm_status batch_plan(lbm_batch *b)
             c.yf0 = b->walls ? 1 : 0;
             c.nyf = b->walls ? c.grid.ny - 2 : c.grid.ny;
             c.units = (long long)c.nstrips * c.nyf;
+            // bands never start at the row pair ny-3|ny-2 (rows 1|2 need band >= 2)
+            c.band = b->band_opt > 0 ? std::min(c.nyf, std::max(8, b->band_opt)) : c.nyf;
+            if (b->walls)
+                while (c.band < c.nyf && (c.nyf - 1) % c.band == 0) ++c.band;
+            c.nbands = (c.nyf + c.band - 1) / c.band;
             c.unit_base = U;
             U += c.units;
             all4 = all4 && (c.pitch % 4 == 0) && (W % 4 == 0);
@@ -291,13 +298,19 @@ lbm_status batch_plan(lbm_batch *b)
     G = std::min<long long>(G, lbm::MAX_CTAS);
     b->nctas = (int)std::max<long long>(1, G);
 
-    auto locate = [&](long long u, int &ci, int &s, int &row) {
+    // unit u -> (channel, strip, row) in the band-major order of each
+    // channel; `piece_end`: the first unit after u's (band, strip) piece
+    auto locate = [&](long long u, int &ci, int &s, int &row, long long *piece_end = nullptr) {
         ci = 0;
         while (ci + 1 < b->n && b->ch[ci + 1].unit_base <= u) ++ci;
         const ChanHost &c = b->ch[ci];
-        const long long r = u - c.unit_base;
-        s = (int)(r / c.nyf);
-        row = c.yf0 + (int)(r - (long long)s * c.nyf);
+        const long long r = u - c.unit_base, full = (long long)c.nstrips * c.band;
+        int j = (int)std::min<long long>(r / full, c.nbands - 1);
+        const int h = j == c.nbands - 1 ? c.nyf - j * c.band : c.band;
+        const long long rem = r - (long long)j * full;
+        s = (int)(rem / h);
+        row = c.yf0 + j * c.band + (int)(rem - (long long)s * h);
+        if (piece_end) *piece_end = c.unit_base + (long long)j * full + (long long)(s + 1) * h;
     };
     auto cut = [&](long long k) {
         long long u = (k * U) / b->nctas;
@@ -315,10 +328,9 @@ lbm_status batch_plan(lbm_batch *b)
         long long u = cut(k), u1 = cut(k + 1);
         while (u < u1) {
             int ci, s, row;
-            locate(u, ci, s, row);
-            const ChanHost &c = b->ch[ci];
-            const long long strip_end = c.unit_base + (long long)(s + 1) * c.nyf;
-            const long long ue = std::min(u1, strip_end);
+            long long piece_end;
+            locate(u, ci, s, row, &piece_end);
+            const long long ue = std::min(u1, piece_end);
             b->segs.push_back(lbm::BatchSeg{ci, s, row, row + (int)(ue - u)});
             u = ue;
         }
@@ -795,6 +807,10 @@ lbm_status lbm_batch_set_option(lbm_batch *b, lbm_option opt, int64_t value)
         return LBM_OK;
     case LBM_OPT_PERSISTENT:
         b->allow_persist = value != 0;
+        break;
+    case LBM_OPT_BAND:
+        if (value < 0 || value > (1 << 20)) return LBM_ERR_ARG;
+        b->band_opt = (int)value;
         break;
     case LBM_OPT_GRAPH_STEPS:
         if (value < 0 || (value & 1)) return LBM_ERR_ARG;

@@ -127,7 +127,9 @@ __device__ __forceinline__ float2 stage_pair(const float *slot, int i, int sc)
 // the copy of the final pair is never issued, so the wait for it gives up
 // after KArgs::poll_limit polls; no later copy reuses that slot, so nothing is
 // left in flight when the CTA exits.
-template <bool WALLS, bool PRES, bool PADDED, bool HOOK = false, typename IX = int>
+// EARLY: stencil-row pairs issued together when a segment starts (1 .. the
+// three slots, all free then); later pairs are issued one per iteration.
+template <bool WALLS, bool PRES, bool PADDED, bool HOOK = false, typename IX = int, int EARLY = 1>
 __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom<float> &G, int s, int ya, int yb,
                                                SmemR2 &S, float *stages, uint64_t *bars,
                                                RingPos2 &ring_next, const CUtensorMap *tmap, Acc<float, 1> &acc,
@@ -246,7 +248,12 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
         }
     };
 
-    issue(0);
+    // with EARLY > 1 the first pairs go out together, so only the first wait
+    // of a segment sees the full latency of a stage load (short segments)
+    static_assert(EARLY >= 1 && EARLY <= R2_SLOTS, "early pairs fit the free slots");
+    if (tid == PRODUCER) fence_proxy_async_smem();  // slots last read by the previous segment
+#pragma unroll
+    for (int q = 0; q < EARLY; ++q) issue(q);
     for (int k = 0; k < npairs; ++k) {
         const int yy0 = ya - 2 + 2 * k;
         const uint32_t cur = ring_next.s;
@@ -280,8 +287,10 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
         __syncthreads();  // A: density rows complete; the slot of pair k-2 is free
 
         // (2) refill the slot of pair k-2 with pair k+1; Laplacian of rows yy0-1, yy0
-        if (tid == PRODUCER) fence_proxy_async_smem();
-        issue(k + 1);
+        if (k + 1 >= EARLY) {
+            if (tid == PRODUCER) fence_proxy_async_smem();
+            issue(k + 1);
+        }
         if (k >= 1) {
             const int qm = (yy0 - 2) & RM, q0 = (yy0 - 1) & RM, q1 = yy0 & RM, q2 = (yy0 + 1) & RM;
             if (lapc) {
@@ -441,8 +450,9 @@ __device__ __forceinline__ void run_segment_r2(const KArgs<float> &A, const Geom
 #endif
 // tmap: 2-D tensor map of A.fin (used when A.tma is set). HOOK: the
 // failure-detection test build (see run_segment_r2). IX: the type of
-// population offsets, int while 9 pitch ny < 2^31, long long above.
-template <bool WALLS, bool PRES, bool PADDED, bool HOOK = false, typename IX = int>
+// population offsets, int while 9 pitch ny < 2^31, long long above. EARLY:
+// as run_segment_r2 (3 pays where CTAs hold short segments).
+template <bool WALLS, bool PRES, bool PADDED, bool HOOK = false, typename IX = int, int EARLY = 1>
 __global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS)
     step_kernel_rows2(const KArgs<float> A, const __grid_constant__ CUtensorMap tmap)
 {
@@ -475,7 +485,7 @@ __global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS)
         const int yb = ya + (int)(ue - u);
         u = ue;
         // the test hook applies to the first CTA's last segment
-        run_segment_r2<WALLS, PRES, PADDED, HOOK, IX>(A, G, s, ya, yb, S, stages, bars, ring_next,
+        run_segment_r2<WALLS, PRES, PADDED, HOOK, IX, EARLY>(A, G, s, ya, yb, S, stages, bars, ring_next,
                                                   A.tma ? &tmap : nullptr, acc, lost, HOOK && cta == 0 && u == u1);
     }
     if (lost) atomicOr(A.err, 2);

@@ -10,7 +10,8 @@ channel the same number of steps; throughput is total node updates per second.
   python -m paper_2103_08301_gb300.sweep_bench --batched-only --tma 1 --channels 16 --steps 5
 
 `--batched-only` steps only the batch, with its default plan (no autotune),
-tensor loads on or off (`--tma`), for profiling one batch launch.
+tensor loads on or off (`--tma`) and a band height of the work order
+(`--band`, 0 = strip by strip), for profiling one batch launch.
 """
 from __future__ import annotations
 
@@ -85,7 +86,7 @@ def run(steps=200, n=64, seed=3, precision=32):
     }
 
 
-def run_batched_only(steps=5, n=16, seed=3, precision=32, tma=0):
+def run_batched_only(steps=5, n=16, seed=3, precision=32, tma=0, band=0):
     import torch
 
     import paper_2103_08301_gb300 as lbm
@@ -101,6 +102,7 @@ def run_batched_only(steps=5, n=16, seed=3, precision=32, tma=0):
     nodes = sum(c["nx"] * c["ny"] for c in chans)
     with lbm.Batch(chans, precision=precision, **kw) as b:
         b.set_option(lbm.LBM_OPT_TMA, tma)
+        b.set_option(lbm.LBM_OPT_BAND, band)
         b.step(3)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -108,7 +110,8 @@ def run_batched_only(steps=5, n=16, seed=3, precision=32, tma=0):
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
         info = b.launch_info()
-    return {"channels": n, "nodes": nodes, "steps": steps, "tma": tma, "batched_mlups": nodes * steps / t / 1e6,
+    return {"channels": n, "nodes": nodes, "steps": steps, "tma": tma, "band": band,
+            "batched_mlups": nodes * steps / t / 1e6,
             "launch": info}
 
 
@@ -118,9 +121,10 @@ def main():
     ap.add_argument("--channels", type=int, default=64)
     ap.add_argument("--batched-only", action="store_true")
     ap.add_argument("--tma", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--band", type=int, default=0, help="LBM_OPT_BAND of the batched-only run")
     args = ap.parse_args()
     if args.batched_only:
-        print(json.dumps(run_batched_only(steps=args.steps, n=args.channels, tma=args.tma)))
+        print(json.dumps(run_batched_only(steps=args.steps, n=args.channels, tma=args.tma, band=args.band)))
     else:
         print(json.dumps(run(steps=args.steps, n=args.channels)))
 

@@ -204,3 +204,28 @@ def test_persistent_batch_matches_per_step_launches_bitwise(orc, lbm, kind):
         for k in ("mass", "wall_shear_sum", "tau_wall_min", "tau_wall_max", "p_wall_min", "p_wall_max",
                   "nan_detected"):
             assert da[k] == db[k], k
+
+
+@pytest.mark.parametrize("band", [8, 37, 64])
+def test_band_major_work_order_matches_strip_major_bitwise(orc, lbm, band):
+    """The batch's work order cut into bands (LBM_OPT_BAND) against the
+    strip-by-strip order: the same populations bit for bit, the same extrema
+    and error word, and sums equal to rounding (the segments change), with the
+    persistent launch (segment dependencies over bands) as well."""
+    chans = _channels(orc, STAGED_SPECS + [(2048, 300, 1e-3, 12, 512, 128)])
+    steps = 41
+    out = []
+    for band_opt, persistent in ((0, 0), (band, 0), (band, 1)):
+        with lbm.Batch(chans, precision=32, **KW) as b:
+            b.set_option(lbm.LBM_OPT_BAND, band_opt)
+            b.set_option(lbm.LBM_OPT_PERSISTENT, persistent)
+            b.step(steps)
+            out.append([(b.populations(i), b.diag(i)) for i in range(len(chans))])
+    for other in out[1:]:
+        for (pa, da), (pb, db) in zip(out[0], other):
+            assert np.array_equal(pa.view(np.uint32), pb.view(np.uint32))
+            for k in ("tau_wall_min", "tau_wall_max", "p_wall_min", "p_wall_max", "nan_detected"):
+                assert da[k] == db[k], k
+            # per-segment partials are FP32 sums of up to 16 rows per lane
+            assert abs(da["mass"] / db["mass"] - 1) <= 1e-6
+            assert abs(da["wall_shear_sum"] - db["wall_shear_sum"]) <= 1e-5 * abs(da["wall_shear_sum"]) + 1e-9
