@@ -246,6 +246,22 @@ def _extras(stream, op):
                                "hbm_gbs_at_72B": 72 * nodes / ms / 1e6,
                                "workload": "same channel, constrictions on both walls every 2048 columns "
                                            "(general-geometry kernels)"}
+    # past 2^31 population slots: the step with 64-bit population offsets
+    # (16384 x 14600 periodic two-phase slabs, 2 x 8.6 GB of FP32 populations)
+    bx, by = 16384, 14600
+    eos8 = lbm.lbm_eos(1.0, 4.0, 1.0, 0.8, 1.0, 0.5)
+    _, g8, l8, _ = lbm.lbm_coexistence(eos8)
+    xs = np.arange(bx)
+    row = g8 + (l8 - g8) * 0.5 * (1 - np.tanh(2 * (np.abs((xs % 512) - 256.0) - 100.0) / 4.0))
+    big_rho = np.broadcast_to(row, (by, bx))
+    with lbm.Lattice(bx, by, big_rho, stream=stream, precision=32, T_over_Tc=0.8, kappa=0.5) as lat:
+        del big_rho
+        ms = _timed_steps(lat, stream, 20)
+        nan = lat.diag()["nan_detected"]
+    out["fp32_step_64bit_offsets"] = {"ms_per_step": ms, "mlups": bx * by / ms / 1e3, "nan": bool(nan),
+                                      "hbm_gbs_at_72B": 72 * bx * by / ms / 1e6,
+                                      "workload": "16384x14600 periodic, liquid slabs every 512 columns, "
+                                                  "9 nx ny = 2.15e9 population slots (64-bit offsets)"}
     out["configs"] = _configs(stream, op)
     out["trends"] = _trends(stream, op)
     return out

@@ -472,8 +472,27 @@ lbm_status build_graph(lbm_ctx *ctx)
 }
 
 template <typename real>
+lbm_status one_step(lbm_ctx *ctx)
+{
+    lbm::KArgs<real> A = make_args<real>(ctx);
+    cudaError_t e = ctx->mask ? lbm::mask_launch<real>(ctx->mask, A, lbm::MODE_STEP, ctx->stream)
+                              : launch<real, lbm::MODE_STEP>(ctx, A);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
+    ctx->cur = 1 - ctx->cur;
+    ctx->step += 1;
+    return LBM_OK;
+}
+
+template <typename real>
 lbm_status do_steps(lbm_ctx *ctx, int64_t n)
 {
+    // the graph starts from buffer 0: a run that starts from buffer 1 takes one
+    // single launch first
+    if (ctx->graph_steps > 0 && ctx->stream && ctx->cur == 1 && n > ctx->graph_steps) {
+        lbm_status s = one_step<real>(ctx);
+        if (s != LBM_OK) return s;
+        --n;
+    }
     while (ctx->graph_steps > 0 && ctx->stream && n >= ctx->graph_steps && ctx->cur == 0) {
         if (!ctx->graph) {
             lbm_status s = build_graph<real>(ctx);
@@ -484,12 +503,8 @@ lbm_status do_steps(lbm_ctx *ctx, int64_t n)
         n -= ctx->graph_steps;
     }
     for (int64_t s = 0; s < n; ++s) {
-        lbm::KArgs<real> A = make_args<real>(ctx);
-        cudaError_t e = ctx->mask ? lbm::mask_launch<real>(ctx->mask, A, lbm::MODE_STEP, ctx->stream)
-                                  : launch<real, lbm::MODE_STEP>(ctx, A);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
-        ctx->cur = 1 - ctx->cur;
-        ctx->step += 1;
+        lbm_status st = one_step<real>(ctx);
+        if (st != LBM_OK) return st;
     }
     return LBM_OK;
 }

@@ -323,7 +323,8 @@ def test_l2_prefetch_changes_nothing(orc, lbm, pf):
 def test_graph_replayed_steps_match_single_launches(orc, lbm, precision):
     """lbm_step replayed from a captured CUDA graph (a context with its own
     stream) against one launch per call: identical populations and sums, over
-    an odd number of steps and across an option change that drops the graph."""
+    an odd number of steps, across an option change that drops the graph, and
+    for a run that starts from the second buffer."""
     import torch
     nx, ny, kw = 384, 80, dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=1e-3)
     rho0 = _airway(orc, nx, ny, 5, 100, 40)
@@ -335,6 +336,8 @@ def test_graph_replayed_steps_match_single_launches(orc, lbm, precision):
             lat.set_option(lbm.LBM_OPT_REVERSE, 0)
             lat.step(1)
             lat.step(128)
+            lat.step(5)    # ends in buffer 1: the next run starts with one single launch
+            lat.step(200)
             out.append((lat.populations(), lat.diag()))
     u = np.uint32 if precision == 32 else np.uint64
     assert np.array_equal(out[0][0].view(u), out[1][0].view(u))
