@@ -287,10 +287,15 @@ typedef enum {
     LBM_OPT_GENERAL = 9,
     LBM_OPT_FAULT_SKIP_COPY = 10,
     LBM_OPT_PERSISTENT = 11, /* batches only, see lbm_batch_step */
-    LBM_OPT_BAND = 12        /* batches only: rows per band of the work order, 0 (default) = each
+    LBM_OPT_BAND = 12,       /* batches only: rows per band of the work order, 0 (default) = each
                                 channel's height (strip by strip); otherwise each channel is cut
                                 into bands of that many rows (at least 8), taken band by band and,
                                 within a band, strip by strip. Identical results. */
+    LBM_OPT_PDL = 13         /* contexts: nonzero (default) launches the FP32 row-pair step with
+                                programmatic stream serialization, so a step's launch and set-up
+                                overlap the previous step's tail (the kernel waits for the previous
+                                grid before any memory access); zero: plain launches. Identical
+                                results. */
 } lbm_option;
 lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value);
 /* Launch geometry of the step kernel: CTAs, threads per CTA, work units and

@@ -106,6 +106,7 @@ struct lbm_ctx {
     int pitch = 0;  // plane pitch of the population rows (>= nx)
     bool big = false;  // 9 pitch ny >= 2^31: kernels with 64-bit population offsets
     bool early = false;  // row-pair kernel issuing a segment's first three stage pairs together
+    bool pdl = true;     // LBM_OPT_PDL: row-pair steps launched with programmatic serialization
     long long units = 0;
     int band = 0;  // rows per band of the work-unit order
     int nctas = 0;
@@ -429,6 +430,22 @@ cudaError_t launch(lbm_ctx *ctx, const lbm::KArgs<real> &A)
         }
         const CUtensorMap *m = B.tma ? &ctx->tmap[ctx->cur] : &unused;
         void *args[] = {(void *)&B, (void *)m};
+        if (ctx->pdl && !ctx->fault_skip) {
+            // programmatic dependent launch: the kernel waits for the previous
+            // grid before touching memory, so its launch and set-up overlap
+            // the previous step's tail
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            at[0].val.programmaticStreamSerializationAllowed = 1;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(ctx->nctas);
+            cfg.blockDim = dim3(threads_of(ctx, MODE));
+            cfg.dynamicSmemBytes = dyn_smem(ctx, MODE);
+            cfg.stream = ctx->stream;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            return cudaLaunchKernelExC(&cfg, fn, args);
+        }
         return cudaLaunchKernel(fn, dim3(ctx->nctas), dim3(threads_of(ctx, MODE)), args, dyn_smem(ctx, MODE),
                                 ctx->stream);
     }
@@ -986,6 +1003,10 @@ lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
         if (value != 0 && ctx->big) return LBM_ERR_ARG;  // 32-bit offsets only
         ctx->force_general = value != 0;
         break;
+    case LBM_OPT_PDL:
+        ctx->pdl = value != 0;
+        drop_graph(ctx);
+        return LBM_OK;
     case LBM_OPT_GRAPH_STEPS:
         if (value < 0 || (value & 1) || value > 1 << 20) return LBM_ERR_ARG;
         ctx->graph_steps = (int)value;

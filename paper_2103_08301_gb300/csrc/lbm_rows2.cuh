@@ -64,6 +64,12 @@ constexpr size_t rows2_smem_bytes()
 // maps are 2-D views of a buffer: x = column (pitch wide), y = 9 * row + plane;
 // the box is R2_SP columns by 9 planes, so one load brings a stencil row.
 // Columns outside the array (x < 0 or beyond the pitch) read as zero.
+// Programmatic dependent launch: let the next grid in the stream be scheduled,
+// and wait until the grids this one depends on have completed and their
+// memory is visible (both no-ops for a grid launched without the attribute).
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
 {
     asm volatile(
@@ -476,6 +482,11 @@ __global__ void __launch_bounds__(R2_BLOCK, LBM_R2_MIN_BLOCKS)
         mbar_init_fence();
     }
     __syncthreads();
+    // launched with programmatic serialization, the next step's CTAs may
+    // start their set-up while this grid runs; every access to the state and
+    // to the per-CTA slots follows the wait for the previous grid
+    griddep_launch_dependents();
+    griddep_wait();
 
     while (u < u1) {
         int s, ya;

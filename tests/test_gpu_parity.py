@@ -483,3 +483,23 @@ def test_maximum_size_grid_windows_against_oracle(orc, lbm, name):
         err = np.abs(got - ref[:, 3:-3, 3:-3]).max() / np.abs(ref).max()
         assert err <= 2e-6, (y0, x0, err)
     del f0, f1
+
+
+def test_programmatic_launch_matches_plain_launches(orc, lbm):
+    """Row-pair steps launched with programmatic stream serialization (the
+    default) against plain launches, with and without graph replay: the same
+    populations and diagnostics bit for bit."""
+    import torch
+    nx, ny, kw = 1024, 128, dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=1e-3)
+    rho0 = _airway(orc, nx, ny, 6, 256, 96)
+    out = []
+    for pdl, graphs in ((1, 64), (1, 0), (0, 0)):
+        with lbm.Lattice(nx, ny, rho0, precision=32, stream=torch.cuda.Stream(), **kw) as lat:
+            lat.set_option(lbm.LBM_OPT_PDL, pdl)
+            lat.set_option(lbm.LBM_OPT_GRAPH_STEPS, graphs)
+            lat.step(301)
+            out.append((lat.populations(), lat.diag()))
+    for f, d in out[1:]:
+        assert np.array_equal(f.view(np.uint32), out[0][0].view(np.uint32))
+        for k in ("mass", "wall_shear_sum", "tau_wall_min", "tau_wall_max", "p_wall_min", "p_wall_max"):
+            assert d[k] == out[0][1][k], k
