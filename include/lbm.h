@@ -292,7 +292,8 @@ typedef enum {
                                 into bands of that many rows (at least 8), taken band by band and,
                                 within a band, strip by strip. Identical results. */
     LBM_OPT_PDL = 13         /* contexts: nonzero (default) launches the FP32 row-pair step with
-                                programmatic stream serialization, so a step's launch and set-up
+                                programmatic stream serialization where the plan gives CTAs short
+                                segments (under 128 rows each), so a step's launch and set-up
                                 overlap the previous step's tail (the kernel waits for the previous
                                 grid before any memory access); zero: plain launches. Identical
                                 results. */
