@@ -513,9 +513,14 @@ def run_ours(args, world, rank, local):
     e2e_val = whole_job_mlups(world, nodes, args.steps, allreduce_max(e2e_t, dist, "cuda"))
 
     sweep = None
-    if rank == 0 and world == 1 and not args.no_sweep:
+    if world == 1 and not args.no_sweep:
         from paper_2103_08301_gb300 import sweep_bench
         sweep = sweep_bench.run(steps=200)
+    elif not args.no_sweep:
+        # the sweep's channels are independent problems: shard them over the
+        # ranks, no collective on the data path
+        from paper_2103_08301_gb300 import sweep_bench
+        sweep = sweep_bench.run_sharded(rank, world, dist, steps=200)
     extras = _extras(stream, op) if (rank == 0 and world == 1 and not args.no_sweep) else None
 
     if rank == 0:

@@ -31,6 +31,58 @@ def _sweep_channels(n, seed):
     return synth.sweep_channels(n=n, seed=seed)
 
 
+def shard_channels(sizes, world):
+    """Split channels of `sizes` (node counts) over `world` ranks: largest
+    first onto the least-loaded rank (ties to the lower rank), so every rank
+    computes the same assignment. Returns one sorted list of channel indices
+    per rank. The channels are independent problems: no data crosses ranks."""
+    loads = [0] * world
+    out = [[] for _ in range(world)]
+    for i in sorted(range(len(sizes)), key=lambda k: (-sizes[k], k)):
+        r = min(range(world), key=lambda q: (loads[q], q))
+        out[r].append(i)
+        loads[r] += sizes[i]
+    return [sorted(o) for o in out]
+
+
+def run_sharded(rank, world, dist=None, steps=200, n=64, seed=3, precision=32):
+    """The sweep split over `world` ranks (one GPU each): rank `rank` steps its
+    shard of the channels as one batch; the time is the maximum over ranks
+    (a barrier on both sides) and the throughput is all channels' node
+    updates over it."""
+    import torch
+
+    import paper_2103_08301_gb300 as lbm
+
+    kw = dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5)
+    eos = lbm.lbm_eos(1.0, 4.0, 1.0, kw["T_over_Tc"], 1.0, kw["kappa"])
+    _, g, l, _ = lbm.lbm_coexistence(eos)
+    specs = _sweep_channels(n, seed)
+    shard = shard_channels([s["nx"] * s["ny"] for s in specs], world)[rank]
+    chans = [{"nx": specs[i]["nx"], "ny": specs[i]["ny"], "dp": specs[i]["dp"],
+              "rho0": lbm.lbm_airway_rho0(specs[i]["nx"], specs[i]["ny"], specs[i]["film"], specs[i]["plug_x"],
+                                          specs[i]["plug_len"], l, g)} for i in shard]
+    nodes = sum(s["nx"] * s["ny"] for s in specs)
+    with lbm.Batch(chans, precision=precision, **kw) as b:
+        b.step(64)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        b.step(steps)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return {"channels": len(specs), "ranks": world, "shard_channels": len(shard), "nodes": nodes,
+            "steps": steps, "batched_mlups": nodes * steps / t / 1e6, "scaling": "strong",
+            "workload": "64 airway channels split over the ranks by node count (largest first)"}
+
+
 def run(steps=200, n=64, seed=3, precision=32):
     import torch
 
