@@ -503,3 +503,37 @@ def test_programmatic_launch_matches_plain_launches(orc, lbm):
         assert np.array_equal(f.view(np.uint32), out[0][0].view(np.uint32))
         for k in ("mass", "wall_shear_sum", "tau_wall_min", "tau_wall_max", "p_wall_min", "p_wall_max"):
             assert d[k] == out[0][1][k], k
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_full_size_translation_invariance_over_1000_steps(orc, lbm, precision):
+    """The benchmark channel at full size (16384 x 2048, walls and pressure
+    columns, the benchmark's launch configuration) from a state periodic in x
+    with period 512 (liquid slabs whose width varies along y, x-periodic
+    noise). A step reads only nodes within three of the one it updates, so
+    after 1000 steps every column more than 3000 nodes from both pressure
+    columns must still equal, bit for bit, the column 512 further on: any
+    strip, band or segment boundary of the work split that changed a node's
+    arithmetic would break the shift symmetry."""
+    nx, ny, per, steps = 16384, 2048, 512, 1000
+    s = orc.Setup(nx=8, ny=8, T_over_Tc=0.85, kappa=0.5)
+    g, l, _ = s.coexistence()
+    y, x = np.mgrid[0:ny, 0:per].astype(np.float64)
+    half = 100.0 + 20.0 * np.sin(2 * np.pi * y / ny)
+    d = np.abs(x - 256.0) - half
+    tile = g + (l - g) * 0.5 * (1 - np.tanh(2 * d / 4.0)) + synth.node_noise(per, ny, 1e-3, 11)
+    rho0 = np.tile(tile, (1, nx // per))
+    kw = dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=1e-3)
+    with lbm.Lattice(nx, ny, rho0, precision=precision, **kw) as lat:
+        if precision == 32:
+            assert lat.launch_info()["ctas"] == 760  # the benchmark's launch
+        lat.step(steps)
+        assert not lat.diag()["nan_detected"]
+        f = lat.populations()
+    u = np.uint32 if precision == 32 else np.uint64
+    lo, hi = 3 * steps + 100, nx - 3 * steps - 100 - per
+    a = f[:, 1:-1, lo:hi].view(u)
+    b = f[:, 1:-1, lo + per:hi + per].view(u)
+    assert np.array_equal(a, b)
+    # and the dynamics did move the state away from the initial one
+    assert np.abs(f[:, 1:-1, lo:hi].sum(axis=0) - rho0[1:-1, lo:hi]).max() > 1e-4
