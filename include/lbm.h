@@ -196,6 +196,16 @@ lbm_status lbm_fields(lbm_ctx *ctx, void *rho, void *ux, void *uy, void *tau_wal
 /* Reduce the diagnostics on the GPU (fixed order, deterministic) and return
  * them in *out (host). Synchronises the stream. */
 lbm_status lbm_diag(lbm_ctx *ctx, lbm_diag_t *out);
+/* lbm_diag without the synchronisation, for a caller that reads every step's
+ * diagnostics while the next steps run: enqueues on the context's stream the
+ * same reduction and an asynchronous copy of 7 doubles into dst (pinned host
+ * or device memory, 8-byte aligned): mass, wall-shear sum, tau_w min/max,
+ * p_w min/max (as lbm_diag; the extrema read +-inf before a wall row was
+ * stepped) and the error word (bit 0 = bad density, bit 1 = a stage wait gave
+ * up). dst is valid once the stream has passed this point (an event recorded
+ * after the call, or a synchronisation). Errors: LBM_ERR_ARG (NULL or
+ * misaligned dst), LBM_ERR_CUDA. */
+lbm_status lbm_diag_async(lbm_ctx *ctx, double *dst);
 
 /* Restart the diagnostic accumulators (wall-shear sum, wall shear and wall
  * pressure extrema) so that they cover the steps issued afterwards; the step

@@ -72,6 +72,7 @@ _SIGS = {
     "lbm_step": (C.c_int, [_P, C.c_int64]),
     "lbm_fields": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "lbm_diag": (C.c_int, [_P, C.POINTER(lbm_diag_t)]),
+    "lbm_diag_async": (C.c_int, [_P, _P]),
     "lbm_populations": (C.c_int, [_P, _P]),
     "lbm_reset_diag": (C.c_int, [_P]),
     "lbm_batch_reset_diag": (C.c_int, [_P]),
@@ -329,6 +330,13 @@ class Lattice:
         d = lbm_diag_t()
         _check(lib().lbm_diag(self.ctx, C.byref(d)), self.ctx)
         return d.as_dict()
+
+    def diag_async(self, dst):
+        """lbm_diag_async into `dst` (7 float64: a pinned host or device torch
+        tensor, or a numpy array in pinned memory); valid once the stream has
+        passed this point."""
+        ptr = dst.data_ptr() if hasattr(dst, "data_ptr") else dst.ctypes.data
+        _check(lib().lbm_diag_async(self.ctx, _P(ptr)), self.ctx)
 
     def reset_diag(self):
         """lbm_reset_diag: the accumulators restart from the next step."""

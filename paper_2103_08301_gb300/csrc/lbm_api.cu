@@ -832,10 +832,9 @@ lbm_status lbm_fields(lbm_ctx *ctx, void *rho, void *ux, void *uy, void *tau_wal
                                      : do_fields<float>(ctx, rho, ux, uy, tau_wall, p_wall);
 }
 
-lbm_status lbm_diag(lbm_ctx *ctx, lbm_diag_t *out)
+namespace {
+void enqueue_diag(lbm_ctx *ctx, double *dout)
 {
-    if (!ctx || !out) return LBM_ERR_ARG;
-    double *dout = (double *)(ctx->ws + ctx->L.dout);
     if (ctx->grid.precision == 64)
         lbm::diag_kernel<double><<<1, 256, 0, ctx->stream>>>(
             (double *)(ctx->ws + ctx->L.mass), (double *)(ctx->ws + ctx->L.J),
@@ -844,6 +843,24 @@ lbm_status lbm_diag(lbm_ctx *ctx, lbm_diag_t *out)
         lbm::diag_kernel<float><<<1, 256, 0, ctx->stream>>>(
             (double *)(ctx->ws + ctx->L.mass), (double *)(ctx->ws + ctx->L.J),
             (float *)(ctx->ws + ctx->L.ext), (int *)(ctx->ws + ctx->L.err), ctx->nctas, dout);
+}
+}  // namespace
+
+lbm_status lbm_diag_async(lbm_ctx *ctx, double *dst)
+{
+    if (!ctx || !dst || ((uintptr_t)dst % 8) != 0) return LBM_ERR_ARG;
+    double *dout = (double *)(ctx->ws + ctx->L.dout);
+    enqueue_diag(ctx, dout);
+    CK(cudaGetLastError(), "diag launch");
+    CK(cudaMemcpyAsync(dst, dout, 7 * sizeof(double), cudaMemcpyDefault, ctx->stream), "diag copy");
+    return LBM_OK;
+}
+
+lbm_status lbm_diag(lbm_ctx *ctx, lbm_diag_t *out)
+{
+    if (!ctx || !out) return LBM_ERR_ARG;
+    double *dout = (double *)(ctx->ws + ctx->L.dout);
+    enqueue_diag(ctx, dout);
     CK(cudaGetLastError(), "diag launch");
     double h[8];
     CK(cudaMemcpyAsync(h, dout, 7 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "diag copy");

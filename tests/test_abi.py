@@ -159,6 +159,7 @@ def test_adjoint_rejects_bad_arguments_before_touching_the_gpu(lbm):
     g = (C.c_double * 3)()
     assert lbm.lib().lbm_adjoint_backward(None, 1.0, 0.0, None, g) == lbm.LBM_ERR_ARG
     assert lbm.lib().lbm_adjoint_set_precision(None, 32) == lbm.LBM_ERR_ARG
+    assert lbm.lib().lbm_diag_async(None, C.c_void_p(64)) == lbm.LBM_ERR_ARG
     lbm.lib().lbm_adjoint_free(None)  # NULL-safe
 
 

@@ -537,3 +537,30 @@ def test_full_size_translation_invariance_over_1000_steps(orc, lbm, precision):
     assert np.array_equal(a, b)
     # and the dynamics did move the state away from the initial one
     assert np.abs(f[:, 1:-1, lo:hi].sum(axis=0) - rho0[1:-1, lo:hi]).max() > 1e-4
+
+
+def test_async_diagnostics_match_lbm_diag(orc, lbm):
+    """lbm_diag_async into pinned host memory, read after an event, against
+    the synchronous lbm_diag of the same state; and one step later the copy
+    of the earlier step is left as it was."""
+    import torch
+    nx, ny, kw = 512, 64, dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=1e-3)
+    rho0 = _airway(orc, nx, ny, 5, 100, 40)
+    st = torch.cuda.Stream()
+    buf = [torch.zeros(7, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    with lbm.Lattice(nx, ny, rho0, precision=32, stream=st, **kw) as lat:
+        lat.step(10)
+        lat.diag_async(buf[0])
+        ev = torch.cuda.Event()
+        ev.record(st)
+        lat.step(1)
+        lat.diag_async(buf[1])
+        ev.synchronize()
+        first = buf[0].clone()
+        d = lat.diag()  # after step 11
+        st.synchronize()
+    assert buf[1][0].item() == d["mass"] and buf[1][1].item() == d["wall_shear_sum"]
+    assert (buf[1][2].item(), buf[1][3].item()) == (d["tau_wall_min"], d["tau_wall_max"])
+    assert (buf[1][4].item(), buf[1][5].item()) == (d["p_wall_min"], d["p_wall_max"])
+    assert buf[1][6].item() == 0.0
+    assert torch.equal(first, buf[0]) and first[0].item() > 0 and first[0].item() != buf[1][0].item()
