@@ -467,6 +467,14 @@ def test_maximum_size_grid_windows_against_oracle(orc, lbm, name):
         f1 = torch.empty_like(f0)
         assert lbm.lib().lbm_populations(lat.ctx, C.c_void_p(f1.data_ptr())) == lbm.LBM_OK
         assert not lat.diag()["nan_detected"]
+        # the fields kernel on the same state (64-bit offsets past 2^31):
+        # rho = sum of the populations at interior rows of the top band
+        rho_f = torch.empty((ny, nx), dtype=torch.float32, device="cuda")
+        assert lbm.lib().lbm_fields(lat.ctx, C.c_void_p(rho_f.data_ptr()), None, None, None, None) == lbm.LBM_OK
+        band = slice(ny - 40, ny - 8)
+        ref_rho = f1[:, band, 8:nx - 8].double().sum(0)
+        assert torch.allclose(rho_f[band, 8:nx - 8].double(), ref_rho, rtol=1e-6, atol=0)
+        del rho_f, ref_rho
     h = w = 24
     if kw.get("walls"):
         corners = [(ny - h - 6, nx - w - 6), (ny - h - 6, 6), (ny // 2, nx // 2 + 3), (6, 6)]
