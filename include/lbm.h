@@ -301,11 +301,18 @@ typedef enum {
                                 channel's height (strip by strip); otherwise each channel is cut
                                 into bands of that many rows (at least 8), taken band by band and,
                                 within a band, strip by strip. Identical results. */
-    LBM_OPT_PDL = 13         /* contexts: nonzero (default) launches the FP32 row-pair step with
+    LBM_OPT_PDL = 13,        /* contexts: nonzero (default) launches the FP32 row-pair step with
                                 programmatic stream serialization where the plan gives CTAs short
                                 segments (under 128 rows each), so a step's launch and set-up
                                 overlap the previous step's tail (the kernel waits for the previous
                                 grid before any memory access); zero: plain launches. Identical
+                                results. */
+    LBM_OPT_TILE = 14        /* contexts: nonzero steps FP32 grids whose plan gives CTAs short
+                                segments (under 128 rows each) with one CTA per 32 x 8 tile that
+                                stages all its stencil rows at once, where the geometry allows
+                                (tensor loads, at most 8192 tiles, with walls no tile boundary
+                                between rows ny-3 | ny-2, with pressure columns nx % 32 != 1);
+                                zero (default, faster on GB300): the row-pair kernel. Identical
                                 results. */
 } lbm_option;
 lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value);

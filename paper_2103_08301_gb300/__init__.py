@@ -22,8 +22,8 @@ LIB_PATH = os.path.join(_HERE, "liblbm.so")
 LBM_OK, LBM_ERR_ARG, LBM_ERR_PARAM, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_NAN, LBM_ERR_STATE, LBM_ERR_TIMEOUT = range(8)
 LBM_OPT_CTAS_PER_SM, LBM_OPT_REVERSE, LBM_OPT_STRIP, LBM_OPT_STAGED, LBM_OPT_GRAPH_STEPS, LBM_OPT_ROWS2, LBM_OPT_TMA = \
     1, 2, 3, 4, 5, 6, 7
-LBM_OPT_PREFETCH, LBM_OPT_GENERAL, LBM_OPT_FAULT_SKIP_COPY, LBM_OPT_PERSISTENT, LBM_OPT_BAND, LBM_OPT_PDL = \
-    8, 9, 10, 11, 12, 13
+LBM_OPT_PREFETCH, LBM_OPT_GENERAL, LBM_OPT_FAULT_SKIP_COPY, LBM_OPT_PERSISTENT, LBM_OPT_BAND, LBM_OPT_PDL, \
+    LBM_OPT_TILE = 8, 9, 10, 11, 12, 13, 14
 
 
 class lbm_grid(C.Structure):

@@ -18,6 +18,7 @@
 #include "lbm.h"
 #include "lbm_internal.h"
 #include "lbm_kernels.cuh"
+#include "lbm_tile.cuh"
 
 namespace {
 
@@ -131,6 +132,11 @@ struct lbm_ctx {
     cudaGraphExec_t graph = nullptr;
     bool tma_ok = false;       // tmap[] encoded (FP32, pitch a multiple of 4)
     CUtensorMap tmap[2];       // 2-D views of the two population buffers for the row-pair stage
+    bool tile_maps_ok = false;  // tmap_tile[] encoded
+    CUtensorMap tmap_tile[2];   // the same views with the tile kernel's boxes (T_BOX x 9)
+    bool allow_tile = false;    // LBM_OPT_TILE (measured slower than the row-pair kernel)
+    bool tile = false;          // the plan steps with step_kernel_tile (ntx tiles along x)
+    int ntx = 0;
     // fields scratch (allocated on first host-pointer lbm_fields)
     unsigned char *fscratch = nullptr;
     // non-blocking NaN check
@@ -326,13 +332,13 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 // The 2-D view of one FP32 population buffer that the row-pair stage reads:
 // x = column (pitch wide, stride 4 pitch bytes per y), y = 9 * row + plane;
 // boxes of R2_SP columns by 9 planes (one stencil row), zero fill outside.
-bool encode_population_map(CUtensorMap *map, void *base, int pitch, int ny)
+bool encode_population_map(CUtensorMap *map, void *base, int pitch, int ny, int box_cols = lbm::R2_SP)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc || pitch % 4 != 0) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)9 * (cuuint64_t)ny};
     const cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)lbm::R2_SP, 9u};
+    const cuuint32_t box[2] = {(cuuint32_t)box_cols, 9u};
     const cuuint32_t elem[2] = {1u, 1u};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -411,6 +417,29 @@ lbm_status plan_launch(lbm_ctx *ctx)
                                              (int)dyn_smem(ctx, lbm::MODE_STEP));
         if (e != cudaSuccess) return cuda_fail(ctx, e, "smem attribute");
     }
+    // short segments with tensor-load staging: one CTA per 32 x 8 tile instead
+    // (no tile boundary between the wall-shear rows ny-3 | ny-2, and the
+    // outlet column never alone in a tile: its stencil reaches two columns back)
+    ctx->tile = false;
+    if (ctx->early && ctx->allow_tile && ctx->tile_maps_ok && ctx->allow_tma && !ctx->fault_skip) {
+        const int nx = ctx->grid.nx;
+        const long long ntx = (nx + lbm::T_TX - 1) / lbm::T_TX, nty = (ctx->nyf + lbm::T_TY - 1) / lbm::T_TY;
+        bool ok = ntx * nty <= lbm::MAX_CTAS;
+        if (ctx->grid.walls) ok = ok && (ctx->nyf - 1) % lbm::T_TY != 0;
+        if (ctx->grid.bc_x) ok = ok && nx % lbm::T_TX != 1;
+        if (ok) {
+            void *fn = ctx->grid.walls ? (ctx->grid.bc_x ? (void *)lbm::step_kernel_tile<true, true>
+                                                         : (void *)lbm::step_kernel_tile<true, false>)
+                                       : (ctx->grid.bc_x ? (void *)lbm::step_kernel_tile<false, true>
+                                                         : (void *)lbm::step_kernel_tile<false, false>);
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)lbm::tile_smem_bytes());
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "smem attribute");
+            ctx->tile = true;
+            ctx->ntx = (int)ntx;
+            ctx->nctas = (int)(ntx * nty);
+        }
+    }
     return LBM_OK;
 }
 
@@ -418,6 +447,27 @@ template <typename real, int MODE>
 cudaError_t launch(lbm_ctx *ctx, const lbm::KArgs<real> &A)
 {
     void *fn = step_kernel_ptr(ctx, MODE);
+    if (MODE == lbm::MODE_STEP && ctx->tile) {
+        // one CTA per 32 x 8 tile, every stencil row staged by a tensor load
+        lbm::KArgs<real> B = A;
+        fn = ctx->grid.walls ? (ctx->grid.bc_x ? (void *)lbm::step_kernel_tile<true, true>
+                                               : (void *)lbm::step_kernel_tile<true, false>)
+                             : (ctx->grid.bc_x ? (void *)lbm::step_kernel_tile<false, true>
+                                               : (void *)lbm::step_kernel_tile<false, false>);
+        int ntx = ctx->ntx;
+        void *args[] = {(void *)&B, (void *)&ctx->tmap_tile[ctx->cur], (void *)&ntx};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(ctx->nctas);
+        cfg.blockDim = dim3(lbm::T_THREADS);
+        cfg.dynamicSmemBytes = lbm::tile_smem_bytes();
+        cfg.stream = ctx->stream;
+        cfg.attrs = at;
+        cfg.numAttrs = ctx->pdl ? 1 : 0;
+        return cudaLaunchKernelExC(&cfg, fn, args);
+    }
     if (MODE == lbm::MODE_STEP && ctx->rows2) {
         // the row-pair kernel also takes the tensor map of its source buffer
         static const CUtensorMap unused{};
@@ -717,14 +767,19 @@ lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, const 
     }
     *ctx->h_err = 0;
 
+    // tensor maps of both buffers (the plan chooses kernels by them)
+    if (grid->precision == 32)
+        ctx->tma_ok = encode_population_map(&ctx->tmap[0], ctx->ws + ctx->L.f0, ctx->pitch, grid->ny) &&
+                      encode_population_map(&ctx->tmap[1], ctx->ws + ctx->L.f1, ctx->pitch, grid->ny);
+    if (grid->precision == 32)
+        ctx->tile_maps_ok =
+            encode_population_map(&ctx->tmap_tile[0], ctx->ws + ctx->L.f0, ctx->pitch, grid->ny, lbm::T_BOX) &&
+            encode_population_map(&ctx->tmap_tile[1], ctx->ws + ctx->L.f1, ctx->pitch, grid->ny, lbm::T_BOX);
     lbm_status st = plan_launch(ctx);
     if (st != LBM_OK) { lbm_free(ctx); return st; }
     if (wall_mask) ctx->mask_host.assign(wall_mask, wall_mask + (size_t)grid->nx * grid->ny);
     st = plan_geometry(ctx);
     if (st != LBM_OK) { lbm_free(ctx); return st; }
-    if (grid->precision == 32)
-        ctx->tma_ok = encode_population_map(&ctx->tmap[0], ctx->ws + ctx->L.f0, ctx->pitch, grid->ny) &&
-                      encode_population_map(&ctx->tmap[1], ctx->ws + ctx->L.f1, ctx->pitch, grid->ny);
 
     // Initial state f = f_eq(rho0, 0) in both arrays.
     const size_t N = (size_t)grid->nx * grid->ny;
@@ -1012,7 +1067,7 @@ lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
         break;
     case LBM_OPT_TMA:
         ctx->allow_tma = value != 0;
-        return LBM_OK;
+        break;  // re-plan: the tile kernel needs tensor loads
     case LBM_OPT_PREFETCH:
         if (value < 0 || value > 4) return LBM_ERR_ARG;
         ctx->pf = (int)value;
@@ -1042,7 +1097,10 @@ lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
             if (e != cudaSuccess) return cuda_fail(ctx, e, "smem attribute");
         }
         ctx->fault_skip = value != 0;
-        return LBM_OK;
+        break;  // re-plan: the test build is a row-pair kernel
+    case LBM_OPT_TILE:
+        ctx->allow_tile = value != 0;
+        break;
     default:
         return LBM_ERR_ARG;
     }

@@ -572,3 +572,60 @@ def test_async_diagnostics_match_lbm_diag(orc, lbm):
     assert (buf[1][4].item(), buf[1][5].item()) == (d["p_wall_min"], d["p_wall_max"])
     assert buf[1][6].item() == 0.0
     assert torch.equal(first, buf[0]) and first[0].item() > 0 and first[0].item() != buf[1][0].item()
+
+
+TILE_CASES = {
+    # (nx, ny, kw, rho0 kind); the tile kernel's eligibility per case in the comment
+    "airway512x128": (512, 128, dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=1e-3), "airway"),
+    "ragged130x21": (130, 21, dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=2e-4), "airway"),
+    "droplet128": (128, 128, dict(T_over_Tc=0.8, kappa=0.5), "disk"),
+    "ragged200x37": (200, 37, dict(T_over_Tc=0.8, kappa=0.5), "disk"),
+    "wet96x40": (96, 40, dict(walls=True, T_over_Tc=0.8, kappa=0.5, wetting=0.01), "airway"),
+    "mrt_airway256x64": (256, 64, dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, tau=1.2, dp=1e-3,
+                                       collision="mrt", s_e=1 / 1.2, s_eps=1.54, s_q=1 / 1.2, s_j=1 / 1.2), "airway"),
+    "pr_droplet96": (96, 96, dict(eos="pr", a=2 / 49, b=2 / 21, T_over_Tc=0.8, k=1.0, kappa=0.01, tau=1.2), "disk"),
+    "bodyforce256x64": (256, 64, dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=0.0, gx=1e-6), "airway"),
+    "tiny5x4": (5, 4, dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=1e-4), "airway"),
+    "periodic36x12": (36, 12, dict(T_over_Tc=0.8, kappa=0.5), "disk"),
+    # not eligible: nx % 32 == 1 with pressure columns (the outlet column alone in a tile)
+    "ragged129x20": (129, 20, dict(walls=True, bc_x=True, T_over_Tc=0.85, kappa=0.5, dp=2e-4), "airway"),
+    # not eligible: a tile boundary between rows ny-3 | ny-2 ((ny - 3) % 8 == 0)
+    "walls64x19": (64, 19, dict(walls=True, T_over_Tc=0.8, kappa=0.5), "airway"),
+}
+
+
+@pytest.mark.parametrize("name", list(TILE_CASES))
+def test_tile_kernel_matches_row_pair_kernel_bitwise(orc, lbm, name):
+    """The small-grid tile kernel (one CTA per 32 x 8 tile) against the row-pair
+    kernel over 150 steps: populations, fields and extrema bit for bit, sums to
+    rounding (the reductions group the nodes differently)."""
+    nx, ny, kw, kind = TILE_CASES[name]
+    okw = {k: v for k, v in kw.items() if k not in ("wetting",)}
+    if "wetting" in kw:
+        okw["wet"] = kw["wetting"]
+    g, l, _ = orc.Setup(nx=nx, ny=ny, **okw).coexistence()
+    if kind == "disk":
+        rho0 = synth.disk_rho0(nx, ny, max(3, min(nx, ny) // 5), l, g, noise=1e-3, seed=nx + ny)
+    else:
+        rho0 = synth.airway_rho0(nx, ny, max(1, ny // 12), nx // 4, max(2, nx // 8), l, g, noise=1e-3, seed=ny)
+    walls = kw.get("walls", False)
+    nyf = ny - 2 if walls else ny
+    ntiles = -(-nx // 32) * -(-nyf // 8)
+    eligible = not (kw.get("bc_x") and nx % 32 == 1) and not (walls and (nyf - 1) % 8 == 0)
+    out = []
+    for tile in (1, 0):
+        with lbm.Lattice(nx, ny, rho0, precision=32, **kw) as lat:
+            lat.set_option(lbm.LBM_OPT_TILE, tile)
+            ctas = lat.launch_info()["ctas"]
+            if tile:
+                assert (ctas == ntiles) == eligible, (ctas, ntiles, eligible)
+            lat.step(150)
+            out.append((lat.populations(), lat.fields(), lat.diag()))
+    (fa, Fa, da), (fb, Fb, db) = out
+    assert np.array_equal(fa.view(np.uint32), fb.view(np.uint32))
+    for k in ("rho", "vx", "vy", "tau_wall", "p_wall"):
+        assert np.array_equal(Fa[k].view(np.uint32), Fb[k].view(np.uint32)), k
+    for k in ("tau_wall_min", "tau_wall_max", "p_wall_min", "p_wall_max", "nan_detected"):
+        assert da[k] == db[k], k
+    assert abs(da["mass"] / db["mass"] - 1) <= 1e-6
+    assert abs(da["wall_shear_sum"] - db["wall_shear_sum"]) <= 1e-5 * abs(db["wall_shear_sum"]) + 1e-9
