@@ -1033,10 +1033,13 @@ __device__ __forceinline__ void cta_reduce(Acc<real, CP> &acc, SM &S, double &m,
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     acc.flush();
+    // only warps that hold wall rows carry a wall-shear sum: the others skip
+    // its FP64 shuffles (GB300 runs FP64 at 1/64 of the FP32 rate)
+    const bool anyJ = __any_sync(0xffffffffu, acc.J != 0.0);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         acc.mass += __shfl_xor_sync(0xffffffffu, acc.mass, o);
-        acc.J += __shfl_xor_sync(0xffffffffu, acc.J, o);
+        if (anyJ) acc.J += __shfl_xor_sync(0xffffffffu, acc.J, o);
         acc.tmin = fmin(acc.tmin, __shfl_xor_sync(0xffffffffu, acc.tmin, o));
         acc.tmax = fmax(acc.tmax, __shfl_xor_sync(0xffffffffu, acc.tmax, o));
         acc.pmin = fmin(acc.pmin, __shfl_xor_sync(0xffffffffu, acc.pmin, o));
