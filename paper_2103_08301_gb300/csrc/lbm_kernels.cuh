@@ -568,32 +568,53 @@ __device__ __forceinline__ real wall_pressure(const KArgs<real> &A, const real (
     return fma_(fma_(grx, grx, mul_(gry, gry)), mul_(real(-0.5), A.kappa), t);
 }
 
+// h + l += x for an unevaluated FP32 pair (h, l): Knuth's two-sum gives the
+// rounding error of h + x exactly, which l collects.
+__device__ __forceinline__ void two_sum_acc(float &h, float &l, float x)
+{
+    const float s = __fadd_rn(h, x);
+    const float bp = __fsub_rn(s, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    h = s;
+    l = __fadd_rn(l, err);
+}
+
 // Per-thread diagnostic accumulators of the states read. The density sum is
-// kept in the working precision and flushed to FP64 every 16 rows (at most 16
-// terms per flush); the density range is tracked with min / max, and a
-// non-finite density shows up in the mass sum (min / max ignore NaN).
+// kept in the working precision and flushed every 16 rows (at most 16 terms
+// per flush): FP64 builds into a double, FP32 builds into a compensated FP32
+// pair (two-sum, on the FP32 pipes: GB300 runs FP64 at 1/64 of that rate),
+// which the CTA reduction combines in FP64. The density range is tracked
+// with min / max, and a non-finite density shows up in the mass sum (min /
+// max ignore NaN).
 template <typename real, int CP>
 struct Acc {
     using V = typename Pack<real, CP>::T;
+    static constexpr bool PAIR = sizeof(real) == 4;
     double mass, J;
+    float mhi, mlo;  // FP32 builds: the flushed sums as hi + lo
     V macc, rmin, rmax;
     real tmin, tmax, pmin, pmax;
     __device__ __forceinline__ void reset()
     {
-        mass = 0.0; J = 0.0; macc = bc<V>(0.0);
+        mass = 0.0; J = 0.0; mhi = mlo = 0.f; macc = bc<V>(0.0);
         rmin = bc<V>(INFINITY); rmax = bc<V>(-INFINITY);
         tmin = pmin = real(INFINITY); tmax = pmax = real(-INFINITY);
     }
     __device__ __forceinline__ void flush()
     {
+        if constexpr (PAIR) {
 #pragma unroll
-        for (int k = 0; k < CP; ++k) mass += (double)el(macc, k);
+            for (int k = 0; k < CP; ++k) two_sum_acc(mhi, mlo, (float)el(macc, k));
+        } else {
+#pragma unroll
+            for (int k = 0; k < CP; ++k) mass += (double)el(macc, k);
+        }
         macc = bc<V>(0.0);
     }
     // a density that is not in (0, 1e30) or a non-finite mass
     __device__ __forceinline__ bool bad() const
     {
-        bool b = !(mass - mass == 0.0);
+        bool b = PAIR ? !(mhi - mhi == 0.f) : !(mass - mass == 0.0);
 #pragma unroll
         for (int k = 0; k < CP; ++k) b = b || !(el(rmin, k) > real(0)) || !(el(rmax, k) < real(1e30));
         return b;
@@ -1036,9 +1057,21 @@ __device__ __forceinline__ void cta_reduce(Acc<real, CP> &acc, SM &S, double &m,
     // only warps that hold wall rows carry a wall-shear sum: the others skip
     // its FP64 shuffles (GB300 runs FP64 at 1/64 of the FP32 rate)
     const bool anyJ = __any_sync(0xffffffffu, acc.J != 0.0);
+    if constexpr (Acc<real, CP>::PAIR) {
+        // FP32 builds: the pairs summed across the warp with two-sum (lane 0's
+        // result is the one kept), then one FP64 addition
+        float h = acc.mhi, l = acc.mlo;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+            two_sum_acc(h, l, h2);
+            l = __fadd_rn(l, l2);
+        }
+        acc.mass = (double)h + (double)l;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        acc.mass += __shfl_xor_sync(0xffffffffu, acc.mass, o);
+        if constexpr (!Acc<real, CP>::PAIR) acc.mass += __shfl_xor_sync(0xffffffffu, acc.mass, o);
         if (anyJ) acc.J += __shfl_xor_sync(0xffffffffu, acc.J, o);
         acc.tmin = fmin(acc.tmin, __shfl_xor_sync(0xffffffffu, acc.tmin, o));
         acc.tmax = fmax(acc.tmax, __shfl_xor_sync(0xffffffffu, acc.tmax, o));
