@@ -1281,40 +1281,52 @@ __global__ void init_kernel(const double *__restrict__ rho0, real *__restrict__ 
 }
 
 // Fixed-order reduction of the per-CTA partials into out[0..6]:
-// mass, J, tw_min, tw_max, pw_min, pw_max, err.
+// mass, J, tw_min, tw_max, pw_min, pw_max, err. One block of 256 threads:
+// strided per-thread sums, warp butterflies (extrema in the partials' own
+// precision, exact), then the eight warps in order.
 template <typename real>
 __global__ void diag_kernel(const double *__restrict__ mass_part, const double *__restrict__ J_acc,
                             const real *__restrict__ ext, const int *__restrict__ err, int nctas,
                             double *__restrict__ out)
 {
-    __shared__ double sm[256], sj[256], se[4][256];
-    const int t = threadIdx.x;
+    __shared__ double sm[8], sj[8];
+    __shared__ real se[4][8];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     double m = 0.0, j = 0.0;
-    double e0 = INFINITY, e1 = -INFINITY, e2 = INFINITY, e3 = -INFINITY;
+    real e0 = real(INFINITY), e1 = real(-INFINITY), e2 = real(INFINITY), e3 = real(-INFINITY);
     for (int c = t; c < nctas; c += 256) {
         m += mass_part[c];
         j += J_acc[c];
-        e0 = fmin(e0, (double)ext[4 * c + 0]);
-        e1 = fmax(e1, (double)ext[4 * c + 1]);
-        e2 = fmin(e2, (double)ext[4 * c + 2]);
-        e3 = fmax(e3, (double)ext[4 * c + 3]);
+        e0 = fmin(e0, ext[4 * c + 0]);
+        e1 = fmax(e1, ext[4 * c + 1]);
+        e2 = fmin(e2, ext[4 * c + 2]);
+        e3 = fmax(e3, ext[4 * c + 3]);
     }
-    sm[t] = m; sj[t] = j; se[0][t] = e0; se[1][t] = e1; se[2][t] = e2; se[3][t] = e3;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        m += __shfl_xor_sync(0xffffffffu, m, o);
+        j += __shfl_xor_sync(0xffffffffu, j, o);
+        e0 = fmin(e0, __shfl_xor_sync(0xffffffffu, e0, o));
+        e1 = fmax(e1, __shfl_xor_sync(0xffffffffu, e1, o));
+        e2 = fmin(e2, __shfl_xor_sync(0xffffffffu, e2, o));
+        e3 = fmax(e3, __shfl_xor_sync(0xffffffffu, e3, o));
+    }
+    if (lane == 0) {
+        sm[w] = m; sj[w] = j;
+        se[0][w] = e0; se[1][w] = e1; se[2][w] = e2; se[3][w] = e3;
+    }
     __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (t < s) {
-            sm[t] += sm[t + s];
-            sj[t] += sj[t + s];
-            se[0][t] = fmin(se[0][t], se[0][t + s]);
-            se[1][t] = fmax(se[1][t], se[1][t + s]);
-            se[2][t] = fmin(se[2][t], se[2][t + s]);
-            se[3][t] = fmax(se[3][t], se[3][t + s]);
-        }
-        __syncthreads();
-    }
     if (t == 0) {
-        out[0] = sm[0]; out[1] = sj[0];
-        out[2] = se[0][0]; out[3] = se[1][0]; out[4] = se[2][0]; out[5] = se[3][0];
+        double M = 0.0, Jt = 0.0;
+        real a0 = se[0][0], a1 = se[1][0], a2 = se[2][0], a3 = se[3][0];
+        for (int k = 0; k < 8; ++k) {
+            M += sm[k];
+            Jt += sj[k];
+            a0 = fmin(a0, se[0][k]); a1 = fmax(a1, se[1][k]);
+            a2 = fmin(a2, se[2][k]); a3 = fmax(a3, se[3][k]);
+        }
+        out[0] = M; out[1] = Jt;
+        out[2] = (double)a0; out[3] = (double)a1; out[4] = (double)a2; out[5] = (double)a3;
         out[6] = (double)(*err);
     }
 }
