@@ -137,7 +137,9 @@ __global__ void __launch_bounds__(MB) mask_collide_kernel(const KArgs<real> A, c
 {
     const int nx = m.nx, ny = m.ny, P = m.pitch, rstride = 9 * P, sx = m.sx;
     const int n = nx * ny;
+    constexpr bool PAIR = sizeof(real) == 4;  // FP32: the mass as a compensated FP32 pair (FP64 is 1/64 rate)
     double mass = 0.0;
+    float mhi = 0.f, mlo = 0.f;
     bool bad = false;
     for (int k = blockIdx.x * MB + threadIdx.x; k < n; k += gridDim.x * MB) {
         if (m.solid[k]) continue;
@@ -203,7 +205,8 @@ __global__ void __launch_bounds__(MB) mask_collide_kernel(const KArgs<real> A, c
                 }
                 A.fout[ty * rstride + i * P + tx] = fs[i];
             }
-            mass += (double)rho_own;
+            if constexpr (PAIR) two_sum_acc(mhi, mlo, (float)rho_own);
+            else mass += (double)rho_own;
             bad = bad || !(rho > real(0)) || !(rho < real(1e30));
         }
         if (m.walls && !anyp) {
@@ -230,8 +233,18 @@ __global__ void __launch_bounds__(MB) mask_collide_kernel(const KArgs<real> A, c
     __shared__ double red[MB / 32];
     __shared__ int anybad;
     if (threadIdx.x == 0) anybad = 0;
+    if constexpr (PAIR) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mass += __shfl_xor_sync(0xffffffffu, mass, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, mhi, o), l2 = __shfl_xor_sync(0xffffffffu, mlo, o);
+            two_sum_acc(mhi, mlo, h2);
+            mlo = __fadd_rn(mlo, l2);
+        }
+        mass = (double)mhi + (double)mlo;
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mass += __shfl_xor_sync(0xffffffffu, mass, o);
+    }
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mass;
     if (bad) anybad = 1;
