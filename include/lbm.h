@@ -382,13 +382,14 @@ typedef struct lbm_batch lbm_batch; /* opaque, owned by the library */
  * Errors: LBM_ERR_ARG, LBM_ERR_PARAM, LBM_ERR_OOM, LBM_ERR_CUDA. */
 lbm_status lbm_batch_init(int32_t n, const lbm_grid *grids, const lbm_eos *eos, double tau, double wetting,
                           const lbm_drive *drives, const double *const *rho0s, void *stream, lbm_batch **out);
-/* Advance every channel n steps (asynchronous): one launch per step,
- * replayed from CUDA graphs of LBM_OPT_GRAPH_STEPS steps (default 64). With
- * LBM_OPT_PERSISTENT = 1, row-pair (FP32, staged) batches run persistently
- * instead: one cooperative launch carries up to 4096 steps, every segment
- * (channel, strip, rows) waiting, bounded, for the step counters of the
- * segments next to it before each step; a wait that gives up reports
- * LBM_ERR_TIMEOUT. Identical results either way. */
+/* Advance every channel n steps (asynchronous). Row-pair (FP32, staged)
+ * batches run persistently by default (LBM_OPT_PERSISTENT = 1): one
+ * cooperative launch carries up to 4096 steps, every segment (channel,
+ * strip, rows) waiting, bounded, for the step counters of the segments next
+ * to it before each step; a wait that gives up reports LBM_ERR_TIMEOUT. With
+ * LBM_OPT_PERSISTENT = 0, and for other batches: one launch per step,
+ * replayed from CUDA graphs of LBM_OPT_GRAPH_STEPS steps (default 64).
+ * Identical results either way. */
 lbm_status lbm_batch_step(lbm_batch *b, int64_t n);
 /* Per-channel outputs, as lbm_fields / lbm_diag / lbm_populations. */
 lbm_status lbm_batch_fields(lbm_batch *b, int32_t channel, void *rho, void *ux, void *uy, void *tau_wall,

@@ -81,7 +81,7 @@ struct lbm_batch {
     // persistent stepping (row-pair batches): one cooperative launch per chunk
     // of steps, segments ordered by step counters (LBM_OPT_PERSISTENT; off by
     // default: one launch per step from CUDA graphs measured faster)
-    bool allow_persist = false, persist = false;
+    bool allow_persist = true, persist = false;  // LBM_OPT_PERSISTENT (default on)
     int *d_done = nullptr, *d_abort = nullptr, *d_dep_beg = nullptr, *d_dep = nullptr;
     // fields scratch and non-blocking NaN check
     unsigned char *fscratch = nullptr;

@@ -112,8 +112,8 @@ def run(steps=200, n=64, seed=3, precision=32):
             torch.cuda.synchronize()
             seq_t += time.perf_counter() - t0
 
-    # batched: every channel in one launch per step replayed from graphs (the
-    # default), and in one persistent cooperative launch; autotuned plan
+    # batched: every channel in one persistent cooperative launch (the
+    # default), and in one launch per step replayed from graphs; autotuned plan
     bat = {}
     for mode, persistent in (("per_step", 0), ("persistent", 1)):
         with lbm.Batch(chans, precision=precision, **kw) as b:
@@ -132,7 +132,8 @@ def run(steps=200, n=64, seed=3, precision=32):
         "batched_mlups": nodes * steps / bat_t / 1e6, "sequential_mlups": nodes * steps / seq_t / 1e6,
         "persistent_launch_mlups": nodes * steps / bat["persistent"][0] / 1e6,
         "speedup": seq_t / bat_t, "autotune": tune, "launch": info, "nan": bool(nan or bat["persistent"][3]),
-        "mode": "one launch per step, CUDA graphs (persistent_launch_mlups: one persistent cooperative launch)",
+        "mode": "batched_mlups: one launch per step, CUDA graphs; persistent_launch_mlups: one persistent "
+                "cooperative launch (the library default)",
         "workload": "64 airway channels, H 128-512, L 1024-4096, dp 5e-4..3e-3, plug 64-256, film 4-24 "
                     "(SplitMix64 seed 3), FP32",
     }
