@@ -79,9 +79,9 @@ struct lbm_batch {
     int graph_steps = DEFAULT_GRAPH_STEPS;
     cudaGraphExec_t graph = nullptr;
     // persistent stepping (row-pair batches): one cooperative launch per chunk
-    // of steps, segments ordered by step counters (LBM_OPT_PERSISTENT; off by
-    // default: one launch per step from CUDA graphs measured faster)
-    bool allow_persist = true, persist = false;  // LBM_OPT_PERSISTENT (default on)
+    // of steps, segments ordered by step counters (LBM_OPT_PERSISTENT, on by
+    // default: as fast as per-step graph launches on the 64-channel sweep)
+    bool allow_persist = true, persist = false;
     int *d_done = nullptr, *d_abort = nullptr, *d_dep_beg = nullptr, *d_dep = nullptr;
     // fields scratch and non-blocking NaN check
     unsigned char *fscratch = nullptr;
