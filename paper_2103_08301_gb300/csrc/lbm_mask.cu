@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(MB) mask_wall_kernel(const KArgs<real> A, cons
     const real third = real(1.0 / 3.0);
     double J = 0.0;
     real e[4] = {real(INFINITY), real(-INFINITY), real(INFINITY), real(-INFINITY)};
-    for (int x = threadIdx.x; x < nx; x += MB) {
+    for (int x = blockIdx.x * MB + threadIdx.x; x < nx; x += gridDim.x * MB) {
         if (m.bc_x && (x == 0 || x == nx - 1)) continue;
         if (!m.solid[nx + x] && !m.solid[2 * nx + x]) {
             const real tw = mul_(mul_(E[ext(m, x, 1)], A.nu), mul_(fma_(real(9), wv[x], -wv[nx + x]), third));
@@ -309,10 +309,11 @@ __global__ void __launch_bounds__(MB) mask_wall_kernel(const KArgs<real> A, cons
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        A.J_acc[0] += sj[0];
-        A.ext[0] = fmin(A.ext[0], se[0][0]); A.ext[1] = fmax(A.ext[1], se[1][0]);
-        A.ext[2] = fmin(A.ext[2], se[2][0]); A.ext[3] = fmax(A.ext[3], se[3][0]);
+    if (threadIdx.x == 0) {  // one slot per block (the collide kernel's slot count bounds the grid)
+        real *ex = A.ext + 4 * blockIdx.x;
+        A.J_acc[blockIdx.x] += sj[0];
+        ex[0] = fmin(ex[0], se[0][0]); ex[1] = fmax(ex[1], se[1][0]);
+        ex[2] = fmin(ex[2], se[2][0]); ex[3] = fmax(ex[3], se[3][0]);
     }
 }
 
@@ -497,12 +498,15 @@ cudaError_t mask_launch(const MaskPath *m, const KArgs<real> &A, int mode, cudaS
     if (d.bc_x) mask_columns_kernel<real><<<grid_for(d.ny, cap), MB, 0, s>>>(A, d, E);
     mask_ghost_kernel<real><<<grid_for(d.nghost, cap), MB, 0, s>>>(A, d, E);
     mask_phi_lap_kernel<real><<<grid_for((long long)(d.nx + 2) * (d.ny + 2), cap), MB, 0, s>>>(A, d, E, Pa, La);
+    // the wall columns spread over as many blocks as fill them (at most the
+    // collide kernel's block count, whose per-block slots the partials use)
+    const int wb = (int)std::min<long long>(cap, ((long long)d.nx + MB - 1) / MB);
     if (mode == MODE_STEP) {
         mask_collide_kernel<real, MODE_STEP><<<m->blocks, MB, 0, s>>>(A, d, E, Pa, La, wv, pw);
-        if (d.walls) mask_wall_kernel<real, MODE_STEP><<<1, MB, 0, s>>>(A, d, E, wv, pw);
+        if (d.walls) mask_wall_kernel<real, MODE_STEP><<<wb, MB, 0, s>>>(A, d, E, wv, pw);
     } else {
         mask_collide_kernel<real, MODE_FIELDS><<<m->blocks, MB, 0, s>>>(A, d, E, Pa, La, wv, pw);
-        if (d.walls) mask_wall_kernel<real, MODE_FIELDS><<<1, MB, 0, s>>>(A, d, E, wv, pw);
+        if (d.walls) mask_wall_kernel<real, MODE_FIELDS><<<wb, MB, 0, s>>>(A, d, E, wv, pw);
     }
     return cudaGetLastError();
 }

@@ -5,7 +5,7 @@ bottom, wall films ny/32 thick, a liquid plug nx/16 long at x = nx/4,
 pressure columns with a drop of 1e-3, CS EOS at 0.85 Tc, tau = 1, k = 1,
 kappa = 0.5, seeded synthetic initial density.
 
-  python -m paper_2103_08301_gb300.profile_step --nx 4096 --ny 2048 --steps 5 [--precision 32]
+  python -m paper_2103_08301_gb300.profile_step --nx 4096 --ny 2048 --steps 5 [--precision 32] [--mask]
 
 Prints the mean kernel time and effective bandwidth (72 B/node in FP32).
 """
@@ -24,6 +24,8 @@ def main():
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--staged", type=int, default=1, help="1: bulk-copy staged kernel, 0: register prefetch")
     ap.add_argument("--prefetch", type=int, default=-1, help="LBM_OPT_PREFETCH (row pairs ahead); -1: default")
+    ap.add_argument("--mask", action="store_true",
+                    help="constrictions on both walls every 2048 columns (the general-geometry kernels)")
     args = ap.parse_args()
 
     import torch
@@ -37,8 +39,15 @@ def main():
     nx, ny = args.nx, args.ny
     rho0 = lbm.lbm_airway_rho0(nx, ny, ny / 32.0, nx / 4.0, nx / 16.0, l, g)
     stream = torch.cuda.Stream()
+    mask = None
+    if args.mask:
+        import numpy as np
+        mask = np.zeros((ny, nx), np.uint8)
+        for x0 in range(1024, nx - 512, 2048):
+            mask[1:ny // 4, x0:x0 + 64] = 1
+            mask[ny - ny // 4:ny - 1, x0:x0 + 64] = 1
     with lbm.Lattice(nx, ny, rho0, walls=True, bc_x=True, precision=args.precision, T_over_Tc=0.85,
-                     kappa=0.5, dp=1e-3, stream=stream) as lat:
+                     kappa=0.5, dp=1e-3, stream=stream, mask=mask) as lat:
         lat.set_option(lbm.LBM_OPT_STAGED, args.staged)
         if args.ctas_per_sm:
             lat.set_option(lbm.LBM_OPT_CTAS_PER_SM, args.ctas_per_sm)
