@@ -49,6 +49,7 @@ constexpr int MB = 256;  // threads per block of the mask kernels
 struct MaskDev {
     int nx, ny, pitch, walls, bc_x, sx;  // sx = nx + 4: row stride of the extended arrays
     const uint8_t *solid;                 // nx * ny
+    const uint16_t *links;                // nx * ny: bit i = the push along e_i bounces back; bit 15 = solid
     const int *gdst, *gbeg, *gsrc;        // ghost table (CSR)
     const uint8_t *gwet;
     int nghost;
@@ -142,7 +143,8 @@ __global__ void __launch_bounds__(MB) mask_collide_kernel(const KArgs<real> A, c
     float mhi = 0.f, mlo = 0.f;
     bool bad = false;
     for (int k = blockIdx.x * MB + threadIdx.x; k < n; k += gridDim.x * MB) {
-        if (m.solid[k]) continue;
+        const unsigned lk = m.links[k];
+        if (lk >> 15) continue;  // solid
         const int y = k / nx, xa = k - y * nx;
         const bool pin = m.bc_x && xa == 0, pout = m.bc_x && xa == nx - 1, anyp = pin || pout;
         const int xs = pin ? 1 : (pout ? nx - 2 : xa);  // a pressure column collides its interior neighbour
@@ -188,21 +190,17 @@ __global__ void __launch_bounds__(MB) mask_collide_kernel(const KArgs<real> A, c
             const int oi = y * rstride + xa;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                int tx = xa + ex_(i), ty = y + ey_(i);
-                if (m.walls && (ty == 0 || ty == ny - 1)) {
-                    A.fout[oi + opp_(i) * P] = fs[i];  // half-way bounce-back at a wall row
+                if ((lk >> i) & 1u) {
+                    A.fout[oi + opp_(i) * P] = fs[i];  // half-way bounce-back at a wall row or an obstacle
                     continue;
                 }
+                int tx = xa + ex_(i), ty = y + ey_(i);
                 if (m.bc_x) {
                     if (tx < 0 || tx >= nx) continue;  // leaves through the column
                 } else {
                     tx = tx < 0 ? tx + nx : (tx >= nx ? tx - nx : tx);
                 }
                 if (!m.walls) ty = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
-                if (m.solid[ty * nx + tx]) {
-                    A.fout[oi + opp_(i) * P] = fs[i];  // half-way bounce-back at an obstacle
-                    continue;
-                }
                 A.fout[ty * rstride + i * P + tx] = fs[i];
             }
             if constexpr (PAIR) two_sum_acc(mhi, mlo, (float)rho_own);
@@ -437,16 +435,43 @@ lbm_status mask_setup(const uint8_t *mask, const lbm_grid &g, int pitch, int sms
             gwet.push_back(1);
         }
 
+    // per-node link table: which pushes bounce back (a wall-row target first,
+    // as the channel kernels order it; targets beyond a pressure column leave
+    // and are not marked), and whether the node itself is solid
+    static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1}, EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    std::vector<uint16_t> links((size_t)nx * ny, 0);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            if (solid[(size_t)y * nx + x]) {  // never pushes; its targets may lie outside the lattice
+                links[(size_t)y * nx + x] = (uint16_t)0x8000u;
+                continue;
+            }
+            uint16_t l = 0;
+            for (int i = 1; i < 9; ++i) {
+                int tx = x + EX[i], ty = y + EY[i];
+                if (g.walls && (ty == 0 || ty == ny - 1)) { l |= (uint16_t)(1u << i); continue; }
+                if (g.bc_x) {
+                    if (tx < 0 || tx >= nx) continue;
+                } else {
+                    tx = (tx + nx) % nx;
+                }
+                if (!g.walls) ty = (ty + ny) % ny;
+                if (solid[(size_t)ty * nx + tx]) l |= (uint16_t)(1u << i);
+            }
+            links[(size_t)y * nx + x] = l;
+        }
+
     MaskPath *m = new (std::nothrow) MaskPath();
     if (!m) return LBM_ERR_OOM;
     m->precision = g.precision;
     const size_t sz = g.precision == 64 ? 8 : 4;
     m->ne = (size_t)(nx + 4) * (ny + 4);
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t b_solid = al(solid.size()), b_ext = al(m->ne * sz), b_dst = al(gdst.size() * 4),
+    const size_t b_solid = al(solid.size()), b_links = al(links.size() * 2), b_ext = al(m->ne * sz),
+                 b_dst = al(gdst.size() * 4),
                  b_beg = al(gbeg.size() * 4), b_src = al(std::max<size_t>(1, gsrc.size()) * 4),
                  b_wet = al(gwet.size()), b_wv = al(4 * (size_t)nx * sz), b_pw = al(2 * (size_t)nx * sz);
-    const size_t total = b_solid + 3 * b_ext + b_dst + b_beg + b_src + b_wet + b_wv + b_pw;
+    const size_t total = b_solid + b_links + 3 * b_ext + b_dst + b_beg + b_src + b_wet + b_wv + b_pw;
     if (cudaMalloc((void **)&m->mem, total) != cudaSuccess) {
         cudaGetLastError();
         delete m;
@@ -454,6 +479,7 @@ lbm_status mask_setup(const uint8_t *mask, const lbm_grid &g, int pitch, int sms
     }
     unsigned char *p = m->mem;
     uint8_t *d_solid = p; p += b_solid;
+    uint16_t *d_links = (uint16_t *)p; p += b_links;
     m->E = p; p += b_ext;
     m->Pa = p; p += b_ext;
     m->La = p; p += b_ext;
@@ -465,6 +491,8 @@ lbm_status mask_setup(const uint8_t *mask, const lbm_grid &g, int pitch, int sms
     m->pw = p;
     cudaError_t e = cudaMemsetAsync(m->mem, 0, total, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_solid, solid.data(), solid.size(), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_links, links.data(), links.size() * 2, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_dst, gdst.data(), gdst.size() * 4, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_beg, gbeg.data(), gbeg.size() * 4, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess && !gsrc.empty())
@@ -476,7 +504,8 @@ lbm_status mask_setup(const uint8_t *mask, const lbm_grid &g, int pitch, int sms
         mask_free(m);
         return LBM_ERR_CUDA;
     }
-    m->d = MaskDev{nx, ny, pitch, g.walls, g.bc_x, sx, d_solid, d_dst, d_beg, d_src, d_wet, (int)gdst.size()};
+    m->d = MaskDev{nx, ny, pitch, g.walls, g.bc_x, sx, d_solid, d_links, d_dst, d_beg, d_src, d_wet,
+                   (int)gdst.size()};
     const long long nodes = (long long)nx * ny;
     m->blocks = (int)std::max<long long>(1, std::min<long long>((nodes + MB - 1) / MB, (long long)sms * 8));
     m->blocks = std::min(m->blocks, MAX_CTAS);
