@@ -297,10 +297,13 @@ typedef enum {
     LBM_OPT_GENERAL = 9,
     LBM_OPT_FAULT_SKIP_COPY = 10,
     LBM_OPT_PERSISTENT = 11, /* batches only, see lbm_batch_step */
-    LBM_OPT_BAND = 12,       /* batches only: rows per band of the work order, 0 (default) = each
-                                channel's height (strip by strip); otherwise each channel is cut
-                                into bands of that many rows (at least 8), taken band by band and,
-                                within a band, strip by strip. Identical results. */
+    LBM_OPT_BAND = 12,       /* batches only: the work order. -1 (default): one CTA per strip
+                                column of every channel, tallest first (the hardware scheduler
+                                balances them); 0: the strip-by-strip order cut into equal runs,
+                                one per resident CTA (used whenever LBM_OPT_PERSISTENT is set);
+                                > 0: each channel cut into bands of that many rows (at least 8),
+                                band by band and, within a band, strip by strip, cut likewise.
+                                Identical results. */
     LBM_OPT_PDL = 13,        /* contexts: nonzero (default) launches the FP32 row-pair step with
                                 programmatic stream serialization where the plan gives CTAs short
                                 segments (under 128 rows each), so a step's launch and set-up
@@ -382,14 +385,13 @@ typedef struct lbm_batch lbm_batch; /* opaque, owned by the library */
  * Errors: LBM_ERR_ARG, LBM_ERR_PARAM, LBM_ERR_OOM, LBM_ERR_CUDA. */
 lbm_status lbm_batch_init(int32_t n, const lbm_grid *grids, const lbm_eos *eos, double tau, double wetting,
                           const lbm_drive *drives, const double *const *rho0s, void *stream, lbm_batch **out);
-/* Advance every channel n steps (asynchronous). Row-pair (FP32, staged)
- * batches run persistently by default (LBM_OPT_PERSISTENT = 1): one
- * cooperative launch carries up to 4096 steps, every segment (channel,
- * strip, rows) waiting, bounded, for the step counters of the segments next
- * to it before each step; a wait that gives up reports LBM_ERR_TIMEOUT. With
- * LBM_OPT_PERSISTENT = 0, and for other batches: one launch per step,
- * replayed from CUDA graphs of LBM_OPT_GRAPH_STEPS steps (default 64).
- * Identical results either way. */
+/* Advance every channel n steps (asynchronous): one launch per step,
+ * replayed from CUDA graphs of LBM_OPT_GRAPH_STEPS steps (default 64). With
+ * LBM_OPT_PERSISTENT = 1, row-pair (FP32, staged) batches run persistently
+ * instead: one cooperative launch carries up to 4096 steps, every segment
+ * (channel, strip, rows) waiting, bounded, for the step counters of the
+ * segments next to it before each step; a wait that gives up reports
+ * LBM_ERR_TIMEOUT. Identical results either way. */
 lbm_status lbm_batch_step(lbm_batch *b, int64_t n);
 /* Per-channel outputs, as lbm_fields / lbm_diag / lbm_populations. */
 lbm_status lbm_batch_fields(lbm_batch *b, int32_t channel, void *rho, void *ux, void *uy, void *tau_wall,
@@ -407,8 +409,10 @@ lbm_status lbm_batch_launch_info(const lbm_batch *b, int64_t *ctas, int64_t *seg
                                  int64_t *strip);
 /* Autotuner: times trial_steps steps for each candidate launch plan (CTAs
  * per SM, strip width) on a saved copy of the state, keeps the fastest,
- * restores the state and returns the choice. Resets the diagnostic
- * accumulators. */
+ * restores the state and returns the choice. With the whole-column work
+ * order (LBM_OPT_BAND = -1, not persistent) only the strip width is tried
+ * and best_ctas_per_sm returns the resident occupancy. Resets the
+ * diagnostic accumulators. */
 lbm_status lbm_batch_autotune(lbm_batch *b, int32_t trial_steps, int64_t *best_ctas_per_sm,
                               int64_t *best_strip, double *best_ms_per_step);
 const char *lbm_batch_last_error(const lbm_batch *b);

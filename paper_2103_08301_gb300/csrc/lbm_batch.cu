@@ -58,8 +58,9 @@ struct lbm_batch {
     int cur = 0;
     int64_t step = 0;
     // launch plan and device tables
-    int sms = 0, nctas = 0, nseg = 0, ctas_per_sm_opt = 0, W_opt = 0, reverse = 0;
-    int band_opt = 0;  // LBM_OPT_BAND: rows per band of the work order (0 = the channel's height)
+    int sms = 0, nctas = 0, nseg = 0, per_sm = 0, ctas_per_sm_opt = 0, W_opt = 0, reverse = 0;
+    int band_opt = -1;  // LBM_OPT_BAND: -1 whole strip columns, one CTA each (default); 0 strip-major
+                        // balanced cut; > 0 bands of that many rows
     bool allow_staged = true, staged = false;
     bool allow_rows2 = true, rows2 = false;  // LBM_OPT_ROWS2: row-pair FP32 step
     // LBM_OPT_TMA (off by default for batches: reading 2n maps from device
@@ -79,9 +80,9 @@ struct lbm_batch {
     int graph_steps = DEFAULT_GRAPH_STEPS;
     cudaGraphExec_t graph = nullptr;
     // persistent stepping (row-pair batches): one cooperative launch per chunk
-    // of steps, segments ordered by step counters (LBM_OPT_PERSISTENT, on by
-    // default: as fast as per-step graph launches on the 64-channel sweep)
-    bool allow_persist = true, persist = false;
+    // of steps, segments ordered by step counters (LBM_OPT_PERSISTENT; off by
+    // default: per-step graph launches over whole strip columns measured faster)
+    bool allow_persist = false, persist = false;
     int *d_done = nullptr, *d_abort = nullptr, *d_dep_beg = nullptr, *d_dep = nullptr;
     // fields scratch and non-blocking NaN check
     unsigned char *fscratch = nullptr;
@@ -293,6 +294,7 @@ lbm_status batch_plan(lbm_batch *b)
             per_sm = std::min(per_sm, occ);
         }
     }
+    b->per_sm = per_sm;
     long long G = (long long)b->sms * per_sm;
     G = std::min<long long>(G, std::max<long long>(1, U / 2));
     G = std::min<long long>(G, lbm::MAX_CTAS);
@@ -336,6 +338,22 @@ lbm_status batch_plan(lbm_batch *b)
         }
     }
     begin[b->nctas] = (int)b->segs.size();
+    if (b->band_opt < 0 && !b->persist) {
+        // one CTA per strip column (no cuts), tallest first, so the hardware
+        // scheduler hands the shorter columns to whichever CTA slot frees
+        // (persistent stepping needs every CTA resident: the balanced cut)
+        b->segs.clear();
+        for (int ci = 0; ci < b->n; ++ci) {
+            const ChanHost &c = b->ch[ci];
+            for (int s2 = 0; s2 < c.nstrips; ++s2) b->segs.push_back(lbm::BatchSeg{ci, s2, c.yf0, c.yf0 + c.nyf});
+        }
+        std::stable_sort(b->segs.begin(), b->segs.end(), [](const lbm::BatchSeg &p, const lbm::BatchSeg &q) {
+            return p.yb - p.ya > q.yb - q.ya;
+        });
+        b->nctas = (int)b->segs.size();
+        begin.resize(b->nctas + 1);
+        for (int k = 0; k <= b->nctas; ++k) begin[k] = k;
+    }
     b->nseg = (int)b->segs.size();
 
     // device tables (re-allocated on every plan)
@@ -809,7 +827,7 @@ lbm_status lbm_batch_set_option(lbm_batch *b, lbm_option opt, int64_t value)
         b->allow_persist = value != 0;
         break;
     case LBM_OPT_BAND:
-        if (value < 0 || value > (1 << 20)) return LBM_ERR_ARG;
+        if (value < -1 || value > (1 << 20)) return LBM_ERR_ARG;
         b->band_opt = (int)value;
         break;
     case LBM_OPT_GRAPH_STEPS:
@@ -853,19 +871,21 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int32_t trial_steps, int64_t *best_c
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int occ_max = 1;
+    bool whole = false;  // whole strip columns: CTAs per SM is the occupancy, not a choice
     {
         b->ctas_per_sm_opt = 0;
         b->W_opt = 0;
         lbm_status s = batch_plan(b);
         if (s != LBM_OK) { cudaFree(save); return s; }
         occ_max = std::max(1, (int)((b->nctas + b->sms - 1) / b->sms));
+        whole = b->band_opt < 0 && !b->persist;
     }
     double best = 1e300;
     int best_c = 0, best_w = 0;
     const int strips[] = {128, 64};
     for (int w : strips) {
         if (w > STRIP) continue;
-        for (int c = std::max(1, occ_max - 2); c <= occ_max; ++c) {
+        for (int c = whole ? 0 : std::max(1, occ_max - 2); c <= (whole ? 0 : occ_max); ++c) {
             b->ctas_per_sm_opt = c;
             b->W_opt = w;
             if (batch_plan(b) != LBM_OK) continue;
@@ -900,7 +920,7 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int32_t trial_steps, int64_t *best_c
     b->cur = cur0;
     b->step = step0;
     b->err_pending = false;
-    if (best_ctas_per_sm) *best_ctas_per_sm = best_c;
+    if (best_ctas_per_sm) *best_ctas_per_sm = whole ? b->per_sm : best_c;
     if (best_strip) *best_strip = best_w;
     if (best_ms_per_step) *best_ms_per_step = best;
     return s;

@@ -112,8 +112,9 @@ def run(steps=200, n=64, seed=3, precision=32):
             torch.cuda.synchronize()
             seq_t += time.perf_counter() - t0
 
-    # batched: every channel in one persistent cooperative launch (the
-    # default), and in one launch per step replayed from graphs; autotuned plan
+    # batched: one launch per step over every channel, one CTA per strip
+    # column, replayed from graphs (the default), and one persistent
+    # cooperative launch; autotuned plan
     bat = {}
     for mode, persistent in (("per_step", 0), ("persistent", 1)):
         with lbm.Batch(chans, precision=precision, **kw) as b:
@@ -132,14 +133,14 @@ def run(steps=200, n=64, seed=3, precision=32):
         "batched_mlups": nodes * steps / bat_t / 1e6, "sequential_mlups": nodes * steps / seq_t / 1e6,
         "persistent_launch_mlups": nodes * steps / bat["persistent"][0] / 1e6,
         "speedup": seq_t / bat_t, "autotune": tune, "launch": info, "nan": bool(nan or bat["persistent"][3]),
-        "mode": "batched_mlups: one launch per step, CUDA graphs; persistent_launch_mlups: one persistent "
-                "cooperative launch (the library default)",
+        "mode": "batched_mlups: one launch per step, one CTA per strip column, CUDA graphs (the library "
+                "default); persistent_launch_mlups: one persistent cooperative launch",
         "workload": "64 airway channels, H 128-512, L 1024-4096, dp 5e-4..3e-3, plug 64-256, film 4-24 "
                     "(SplitMix64 seed 3), FP32",
     }
 
 
-def run_batched_only(steps=5, n=16, seed=3, precision=32, tma=0, band=0):
+def run_batched_only(steps=5, n=16, seed=3, precision=32, tma=0, band=-1):
     import torch
 
     import paper_2103_08301_gb300 as lbm
@@ -174,7 +175,7 @@ def main():
     ap.add_argument("--channels", type=int, default=64)
     ap.add_argument("--batched-only", action="store_true")
     ap.add_argument("--tma", type=int, default=0, choices=[0, 1])
-    ap.add_argument("--band", type=int, default=0, help="LBM_OPT_BAND of the batched-only run")
+    ap.add_argument("--band", type=int, default=-1, help="LBM_OPT_BAND of the batched-only run")
     args = ap.parse_args()
     if args.batched_only:
         print(json.dumps(run_batched_only(steps=args.steps, n=args.channels, tma=args.tma, band=args.band)))

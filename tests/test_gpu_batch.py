@@ -180,7 +180,9 @@ def test_persistent_batch_matches_per_step_launches_bitwise(orc, lbm, kind):
     """One cooperative launch carrying many steps (segments ordered by step
     counters) against one launch per step: the same populations, bit for bit,
     and the same diagnostics, over an odd number of steps (the buffers end
-    swapped) and uneven channels."""
+    swapped) and uneven channels. Both take the balanced cut of the work
+    order (LBM_OPT_BAND = 0), so the segments, and with them the partial sums,
+    are the same."""
     if kind == "periodic":
         kw = dict(walls=False, bc_x=False, T_over_Tc=0.8, kappa=0.5)
         g, l, _ = orc.Setup(nx=8, ny=8, **kw).coexistence()
@@ -196,6 +198,7 @@ def test_persistent_batch_matches_per_step_launches_bitwise(orc, lbm, kind):
         with lbm.Batch(chans, precision=32, **kw) as b:
             if kind == "airway_tma":
                 b.set_option(lbm.LBM_OPT_TMA, 1)
+            b.set_option(lbm.LBM_OPT_BAND, 0)
             b.set_option(lbm.LBM_OPT_PERSISTENT, persistent)
             b.step(steps)
             out.append([(b.populations(i), b.diag(i)) for i in range(len(chans))])
@@ -206,7 +209,7 @@ def test_persistent_batch_matches_per_step_launches_bitwise(orc, lbm, kind):
             assert da[k] == db[k], k
 
 
-@pytest.mark.parametrize("band", [8, 37, 64])
+@pytest.mark.parametrize("band", [8, 37, 64, -1])
 def test_band_major_work_order_matches_strip_major_bitwise(orc, lbm, band):
     """The batch's work order cut into bands (LBM_OPT_BAND) against the
     strip-by-strip order: the same populations bit for bit, the same extrema
