@@ -260,7 +260,7 @@ lbm_status lbm_set_collision(lbm_ctx *ctx, const lbm_collision *c);
  *                        FP32 instructions) where it applies (staged, and nx a
  *                        multiple of 4 unless x has pressure columns); zero:
  *                        one row per iteration. Both give identical results.
- *   LBM_OPT_TMA          nonzero (default for contexts, zero for batches):
+ *   LBM_OPT_TMA          nonzero (default, contexts and batches):
  *                        the row-pair kernel stages each stencil row with one
  *                        2-D tensor (TMA) load; zero: nine bulk copies per
  *                        row. Identical results.

@@ -175,7 +175,7 @@ def test_batch_tensor_map_stage_matches_bulk_copies(orc, lbm, specs, kw):
         assert outs[0][c][1]["mass"] == outs[1][c][1]["mass"], c
 
 
-@pytest.mark.parametrize("kind", ["airway", "airway_tma", "periodic"])
+@pytest.mark.parametrize("kind", ["airway_copies", "airway_tma", "periodic"])
 def test_persistent_batch_matches_per_step_launches_bitwise(orc, lbm, kind):
     """One cooperative launch carrying many steps (segments ordered by step
     counters) against one launch per step: the same populations, bit for bit,
@@ -196,8 +196,7 @@ def test_persistent_batch_matches_per_step_launches_bitwise(orc, lbm, kind):
     out = []
     for persistent in (1, 0):
         with lbm.Batch(chans, precision=32, **kw) as b:
-            if kind == "airway_tma":
-                b.set_option(lbm.LBM_OPT_TMA, 1)
+            b.set_option(lbm.LBM_OPT_TMA, 0 if kind == "airway_copies" else 1)
             b.set_option(lbm.LBM_OPT_BAND, 0)
             b.set_option(lbm.LBM_OPT_PERSISTENT, persistent)
             b.step(steps)
