@@ -299,7 +299,8 @@ typedef enum {
     LBM_OPT_PERSISTENT = 11, /* batches only, see lbm_batch_step */
     LBM_OPT_BAND = 12,       /* batches only: the work order. -1 (default): one CTA per strip
                                 column of every channel, tallest first (the hardware scheduler
-                                balances them); 0: the strip-by-strip order cut into equal runs,
+                                balances them; with fewer columns than resident CTA slots each
+                                column is cut into that many equal pieces); 0: the strip-by-strip order cut into equal runs,
                                 one per resident CTA (used whenever LBM_OPT_PERSISTENT is set);
                                 > 0: each channel cut into bands of that many rows (at least 8),
                                 band by band and, within a band, strip by strip, cut likewise.

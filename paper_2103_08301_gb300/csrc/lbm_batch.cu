@@ -343,10 +343,25 @@ lbm_status batch_plan(lbm_batch *b)
         // one CTA per strip column (no cuts), tallest first, so the hardware
         // scheduler hands the shorter columns to whichever CTA slot frees
         // (persistent stepping needs every CTA resident: the balanced cut)
+        // (fewer columns than resident CTA slots: each column cut into equal
+        // pieces, never between rows 1|2 or ny-3|ny-2, until the slots fill)
+        long long ncol = 0;
+        for (const auto &c : b->ch) ncol += c.nstrips;
+        const long long slots = (long long)b->sms * per_sm;
+        const int pieces = (int)std::max<long long>(1, (slots + ncol - 1) / std::max<long long>(1, ncol));
         b->segs.clear();
         for (int ci = 0; ci < b->n; ++ci) {
             const ChanHost &c = b->ch[ci];
-            for (int s2 = 0; s2 < c.nstrips; ++s2) b->segs.push_back(lbm::BatchSeg{ci, s2, c.yf0, c.yf0 + c.nyf});
+            const int p = std::max(1, std::min(pieces, c.nyf / 8));
+            for (int s2 = 0; s2 < c.nstrips; ++s2) {
+                int ya = c.yf0;
+                for (int k = 1; k <= p; ++k) {
+                    int yb = c.yf0 + (int)((long long)k * c.nyf / p);
+                    if (k < p && b->walls && (yb == 2 || yb == c.grid.ny - 2)) yb -= 1;
+                    if (yb > ya) b->segs.push_back(lbm::BatchSeg{ci, s2, ya, yb});
+                    ya = std::max(ya, yb);
+                }
+            }
         }
         std::stable_sort(b->segs.begin(), b->segs.end(), [](const lbm::BatchSeg &p, const lbm::BatchSeg &q) {
             return p.yb - p.ya > q.yb - q.ya;

@@ -140,7 +140,7 @@ def run(steps=200, n=64, seed=3, precision=32):
     }
 
 
-def run_batched_only(steps=5, n=16, seed=3, precision=32, tma=0, band=-1):
+def run_batched_only(steps=5, n=16, seed=3, precision=32, tma=1, band=-1):
     import torch
 
     import paper_2103_08301_gb300 as lbm
@@ -174,7 +174,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--channels", type=int, default=64)
     ap.add_argument("--batched-only", action="store_true")
-    ap.add_argument("--tma", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--tma", type=int, default=1, choices=[0, 1])
     ap.add_argument("--band", type=int, default=-1, help="LBM_OPT_BAND of the batched-only run")
     args = ap.parse_args()
     if args.batched_only:
