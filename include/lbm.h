@@ -173,6 +173,34 @@ lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, const 
                     double wetting, const lbm_drive *drive, const double *rho0, void *workspace,
                     size_t ws_bytes, void *stream, lbm_ctx **out);
 
+/* In-place streaming (the AA pattern of Bailey et al., ICPP 2009): a context
+ * that stores one population array instead of two, plus one density plane
+ * (FP32: 40 bytes per node instead of 72), for grids that would not fit
+ * otherwise. Even steps read each node's own slots and write its
+ * post-collision populations back reversed; odd steps read from and write to
+ * the neighbours' slots, restoring the natural layout. Each step runs two
+ * kernels: the density of every fluid node into the plane (the stencil of
+ * Eq. 2.17 reaches neighbours whose slots may already hold their next state),
+ * then the collision from that plane; traffic is 116 bytes per node and step
+ * (FP32) instead of 72. Populations are identical bit for bit to an lbm_init
+ * context's; diagnostic sums agree to rounding (another summation order).
+ * Arguments as lbm_init, without a wall mask (walls are the channel's rows 0
+ * and ny-1 when grid->walls = 1); the workspace must hold
+ * lbm_workspace_bytes_inplace(grid) bytes. Every other call works on the
+ * context as on an lbm_init context, with these differences: the fields,
+ * populations, checkpoint and lbm_step graph calls first bring an odd-parity
+ * array back to the natural layout (one extra pass over it); checkpoints hold
+ * the one array and restore only into in-place contexts (LBM_ERR_STATE
+ * otherwise); LBM_OPT_GENERAL and LBM_OPT_FAULT_SKIP_COPY are rejected
+ * (LBM_ERR_ARG), and the kernel-selection options (LBM_OPT_STAGED, ROWS2,
+ * TMA, TILE, STRIP, CTAS_PER_SM, PREFETCH, PDL) affect only lbm_fields.
+ * lbm_launch_info reports the step's CTAs, 256 threads, its 32 x 8 tiles as
+ * units, and no staging. Errors: as lbm_init. */
+size_t lbm_workspace_bytes_inplace(const lbm_grid *grid);
+lbm_status lbm_init_inplace(const lbm_grid *grid, const lbm_eos *eos, double tau, double wetting,
+                            const lbm_drive *drive, const double *rho0, void *workspace, size_t ws_bytes,
+                            void *stream, lbm_ctx **out);
+
 /* Advance n >= 0 time steps (one fused kernel launch each), asynchronously.
  * On a context created with a stream of its own, runs of LBM_OPT_GRAPH_STEPS
  * steps (default 64) starting from the first population buffer are replayed

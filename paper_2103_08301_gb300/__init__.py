@@ -69,6 +69,10 @@ _SIGS = {
     "lbm_init": (C.c_int, [C.POINTER(lbm_grid), C.POINTER(lbm_eos), C.c_double, _P, C.c_double,
                            C.POINTER(lbm_drive), C.POINTER(C.c_double), _P, C.c_size_t, _P,
                            C.POINTER(_P)]),
+    "lbm_workspace_bytes_inplace": (C.c_size_t, [C.POINTER(lbm_grid)]),
+    "lbm_init_inplace": (C.c_int, [C.POINTER(lbm_grid), C.POINTER(lbm_eos), C.c_double, C.c_double,
+                                   C.POINTER(lbm_drive), C.POINTER(C.c_double), _P, C.c_size_t, _P,
+                                   C.POINTER(_P)]),
     "lbm_step": (C.c_int, [_P, C.c_int64]),
     "lbm_fields": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "lbm_diag": (C.c_int, [_P, C.POINTER(lbm_diag_t)]),
@@ -190,6 +194,23 @@ def lbm_init(grid, eos, tau, wetting, drive, rho0, workspace=None, ws_bytes=0, s
     return ctx
 
 
+def lbm_workspace_bytes_inplace(grid: lbm_grid) -> int:
+    return int(lib().lbm_workspace_bytes_inplace(C.byref(grid)))
+
+
+def lbm_init_inplace(grid, eos, tau, wetting, drive, rho0, workspace=None, ws_bytes=0, stream=None):
+    """lbm_init_inplace: a context with one population array (in-place streaming)."""
+    rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+    ctx = _P()
+    st = lib().lbm_init_inplace(C.byref(grid), C.byref(eos), float(tau), float(wetting),
+                                C.byref(drive) if drive is not None else None,
+                                rho0.ctypes.data_as(C.POINTER(C.c_double)),
+                                _P(workspace) if workspace else None, int(ws_bytes),
+                                _P(stream) if stream else None, C.byref(ctx))
+    _check(st)
+    return ctx
+
+
 def lbm_step(ctx, n: int) -> int:
     return int(lib().lbm_step(ctx, int(n)))
 
@@ -272,12 +293,15 @@ class Lattice:
     with nonzero entries at solid nodes. ``workspace`` may be a CUDA torch tensor of at
     least ``lbm_workspace_bytes`` bytes (kept alive by this object); by default
     the library allocates. ``stream`` is a torch.cuda.Stream or None.
+    ``inplace=True`` builds the context with lbm_init_inplace (one population
+    array, in-place streaming; no mask; workspace of lbm_workspace_bytes_inplace).
     """
 
     def __init__(self, nx, ny, rho0, *, walls=False, bc_x=False, precision=32, a=1.0, b=4.0,
                  R=1.0, T_over_Tc=0.8, k=1.0, kappa=0.5, tau=1.0, wetting=0.0, dp=0.0,
                  p_ref=None, gx=0.0, gy=0.0, eos="cs", omega=0.344, collision="bgk", s_e=1.64,
-                 s_eps=1.54, s_j=1.0, s_q=1.7, s_nu=None, workspace=None, stream=None, mask=None):
+                 s_eps=1.54, s_j=1.0, s_q=1.7, s_nu=None, workspace=None, stream=None, mask=None,
+                 inplace=False):
         self.grid = lbm_grid(nx, ny, int(walls), int(bc_x), int(precision))
         self.eos = lbm_eos(a, b, R, T_over_Tc, k, kappa, {"cs": LBM_EOS_CS, "pr": LBM_EOS_PR}[eos], omega)
         self.drive = lbm_drive(dp, math.nan if p_ref is None else p_ref, gx, gy)
@@ -289,8 +313,13 @@ class Lattice:
         if workspace is not None:
             ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
         sptr = stream.cuda_stream if stream is not None else None
-        self.ctx = lbm_init(self.grid, self.eos, tau, wetting, self.drive, rho0, ws_ptr, ws_bytes, sptr,
-                            wall_mask=mask)
+        if inplace:
+            if mask is not None:
+                raise ValueError("in-place contexts take no wall mask")
+            self.ctx = lbm_init_inplace(self.grid, self.eos, tau, wetting, self.drive, rho0, ws_ptr, ws_bytes, sptr)
+        else:
+            self.ctx = lbm_init(self.grid, self.eos, tau, wetting, self.drive, rho0, ws_ptr, ws_bytes, sptr,
+                                wall_mask=mask)
         if collision != "bgk":
             if collision != "mrt":
                 raise ValueError(collision)

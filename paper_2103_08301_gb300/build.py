@@ -1,11 +1,12 @@
 """Build the solver's shared library (liblbm.so) in-tree for sm_103a.
 
-Six translation units, compiled in parallel and linked with nvcc:
+Seven translation units, compiled in parallel and linked with nvcc:
   csrc/lbm_api.cu     - single-channel C ABI and the step kernels (nvcc, -gencode sm_103a)
   csrc/lbm_big.cu     - the step kernels with 64-bit population offsets (grids of 9 pitch ny >= 2^31)
   csrc/lbm_batch.cu   - batched multi-channel sweep (nvcc)
   csrc/lbm_adjoint.cu - discrete adjoint with checkpoint-and-recompute (nvcc)
   csrc/lbm_mask.cu    - general wall geometry (per-node solid mask) step kernels (nvcc)
+  csrc/lbm_inplace.cu - in-place (AA pattern) single-context step kernels (nvcc)
   csrc/lbm_host.cpp   - host FP64 thermodynamics, initial profiles, plug analysis (g++)
 Run as ``python -m paper_2103_08301_gb300.build`` or call ``build()``.
 """
@@ -25,7 +26,8 @@ LIB = os.path.join(HERE, "liblbm.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["lbm_api.cu", "lbm_big.cu", "lbm_batch.cu", "lbm_adjoint.cu", "lbm_mask.cu", "lbm_host.cpp", "lbm_kernels.cuh",
+SOURCES = ["lbm_api.cu", "lbm_big.cu", "lbm_batch.cu", "lbm_adjoint.cu", "lbm_mask.cu", "lbm_inplace.cu", "lbm_host.cpp",
+           "lbm_kernels.cuh",
            "lbm_rows2.cuh", "lbm_tile.cuh", "lbm_internal.h"]
 
 
@@ -57,6 +59,7 @@ def build(force: bool = False, verbose: bool = False, out: str | None = None) ->
     host_o = os.path.join(bdir, "lbm_host.o")
     mask_o = os.path.join(bdir, "lbm_mask.o")
     big_o = os.path.join(bdir, "lbm_big.o")
+    aa_o = os.path.join(bdir, "lbm_inplace.o")
     extra = os.environ.get("LBM_NVCC_FLAGS", "").split()  # tuning experiments, e.g. -DLBM_STAGE_AHEAD=2
 
     def nvcc(src, obj):
@@ -68,14 +71,15 @@ def build(force: bool = False, verbose: bool = False, out: str | None = None) ->
 
     gxx = ["g++", "-O2", "-std=c++17", "-fPIC", "-I", INCLUDE, "-I", CSRC, "-c",
            os.path.join(CSRC, "lbm_host.cpp"), "-o", host_o]
-    with ThreadPoolExecutor(6) as ex:
+    with ThreadPoolExecutor(7) as ex:
         outs = list(ex.map(_run, [nvcc("lbm_api.cu", api_o), nvcc("lbm_big.cu", big_o), nvcc("lbm_batch.cu", batch_o),
-                                  nvcc("lbm_adjoint.cu", adj_o), nvcc("lbm_mask.cu", mask_o), gxx]))
+                                  nvcc("lbm_adjoint.cu", adj_o), nvcc("lbm_mask.cu", mask_o),
+                                  nvcc("lbm_inplace.cu", aa_o), gxx]))
     if verbose:
-        for o in outs[:5]:
+        for o in outs[:6]:
             print(o)
     tmp = lib + f".tmp{os.getpid()}"
-    _run([NVCC, *ARCH, "-shared", "-o", tmp, api_o, big_o, batch_o, adj_o, mask_o, host_o, "-lcudart"])
+    _run([NVCC, *ARCH, "-shared", "-o", tmp, api_o, big_o, batch_o, adj_o, mask_o, aa_o, host_o, "-lcudart"])
     os.replace(tmp, lib)
     return lib
 

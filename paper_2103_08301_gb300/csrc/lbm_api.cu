@@ -53,16 +53,25 @@ bool fault_is(const char *kind)
 struct Layout {
     size_t pops;      // one population array
     size_t f0, f1, mass, J, ext, err, dout, total;
+    size_t rho, side;  // in-place contexts: density plane and pressure-column side buffer
 };
 
-Layout layout_of(int nx, int ny, int precision)
+// inplace: one population array (f1 = f0) plus the density plane and the side
+// buffer of the in-place step
+Layout layout_of(int nx, int ny, int precision, bool inplace = false)
 {
     Layout L{};
     const size_t sz = precision == 64 ? 8 : 4;
     L.pops = align_up((size_t)9 * lbm::pitch_of(nx) * ny * sz);
     size_t o = 0;
     L.f0 = o; o += L.pops;
-    L.f1 = o; o += L.pops;
+    if (inplace) {
+        L.f1 = L.f0;
+        L.rho = o; o += align_up((size_t)lbm::pitch_of(nx) * ny * sz);
+        L.side = o; o += align_up((size_t)2 * 9 * ny * sz);
+    } else {
+        L.f1 = o; o += L.pops;
+    }
     L.mass = o; o += align_up(lbm::MAX_CTAS * sizeof(double));
     L.J = o; o += align_up(lbm::MAX_CTAS * sizeof(double));
     L.ext = o; o += align_up((size_t)lbm::MAX_CTAS * 4 * sz);
@@ -101,6 +110,11 @@ struct lbm_ctx {
     bool own_ws = false;
     Layout L{};
     int cur = 0;          // which population array holds the current state
+    // in-place streaming (lbm_init_inplace): one population array, cur = 0;
+    // aa_odd: the array holds the odd-parity layout (after an odd number of
+    // in-place steps since it last held the natural one)
+    bool inplace = false, aa_odd = false;
+    lbm::AAPlan aa{};
     int64_t step = 0;
     int W = STRIP, nstrips = 0, yf0 = 0, nyf = 0;
     int W_opt = 0;  // LBM_OPT_STRIP (0: widest)
@@ -237,6 +251,7 @@ void *kernel_ptr(bool walls, bool pres, bool staged, bool padded)
 }  // namespace
 
 namespace {
+lbm_status aa_natural(lbm_ctx *ctx);
 size_t state_bytes(const lbm_ctx *ctx)
 {
     return (size_t)9 * ctx->pitch * ctx->grid.ny * (ctx->grid.precision == 64 ? 8 : 4);
@@ -245,17 +260,24 @@ size_t state_bytes(const lbm_ctx *ctx)
 
 cudaError_t lbm_ctx_copy_state(lbm_ctx *ctx, void *dst)
 {
+    if (aa_natural(ctx) != LBM_OK) return cudaErrorLaunchFailure;
     return cudaMemcpyAsync(dst, ctx->ws + (ctx->cur ? ctx->L.f1 : ctx->L.f0), state_bytes(ctx),
                            cudaMemcpyDeviceToDevice, ctx->stream);
 }
 
-const void *lbm_ctx_state(const lbm_ctx *ctx) { return ctx->ws + (ctx->cur ? ctx->L.f1 : ctx->L.f0); }
+const void *lbm_ctx_state(const lbm_ctx *ctx)
+{
+    if (aa_natural(const_cast<lbm_ctx *>(ctx)) != LBM_OK) return nullptr;
+    return ctx->ws + (ctx->cur ? ctx->L.f1 : ctx->L.f0);
+}
 
 cudaError_t lbm_ctx_load_state(lbm_ctx *ctx, const void *src)
 {
     const size_t bytes = state_bytes(ctx);
     cudaError_t e = cudaMemcpyAsync(ctx->ws + ctx->L.f0, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->ws + ctx->L.f1, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess && !ctx->inplace)
+        e = cudaMemcpyAsync(ctx->ws + ctx->L.f1, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    ctx->aa_odd = false;
     return e;
 }
 
@@ -523,6 +545,7 @@ lbm_status build_graph(lbm_ctx *ctx)
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
     const int cur0 = ctx->cur;
+    const bool odd0 = ctx->aa_odd;
     const int64_t step0 = ctx->step;
     const int keep = ctx->graph_steps;
     ctx->graph_steps = 0;  // capture single launches
@@ -530,6 +553,7 @@ lbm_status build_graph(lbm_ctx *ctx)
     ctx->graph_steps = keep;
     cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
     ctx->cur = cur0;  // capture records; nothing ran
+    ctx->aa_odd = odd0;
     ctx->step = step0;
     if (st != LBM_OK) { if (g) cudaGraphDestroy(g); return st; }
     if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "graph end capture");
@@ -539,10 +563,23 @@ lbm_status build_graph(lbm_ctx *ctx)
     return LBM_OK;
 }
 
+// the phase lbm_step's graphs start from: buffer 0, or for in-place
+// contexts the natural layout
+int phase_of(const lbm_ctx *ctx) { return ctx->inplace ? (ctx->aa_odd ? 1 : 0) : ctx->cur; }
+
 template <typename real>
 lbm_status one_step(lbm_ctx *ctx)
 {
     lbm::KArgs<real> A = make_args<real>(ctx);
+    if (ctx->inplace) {
+        cudaError_t e = lbm::aa_step<real>(A, (real *)(ctx->ws + ctx->L.f0), (real *)(ctx->ws + ctx->L.rho),
+                                           (real *)(ctx->ws + ctx->L.side), ctx->grid.walls, ctx->grid.bc_x,
+                                           ctx->aa_odd, ctx->big, ctx->aa, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "in-place step launch");
+        ctx->aa_odd = !ctx->aa_odd;
+        ctx->step += 1;
+        return LBM_OK;
+    }
     cudaError_t e = ctx->mask ? lbm::mask_launch<real>(ctx->mask, A, lbm::MODE_STEP, ctx->stream)
                               : launch<real, lbm::MODE_STEP>(ctx, A);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
@@ -556,18 +593,18 @@ lbm_status do_steps(lbm_ctx *ctx, int64_t n)
 {
     // the graph starts from buffer 0: a run that starts from buffer 1 takes one
     // single launch first
-    if (ctx->graph_steps > 0 && ctx->stream && ctx->cur == 1 && n > ctx->graph_steps) {
+    if (ctx->graph_steps > 0 && ctx->stream && phase_of(ctx) == 1 && n > ctx->graph_steps) {
         lbm_status s = one_step<real>(ctx);
         if (s != LBM_OK) return s;
         --n;
     }
-    while (ctx->graph_steps > 0 && ctx->stream && n >= ctx->graph_steps && ctx->cur == 0) {
+    while (ctx->graph_steps > 0 && ctx->stream && n >= ctx->graph_steps && phase_of(ctx) == 0) {
         if (!ctx->graph) {
             lbm_status s = build_graph<real>(ctx);
             if (s != LBM_OK) return s;
         }
         CK(cudaGraphLaunch(ctx->graph, ctx->stream), "graph launch");
-        ctx->step += ctx->graph_steps;  // an even count: the state ends in buffer 0 again
+        ctx->step += ctx->graph_steps;  // an even count: the state ends in buffer 0 (natural layout) again
         n -= ctx->graph_steps;
     }
     for (int64_t s = 0; s < n; ++s) {
@@ -577,9 +614,25 @@ lbm_status do_steps(lbm_ctx *ctx, int64_t n)
     return LBM_OK;
 }
 
+// In-place contexts: bring the array back to the natural layout (every
+// reader and writer of the state outside the step expects it); asynchronous.
+lbm_status aa_natural(lbm_ctx *ctx)
+{
+    if (!ctx->inplace || !ctx->aa_odd) return LBM_OK;
+    CK(lbm::aa_swap(ctx->grid.precision, ctx->ws + ctx->L.f0, ctx->grid.walls, ctx->grid.bc_x, ctx->big, ctx->grid.nx,
+                    ctx->grid.ny, ctx->pitch, ctx->sms, ctx->stream),
+       "layout swap");
+    ctx->aa_odd = false;
+    return LBM_OK;
+}
+
+// CTAs whose diagnostic slots hold the step's partials
+int diag_ctas(const lbm_ctx *ctx) { return ctx->inplace ? ctx->aa.nctas : ctx->nctas; }
+
 template <typename real>
 lbm_status do_fields(lbm_ctx *ctx, void *rho, void *ux, void *uy, void *tw, void *pw)
 {
+    if (lbm_status s0 = aa_natural(ctx)) return s0;
     const size_t N = (size_t)ctx->grid.nx * ctx->grid.ny, nx = ctx->grid.nx;
     const size_t sz = sizeof(real);
     if (!ctx->fscratch) {
@@ -638,7 +691,7 @@ struct CkptHeader {
     uint64_t magic;
     int32_t nx, ny, walls, bc_x, precision, nctas;
     int64_t step;
-    int32_t cur, pad;
+    int32_t cur, inplace;  // inplace: one population array (in the natural layout) follows
 };
 
 } // namespace
@@ -697,9 +750,19 @@ size_t lbm_workspace_bytes(const lbm_grid *grid)
     return layout_of(grid->nx, grid->ny, grid->precision).total;
 }
 
-lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, const uint8_t *wall_mask,
+size_t lbm_workspace_bytes_inplace(const lbm_grid *grid)
+{
+    if (!grid_ok(grid, true)) return 0;
+    return layout_of(grid->nx, grid->ny, grid->precision, true).total;
+}
+
+} // extern "C"
+
+namespace {
+
+lbm_status init_ctx(const lbm_grid *grid, const lbm_eos *eos, double tau, const uint8_t *wall_mask,
                     double wetting, const lbm_drive *drive, const double *rho0, void *workspace, size_t ws_bytes,
-                    void *stream, lbm_ctx **out)
+                    void *stream, bool inplace, lbm_ctx **out)
 {
     if (!out) return LBM_ERR_ARG;
     *out = nullptr;
@@ -739,7 +802,8 @@ lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, const 
         return s;
     }
 
-    ctx->L = layout_of(grid->nx, grid->ny, grid->precision);
+    ctx->inplace = inplace;
+    ctx->L = layout_of(grid->nx, grid->ny, grid->precision, inplace);
     ctx->pitch = lbm::pitch_of(grid->nx);
     ctx->big = !lbm::idx32_ok(grid->nx, grid->ny);
     if (workspace) {
@@ -780,6 +844,14 @@ lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, const 
     if (wall_mask) ctx->mask_host.assign(wall_mask, wall_mask + (size_t)grid->nx * grid->ny);
     st = plan_geometry(ctx);
     if (st != LBM_OK) { lbm_free(ctx); return st; }
+    if (inplace) {
+        e = lbm::aa_plan(grid->precision, ctx->big, grid->walls, grid->bc_x, grid->nx, grid->ny, ctx->sms, &ctx->aa);
+        if (e != cudaSuccess) {
+            lbm_status s = cuda_fail(ctx, e, "in-place plan");
+            lbm_free(ctx);
+            return s;
+        }
+    }
 
     // Initial state f = f_eq(rho0, 0) in both arrays.
     const size_t N = (size_t)grid->nx * grid->ny;
@@ -811,6 +883,24 @@ lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, const 
     }
     *out = ctx;
     return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, const uint8_t *wall_mask,
+                    double wetting, const lbm_drive *drive, const double *rho0, void *workspace, size_t ws_bytes,
+                    void *stream, lbm_ctx **out)
+{
+    return init_ctx(grid, eos, tau, wall_mask, wetting, drive, rho0, workspace, ws_bytes, stream, false, out);
+}
+
+lbm_status lbm_init_inplace(const lbm_grid *grid, const lbm_eos *eos, double tau, double wetting,
+                            const lbm_drive *drive, const double *rho0, void *workspace, size_t ws_bytes,
+                            void *stream, lbm_ctx **out)
+{
+    return init_ctx(grid, eos, tau, nullptr, wetting, drive, rho0, workspace, ws_bytes, stream, true, out);
 }
 
 lbm_status lbm_relaxed_coexistence(const lbm_eos *eos, double tau, const lbm_collision *coll, int32_t precision,
@@ -893,11 +983,11 @@ void enqueue_diag(lbm_ctx *ctx, double *dout)
     if (ctx->grid.precision == 64)
         lbm::diag_kernel<double><<<1, 256, 0, ctx->stream>>>(
             (double *)(ctx->ws + ctx->L.mass), (double *)(ctx->ws + ctx->L.J),
-            (double *)(ctx->ws + ctx->L.ext), (int *)(ctx->ws + ctx->L.err), ctx->nctas, dout);
+            (double *)(ctx->ws + ctx->L.ext), (int *)(ctx->ws + ctx->L.err), diag_ctas(ctx), dout);
     else
         lbm::diag_kernel<float><<<1, 256, 0, ctx->stream>>>(
             (double *)(ctx->ws + ctx->L.mass), (double *)(ctx->ws + ctx->L.J),
-            (float *)(ctx->ws + ctx->L.ext), (int *)(ctx->ws + ctx->L.err), ctx->nctas, dout);
+            (float *)(ctx->ws + ctx->L.ext), (int *)(ctx->ws + ctx->L.err), diag_ctas(ctx), dout);
 }
 }  // namespace
 
@@ -954,6 +1044,7 @@ lbm_status lbm_reset_diag(lbm_ctx *ctx)
 lbm_status lbm_populations(lbm_ctx *ctx, void *dst)
 {
     if (!ctx || !dst) return LBM_ERR_ARG;
+    if (lbm_status s = aa_natural(ctx)) return s;
     CK(copy_planes(ctx, dst, ctx->ws + (ctx->cur ? ctx->L.f1 : ctx->L.f0), true), "populations copy");
     CK(cudaStreamSynchronize(ctx->stream), "populations sync");
     return LBM_OK;
@@ -965,7 +1056,8 @@ lbm_status lbm_load_populations(lbm_ctx *ctx, const void *src)
     // both arrays, so never-written slots (solid rows, unreached boundary
     // slots) agree with the loaded state
     CK(copy_planes(ctx, ctx->ws + ctx->L.f0, src, false), "load copy");
-    CK(copy_planes(ctx, ctx->ws + ctx->L.f1, src, false), "load copy");
+    if (!ctx->inplace) CK(copy_planes(ctx, ctx->ws + ctx->L.f1, src, false), "load copy");
+    ctx->aa_odd = false;
     CK(cudaStreamSynchronize(ctx->stream), "load sync");
     return LBM_OK;
 }
@@ -974,21 +1066,25 @@ size_t lbm_checkpoint_bytes(const lbm_ctx *ctx)
 {
     if (!ctx) return 0;
     const size_t sz = ctx->grid.precision == 64 ? 8 : 4;
-    return sizeof(CkptHeader) + 2 * ctx->L.pops + (size_t)lbm::MAX_CTAS * (16 + 4 * sz) + sizeof(int);
+    return sizeof(CkptHeader) + (ctx->inplace ? 1 : 2) * ctx->L.pops + (size_t)lbm::MAX_CTAS * (16 + 4 * sz) +
+           sizeof(int);
 }
 
 lbm_status lbm_checkpoint(lbm_ctx *ctx, void *host_buf, size_t bytes)
 {
     if (!ctx || !host_buf || bytes < lbm_checkpoint_bytes(ctx)) return LBM_ERR_ARG;
     const size_t sz = ctx->grid.precision == 64 ? 8 : 4;
+    if (lbm_status s = aa_natural(ctx)) return s;
+    const int narr = ctx->inplace ? 1 : 2;
     CkptHeader h{CKPT_MAGIC, ctx->grid.nx, ctx->grid.ny, ctx->grid.walls, ctx->grid.bc_x,
-                 ctx->grid.precision, ctx->nctas, ctx->step, ctx->cur, 0};
+                 ctx->grid.precision, diag_ctas(ctx), ctx->step, ctx->cur, ctx->inplace ? 1 : 0};
     unsigned char *p = (unsigned char *)host_buf;
     std::memcpy(p, &h, sizeof h);
     p += sizeof h;
     // both population arrays: slots no population reaches keep older values
-    CK(cudaMemcpyAsync(p, ctx->ws + ctx->L.f0, 2 * ctx->L.pops, cudaMemcpyDeviceToHost, ctx->stream), "ckpt");
-    p += 2 * ctx->L.pops;
+    // (in-place contexts: the one array, in the natural layout)
+    CK(cudaMemcpyAsync(p, ctx->ws + ctx->L.f0, narr * ctx->L.pops, cudaMemcpyDeviceToHost, ctx->stream), "ckpt");
+    p += narr * ctx->L.pops;
     CK(cudaMemcpyAsync(p, ctx->ws + ctx->L.mass, lbm::MAX_CTAS * 8, cudaMemcpyDeviceToHost, ctx->stream), "ckpt");
     p += lbm::MAX_CTAS * 8;
     CK(cudaMemcpyAsync(p, ctx->ws + ctx->L.J, lbm::MAX_CTAS * 8, cudaMemcpyDeviceToHost, ctx->stream), "ckpt");
@@ -1006,12 +1102,13 @@ lbm_status lbm_restore(lbm_ctx *ctx, const void *host_buf, size_t bytes)
     CkptHeader h;
     std::memcpy(&h, host_buf, sizeof h);
     if (h.magic != CKPT_MAGIC || h.nx != ctx->grid.nx || h.ny != ctx->grid.ny || h.walls != ctx->grid.walls ||
-        h.bc_x != ctx->grid.bc_x || h.precision != ctx->grid.precision)
+        h.bc_x != ctx->grid.bc_x || h.precision != ctx->grid.precision || (h.inplace != 0) != ctx->inplace)
         return LBM_ERR_STATE;
     const size_t sz = ctx->grid.precision == 64 ? 8 : 4;
+    const int narr = ctx->inplace ? 1 : 2;
     const unsigned char *p = (const unsigned char *)host_buf + sizeof h;
-    CK(cudaMemcpyAsync(ctx->ws + ctx->L.f0, p, 2 * ctx->L.pops, cudaMemcpyHostToDevice, ctx->stream), "restore");
-    p += 2 * ctx->L.pops;
+    CK(cudaMemcpyAsync(ctx->ws + ctx->L.f0, p, narr * ctx->L.pops, cudaMemcpyHostToDevice, ctx->stream), "restore");
+    p += narr * ctx->L.pops;
     CK(cudaMemcpyAsync(ctx->ws + ctx->L.mass, p, lbm::MAX_CTAS * 8, cudaMemcpyHostToDevice, ctx->stream), "restore");
     p += lbm::MAX_CTAS * 8;
     CK(cudaMemcpyAsync(ctx->ws + ctx->L.J, p, lbm::MAX_CTAS * 8, cudaMemcpyHostToDevice, ctx->stream), "restore");
@@ -1022,6 +1119,7 @@ lbm_status lbm_restore(lbm_ctx *ctx, const void *host_buf, size_t bytes)
     CK(cudaStreamSynchronize(ctx->stream), "restore sync");
     ctx->step = h.step;
     ctx->cur = h.cur;
+    ctx->aa_odd = false;
     ctx->err_pending = false;
     // Per-CTA accumulators only line up with the same launch geometry; with
     // another CTA count they stay valid as totals but the summation order changes.
@@ -1073,7 +1171,7 @@ lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
         ctx->pf = (int)value;
         return LBM_OK;
     case LBM_OPT_GENERAL:
-        if (value != 0 && ctx->big) return LBM_ERR_ARG;  // 32-bit offsets only
+        if (value != 0 && (ctx->big || ctx->inplace)) return LBM_ERR_ARG;  // 32-bit offsets, two arrays only
         ctx->force_general = value != 0;
         break;
     case LBM_OPT_PDL:
@@ -1088,7 +1186,7 @@ lbm_status lbm_set_option(lbm_ctx *ctx, lbm_option opt, int64_t value)
     case LBM_OPT_FAULT_SKIP_COPY:
         // the test build exists for walls, pressure columns and unpadded rows
         if (value != 0) {
-            if (!(ctx->rows2 && !ctx->mask && !ctx->big && ctx->grid.walls && ctx->grid.bc_x &&
+            if (!(ctx->rows2 && !ctx->inplace && !ctx->mask && !ctx->big && ctx->grid.walls && ctx->grid.bc_x &&
                   ctx->pitch == ctx->grid.nx))
                 return LBM_ERR_ARG;
             cudaError_t e = cudaFuncSetAttribute((void *)lbm::step_kernel_rows2<true, true, false, true>,
@@ -1119,6 +1217,14 @@ lbm_status lbm_launch_info(const lbm_ctx *ctx, int64_t *ctas, int64_t *threads, 
                            int64_t *staged)
 {
     if (!ctx) return LBM_ERR_ARG;
+    if (ctx->inplace) {
+        // one node per thread, CTAs striding over the 32 x 8 tiles
+        if (ctas) *ctas = ctx->aa.nctas;
+        if (threads) *threads = 256;
+        if (units) *units = (int64_t)ctx->aa.ntx * ctx->aa.nty;
+        if (staged) *staged = 0;
+        return LBM_OK;
+    }
     if (ctas) *ctas = ctx->nctas;
     if (threads) *threads = ctx->mask ? 256 : threads_of(ctx, lbm::MODE_STEP);
     if (units) *units = ctx->mask ? (int64_t)ctx->grid.nx * ctx->grid.ny : ctx->units;

@@ -320,7 +320,9 @@ lbm_status batch_plan(lbm_batch *b)
         if (b->walls && u > 0 && u < U) {
             int ci, s, row;
             locate(u, ci, s, row);
-            if (row == 2 || row == b->ch[ci].grid.ny - 2) u -= 1;
+            // one row back from ny-2 is ny-3, which is row 2 itself when ny = 5
+            if (row == b->ch[ci].grid.ny - 2) { u -= 1; --row; }
+            if (row == 2) u -= 1;
         }
         return u;
     };
@@ -357,7 +359,8 @@ lbm_status batch_plan(lbm_batch *b)
                 int ya = c.yf0;
                 for (int k = 1; k <= p; ++k) {
                     int yb = c.yf0 + (int)((long long)k * c.nyf / p);
-                    if (k < p && b->walls && (yb == 2 || yb == c.grid.ny - 2)) yb -= 1;
+                    if (k < p && b->walls && yb == c.grid.ny - 2) --yb;
+                    if (k < p && b->walls && yb == 2) --yb;
                     if (yb > ya) b->segs.push_back(lbm::BatchSeg{ci, s2, ya, yb});
                     ya = std::max(ya, yb);
                 }

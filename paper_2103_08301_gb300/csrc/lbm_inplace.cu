@@ -1,0 +1,446 @@
+// In-place streaming for single contexts: one population array instead of
+// two (the AA pattern, Bailey, Myre, Walsh, Lilja and Wilson, ICPP 2009),
+// plus a density plane.
+//
+// Even steps find the natural layout, F[x][i] = f_i(x): a node reads its own
+// nine slots and writes its post-collision populations back reversed,
+// F[x][opp(i)] = f*_i(x). Odd steps read f_i(x) from F[x - e_i][opp(i)] and
+// write f*_i(x) to F[x + e_i][i], which restores the natural layout. Each slot
+// is read and written by one node only, so neither step races. Half-way
+// bounce-back (Sec. 2.2 walls) writes into the wall row's slot on even steps
+// (F[x + e_i][i]) and into the node's own reversed slot on odd steps; the
+// populations that leave through a pressure column are dropped.
+//
+// The force of Eq. 2.17 reads densities up to two nodes away, and in place a
+// neighbour's slots may already hold its next state, so every step first
+// writes the density sum of each fluid node into a plane of its own
+// (aa_density_kernel) and then collides from that plane (aa_step_kernel, one
+// CTA per 32 x 8 tile at a time). A pressure column collides with its interior
+// neighbour's populations (Sec. 2.2 pressure-driven ends); the density pass
+// copies those into a side buffer, for the same reason.
+//
+// The node arithmetic is the one-row step kernel's helper sequence, in the
+// same order and precision, so the populations match the two-array step bit
+// for bit; only the summation order of the diagnostics differs.
+//
+// Traffic per node and step (FP32): 36 B read and 4 B written by the density
+// pass, 36 B read, 36 B written and 4 B of densities read by the step, 116 B
+// against the two-array step's 72 B; storage 40 B against 72 B.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+constexpr int AA_TX = 32;                   // tile columns: one warp
+constexpr int AA_TY = 8;                    // tile rows: one warp each
+constexpr int AA_THREADS = AA_TX * AA_TY;   // one node per thread
+constexpr int AA_SW = AA_TX + 4;            // ring columns x0-2 .. x0+AA_TX+1
+constexpr int AA_ROWS = AA_TY + 4;          // ring rows y0-2 .. y0+AA_TY+1
+
+template <typename real>
+struct SmemAA {
+    real rho[AA_ROWS][AA_SW];
+    real phi[AA_ROWS][AA_SW];
+    real lap[AA_ROWS][AA_SW];
+    real brho1[AA_TX], bv1[AA_TX], tv2[AA_TX];  // row 1 (rho, v) and row ny-3 (v) for the wall shear
+    double red[AA_THREADS / 32][2];
+    real ext[AA_THREADS / 32][4];
+    int bad;
+};
+
+// x +- 1 on a periodic axis of n nodes (n >= 1)
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// offset of slot (x, y, i): rows of nine planes of pitch P
+template <typename IX>
+__device__ __forceinline__ IX aa_slot(int x, int y, int i, int P)
+{
+    return (IX)y * (IX)(9 * (IX)P) + (IX)i * P + x;
+}
+
+// Density sum of every fluid node into rho (plane pitch P), in the step
+// kernels' summation order; pressure columns are skipped (their density is
+// derived from the neighbour's), and the populations of columns 1 and nx-2
+// go to side[2][ny][9] for the pressure columns' extrapolation.
+template <typename real, bool WALLS, bool PRES, bool ODD, typename IX>
+__global__ void __launch_bounds__(256) aa_density_kernel(const real *F, real *rho, real *side, int nx, int ny, int P,
+                                                         int yf0, int nyf)
+{
+    const long long n = (long long)nx * nyf;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int yl = (int)(k / nx), x = (int)(k - (long long)yl * nx), y = yf0 + yl;
+        if (PRES && (x == 0 || x == nx - 1)) continue;
+        real f[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if (ODD) {
+                // interior columns of a channel with pressure columns, and the
+                // fluid rows of a walled one, have all their sources in the array
+                const int sx = PRES ? x - ex_(i) : wrap1(x - ex_(i), nx);
+                const int sy = WALLS ? y - ey_(i) : wrap1(y - ey_(i), ny);
+                f[i] = F[aa_slot<IX>(sx, sy, opp_(i), P)];
+            } else {
+                f[i] = F[aa_slot<IX>(x, y, i, P)];
+            }
+        }
+        real sum = add_(add_(add_(f[0], f[1]), add_(f[2], f[3])), add_(add_(f[4], f[5]), add_(f[6], f[7])));
+        sum = add_(sum, f[8]);
+        rho[(IX)y * P + x] = sum;
+        if (PRES && (x == 1 || x == nx - 2)) {
+            real *s = side + ((size_t)(x == 1 ? 0 : 1) * ny + y) * 9;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) s[i] = f[i];
+        }
+    }
+}
+
+// Odd-parity layout <-> natural layout, in place: the slots (x, i) and
+// (x - e_i, opp(i)) trade values, one thread per representative i in
+// {1, 2, 5, 6}. Pairs with a slot outside the array (beyond a pressure
+// column or a wall row) hold no population that is ever read and stay.
+template <typename real, bool WALLS, bool PRES, typename IX>
+__global__ void __launch_bounds__(256) aa_swap_kernel(real *F, int nx, int ny, int P)
+{
+    const long long n = (long long)nx * ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / nx), x = (int)(k - (long long)y * nx);
+        const int rep[4] = {1, 2, 5, 6};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = rep[r];
+            int sx = x - ex_(i), sy = y - ey_(i);
+            if (PRES) { if (sx < 0 || sx >= nx) continue; }
+            else sx = wrap1(sx, nx);
+            if (WALLS) { if (sy < 0 || sy >= ny) continue; }
+            else sy = wrap1(sy, ny);
+            const IX a = aa_slot<IX>(x, y, i, P), b = aa_slot<IX>(sx, sy, opp_(i), P);
+            const real t = F[a];
+            F[a] = F[b];
+            F[b] = t;
+        }
+    }
+}
+
+// Tile grid of the step: ntx x nty tiles of AA_TX x AA_TY nodes, the first
+// starting sx columns left of column 0 and sy rows below the first fluid row.
+// The shifts keep the outlet column off a tile's first lane (its stencil is
+// its neighbour's, which reaches two columns back) and the wall-shear rows
+// ny-3 | ny-2 in one tile (rows 1 | 2 always are).
+struct AATiles {
+    int ntx, nty, sx, sy;
+};
+
+// One step of the interior of every tile, CTAs striding over the tiles:
+// (1) densities (with the mirror, pressure-column and periodic rules of the
+// stencil) and the EOS potential on the tile plus two halo nodes, (2) the
+// Laplacian on the tile plus one, (3) force, collision, boundaries and the
+// in-place write of each node (one per thread), then the diagnostics.
+template <typename real, bool WALLS, bool PRES, bool ODD, typename IX>
+__global__ void __launch_bounds__(AA_THREADS) aa_step_kernel(const KArgs<real> A, real *F, const real *rho_in,
+                                                             const real *side, const AATiles T)
+{
+    __shared__ SmemAA<real> S;
+    const int tid = threadIdx.x, lane = tid & 31, rl = tid >> 5;
+    const int nx = A.nx, ny = A.ny, P = A.pitch;
+    const real third = real(1.0 / 3.0);
+    const Geom<real> G{nullptr, nullptr, nx, ny, A.W, P, A.rho_in_g, A.rho_in_l, A.rho_out_g, A.rho_out_l};
+    const int yf0 = A.yf0, yf1 = A.yf0 + A.nyf;
+    Acc<real, 1> acc;
+    acc.reset();
+    const long long ntiles = (long long)T.ntx * T.nty;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int tx = (int)(t % T.ntx), ty = (int)(t / T.ntx);
+        const int x0 = tx * AA_TX - T.sx, y0 = yf0 - T.sy + ty * AA_TY;
+        // stencil rows the tile's fluid rows read
+        const int ylo = max(y0, yf0) - 2, yhi = min(y0 + AA_TY, yf1) + 1;
+
+        // (1) densities and phi at ring row j (stencil row y0-2+j), column c (x0-2+c)
+        for (int k = tid; k < AA_ROWS * AA_SW; k += AA_THREADS) {
+            const int j = k / AA_SW, c = k - j * AA_SW;
+            const int yy = y0 - 2 + j, g = x0 - 2 + c;
+            real rho_c = real(0), ph = real(0);
+            if (yy >= ylo && yy <= yhi) {
+                bool mir;
+                const int row = map_row<WALLS>(yy, ny, mir);
+                const real *rr = rho_in + (IX)row * P;
+                real v;
+                if (PRES) {
+                    if (g <= 0) v = column_density(A, G, false, rr[1]);
+                    else if (g >= nx - 1) v = column_density(A, G, true, rr[nx - 2]);
+                    else v = rr[g];
+                } else {
+                    int gw = g % nx;
+                    v = rr[gw < 0 ? gw + nx : gw];
+                }
+                rho_c = add_(v, mir ? A.wet : real(0));
+                ph = eos_phi<real>(A, rho_c);
+            }
+            S.rho[j][c] = rho_c;
+            S.phi[j][c] = ph;
+        }
+        __syncthreads();
+
+        // (2) Laplacian at ring rows 1 .. AA_ROWS-2, columns 1 .. AA_SW-2
+        for (int k = tid; k < (AA_ROWS - 2) * (AA_SW - 2); k += AA_THREADS) {
+            const int j = 1 + k / (AA_SW - 2), c = 1 + k % (AA_SW - 2);
+            S.lap[j][c] = lap9<real>(row3<real, 1, AA_SW>(S.rho, j - 1, c), row3<real, 1, AA_SW>(S.rho, j, c),
+                                     row3<real, 1, AA_SW>(S.rho, j + 1, c));
+        }
+        __syncthreads();
+
+        // (3) the node (x0 + lane, y0 + rl)
+        const int x = x0 + lane, y = y0 + rl;
+        const bool active = x >= 0 && x < nx && y >= yf0 && y < yf1;
+        const bool pin = PRES && x == 0, pout = PRES && x == nx - 1, anyp = pin || pout;
+        const int lcol = (pin ? 1 : (pout ? nx - 2 : x)) - x0;  // a pressure column collides its neighbour
+        const int ccol = lcol + 2;
+        const int q0 = rl + 2, qm = q0 - 1, qp = q0 + 1;
+        real rho = real(0), vx = real(0);
+        if (active) {
+            real f[9];
+            if (anyp) {
+                const real *s = side + ((size_t)(pout ? 1 : 0) * ny + y) * 9;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) f[i] = s[i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    if (ODD) {
+                        const int sx = PRES ? x - ex_(i) : wrap1(x - ex_(i), nx);
+                        const int sy = WALLS ? y - ey_(i) : wrap1(y - ey_(i), ny);
+                        f[i] = F[aa_slot<IX>(sx, sy, opp_(i), P)];
+                    } else {
+                        f[i] = F[aa_slot<IX>(x, y, i, P)];
+                    }
+                }
+            }
+            real ngpx, ngpy, glx, gly;
+            ngrad12<real>(row3<real, 1, AA_SW>(S.phi, qm, ccol), row3<real, 1, AA_SW>(S.phi, q0, ccol),
+                          row3<real, 1, AA_SW>(S.phi, qp, ccol), ngpx, ngpy);
+            grad12<real>(row3<real, 1, AA_SW>(S.lap, qm, ccol), row3<real, 1, AA_SW>(S.lap, q0, ccol),
+                         row3<real, 1, AA_SW>(S.lap, qp, ccol), glx, gly);
+            rho = S.rho[q0][ccol];
+            const real kr = mul_(A.kappa, rho);
+            const real Fx = add_(mulk(fma_(kr, glx, ngpx), 1.0 / 12.0), A.gx);
+            const real Fy = add_(mulk(fma_(kr, gly, ngpy), 1.0 / 12.0), A.gy);
+            const real jx = add_(add_(sub_(f[1], f[3]), sub_(f[5], f[6])), sub_(f[8], f[7]));
+            const real jy = sub_(add_(sub_(f[2], f[4]), add_(f[5], f[6])), add_(f[7], f[8]));
+            const real irho = rcp_(rho);
+            const real ux = mul_(jx, irho), uy = mul_(jy, irho);
+            const real hFi = mul_(irho, bc<real>(0.5));
+            vx = fma_(hFi, Fx, ux);
+            const real vy = fma_(hFi, Fy, uy);
+            const real rho_own = anyp ? S.rho[q0][lane + 2] : rho;  // a pressure column's own is rho_b
+
+            real fs[9];
+            {
+                // shifted equilibrium: momentum j + ushift F, velocity (j + ushift F) / rho
+                const real mx = fma_(A.ushift, Fx, jx), my = fma_(A.ushift, Fy, jy);
+                real fe[9];
+                feq_pairs<real>(rho, mul_(mx, irho), mul_(my, irho), mx, my, fe);
+                if (A.mrt) {
+                    mrt_relax<real, real>(A, f, fe, fs);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) fs[i] = fma_(sub_(fe[i], f[i]), A.inv_tau, f[i]);
+                }
+            }
+            if (anyp) {
+                // extrapolation from the interior neighbour, momentum of v = (j + F/2) / rho
+                const real mvx = fma_(real(0.5), Fx, jx), mvy = fma_(real(0.5), Fy, jy);
+                real fsc[9];
+                column_extrapolate<real>(A, rho_own, rho, vx, vy, mvx, mvy, f, fsc);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) fs[i] = fsc[i];
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const int ty2 = y + ey_(i);
+                const bool wall = WALLS && (ty2 == 0 || ty2 == ny - 1);
+                int tx2 = x + ex_(i);
+                bool inx = true;
+                if (PRES) inx = tx2 >= 0 && tx2 < nx;
+                else tx2 = wrap1(tx2, nx);
+                const int tyw = WALLS ? ty2 : wrap1(ty2, ny);
+                if (ODD) {
+                    if (wall) F[aa_slot<IX>(x, y, opp_(i), P)] = fs[i];
+                    else if (inx) F[aa_slot<IX>(tx2, tyw, i, P)] = fs[i];  // else it leaves through the column
+                } else {
+                    if (wall) {
+                        if (inx) F[aa_slot<IX>(tx2, ty2, i, P)] = fs[i];
+                    } else {
+                        F[aa_slot<IX>(x, y, opp_(i), P)] = fs[i];
+                    }
+                }
+            }
+            acc.macc = add_(acc.macc, rho_own);
+            acc.rmin = vmin_(acc.rmin, rho);
+            acc.rmax = vmax_(acc.rmax, rho);
+            if (WALLS && !anyp) {
+                if (y == 1) { S.brho1[lane] = rho; S.bv1[lane] = vx; }
+                if (y == ny - 3) S.tv2[lane] = vx;
+            }
+        }
+        acc.flush();
+        if (WALLS) {
+            __syncthreads();  // rows 1 and ny-3 of the tile published
+            if (active && !anyp && (y == 1 || y == 2 || y == ny - 2)) {
+                // wall shear: quadratic through v = 0 on the half-way plane and
+                // v at distances 1/2 and 3/2; wall pressure: Eq. 2.4 in mesh units
+                if (y == 1) {
+                    const real pw = wall_pressure<real, AA_SW>(A, S.rho, S.phi, S.lap[q0][ccol], qm, q0, qp, ccol, rho);
+                    acc.pmin = fmin(acc.pmin, pw); acc.pmax = fmax(acc.pmax, pw);
+                }
+                if (y == 2) {
+                    const real tw = mul_(mul_(S.brho1[lane], A.nu), mul_(fma_(real(9), S.bv1[lane], -vx), third));
+                    acc.J += (double)tw; acc.tmin = fmin(acc.tmin, tw); acc.tmax = fmax(acc.tmax, tw);
+                }
+                if (y == ny - 2) {
+                    const real tw = mul_(mul_(rho, A.nu), mul_(fma_(real(9), vx, -S.tv2[lane]), third));
+                    const real pw = wall_pressure<real, AA_SW>(A, S.rho, S.phi, S.lap[q0][ccol], qm, q0, qp, ccol, rho);
+                    acc.J += (double)tw;
+                    acc.tmin = fmin(acc.tmin, tw); acc.tmax = fmax(acc.tmax, tw);
+                    acc.pmin = fmin(acc.pmin, pw); acc.pmax = fmax(acc.pmax, pw);
+                }
+            }
+        }
+        __syncthreads();  // the ring is rewritten by the next tile
+    }
+
+    double m, j;
+    real e[4];
+    bool anybad;
+    cta_reduce<real, AA_THREADS, 1>(acc, S, m, j, e, anybad);
+    if (tid == 0) {
+        const int cta = blockIdx.x;
+        A.mass_part[cta] = m;
+        A.J_acc[cta] += j;
+        real *ex = A.ext + 4 * cta;
+        ex[0] = fmin(ex[0], e[0]); ex[1] = fmax(ex[1], e[1]);
+        ex[2] = fmin(ex[2], e[2]); ex[3] = fmax(ex[3], e[3]);
+        if (anybad) atomicOr(A.err, 1);
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Host side: kernel selection, the tile plan and the launches.
+// ---------------------------------------------------------------------------
+namespace {
+
+// v = 4 walls + 2 pressure columns + odd
+template <typename real, typename IX>
+void *aa_step_fn(int v)
+{
+    switch (v) {
+    case 0: return (void *)aa_step_kernel<real, false, false, false, IX>;
+    case 1: return (void *)aa_step_kernel<real, false, false, true, IX>;
+    case 2: return (void *)aa_step_kernel<real, false, true, false, IX>;
+    case 3: return (void *)aa_step_kernel<real, false, true, true, IX>;
+    case 4: return (void *)aa_step_kernel<real, true, false, false, IX>;
+    case 5: return (void *)aa_step_kernel<real, true, false, true, IX>;
+    case 6: return (void *)aa_step_kernel<real, true, true, false, IX>;
+    default: return (void *)aa_step_kernel<real, true, true, true, IX>;
+    }
+}
+
+template <typename real, typename IX>
+void *aa_density_fn(int v)
+{
+    switch (v) {
+    case 0: return (void *)aa_density_kernel<real, false, false, false, IX>;
+    case 1: return (void *)aa_density_kernel<real, false, false, true, IX>;
+    case 2: return (void *)aa_density_kernel<real, false, true, false, IX>;
+    case 3: return (void *)aa_density_kernel<real, false, true, true, IX>;
+    case 4: return (void *)aa_density_kernel<real, true, false, false, IX>;
+    case 5: return (void *)aa_density_kernel<real, true, false, true, IX>;
+    case 6: return (void *)aa_density_kernel<real, true, true, false, IX>;
+    default: return (void *)aa_density_kernel<real, true, true, true, IX>;
+    }
+}
+
+// v = 2 walls + pressure columns
+template <typename real, typename IX>
+void *aa_swap_fn(int v)
+{
+    switch (v) {
+    case 0: return (void *)aa_swap_kernel<real, false, false, IX>;
+    case 1: return (void *)aa_swap_kernel<real, false, true, IX>;
+    case 2: return (void *)aa_swap_kernel<real, true, false, IX>;
+    default: return (void *)aa_swap_kernel<real, true, true, IX>;
+    }
+}
+
+template <typename real>
+void *step_fn(bool big, int v)
+{
+    return big ? aa_step_fn<real, long long>(v) : aa_step_fn<real, int>(v);
+}
+
+}  // namespace
+
+cudaError_t aa_plan(int precision, bool big, bool walls, bool pres, int nx, int ny, int sms, AAPlan *p)
+{
+    AAPlan q{};
+    const int nyf = walls ? ny - 2 : ny;
+    q.sx = (pres && (nx - 1) % AA_TX == 0) ? 1 : 0;
+    q.sy = (walls && (ny - 3) % AA_TY == 0) ? 1 : 0;
+    q.ntx = (nx + q.sx + AA_TX - 1) / AA_TX;
+    q.nty = (nyf + q.sy + AA_TY - 1) / AA_TY;
+    int occ = 0;
+    void *fn = precision == 64 ? step_fn<double>(big, 0) : step_fn<float>(big, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, AA_THREADS, 0);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (long long)q.ntx * q.nty;
+    q.nctas = (int)std::max<long long>(1, std::min<long long>({tiles, (long long)sms * std::max(1, occ),
+                                                               (long long)MAX_CTAS}));
+    const long long nodes = (long long)nx * nyf;
+    q.dens_blocks = (int)std::max<long long>(1, std::min<long long>((nodes + 255) / 256, (long long)sms * 8));
+    *p = q;
+    return cudaSuccess;
+}
+
+template <typename real>
+cudaError_t aa_step(const KArgs<real> &A, real *F, real *rho, real *side, bool walls, bool pres, bool odd, bool big,
+                    const AAPlan &p, cudaStream_t st)
+{
+    const int v = 4 * walls + 2 * pres + odd;
+    int nx = A.nx, ny = A.ny, P = A.pitch, yf0 = A.yf0, nyf = A.nyf;
+    const real *Fc = F;
+    void *dargs[] = {(void *)&Fc, (void *)&rho, (void *)&side, (void *)&nx, (void *)&ny, (void *)&P, (void *)&yf0,
+                     (void *)&nyf};
+    void *dfn = big ? aa_density_fn<real, long long>(v) : aa_density_fn<real, int>(v);
+    cudaError_t e = cudaLaunchKernel(dfn, dim3(p.dens_blocks), dim3(256), dargs, 0, st);
+    if (e != cudaSuccess) return e;
+    const AATiles T{p.ntx, p.nty, p.sx, p.sy};
+    const real *rc = rho, *sc = side;
+    void *sargs[] = {(void *)&A, (void *)&F, (void *)&rc, (void *)&sc, (void *)&T};
+    return cudaLaunchKernel(step_fn<real>(big, v), dim3(p.nctas), dim3(AA_THREADS), sargs, 0, st);
+}
+
+cudaError_t aa_swap(int precision, void *F, bool walls, bool pres, bool big, int nx, int ny, int P, int sms,
+                    cudaStream_t st)
+{
+    const int v = 2 * walls + pres;
+    void *fn = precision == 64 ? (big ? aa_swap_fn<double, long long>(v) : aa_swap_fn<double, int>(v))
+                               : (big ? aa_swap_fn<float, long long>(v) : aa_swap_fn<float, int>(v));
+    void *args[] = {(void *)&F, (void *)&nx, (void *)&ny, (void *)&P};
+    const long long nodes = (long long)nx * ny;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((nodes + 255) / 256, (long long)sms * 8));
+    return cudaLaunchKernel(fn, dim3(blocks), dim3(256), args, 0, st);
+}
+
+template cudaError_t aa_step<float>(const KArgs<float> &, float *, float *, float *, bool, bool, bool, bool,
+                                    const AAPlan &, cudaStream_t);
+template cudaError_t aa_step<double>(const KArgs<double> &, double *, double *, double *, bool, bool, bool, bool,
+                                     const AAPlan &, cudaStream_t);
+
+}  // namespace lbm

@@ -104,6 +104,24 @@ void mask_free(MaskPath *m);
 int mask_blocks(const MaskPath *m);  // CTAs of the collide kernel (diagnostic slots)
 template <typename real>
 cudaError_t mask_launch(const MaskPath *m, const KArgs<real> &A, int mode, cudaStream_t stream);
+
+// In-place streaming (the AA pattern) of a single context (lbm_inplace.cu):
+// one population array F, a density plane rho (pitch * ny) and a side buffer
+// (2 * ny * 9) for the pressure columns. aa_plan sizes the tile grid and the
+// CTA counts; aa_step runs one step of F (even: natural layout in, odd-parity
+// layout out; odd: the reverse); aa_swap turns an odd-parity F back into the
+// natural layout in place.
+struct AAPlan {
+    int ntx, nty, sx, sy;  // tile grid of the step and its shifts
+    int nctas;             // CTAs of the step (its diagnostic slots)
+    int dens_blocks;       // CTAs of the density pass
+};
+cudaError_t aa_plan(int precision, bool big, bool walls, bool pres, int nx, int ny, int sms, AAPlan *p);
+template <typename real>
+cudaError_t aa_step(const KArgs<real> &A, real *F, real *rho, real *side, bool walls, bool pres, bool odd, bool big,
+                    const AAPlan &p, cudaStream_t st);
+cudaError_t aa_swap(int precision, void *F, bool walls, bool pres, bool big, int nx, int ny, int P, int sms,
+                    cudaStream_t st);
 }  // namespace lbm
 #endif
 

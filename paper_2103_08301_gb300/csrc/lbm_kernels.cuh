@@ -341,7 +341,10 @@ __device__ __forceinline__ long long cut_units(const KArgs<real> &A, int c)
         int s, y;
         long long e;
         unit_run(A, u, s, y, e);
-        if (y == 2 || y == A.ny - 2) u -= 1;
+        // ny-2 is never a run's first row: one row back is ny-3, which is
+        // row 2 itself when ny = 5
+        if (y == A.ny - 2) { u -= 1; --y; }
+        if (y == 2) u -= 1;
     }
     return u;
 }

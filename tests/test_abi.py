@@ -62,6 +62,27 @@ def test_workspace_bytes(lbm):
     assert lbm.lbm_workspace_bytes(big) >= 2 * 9 * 16384 * 16384 * 4
 
 
+def test_inplace_workspace_bytes(lbm):
+    """An in-place context stores one population array, a density plane and a
+    small side buffer: 40 (FP32) or 80 (FP64) bytes per node plus alignment."""
+    for prec, sz in ((32, 4), (64, 8)):
+        g = lbm.lbm_grid(1024, 256, 1, 1, prec)
+        one, two = lbm.lbm_workspace_bytes_inplace(g), lbm.lbm_workspace_bytes(g)
+        assert 10 * sz * 1024 * 256 <= one < 10 * sz * 1024 * 256 + (1 << 20)
+        assert 18 * sz * 1024 * 256 <= two and one < 0.6 * two
+    assert lbm.lbm_workspace_bytes_inplace(lbm.lbm_grid(0, 64, 0, 0, 32)) == 0
+    big = lbm.lbm_grid(16384, 14600, 1, 1, 32)  # 64-bit population offsets
+    assert lbm.lbm_workspace_bytes_inplace(big) >= 10 * 4 * 16384 * 14600
+    e = lbm.lbm_eos(1.0, 4.0, 1.0, 0.8, 1.0, 0.5)
+    rho0 = np.full((16, 16), 0.1)
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_init_inplace(lbm.lbm_grid(16, 16, 0, 0, 32), e, 0.5, 0.0, None, rho0)  # tau must exceed 1/2
+    assert ei.value.status == lbm.LBM_ERR_PARAM
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_init_inplace(lbm.lbm_grid(0, 16, 0, 0, 32), e, 1.0, 0.0, None, rho0)
+    assert ei.value.status == lbm.LBM_ERR_ARG
+
+
 def test_paths_with_32_bit_offsets_reject_larger_grids(lbm):
     """The batch, the allocation-free step and the adjoint keep 9 pitch ny < 2^31
     and refuse larger grids before touching the GPU."""

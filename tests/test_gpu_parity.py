@@ -163,6 +163,12 @@ def test_tiny_and_degenerate_grids_fp64(orc, lbm, nx, ny, walls, bc_x):
         mask[:, 0] = mask[:, -1] = False
     assert np.abs(pops[:, mask] - f_ref[:, mask]).max() <= 1e-12
     assert abs(d["mass"] - d_ref["mass"]) <= 1e-12 * d_ref["mass"]
+    if walls:
+        # the wall shear pairs rows 1 | 2 and ny-3 | ny-2 (one CTA must hold
+        # both rows of each pair; with ny = 5 row 2 belongs to both pairs)
+        tw = max(abs(d_ref["tw_min"]), abs(d_ref["tw_max"]))
+        assert abs(d["wall_shear_sum"] - d_ref["J"]) <= 1e-9 * max(abs(d_ref["J"]), 200 * 2 * nx * tw * 1e-3)
+        assert abs(d["tau_wall_min"] - d_ref["tw_min"]) <= 1e-12 and abs(d["tau_wall_max"] - d_ref["tw_max"]) <= 1e-12
 
 
 @pytest.mark.parametrize("nx,ny,walls,bc_x", [(4, 4, True, True), (4, 4, False, False), (8, 6, True, False),
