@@ -42,6 +42,12 @@ constexpr int AA_TY = 8;                    // tile rows: one warp each
 constexpr int AA_THREADS = AA_TX * AA_TY;   // one node per thread
 constexpr int AA_SW = AA_TX + 4;            // ring columns x0-2 .. x0+AA_TX+1
 constexpr int AA_ROWS = AA_TY + 4;          // ring rows y0-2 .. y0+AA_TY+1
+// resident CTAs per SM the step is compiled for: 4 (64 registers) measured
+// fastest on 16384 x 2048 FP32 (0.992 ms against 1.20 ms at 80 registers and
+// 3 CTAs, 1.15 ms at 5 CTAs with spills)
+#ifndef LBM_AA_MIN_BLOCKS
+#define LBM_AA_MIN_BLOCKS 4
+#endif
 
 template <typename real>
 struct SmemAA {
@@ -144,7 +150,7 @@ struct AATiles {
 // Laplacian on the tile plus one, (3) force, collision, boundaries and the
 // in-place write of each node (one per thread), then the diagnostics.
 template <typename real, bool WALLS, bool PRES, bool ODD, typename IX>
-__global__ void __launch_bounds__(AA_THREADS) aa_step_kernel(const KArgs<real> A, real *F, const real *rho_in,
+__global__ void __launch_bounds__(AA_THREADS, LBM_AA_MIN_BLOCKS) aa_step_kernel(const KArgs<real> A, real *F, const real *rho_in,
                                                              const real *side, const AATiles T)
 {
     __shared__ SmemAA<real> S;
@@ -156,35 +162,119 @@ __global__ void __launch_bounds__(AA_THREADS) aa_step_kernel(const KArgs<real> A
     Acc<real, 1> acc;
     acc.reset();
     const long long ntiles = (long long)T.ntx * T.nty;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int tx = (int)(t % T.ntx), ty = (int)(t / T.ntx);
-        const int x0 = tx * AA_TX - T.sx, y0 = yf0 - T.sy + ty * AA_TY;
-        // stencil rows the tile's fluid rows read
-        const int ylo = max(y0, yf0) - 2, yhi = min(y0 + AA_TY, yf1) + 1;
-
-        // (1) densities and phi at ring row j (stencil row y0-2+j), column c (x0-2+c)
-        for (int k = tid; k < AA_ROWS * AA_SW; k += AA_THREADS) {
+    constexpr int RN = (AA_ROWS * AA_SW + AA_THREADS - 1) / AA_THREADS;  // ring entries per thread
+    struct TileGeom {
+        int x0, y0, ylo, yhi;  // origin, and the stencil rows its fluid rows read
+    };
+    auto tile_geom = [&](long long t) {
+        const int ty = (int)(t / T.ntx), tx = (int)(t - (long long)ty * T.ntx);
+        TileGeom g;
+        g.x0 = tx * AA_TX - T.sx;
+        g.y0 = yf0 - T.sy + ty * AA_TY;
+        g.ylo = max(g.y0, yf0) - 2;
+        g.yhi = min(g.y0 + AA_TY, yf1) + 1;
+        return g;
+    };
+    // the populations of this thread's node (x0 + lane, y0 + rl) of a tile
+    auto load_f = [&](const TileGeom &g, real (&f)[9]) {
+        const int x = g.x0 + lane, y = g.y0 + rl;
+        if (!(x >= 0 && x < nx && y >= yf0 && y < yf1)) return;
+        if (PRES && (x == 0 || x == nx - 1)) {
+            const real *s = side + ((size_t)(x == 0 ? 0 : 1) * ny + y) * 9;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = s[i];
+            return;
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if (ODD) {
+                const int sx = PRES ? x - ex_(i) : wrap1(x - ex_(i), nx);
+                const int sy = WALLS ? y - ey_(i) : wrap1(y - ey_(i), ny);
+                f[i] = F[aa_slot<IX>(sx, sy, opp_(i), P)];
+            } else {
+                f[i] = F[aa_slot<IX>(x, y, i, P)];
+            }
+        }
+    };
+    // the stored density sums behind this thread's ring entries k = tid + q
+    // AA_THREADS (ring row j = stencil row y0-2+j, column c = x0-2+c): the
+    // mirrored row, the pressure column's interior neighbour, the periodic image
+    auto load_ring = [&](const TileGeom &g, real (&r)[RN]) {
+#pragma unroll
+        for (int q = 0; q < RN; ++q) {
+            const int k = tid + q * AA_THREADS;
             const int j = k / AA_SW, c = k - j * AA_SW;
-            const int yy = y0 - 2 + j, g = x0 - 2 + c;
-            real rho_c = real(0), ph = real(0);
-            if (yy >= ylo && yy <= yhi) {
+            const int yy = g.y0 - 2 + j, gc = g.x0 - 2 + c;
+            r[q] = real(0);
+            if (k < AA_ROWS * AA_SW && yy >= g.ylo && yy <= g.yhi) {
                 bool mir;
                 const int row = map_row<WALLS>(yy, ny, mir);
-                const real *rr = rho_in + (IX)row * P;
-                real v;
+                int col;
                 if (PRES) {
-                    if (g <= 0) v = column_density(A, G, false, rr[1]);
-                    else if (g >= nx - 1) v = column_density(A, G, true, rr[nx - 2]);
-                    else v = rr[g];
+                    col = gc <= 0 ? 1 : (gc >= nx - 1 ? nx - 2 : gc);
                 } else {
-                    int gw = g % nx;
-                    v = rr[gw < 0 ? gw + nx : gw];
+                    col = gc % nx;
+                    col = col < 0 ? col + nx : col;
                 }
-                rho_c = add_(v, mir ? A.wet : real(0));
-                ph = eos_phi<real>(A, rho_c);
+                r[q] = rho_in[(IX)row * P + col];
             }
-            S.rho[j][c] = rho_c;
-            S.phi[j][c] = ph;
+        }
+    };
+
+    // CTAs stride over the tiles in row-major order, so that at any time the
+    // grid works on a few rows of tiles whose halos meet in L2; software
+    // pipeline: the next tile's populations and densities are loaded while
+    // this tile computes
+    long long t = blockIdx.x;
+    TileGeom gcur{0, 0, 0, 0};
+    real fcur[9], rcur[RN];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fcur[i] = real(0);
+    if (t < ntiles) {
+        gcur = tile_geom(t);
+        load_f(gcur, fcur);
+        load_ring(gcur, rcur);
+    }
+    for (; t < ntiles; t += gridDim.x) {
+        TileGeom gnext = gcur;
+        real fnext[9], rnext[RN];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fnext[i] = real(0);
+        if (t + gridDim.x < ntiles) {
+            gnext = tile_geom(t + gridDim.x);
+            load_f(gnext, fnext);
+            load_ring(gnext, rnext);
+        }
+        const int x0 = gcur.x0, y0 = gcur.y0;
+        const int x = x0 + lane, y = y0 + rl;
+        const bool active = x >= 0 && x < nx && y >= yf0 && y < yf1;
+        const bool pin = PRES && x == 0, pout = PRES && x == nx - 1, anyp = pin || pout;
+        const int lcol = (pin ? 1 : (pout ? nx - 2 : x)) - x0;  // a pressure column collides its neighbour
+        const int ccol = lcol + 2;
+        const int q0 = rl + 2, qm = q0 - 1, qp = q0 + 1;
+
+        // (1) densities (mirror offset, pressure-column density) and phi of the ring
+#pragma unroll
+        for (int q = 0; q < RN; ++q) {
+            const int k = tid + q * AA_THREADS;
+            if (k < AA_ROWS * AA_SW) {
+                const int j = k / AA_SW, c = k - j * AA_SW;
+                const int yy = y0 - 2 + j, gc = x0 - 2 + c;
+                real rho_c = real(0), ph = real(0);
+                if (yy >= gcur.ylo && yy <= gcur.yhi) {
+                    bool mir;
+                    map_row<WALLS>(yy, ny, mir);
+                    real v = rcur[q];
+                    if (PRES) {
+                        if (gc <= 0) v = column_density(A, G, false, v);
+                        else if (gc >= nx - 1) v = column_density(A, G, true, v);
+                    }
+                    rho_c = add_(v, mir ? A.wet : real(0));
+                    ph = eos_phi<real>(A, rho_c);
+                }
+                S.rho[j][c] = rho_c;
+                S.phi[j][c] = ph;
+            }
         }
         __syncthreads();
 
@@ -196,32 +286,10 @@ __global__ void __launch_bounds__(AA_THREADS) aa_step_kernel(const KArgs<real> A
         }
         __syncthreads();
 
-        // (3) the node (x0 + lane, y0 + rl)
-        const int x = x0 + lane, y = y0 + rl;
-        const bool active = x >= 0 && x < nx && y >= yf0 && y < yf1;
-        const bool pin = PRES && x == 0, pout = PRES && x == nx - 1, anyp = pin || pout;
-        const int lcol = (pin ? 1 : (pout ? nx - 2 : x)) - x0;  // a pressure column collides its neighbour
-        const int ccol = lcol + 2;
-        const int q0 = rl + 2, qm = q0 - 1, qp = q0 + 1;
+        // (3) force, collision, boundaries and the in-place write of the node
         real rho = real(0), vx = real(0);
         if (active) {
-            real f[9];
-            if (anyp) {
-                const real *s = side + ((size_t)(pout ? 1 : 0) * ny + y) * 9;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) f[i] = s[i];
-            } else {
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    if (ODD) {
-                        const int sx = PRES ? x - ex_(i) : wrap1(x - ex_(i), nx);
-                        const int sy = WALLS ? y - ey_(i) : wrap1(y - ey_(i), ny);
-                        f[i] = F[aa_slot<IX>(sx, sy, opp_(i), P)];
-                    } else {
-                        f[i] = F[aa_slot<IX>(x, y, i, P)];
-                    }
-                }
-            }
+            const real (&f)[9] = fcur;
             real ngpx, ngpy, glx, gly;
             ngrad12<real>(row3<real, 1, AA_SW>(S.phi, qm, ccol), row3<real, 1, AA_SW>(S.phi, q0, ccol),
                           row3<real, 1, AA_SW>(S.phi, qp, ccol), ngpx, ngpy);
@@ -313,6 +381,11 @@ __global__ void __launch_bounds__(AA_THREADS) aa_step_kernel(const KArgs<real> A
             }
         }
         __syncthreads();  // the ring is rewritten by the next tile
+        gcur = gnext;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fcur[i] = fnext[i];
+#pragma unroll
+        for (int q = 0; q < RN; ++q) rcur[q] = rnext[q];
     }
 
     double m, j;
