@@ -208,6 +208,17 @@ def _extras(stream, op):
         ms = _timed_steps(lat, stream, 100)
     out["fp64_step"] = {"ms_per_step": ms, "mlups": nodes / ms / 1e3,
                         "hbm_gbs": BYTES_PER_NODE[64] * nodes / ms / 1e6}
+    # in-place streaming (one population array plus a density plane): 40 B per
+    # node stored, 116 B per node and step moved (36 + 4 by the density pass,
+    # 36 + 36 + 4 by the step)
+    peak, _ = _hbm_peak()
+    with lbm.Lattice(NX, NY, rho0, stream=stream, inplace=True, **_lattice_kw(32, op)) as lat:
+        ms = _timed_steps(lat, stream, 200)
+        nan = lat.diag()["nan_detected"]
+    out["inplace_fp32_step"] = {"ms_per_step": ms, "mlups": nodes / ms / 1e3, "nan": bool(nan),
+                                "storage_bytes_per_node": 40, "traffic_bytes_per_node": 116,
+                                "hbm_gbs": 116 * nodes / ms / 1e6, "frac_of_measured": 116 * nodes / ms / 1e6 / peak,
+                                "workload": "same channel, FP32, lbm_init_inplace (AA pattern)"}
     pr = dict(walls=True, bc_x=True, precision=32, eos="pr", a=2 / 49, b=2 / 21, T_over_Tc=0.8, k=1.0,
               kappa=0.01, tau=1.2, dp=1e-4, collision="mrt", s_e=1.64, s_eps=1.54, s_q=1 / 1.2, s_j=1 / 1.2)
     _, g, l, _ = lbm.lbm_coexistence(lbm.lbm_eos(2 / 49, 2 / 21, 1.0, 0.8, 1.0, 0.01, lbm.LBM_EOS_PR, 0.344))
