@@ -1218,9 +1218,9 @@ lbm_status lbm_launch_info(const lbm_ctx *ctx, int64_t *ctas, int64_t *threads, 
 {
     if (!ctx) return LBM_ERR_ARG;
     if (ctx->inplace) {
-        // one node per thread, CTAs striding over the 32 x 8 tiles
+        // CTAs striding over the 32 x 8 tiles (FP32: two rows per thread)
         if (ctas) *ctas = ctx->aa.nctas;
-        if (threads) *threads = 256;
+        if (threads) *threads = ctx->aa.threads;
         if (units) *units = (int64_t)ctx->aa.ntx * ctx->aa.nty;
         if (staged) *staged = 0;
         return LBM_OK;

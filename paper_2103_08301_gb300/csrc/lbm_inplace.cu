@@ -14,8 +14,10 @@
 // The force of Eq. 2.17 reads densities up to two nodes away, and in place a
 // neighbour's slots may already hold its next state, so every step first
 // writes the density sum of each fluid node into a plane of its own
-// (aa_density_kernel) and then collides from that plane (aa_step_kernel, one
-// CTA per 32 x 8 tile at a time). A pressure column collides with its interior
+// (aa_density_kernel) and then collides from that plane (aa_step_kernel_f2
+// for FP32, two rows per thread on the paired FP32 instructions, and
+// aa_step_kernel for FP64, one node per thread; a CTA takes one 32 x 8 tile at
+// a time). A pressure column collides with its interior
 // neighbour's populations (Sec. 2.2 pressure-driven ends); the density pass
 // copies those into a side buffer, for the same reason.
 //
@@ -42,9 +44,10 @@ constexpr int AA_TY = 8;                    // tile rows: one warp each
 constexpr int AA_THREADS = AA_TX * AA_TY;   // one node per thread
 constexpr int AA_SW = AA_TX + 4;            // ring columns x0-2 .. x0+AA_TX+1
 constexpr int AA_ROWS = AA_TY + 4;          // ring rows y0-2 .. y0+AA_TY+1
-// resident CTAs per SM the step is compiled for: 4 (64 registers) measured
-// fastest on 16384 x 2048 FP32 (0.992 ms against 1.20 ms at 80 registers and
-// 3 CTAs, 1.15 ms at 5 CTAs with spills)
+// resident CTAs per SM the one-node-per-thread step is compiled for: 4 (64
+// registers) measured fastest on 16384 x 2048 FP32 (0.992 ms against 1.20 ms
+// at 80 registers and 3 CTAs, 1.15 ms at 5 CTAs with spills); FP32 contexts
+// now step with the row-pair kernel below, FP64 ones with this kernel
 #ifndef LBM_AA_MIN_BLOCKS
 #define LBM_AA_MIN_BLOCKS 4
 #endif
@@ -404,6 +407,316 @@ __global__ void __launch_bounds__(AA_THREADS, LBM_AA_MIN_BLOCKS) aa_step_kernel(
 }
 
 
+// The FP32 step with two rows per thread: the same phases, with the ring's
+// densities, EOS potential and Laplacian and the node arithmetic on the paired
+// FP32 instructions, which round each element as the scalar instruction does,
+// so the populations are the scalar kernel's bit for bit. 128 threads: lane =
+// column, warp = row pair of the 32 x 8 tile.
+// Compiled for 4 resident CTAs per SM (118 registers, no spills): 0.8815 ms
+// per 16384 x 2048 step, against 1.017 ms at 5 (96 registers, small spills)
+// and 1.264 ms at 6.
+constexpr int AA2_THREADS = AA_TX * AA_TY / 2;
+#ifndef LBM_AA2_MIN_BLOCKS
+#define LBM_AA2_MIN_BLOCKS 4
+#endif
+
+// West, centre and east float2 packs (ring rows ra, rb) of ring column c.
+__device__ __forceinline__ Row3<float2> aa_row3p(const float (*S)[AA_SW], int ra, int rb, int c)
+{
+    Row3<float2> r;
+    r.w = make_float2(S[ra][c - 1], S[rb][c - 1]);
+    r.c = make_float2(S[ra][c], S[rb][c]);
+    r.e = make_float2(S[ra][c + 1], S[rb][c + 1]);
+    return r;
+}
+
+template <bool WALLS, bool PRES, bool ODD, typename IX>
+__global__ void __launch_bounds__(AA2_THREADS, LBM_AA2_MIN_BLOCKS)
+    aa_step_kernel_f2(const KArgs<float> A, float *F, const float *rho_in, const float *side, const AATiles T)
+{
+    using V = float2;
+    __shared__ SmemAA<float> S;
+    const int tid = threadIdx.x, lane = tid & 31, pr = tid >> 5;
+    const int nx = A.nx, ny = A.ny, P = A.pitch;
+    const float third = 1.0f / 3.0f;
+    const Geom<float> G{nullptr, nullptr, nx, ny, A.W, P, A.rho_in_g, A.rho_in_l, A.rho_out_g, A.rho_out_l};
+    const int yf0 = A.yf0, yf1 = A.yf0 + A.nyf;
+    Acc<float, 1> acc;
+    acc.reset();
+    const long long ntiles = (long long)T.ntx * T.nty;
+    constexpr int NP = (AA_ROWS / 2) * AA_SW;                  // ring entries as row pairs
+    constexpr int RN = (NP + AA2_THREADS - 1) / AA2_THREADS;   // per thread
+    struct TileGeom {
+        int x0, y0, ylo, yhi;  // origin, and the stencil rows its fluid rows read
+    };
+    auto tile_geom = [&](long long t) {
+        const int ty = (int)(t / T.ntx), tx = (int)(t - (long long)ty * T.ntx);
+        TileGeom g;
+        g.x0 = tx * AA_TX - T.sx;
+        g.y0 = yf0 - T.sy + ty * AA_TY;
+        g.ylo = max(g.y0, yf0) - 2;
+        g.yhi = min(g.y0 + AA_TY, yf1) + 1;
+        return g;
+    };
+    // the populations of this thread's nodes (x0 + lane, y0 + 2 pr + e)
+    auto load_f = [&](const TileGeom &g, V (&f)[9]) {
+        const int x = g.x0 + lane;
+        if (x < 0 || x >= nx) return;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int y = g.y0 + 2 * pr + e;
+            if (y < yf0 || y >= yf1) continue;
+            if (PRES && (x == 0 || x == nx - 1)) {
+                const float *s = side + ((size_t)(x == 0 ? 0 : 1) * ny + y) * 9;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) set_el(f[i], e, s[i]);
+                continue;
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                if (ODD) {
+                    const int sx = PRES ? x - ex_(i) : wrap1(x - ex_(i), nx);
+                    const int sy = WALLS ? y - ey_(i) : wrap1(y - ey_(i), ny);
+                    set_el(f[i], e, F[aa_slot<IX>(sx, sy, opp_(i), P)]);
+                } else {
+                    set_el(f[i], e, F[aa_slot<IX>(x, y, i, P)]);
+                }
+            }
+        }
+    };
+    // the stored density sums behind this thread's ring pair entries k = tid +
+    // q AA2_THREADS (ring rows 2 jp, 2 jp + 1, column c)
+    auto load_ring = [&](const TileGeom &g, V (&r)[RN]) {
+#pragma unroll
+        for (int q = 0; q < RN; ++q) {
+            const int k = tid + q * AA2_THREADS;
+            const int jp = k / AA_SW, c = k - jp * AA_SW;
+            const int gc = g.x0 - 2 + c;
+            int col;
+            if (PRES) {
+                col = gc <= 0 ? 1 : (gc >= nx - 1 ? nx - 2 : gc);
+            } else {
+                col = gc % nx;
+                col = col < 0 ? col + nx : col;
+            }
+            r[q] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int yy = g.y0 - 2 + 2 * jp + e;
+                if (k < NP && yy >= g.ylo && yy <= g.yhi) {
+                    bool mir;
+                    const int row = map_row<WALLS>(yy, ny, mir);
+                    set_el(r[q], e, rho_in[(IX)row * P + col]);
+                }
+            }
+        }
+    };
+
+    long long t = blockIdx.x;
+    TileGeom gcur{0, 0, 0, 0};
+    V fcur[9], rcur[RN];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fcur[i] = make_float2(0.f, 0.f);
+    if (t < ntiles) {
+        gcur = tile_geom(t);
+        load_f(gcur, fcur);
+        load_ring(gcur, rcur);
+    }
+    for (; t < ntiles; t += gridDim.x) {
+        TileGeom gnext = gcur;
+        V fnext[9], rnext[RN];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fnext[i] = make_float2(0.f, 0.f);
+        if (t + gridDim.x < ntiles) {
+            gnext = tile_geom(t + gridDim.x);
+            load_f(gnext, fnext);
+            load_ring(gnext, rnext);
+        }
+        const int x0 = gcur.x0, y0 = gcur.y0;
+
+        // (1) densities (mirror offset, pressure-column density) and phi of the ring
+#pragma unroll
+        for (int q = 0; q < RN; ++q) {
+            const int k = tid + q * AA2_THREADS;
+            if (k < NP) {
+                const int jp = k / AA_SW, c = k - jp * AA_SW, j = 2 * jp;
+                const int gc = x0 - 2 + c;
+                bool in[2], mir[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int yy = y0 - 2 + j + e;
+                    in[e] = yy >= gcur.ylo && yy <= gcur.yhi;
+                    map_row<WALLS>(yy, ny, mir[e]);
+                }
+                V v = rcur[q];
+                if (PRES && (gc <= 0 || gc >= nx - 1)) {
+                    v.x = column_density(A, G, gc > 0, v.x);
+                    v.y = column_density(A, G, gc > 0, v.y);
+                }
+                const V rho_c = add_(v, make_float2(mir[0] ? A.wet : 0.f, mir[1] ? A.wet : 0.f));
+                const V ph = eos_phi<V>(A, rho_c);
+                S.rho[j][c] = in[0] ? rho_c.x : 0.f;
+                S.rho[j + 1][c] = in[1] ? rho_c.y : 0.f;
+                S.phi[j][c] = in[0] ? ph.x : 0.f;
+                S.phi[j + 1][c] = in[1] ? ph.y : 0.f;
+            }
+        }
+        __syncthreads();
+
+        // (2) Laplacian at ring rows 1 .. AA_ROWS-2 in pairs, columns 1 .. AA_SW-2
+        for (int k = tid; k < ((AA_ROWS - 2) / 2) * (AA_SW - 2); k += AA2_THREADS) {
+            const int j = 1 + 2 * (k / (AA_SW - 2)), c = 1 + k % (AA_SW - 2);
+            const V L = lap9<V>(aa_row3p(S.rho, j - 1, j, c), aa_row3p(S.rho, j, j + 1, c),
+                                aa_row3p(S.rho, j + 1, j + 2, c));
+            S.lap[j][c] = L.x;
+            S.lap[j + 1][c] = L.y;
+        }
+        __syncthreads();
+
+        // (3) force, collision, boundaries and the in-place write of the nodes
+        //     (x, b) and (x, b + 1)
+        const int x = x0 + lane, b = y0 + 2 * pr;
+        const bool xin = x >= 0 && x < nx;
+        const bool act0 = xin && b >= yf0 && b < yf1, act1 = xin && b + 1 >= yf0 && b + 1 < yf1;
+        const bool pin = PRES && x == 0, pout = PRES && x == nx - 1, anyp = pin || pout;
+        const int lcol = (pin ? 1 : (pout ? nx - 2 : x)) - x0;  // a pressure column collides its neighbour
+        const int ccol = lcol + 2;
+        const int q0 = 2 * pr + 2, qm = q0 - 1, q1 = q0 + 1, q2 = q0 + 2;  // ring rows of b-1 .. b+2
+        V rho = make_float2(0.f, 0.f), vx = rho;
+        if (act0 || act1) {
+            const V (&f)[9] = fcur;
+            V ngpx, ngpy, glx, gly;
+            ngrad12<V>(aa_row3p(S.phi, qm, q0, ccol), aa_row3p(S.phi, q0, q1, ccol), aa_row3p(S.phi, q1, q2, ccol),
+                       ngpx, ngpy);
+            grad12<V>(aa_row3p(S.lap, qm, q0, ccol), aa_row3p(S.lap, q0, q1, ccol), aa_row3p(S.lap, q1, q2, ccol),
+                      glx, gly);
+            rho = make_float2(S.rho[q0][ccol], S.rho[q1][ccol]);
+            const V kr = mul_(bcr<V>(A.kappa), rho);
+            const V Fx = add_(mulk(fma_(kr, glx, ngpx), 1.0 / 12.0), bcr<V>(A.gx));
+            const V Fy = add_(mulk(fma_(kr, gly, ngpy), 1.0 / 12.0), bcr<V>(A.gy));
+            const V jx = add_(add_(sub_(f[1], f[3]), sub_(f[5], f[6])), sub_(f[8], f[7]));
+            const V jy = sub_(add_(sub_(f[2], f[4]), add_(f[5], f[6])), add_(f[7], f[8]));
+            const V irho = rcp_(rho);
+            const V ux = mul_(jx, irho), uy = mul_(jy, irho);
+            const V hFi = mul_(irho, bc<V>(0.5));
+            vx = fma_(hFi, Fx, ux);
+            const V vy = fma_(hFi, Fy, uy);
+            const V rho_own = anyp ? make_float2(S.rho[q0][lane + 2], S.rho[q1][lane + 2]) : rho;
+
+            V fs[9];
+            {
+                // shifted equilibrium: momentum j + ushift F, velocity (j + ushift F) / rho
+                const V mx = fma_(bcr<V>(A.ushift), Fx, jx), my = fma_(bcr<V>(A.ushift), Fy, jy);
+                V fe[9];
+                feq_pairs<V>(rho, mul_(mx, irho), mul_(my, irho), mx, my, fe);
+                if (A.mrt) {
+                    mrt_relax<V, float>(A, f, fe, fs);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) fs[i] = fma_(sub_(fe[i], f[i]), bcr<V>(A.inv_tau), f[i]);
+                }
+            }
+            if (anyp) {
+                // extrapolation from the interior neighbour, row by row
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    float ff[9], fsc[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) ff[i] = el(f[i], e);
+                    const float mvx = fma_(0.5f, el(Fx, e), el(jx, e));
+                    const float mvy = fma_(0.5f, el(Fy, e), el(jy, e));
+                    column_extrapolate<float>(A, el(rho_own, e), el(rho, e), el(vx, e), el(vy, e), mvx, mvy, ff, fsc);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) set_el(fs[i], e, fsc[i]);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                if (!(e ? act1 : act0)) continue;
+                const int y = b + e;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const int ty2 = y + ey_(i);
+                    const bool wall = WALLS && (ty2 == 0 || ty2 == ny - 1);
+                    int tx2 = x + ex_(i);
+                    bool inx = true;
+                    if (PRES) inx = tx2 >= 0 && tx2 < nx;
+                    else tx2 = wrap1(tx2, nx);
+                    const int tyw = WALLS ? ty2 : wrap1(ty2, ny);
+                    const float v = el(fs[i], e);
+                    if (ODD) {
+                        if (wall) F[aa_slot<IX>(x, y, opp_(i), P)] = v;
+                        else if (inx) F[aa_slot<IX>(tx2, tyw, i, P)] = v;  // else it leaves through the column
+                    } else {
+                        if (wall) {
+                            if (inx) F[aa_slot<IX>(tx2, ty2, i, P)] = v;
+                        } else {
+                            F[aa_slot<IX>(x, y, opp_(i), P)] = v;
+                        }
+                    }
+                }
+                acc.macc = add_(acc.macc, el(rho_own, e));
+                acc.rmin = vmin_(acc.rmin, el(rho, e));
+                acc.rmax = vmax_(acc.rmax, el(rho, e));
+                if (WALLS && !anyp) {
+                    if (y == 1) { S.brho1[lane] = el(rho, e); S.bv1[lane] = el(vx, e); }
+                    if (y == ny - 3) S.tv2[lane] = el(vx, e);
+                }
+            }
+        }
+        acc.flush();
+        if (WALLS) {
+            __syncthreads();  // rows 1 and ny-3 of the tile published
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int y = b + e;
+                if (!(e ? act1 : act0) || anyp || !(y == 1 || y == 2 || y == ny - 2)) continue;
+                // wall shear: quadratic through v = 0 on the half-way plane and
+                // v at distances 1/2 and 3/2; wall pressure: Eq. 2.4 in mesh units
+                const float rk = el(rho, e), vk = el(vx, e);
+                const int pz = q0 + e;
+                if (y == 1) {
+                    const float pw = wall_pressure<float, AA_SW>(A, S.rho, S.phi, S.lap[pz][ccol], pz - 1, pz, pz + 1,
+                                                                 ccol, rk);
+                    acc.pmin = fmin(acc.pmin, pw); acc.pmax = fmax(acc.pmax, pw);
+                }
+                if (y == 2) {
+                    const float tw = mul_(mul_(S.brho1[lane], A.nu), mul_(fma_(9.0f, S.bv1[lane], -vk), third));
+                    acc.J += (double)tw; acc.tmin = fmin(acc.tmin, tw); acc.tmax = fmax(acc.tmax, tw);
+                }
+                if (y == ny - 2) {
+                    const float tw = mul_(mul_(rk, A.nu), mul_(fma_(9.0f, vk, -S.tv2[lane]), third));
+                    const float pw = wall_pressure<float, AA_SW>(A, S.rho, S.phi, S.lap[pz][ccol], pz - 1, pz, pz + 1,
+                                                                 ccol, rk);
+                    acc.J += (double)tw;
+                    acc.tmin = fmin(acc.tmin, tw); acc.tmax = fmax(acc.tmax, tw);
+                    acc.pmin = fmin(acc.pmin, pw); acc.pmax = fmax(acc.pmax, pw);
+                }
+            }
+        }
+        __syncthreads();  // the ring is rewritten by the next tile
+        gcur = gnext;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fcur[i] = fnext[i];
+#pragma unroll
+        for (int q = 0; q < RN; ++q) rcur[q] = rnext[q];
+    }
+
+    double m, j;
+    float e[4];
+    bool anybad;
+    cta_reduce<float, AA2_THREADS, 1>(acc, S, m, j, e, anybad);
+    if (tid == 0) {
+        const int cta = blockIdx.x;
+        A.mass_part[cta] = m;
+        A.J_acc[cta] += j;
+        float *ex = A.ext + 4 * cta;
+        ex[0] = fmin(ex[0], e[0]); ex[1] = fmax(ex[1], e[1]);
+        ex[2] = fmin(ex[2], e[2]); ex[3] = fmax(ex[3], e[3]);
+        if (anybad) atomicOr(A.err, 1);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Host side: kernel selection, the tile plan and the launches.
 // ---------------------------------------------------------------------------
@@ -452,11 +765,30 @@ void *aa_swap_fn(int v)
     }
 }
 
+template <typename IX>
+void *aa_step_f2_fn(int v)
+{
+    switch (v) {
+    case 0: return (void *)aa_step_kernel_f2<false, false, false, IX>;
+    case 1: return (void *)aa_step_kernel_f2<false, false, true, IX>;
+    case 2: return (void *)aa_step_kernel_f2<false, true, false, IX>;
+    case 3: return (void *)aa_step_kernel_f2<false, true, true, IX>;
+    case 4: return (void *)aa_step_kernel_f2<true, false, false, IX>;
+    case 5: return (void *)aa_step_kernel_f2<true, false, true, IX>;
+    case 6: return (void *)aa_step_kernel_f2<true, true, false, IX>;
+    default: return (void *)aa_step_kernel_f2<true, true, true, IX>;
+    }
+}
+
+// FP32: the row-pair kernel (128 threads); FP64: one node per thread (256)
 template <typename real>
 void *step_fn(bool big, int v)
 {
+    if constexpr (sizeof(real) == 4) return big ? aa_step_f2_fn<long long>(v) : aa_step_f2_fn<int>(v);
     return big ? aa_step_fn<real, long long>(v) : aa_step_fn<real, int>(v);
 }
+template <typename real>
+constexpr int step_threads() { return sizeof(real) == 4 ? AA2_THREADS : AA_THREADS; }
 
 }  // namespace
 
@@ -470,7 +802,8 @@ cudaError_t aa_plan(int precision, bool big, bool walls, bool pres, int nx, int 
     q.nty = (nyf + q.sy + AA_TY - 1) / AA_TY;
     int occ = 0;
     void *fn = precision == 64 ? step_fn<double>(big, 0) : step_fn<float>(big, 0);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, AA_THREADS, 0);
+    q.threads = precision == 64 ? step_threads<double>() : step_threads<float>();
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, q.threads, 0);
     if (e != cudaSuccess) return e;
     const long long tiles = (long long)q.ntx * q.nty;
     q.nctas = (int)std::max<long long>(1, std::min<long long>({tiles, (long long)sms * std::max(1, occ),
@@ -496,7 +829,7 @@ cudaError_t aa_step(const KArgs<real> &A, real *F, real *rho, real *side, bool w
     const AATiles T{p.ntx, p.nty, p.sx, p.sy};
     const real *rc = rho, *sc = side;
     void *sargs[] = {(void *)&A, (void *)&F, (void *)&rc, (void *)&sc, (void *)&T};
-    return cudaLaunchKernel(step_fn<real>(big, v), dim3(p.nctas), dim3(AA_THREADS), sargs, 0, st);
+    return cudaLaunchKernel(step_fn<real>(big, v), dim3(p.nctas), dim3(step_threads<real>()), sargs, 0, st);
 }
 
 cudaError_t aa_swap(int precision, void *F, bool walls, bool pres, bool big, int nx, int ny, int P, int sms,

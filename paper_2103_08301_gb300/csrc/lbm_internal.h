@@ -114,6 +114,7 @@ cudaError_t mask_launch(const MaskPath *m, const KArgs<real> &A, int mode, cudaS
 struct AAPlan {
     int ntx, nty, sx, sy;  // tile grid of the step and its shifts
     int nctas;             // CTAs of the step (its diagnostic slots)
+    int threads;           // threads per CTA of the step
     int dens_blocks;       // CTAs of the density pass
 };
 cudaError_t aa_plan(int precision, bool big, bool walls, bool pres, int nx, int ny, int sms, AAPlan *p);

@@ -6,8 +6,10 @@ pressure columns with a drop of 1e-3, CS EOS at 0.85 Tc, tau = 1, k = 1,
 kappa = 0.5, seeded synthetic initial density.
 
   python -m paper_2103_08301_gb300.profile_step --nx 4096 --ny 2048 --steps 5 [--precision 32] [--mask]
+      [--inplace]
 
-Prints the mean kernel time and effective bandwidth (72 B/node in FP32).
+Prints the mean step time and effective bandwidth (72 B/node in FP32; 116
+B/node for an in-place context, whose step is a density pass and a collide pass).
 """
 from __future__ import annotations
 
@@ -26,6 +28,7 @@ def main():
     ap.add_argument("--prefetch", type=int, default=-1, help="LBM_OPT_PREFETCH (row pairs ahead); -1: default")
     ap.add_argument("--mask", action="store_true",
                     help="constrictions on both walls every 2048 columns (the general-geometry kernels)")
+    ap.add_argument("--inplace", action="store_true", help="an lbm_init_inplace context (in-place streaming)")
     args = ap.parse_args()
 
     import torch
@@ -47,7 +50,7 @@ def main():
             mask[1:ny // 4, x0:x0 + 64] = 1
             mask[ny - ny // 4:ny - 1, x0:x0 + 64] = 1
     with lbm.Lattice(nx, ny, rho0, walls=True, bc_x=True, precision=args.precision, T_over_Tc=0.85,
-                     kappa=0.5, dp=1e-3, stream=stream, mask=mask) as lat:
+                     kappa=0.5, dp=1e-3, stream=stream, mask=mask, inplace=args.inplace) as lat:
         lat.set_option(lbm.LBM_OPT_STAGED, args.staged)
         if args.ctas_per_sm:
             lat.set_option(lbm.LBM_OPT_CTAS_PER_SM, args.ctas_per_sm)
@@ -63,8 +66,8 @@ def main():
         ms = a.elapsed_time(b) / args.steps
         info = lat.launch_info()
         nan = lat.diag()["nan_detected"]
-    bpn = 72 if args.precision == 32 else 144
-    print(json.dumps({"nx": nx, "ny": ny, "precision": args.precision, "ms_per_step": ms,
+    bpn = (116 if args.inplace else 72) if args.precision == 32 else (232 if args.inplace else 144)
+    print(json.dumps({"nx": nx, "ny": ny, "precision": args.precision, "inplace": args.inplace, "ms_per_step": ms,
                       "GBps": bpn * nx * ny / ms / 1e6, "MLUPS": nx * ny / ms / 1e3,
                       "launch": info, "nan": nan}))
 

@@ -178,7 +178,7 @@ def test_inplace_storage_and_options(orc, lbm):
                      device="cuda")
     with lbm.Lattice(512, 128, rho0, precision=32, inplace=True, workspace=ws, **kw) as lat:
         info = lat.launch_info()
-        assert info["threads"] == 256 and info["units"] == 16 * 16 and not info["staged"]
+        assert info["threads"] == 128 and info["units"] == 16 * 16 and not info["staged"]  # FP32: row pairs
         for opt in (lbm.LBM_OPT_GENERAL, lbm.LBM_OPT_FAULT_SKIP_COPY):
             with pytest.raises(lbm.LBMError) as ei:
                 lat.set_option(opt, 1)
