@@ -27,8 +27,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 SOURCES = ["lbm_api.cu", "lbm_big.cu", "lbm_batch.cu", "lbm_adjoint.cu", "lbm_mask.cu", "lbm_inplace.cu", "lbm_host.cpp",
-           "lbm_kernels.cuh",
-           "lbm_rows2.cuh", "lbm_tile.cuh", "lbm_internal.h"]
+           "lbm_kernels.cuh", "lbm_rows2.cuh", "lbm_tile.cuh", "lbm_internal.h"]
 
 
 def _stale() -> bool:

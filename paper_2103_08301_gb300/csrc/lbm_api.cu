@@ -853,7 +853,9 @@ lbm_status init_ctx(const lbm_grid *grid, const lbm_eos *eos, double tau, const 
         }
     }
 
-    // Initial state f = f_eq(rho0, 0) in both arrays.
+    // Initial state f = f_eq(rho0, 0) in both arrays (in-place contexts: the
+    // one array, natural layout; the kernel then stores each value twice to
+    // the same slot).
     const size_t N = (size_t)grid->nx * grid->ny;
     double *d_rho0 = nullptr;
     e = cudaMallocAsync((void **)&d_rho0, N * sizeof(double), ctx->stream);
