@@ -412,12 +412,18 @@ __global__ void __launch_bounds__(AA_THREADS, LBM_AA_MIN_BLOCKS) aa_step_kernel(
 // FP32 instructions, which round each element as the scalar instruction does,
 // so the populations are the scalar kernel's bit for bit. 128 threads: lane =
 // column, warp = row pair of the 32 x 8 tile.
-// Compiled for 4 resident CTAs per SM (118 registers, no spills): 0.8815 ms
-// per 16384 x 2048 step, against 1.017 ms at 5 (96 registers, small spills)
-// and 1.264 ms at 6.
+// The next tile's halo densities are loaded while the current tile computes;
+// its populations too with LBM_AA2_PREFETCH_F = 1 (else each tile loads its
+// own at its start). Measured per 16384 x 2048 step: populations at the tile's
+// start, 5 CTAs per SM (88 registers) 0.837 ms (kept); 6 CTAs (80 registers,
+// small spills) 0.932 ms; populations prefetched, 4 CTAs (118 registers)
+// 0.882 ms, 5 CTAs (96 registers, spills) 1.017 ms.
 constexpr int AA2_THREADS = AA_TX * AA_TY / 2;
 #ifndef LBM_AA2_MIN_BLOCKS
-#define LBM_AA2_MIN_BLOCKS 4
+#define LBM_AA2_MIN_BLOCKS 5
+#endif
+#ifndef LBM_AA2_PREFETCH_F
+#define LBM_AA2_PREFETCH_F 0
 #endif
 
 // West, centre and east float2 packs (ring rows ra, rb) of ring column c.
@@ -517,19 +523,21 @@ __global__ void __launch_bounds__(AA2_THREADS, LBM_AA2_MIN_BLOCKS)
     V fcur[9], rcur[RN];
 #pragma unroll
     for (int i = 0; i < 9; ++i) fcur[i] = make_float2(0.f, 0.f);
+    constexpr bool PF = LBM_AA2_PREFETCH_F != 0;
     if (t < ntiles) {
         gcur = tile_geom(t);
-        load_f(gcur, fcur);
+        if (PF) load_f(gcur, fcur);
         load_ring(gcur, rcur);
     }
     for (; t < ntiles; t += gridDim.x) {
+        if (!PF) load_f(gcur, fcur);
         TileGeom gnext = gcur;
         V fnext[9], rnext[RN];
 #pragma unroll
         for (int i = 0; i < 9; ++i) fnext[i] = make_float2(0.f, 0.f);
         if (t + gridDim.x < ntiles) {
             gnext = tile_geom(t + gridDim.x);
-            load_f(gnext, fnext);
+            if (PF) load_f(gnext, fnext);
             load_ring(gnext, rnext);
         }
         const int x0 = gcur.x0, y0 = gcur.y0;
@@ -697,7 +705,7 @@ __global__ void __launch_bounds__(AA2_THREADS, LBM_AA2_MIN_BLOCKS)
         __syncthreads();  // the ring is rewritten by the next tile
         gcur = gnext;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) fcur[i] = fnext[i];
+        for (int i = 0; i < 9; ++i) fcur[i] = PF ? fnext[i] : make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < RN; ++q) rcur[q] = rnext[q];
     }
