@@ -196,7 +196,8 @@ lbm_status lbm_init(const lbm_grid *grid, const lbm_eos *eos, double tau, const 
  * TMA, TILE, STRIP, CTAS_PER_SM, PREFETCH, PDL) affect only lbm_fields.
  * lbm_launch_info reports the step's CTAs, its threads per CTA (FP32: 128,
  * two rows each; FP64: 256), its 32 x 8 tiles as units, and no staging.
- * Errors: as lbm_init. */
+ * lbm_fields allocates its output scratch (3 nx ny values plus 4 nx) on first
+ * use, as for any context. Errors: as lbm_init. */
 size_t lbm_workspace_bytes_inplace(const lbm_grid *grid);
 lbm_status lbm_init_inplace(const lbm_grid *grid, const lbm_eos *eos, double tau, double wetting,
                             const lbm_drive *drive, const double *rho0, void *workspace, size_t ws_bytes,
