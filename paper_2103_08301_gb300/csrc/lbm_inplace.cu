@@ -17,9 +17,9 @@
 // (aa_density_kernel) and then collides from that plane (aa_step_kernel_f2
 // for FP32, two rows per thread on the paired FP32 instructions, and
 // aa_step_kernel for FP64, one node per thread; a CTA takes one 32 x 8 tile at
-// a time). A pressure column collides with its interior
-// neighbour's populations (Sec. 2.2 pressure-driven ends); the density pass
-// copies those into a side buffer, for the same reason.
+// a time). A pressure column collides with its interior neighbour's
+// populations (Sec. 2.2 pressure-driven ends); the density pass copies those
+// into a side buffer, for the same reason.
 //
 // The node arithmetic is the one-row step kernel's helper sequence, in the
 // same order and precision, so the populations match the two-array step bit
@@ -147,14 +147,15 @@ struct AATiles {
     int ntx, nty, sx, sy;
 };
 
-// One step of the interior of every tile, CTAs striding over the tiles:
-// (1) densities (with the mirror, pressure-column and periodic rules of the
-// stencil) and the EOS potential on the tile plus two halo nodes, (2) the
-// Laplacian on the tile plus one, (3) force, collision, boundaries and the
-// in-place write of each node (one per thread), then the diagnostics.
+// One step of the interior of every tile (the FP64 in-place step; FP32 takes
+// aa_step_kernel_f2 below), CTAs striding over the tiles: (1) densities (with
+// the mirror, pressure-column and periodic rules of the stencil) and the EOS
+// potential on the tile plus two halo nodes, (2) the Laplacian on the tile
+// plus one, (3) force, collision, boundaries and the in-place write of each
+// node (one per thread), then the diagnostics.
 template <typename real, bool WALLS, bool PRES, bool ODD, typename IX>
-__global__ void __launch_bounds__(AA_THREADS, LBM_AA_MIN_BLOCKS) aa_step_kernel(const KArgs<real> A, real *F, const real *rho_in,
-                                                             const real *side, const AATiles T)
+__global__ void __launch_bounds__(AA_THREADS, LBM_AA_MIN_BLOCKS)
+    aa_step_kernel(const KArgs<real> A, real *F, const real *rho_in, const real *side, const AATiles T)
 {
     __shared__ SmemAA<real> S;
     const int tid = threadIdx.x, lane = tid & 31, rl = tid >> 5;
